@@ -1,0 +1,242 @@
+/*
+ * pj.h -- C ABI of the GB300 (sm_103a) polyhedral spatial join library.
+ *
+ * Problem statement (3DPipe, arXiv 2604.19982, section 3): for every object r
+ * of a set R, find the objects s of a set S with
+ *   - intersection:     d(r, s) = 0,
+ *   - within-tau:       d(r, s) <= tau,
+ *   - k nearest (k-NN): the k smallest d(r, s), ties broken by the id of s,
+ * where d is the minimum Euclidean distance between the two triangle
+ * surfaces (section 2.1).  Objects carry levels of detail (LoDs) with
+ * per-facet Hausdorff bounds hd / ph (section 2.1, Eq. 1 and Eq. 2) so that
+ * pairs can be decided at a coarse LoD; the answer is always the one of the
+ * original (finest) surfaces.
+ *
+ * Conventions
+ *   - Every call returns pj_status (0 = PJ_OK, < 0 error).  Outputs are valid
+ *     only on PJ_OK.  On error, pj_last_error(ctx) describes it; the context
+ *     stays usable unless the status is PJ_ECUDA with a sticky CUDA error.
+ *   - No C++ exception crosses this boundary.  A context is used by one host
+ *     thread at a time.
+ *   - "host" pointers are ordinary (pageable or pinned) CPU memory, "device"
+ *     pointers are CUDA global memory of the context's device.  The library
+ *     never frees caller memory and copies what it keeps.
+ *   - All arithmetic of the join runs in this library's CUDA kernels; there is
+ *     no CPU fallback: without a usable GPU, pj_create fails with PJ_ECUDA.
+ */
+#ifndef PJ_H
+#define PJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PJ_OK = 0,
+  PJ_EINVAL = -1,      /* bad argument (null pointer, size, predicate, ...) */
+  PJ_ENOMEM = -2,      /* device or pinned-host allocation failed           */
+  PJ_ECUDA = -3,       /* CUDA runtime error (message in pj_last_error)     */
+  PJ_ETIMEOUT = -4,    /* query deadline (pj_query.timeout_s) expired, or a
+                          device-side wait hit its iteration limit          */
+  PJ_ENONFINITE = -5,  /* a vertex, hd or ph value is NaN or infinite       */
+  PJ_EBOUNDS = -6,     /* an index is out of range (face -> vertex, ...)    */
+  PJ_ECANCELLED = -7,  /* a streaming source asked to stop                  */
+  PJ_ESOURCE = -8      /* a streaming source callback reported an error     */
+} pj_status;
+
+typedef enum { PJ_WITHIN = 0, PJ_INTERSECT = 1, PJ_KNN = 2 } pj_predicate;
+
+/* Arithmetic of the triangle-distance tests.
+ *   PJ_PREC_FP64: every test in double precision (the plain path).
+ *   PJ_PREC_FP32_REDECIDE: tests in single precision with a forward error
+ *     bound per tile; a pair whose single-precision bracket straddles the
+ *     decision threshold at full resolution is re-decided in double
+ *     precision, so decisions equal those of the FP64 path. */
+typedef enum { PJ_PREC_FP64 = 0, PJ_PREC_FP32_REDECIDE = 1 } pj_precision;
+
+/* pj_query.flags */
+enum {
+  PJ_EXACT_DIST = 1,   /* refine every result pair to its exact FP64 distance  */
+  PJ_USE_MLP = 2,      /* learned proposal: order k-NN work, pick start LoD    */
+  PJ_USE_GRAPH = 4,    /* replay the per-LoD launch sequence from a CUDA graph */
+  PJ_AUTOTUNE = 8,     /* pick launch shape per workload (cached per context)  */
+  PJ_TILE_PRUNE = 16   /* skip facet tiles/blocks that cannot change a decision */
+};
+
+typedef struct pj_ctx pj_ctx; /* opaque, library-owned */
+typedef struct pj_set pj_set; /* opaque, library-owned, device resident */
+
+#define PJ_MAX_LODS 8
+
+/* A set of closed triangle meshes with n_lods levels of detail (LoD 0 =
+ * coarsest, n_lods-1 = original surface).  All pointers are HOST memory,
+ * read during pj_load_set only.
+ *   verts[l]     float32 [nv_l][3]; several LoDs may pass the same array.
+ *   vert_off[l]  int64 [n_objects + 1]: object o owns vertices
+ *                vert_off[l][o] .. vert_off[l][o+1]-1 of verts[l].
+ *   faces[l]     int32 [..][3] object-local vertex ids.  With face_off[l]
+ *                non-NULL (int64 [n_objects + 1]) object o owns face rows
+ *                face_off[l][o] .. face_off[l][o+1]-1; with face_off[l] NULL
+ *                all objects share the n_faces_shared[l] rows of faces[l].
+ *   hd[l], ph[l] float32, one per face of the LoD in object order (rows of
+ *                object 0, then object 1, ...): facet-level Hausdorff bound
+ *                hd(f', P) and proxy Hausdorff bound ph(P, f') (section 2.1),
+ *                already rounded up.  NULL means 0 (required at the last LoD).
+ *   anchor       float32 [n_objects][3]: a point of each original surface
+ *                (its distance to another anchor bounds d from above,
+ *                section 2.1 "Object and Voxel Centers").
+ * Errors: PJ_EINVAL for inconsistent sizes, PJ_EBOUNDS for a face index
+ * outside its object's vertices, PJ_ENONFINITE for NaN/Inf data. */
+typedef struct {
+  int32_t n_objects;
+  int32_t n_lods;
+  const float* verts[PJ_MAX_LODS];
+  const int64_t* vert_off[PJ_MAX_LODS];
+  const int32_t* faces[PJ_MAX_LODS];
+  const int64_t* face_off[PJ_MAX_LODS];
+  int32_t n_faces_shared[PJ_MAX_LODS];
+  const float* hd[PJ_MAX_LODS];
+  const float* ph[PJ_MAX_LODS];
+  const float* anchor;
+} pj_mesh_set_desc;
+
+/* One join.  pred PJ_INTERSECT ignores tau (uses 0); PJ_KNN uses k >= 1.
+ * timeout_s <= 0 means no deadline. */
+typedef struct {
+  pj_predicate pred;
+  double tau;
+  int32_t k;
+  pj_precision prec;
+  uint32_t flags;
+  double timeout_s;
+} pj_query;
+
+/* Result pairs, library-owned pinned host memory (free with
+ * pj_result_free).  within/intersection: ordered by (r, s).  k-NN: for each
+ * r in order, min(k, |S|) entries ordered by (d, s).
+ *   d_lo <= d(r, s) <= d_hi always holds; d is the best estimate.
+ *   exact[i] = 1: d_lo = d = d_hi is the FP64 full-resolution distance;
+ *   exact[i] = 2: d is a single-precision full-resolution distance and
+ *                 [d_lo, d_hi] its forward error bracket;
+ *   exact[i] = 0: decided from a coarse LoD or from the anchor bound, only
+ *                 the bracket is known (set PJ_EXACT_DIST to refine). */
+typedef struct {
+  int64_t n;
+  int32_t* r;
+  int32_t* s;
+  double* d_lo;
+  double* d_hi;
+  double* d;
+  uint8_t* exact;
+  void* priv; /* library use */
+} pj_result;
+
+/* Create a context on CUDA device `device`.  options_json may be NULL or a
+ * JSON object with optional keys "persistent_ctas_per_sm" (int),
+ * "autotune_cache" (path string).  Fails with PJ_ECUDA when no GPU of
+ * compute capability 10.x is usable. */
+pj_status pj_create(pj_ctx** out, int device, const char* options_json);
+void pj_destroy(pj_ctx* ctx);
+
+/* Copy a mesh set to the device and lay it out for refinement: per LoD,
+ * de-indexed facets (three float4: vertex xyz + hd, vertex xyz + ph, vertex
+ * xyz + 0), per-object facet offsets, per-256-facet chunk boxes, and per
+ * object its original-surface box and anchor.  Synchronous. */
+pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out);
+
+/* A set streamed in n_chunks pieces during pj_join (R side only).  For each
+ * chunk the library calls fill(user, chunk, &desc) from a loader thread; the
+ * callback fills desc with that chunk's objects (host memory that must stay
+ * valid until the next call of fill or the end of the join).  Object ids of
+ * chunk c continue those of chunk c-1.  A fill returning PJ_ECANCELLED stops
+ * the join with that status; any other non-zero value gives PJ_ESOURCE. */
+typedef pj_status (*pj_fill_fn)(void* user, int chunk, pj_mesh_set_desc* out);
+pj_status pj_load_set_streamed(pj_ctx* ctx, int64_t n_objects, int n_chunks, pj_fill_fn fill,
+                               void* user, pj_set** out);
+void pj_free_set(pj_set* set);
+
+/* Join R against S.  Synchronous; results in *out (caller-allocated struct,
+ * library-allocated arrays). */
+pj_status pj_join(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out);
+
+/* Same as pj_join but every device operation is issued on `cuda_stream`
+ * (a cudaStream_t of the context's device, NULL = the context's stream); the
+ * call returns once the results are on the host, synchronizing only that
+ * stream. */
+pj_status pj_join_async(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q,
+                        void* cuda_stream, pj_result* out);
+void pj_result_free(pj_result* res);
+
+/* Counters and timings of the last join as a JSON object (candidates, pairs
+ * decided per LoD, tiles, triangle tests scheduled/executed per precision,
+ * re-decided pairs, bytes copied, milliseconds per stage). */
+pj_status pj_get_stats(const pj_ctx* ctx, char* json_buf, size_t cap);
+
+/* ------------------------------------------------------------------ *
+ * Learned proposal (optional): a 16 -> 64 -> 64 -> 1 ReLU MLP in bf16 on
+ * the tensor cores predicting log(1 + d) of a pair from box and coarse-LoD
+ * features.  It only orders k-NN refinement and picks the starting LoD; it
+ * never changes a result.
+ * ------------------------------------------------------------------ */
+
+/* Train on n examples: feats HOST float32 [n][16], target HOST float32 [n]
+ * (log(1 + d)).  Mini-batch SGD with momentum, `epochs` passes, shuffled
+ * with `seed`; forward and backward run in the library's kernels. */
+pj_status pj_mlp_train(pj_ctx* ctx, const float* feats, const float* target, int64_t n, int epochs,
+                       uint64_t seed);
+pj_status pj_mlp_save(const pj_ctx* ctx, const char* path);
+pj_status pj_mlp_load(pj_ctx* ctx, const char* path);
+
+/* Weights as float32 HOST arrays (W1 [64][16], b1 [64], W2 [64][64], b2 [64],
+ * W3 [64], b3 [1]); set copies in, get copies out. */
+pj_status pj_mlp_set_weights(pj_ctx* ctx, const float* w1, const float* b1, const float* w2,
+                             const float* b2, const float* w3, const float* b3);
+pj_status pj_mlp_get_weights(const pj_ctx* ctx, float* w1, float* b1, float* w2, float* b2, float* w3,
+                             float* b3);
+
+/* Forward pass on DEVICE buffers: feats float32 [n][16] -> out float32 [n]. */
+pj_status pj_mlp_forward(pj_ctx* ctx, const float* feats, int64_t n, float* out, void* cuda_stream);
+
+/* One forward+backward pass on DEVICE buffers with the current weights:
+ * loss = mean over n of (out - target)^2 / 2; gradients written to DEVICE
+ * float32 buffers of the shapes above (any may be NULL).  loss is a DEVICE
+ * float32 scalar. */
+pj_status pj_mlp_grad(pj_ctx* ctx, const float* feats, const float* target, int64_t n, float* loss,
+                      float* g_w1, float* g_b1, float* g_w2, float* g_b2, float* g_w3, float* g_b3,
+                      void* cuda_stream);
+
+/* Features of candidate pairs (the MLP input), DEVICE out float32 [n][16]
+ * for host pair lists pr/ps. */
+pj_status pj_pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr,
+                           const int32_t* ps, int64_t n, float* out_dev);
+
+/* ------------------------------------------------------------------ *
+ * Kernel-level entry points (the building blocks of pj_join, exposed for
+ * verification).
+ * ------------------------------------------------------------------ */
+
+/* Triangle-triangle minimum distance (section 2.2 plus the meeting test) of
+ * n independent pairs: P, Q DEVICE float32 [n][9] (three xyz vertices),
+ * out DEVICE double [n].  prec selects the FP64 or the FP32 kernel; with
+ * FP32, err_out (DEVICE double [n], may be NULL) receives the forward error
+ * bound used by the FP32 path for that pair. */
+pj_status pj_tri_dist(pj_ctx* ctx, const float* P, const float* Q, int64_t n, pj_precision prec,
+                      double* out, double* err_out, void* cuda_stream);
+
+/* Eq. 1 / Eq. 2 bounds of explicit object pairs at one LoD, every facet pair
+ * evaluated (no pruning): pr, ps HOST int32 [n] (ids in R and S), lod in
+ * [0, n_lods) of both sets, lb/ub HOST double [n].  With FP32 the returned
+ * bracket includes the forward error bound. */
+pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr,
+                         const int32_t* ps, int64_t n, int lod, pj_precision prec, double* lb, double* ub);
+
+const char* pj_last_error(const pj_ctx* ctx);
+const char* pj_status_str(pj_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PJ_H */

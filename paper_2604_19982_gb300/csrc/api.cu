@@ -1,0 +1,581 @@
+// C ABI of the join library (declared in include/pj.h): contexts, device
+// resident mesh sets and the entry points.  No exception crosses the ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tritri.cuh"
+
+namespace pj {
+
+pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                      cudaStream_t st, std::string& stats);
+pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                   cudaStream_t st, std::string& stats);
+pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                        cudaStream_t st, std::string& stats);
+void alloc_result(pj_result* res, int64_t n);
+pj_status mlp_train_impl(pj_ctx* ctx, const float* feats, const float* target, int64_t n, int epochs,
+                         uint64_t seed);
+void mlp_ensure(pj_ctx* ctx);
+
+void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st) {
+  (void)st;
+  DevBuf& b = ctx->ws[slot];
+  if (bytes == 0) bytes = 1;
+  if (b.cap < bytes) {
+    if (b.p) PJ_CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+    size_t cap = std::max(bytes, b.cap + b.cap / 2);
+    PJ_CK(cudaMalloc(&b.p, cap));
+    b.cap = cap;
+  }
+  return b.p;
+}
+
+// ------------------------------------------------------------------ load
+
+__device__ __forceinline__ int64_t upper_obj(const int64_t* off, int n, int64_t f) {
+  // largest o with off[o] <= f (off non-decreasing, off[0] = 0)
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= f) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_expand(int64_t F, int n, const float* verts, const int64_t* voff, const int32_t* faces,
+                         const int64_t* foff, int nf_shared, const float* hd, const float* ph, float4* fac,
+                         int* err) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  int64_t o, row;
+  if (nf_shared > 0) {
+    o = f / nf_shared;
+    row = f - o * nf_shared;
+  } else {
+    o = upper_obj(foff, n, f);
+    row = f;
+  }
+  const int64_t v0 = voff[o], nv = voff[o + 1] - v0;
+  float x[3][3];
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int id = faces[3 * row + k];
+    if (id < 0 || id >= nv) {
+      ok = false;
+      id = 0;
+    }
+    const float* v = verts + 3 * (v0 + id);
+    x[k][0] = v[0];
+    x[k][1] = v[1];
+    x[k][2] = v[2];
+  }
+  float h = hd ? hd[f] : 0.f, p = ph ? ph[f] : 0.f;
+  bool fin = isfinite(h) && isfinite(p) && h >= 0.f && p >= 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) fin = fin && isfinite(x[k][0]) && isfinite(x[k][1]) && isfinite(x[k][2]);
+  if (!ok) set_err(err, ERR_BOUNDS);
+  if (!fin) set_err(err, ERR_NONFINITE);
+  fac[3 * f + 0] = make_float4(x[0][0], x[0][1], x[0][2], h);
+  fac[3 * f + 1] = make_float4(x[1][0], x[1][1], x[1][2], p);
+  fac[3 * f + 2] = make_float4(x[2][0], x[2][1], x[2][2], 0.f);
+}
+
+// one warp per chunk: box, max hd / ph, max edge length, min facet sine
+__global__ void k_chunks(int64_t C, int n, const int64_t* coff, const int64_t* foff, const float4* fac,
+                         float4* chunk) {
+  int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= C) return;
+  int64_t o = upper_obj(coff, n, c);
+  int64_t j = c - coff[o];
+  int64_t f0 = foff[o] + j * CHUNK, f1 = min(f0 + CHUNK, foff[o + 1]);
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  float mhd = 0.f, mph = 0.f, medge = 0.f, smin = 1.f;
+  for (int64_t f = f0 + lane; f < f1; f += 32) {
+    float4 A = fac[3 * f], B = fac[3 * f + 1], Cc = fac[3 * f + 2];
+    float a[3] = {A.x, A.y, A.z}, b[3] = {B.x, B.y, B.z}, cc[3] = {Cc.x, Cc.y, Cc.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(lo[k], fminf(a[k], fminf(b[k], cc[k])));
+      hi[k] = fmaxf(hi[k], fmaxf(a[k], fmaxf(b[k], cc[k])));
+    }
+    mhd = fmaxf(mhd, A.w);
+    mph = fmaxf(mph, B.w);
+    float e0 = 0, e1 = 0, e2 = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e0 += (b[k] - a[k]) * (b[k] - a[k]);
+      e1 += (cc[k] - b[k]) * (cc[k] - b[k]);
+      e2 += (a[k] - cc[k]) * (a[k] - cc[k]);
+    }
+    medge = fmaxf(medge, sqrtf(fmaxf(e0, fmaxf(e1, e2))) * 1.0001f);
+    smin = fminf(smin, facet_sin<float>(a, b, cc) * 0.999f);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = warp_min(lo[k]);
+    hi[k] = -warp_min(-hi[k]);
+  }
+  mhd = -warp_min(-mhd);
+  mph = -warp_min(-mph);
+  medge = -warp_min(-medge);
+  smin = warp_min(smin);
+  if (lane == 0) {
+    chunk[3 * c + 0] = make_float4(lo[0], lo[1], lo[2], mhd);
+    chunk[3 * c + 1] = make_float4(hi[0], hi[1], hi[2], mph);
+    chunk[3 * c + 2] = make_float4(medge, smin, 0.f, 0.f);
+  }
+}
+
+// one warp per object: box of its original-surface vertices
+__global__ void k_mbb(int n, const float* verts, const int64_t* voff, const float* anchor, float* mbb, int* err) {
+  int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (o >= n) return;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t v = voff[o] + lane; v < voff[o + 1]; v += 32)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float x = verts[3 * v + k];
+      lo[k] = fminf(lo[k], x);
+      hi[k] = fmaxf(hi[k], x);
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = warp_min(lo[k]);
+    hi[k] = -warp_min(-hi[k]);
+  }
+  if (lane == 0) {
+    for (int k = 0; k < 3; ++k) {
+      mbb[6 * o + k] = lo[k];
+      mbb[6 * o + 3 + k] = hi[k];
+      if (!isfinite(anchor[3 * o + k])) set_err(err, ERR_NONFINITE);
+    }
+  }
+}
+
+void free_set_storage(pj_set* s) {
+  for (int l = 0; l < PJ_MAX_LODS; ++l) {
+    cudaFree(s->lod[l].fac);
+    cudaFree(s->lod[l].foff);
+    cudaFree(s->lod[l].chunk);
+    cudaFree(s->lod[l].coff);
+    s->lod[l] = LodData();
+  }
+  cudaFree(s->mbb);
+  cudaFree(s->anchor);
+  s->mbb = s->anchor = nullptr;
+}
+
+template <class T>
+static T* upload(const T* h, size_t count, cudaStream_t st) {
+  T* d = nullptr;
+  PJ_CK(cudaMalloc((void**)&d, std::max<size_t>(1, count) * sizeof(T)));
+  if (count) PJ_CK(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+// Lay a described set out on the device (see pj_load_set).
+pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaStream_t st) {
+  const int n = D->n_objects, L = D->n_lods;
+  if (n < 0 || L < 1 || L > PJ_MAX_LODS) throw ApiError{PJ_EINVAL, "n_objects < 0 or n_lods outside [1, 8]"};
+  if (n > 0 && !D->anchor) throw ApiError{PJ_EINVAL, "anchor is NULL"};
+  s->n = n;
+  s->L = L;
+  std::map<const void*, float*> vcache;
+  std::vector<void*> temps;
+  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  float* d_fin_verts = nullptr;
+  int64_t* d_fin_voff = nullptr;
+  for (int l = 0; l < L; ++l) {
+    if (!D->verts[l] || !D->vert_off[l] || !D->faces[l])
+      throw ApiError{PJ_EINVAL, "verts / vert_off / faces of a LoD is NULL"};
+    if (l == L - 1 && (D->hd[l] || D->ph[l]))
+      throw ApiError{PJ_EINVAL, "hd / ph of the original LoD must be NULL (zero)"};
+    const int64_t* vo = D->vert_off[l];
+    if (n > 0 && vo[0] != 0) throw ApiError{PJ_EINVAL, "vert_off must start at 0"};
+    for (int o = 0; o < n; ++o)
+      if (vo[o + 1] < vo[o]) throw ApiError{PJ_EINVAL, "vert_off not non-decreasing"};
+    const int64_t nv = n > 0 ? vo[n] : 0;
+    LodData& ld = s->lod[l];
+    ld.foff_h.assign(n + 1, 0);
+    const bool shared = D->face_off[l] == nullptr;
+    const int nfs = shared ? D->n_faces_shared[l] : 0;
+    if (shared && nfs <= 0 && n > 0) throw ApiError{PJ_EINVAL, "shared topology needs n_faces_shared > 0"};
+    for (int o = 0; o < n; ++o) {
+      int64_t cnt = shared ? nfs : D->face_off[l][o + 1] - D->face_off[l][o];
+      if (cnt < 0) throw ApiError{PJ_EINVAL, "face_off not non-decreasing"};
+      ld.foff_h[o + 1] = ld.foff_h[o] + cnt;
+    }
+    if (!shared && n > 0 && D->face_off[l][0] != 0) throw ApiError{PJ_EINVAL, "face_off must start at 0"};
+    ld.F = ld.foff_h[n];
+    if (ld.F >= (1LL << 31)) throw ApiError{PJ_EINVAL, "more than 2^31 facets in one LoD"};
+    ld.maxF = 0;
+    ld.coff_h.assign(n + 1, 0);
+    for (int o = 0; o < n; ++o) {
+      int64_t fo = ld.foff_h[o + 1] - ld.foff_h[o];
+      ld.maxF = std::max(ld.maxF, fo);
+      ld.coff_h[o + 1] = ld.coff_h[o] + (fo + CHUNK - 1) / CHUNK;
+    }
+    ld.C = ld.coff_h[n];
+    // uploads
+    float* dv;
+    auto it = vcache.find(D->verts[l]);
+    if (it != vcache.end()) {
+      dv = it->second;
+    } else {
+      dv = upload(D->verts[l], (size_t)nv * 3, st);
+      temps.push_back(dv);
+      vcache[D->verts[l]] = dv;
+    }
+    int64_t* dvo = upload(vo, (size_t)n + 1, st);
+    temps.push_back(dvo);
+    size_t nrows = shared ? (size_t)nfs : (size_t)ld.F;
+    int32_t* dfa = upload(D->faces[l], nrows * 3, st);
+    temps.push_back(dfa);
+    ld.foff = upload(ld.foff_h.data(), (size_t)n + 1, st);
+    ld.coff = upload(ld.coff_h.data(), (size_t)n + 1, st);
+    float* dhd = nullptr;
+    float* dph = nullptr;
+    if (D->hd[l]) {
+      dhd = upload(D->hd[l], (size_t)ld.F, st);
+      temps.push_back(dhd);
+    }
+    if (D->ph[l]) {
+      dph = upload(D->ph[l], (size_t)ld.F, st);
+      temps.push_back(dph);
+    }
+    PJ_CK(cudaMalloc((void**)&ld.fac, std::max<int64_t>(1, 3 * ld.F) * sizeof(float4)));
+    PJ_CK(cudaMalloc((void**)&ld.chunk, std::max<int64_t>(1, 3 * ld.C) * sizeof(float4)));
+    if (ld.F > 0) {
+      int th = 256;
+      k_expand<<<(unsigned)((ld.F + th - 1) / th), th, 0, st>>>(ld.F, n, dv, dvo, dfa, ld.foff, nfs, dhd, dph,
+                                                                ld.fac, ctx->d_err);
+      PJ_CK(cudaGetLastError());
+      int64_t thr = ld.C * 32;
+      k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, ld.coff, ld.foff, ld.fac, ld.chunk);
+      PJ_CK(cudaGetLastError());
+    }
+    if (l == L - 1) {
+      d_fin_verts = dv;
+      d_fin_voff = dvo;
+    }
+  }
+  PJ_CK(cudaMalloc((void**)&s->mbb, std::max(1, n) * 6 * sizeof(float)));
+  s->anchor = upload(D->anchor, (size_t)n * 3, st);
+  if (n > 0) {
+    int th = 256;
+    k_mbb<<<(unsigned)(((int64_t)n * 32 + th - 1) / th), th, 0, st>>>(n, d_fin_verts, d_fin_voff, s->anchor,
+                                                                       s->mbb, ctx->d_err);
+    PJ_CK(cudaGetLastError());
+  }
+  s->mbb_h.resize((size_t)n * 6);
+  if (n > 0) PJ_CK(cudaMemcpyAsync(s->mbb_h.data(), s->mbb, (size_t)n * 6 * 4, cudaMemcpyDeviceToHost, st));
+  int herr = 0;
+  PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  for (void* p : temps) cudaFree(p);
+  if (herr & ERR_BOUNDS) throw ApiError{PJ_EBOUNDS, "a face index lies outside its object's vertices"};
+  if (herr & ERR_NONFINITE) throw ApiError{PJ_ENONFINITE, "non-finite vertex, anchor, hd or ph (or negative hd/ph)"};
+  return PJ_OK;
+}
+
+static std::string json_str(const char* js, const char* key) {
+  if (!js) return "";
+  std::string s(js), k = std::string("\"") + key + "\"";
+  size_t p = s.find(k);
+  if (p == std::string::npos) return "";
+  p = s.find(':', p + k.size());
+  if (p == std::string::npos) return "";
+  ++p;
+  while (p < s.size() && (s[p] == ' ' || s[p] == '\t')) ++p;
+  if (p < s.size() && s[p] == '"') {
+    size_t e = s.find('"', p + 1);
+    return e == std::string::npos ? "" : s.substr(p + 1, e - p - 1);
+  }
+  size_t e = p;
+  while (e < s.size() && s[e] != ',' && s[e] != '}') ++e;
+  return s.substr(p, e - p);
+}
+
+}  // namespace pj
+
+using namespace pj;
+
+static pj_status fail(pj_ctx* ctx, pj_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+#define PJ_API_TRY try {
+#define PJ_API_CATCH(ctx)                                                                         \
+  }                                                                                               \
+  catch (const pj::CudaError& e) {                                                                \
+    std::string m = std::string(e.what) + ": " + cudaGetErrorString(e.e);                         \
+    return fail(ctx, e.e == cudaErrorMemoryAllocation ? PJ_ENOMEM : PJ_ECUDA, m);                 \
+  }                                                                                               \
+  catch (const pj::ApiError& e) {                                                                 \
+    return fail(ctx, e.st, e.msg);                                                                \
+  }                                                                                               \
+  catch (const std::bad_alloc&) {                                                                 \
+    return fail(ctx, PJ_ENOMEM, "host allocation failed");                                        \
+  }                                                                                               \
+  catch (...) {                                                                                   \
+    return fail(ctx, PJ_EINVAL, "unexpected internal error");                                     \
+  }
+
+extern "C" {
+
+const char* pj_status_str(pj_status s) {
+  switch (s) {
+    case PJ_OK: return "PJ_OK";
+    case PJ_EINVAL: return "PJ_EINVAL";
+    case PJ_ENOMEM: return "PJ_ENOMEM";
+    case PJ_ECUDA: return "PJ_ECUDA";
+    case PJ_ETIMEOUT: return "PJ_ETIMEOUT";
+    case PJ_ENONFINITE: return "PJ_ENONFINITE";
+    case PJ_EBOUNDS: return "PJ_EBOUNDS";
+    case PJ_ECANCELLED: return "PJ_ECANCELLED";
+    case PJ_ESOURCE: return "PJ_ESOURCE";
+  }
+  return "unknown";
+}
+
+const char* pj_last_error(const pj_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
+  if (!out) return PJ_EINVAL;
+  *out = nullptr;
+  pj_ctx* ctx = new (std::nothrow) pj_ctx();
+  if (!ctx) return PJ_ENOMEM;
+  PJ_API_TRY
+  int ndev = 0;
+  PJ_CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) throw ApiError{PJ_EINVAL, "no such CUDA device"};
+  PJ_CK(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  PJ_CK(cudaGetDeviceProperties(&prop, device));
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->cc_major = prop.major;
+  ctx->cc_minor = prop.minor;
+  if (!(prop.major == 10 && prop.minor == 3))
+    throw ApiError{PJ_ECUDA, "this library is built for sm_103a (GB300); device is sm_" +
+                                 std::to_string(prop.major) + std::to_string(prop.minor)};
+  PJ_CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+  PJ_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  PJ_CK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
+  PJ_CK(cudaMalloc((void**)&ctx->d_counters, 16 * sizeof(unsigned long long)));
+  PJ_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+  PJ_CK(cudaMemset(ctx->d_counters, 0, 16 * sizeof(unsigned long long)));
+  std::string v = json_str(options_json, "persistent_ctas_per_sm");
+  if (!v.empty()) ctx->ctas_per_sm = std::max(0, atoi(v.c_str()));
+  ctx->autotune_cache = json_str(options_json, "autotune_cache");
+  *out = ctx;
+  return PJ_OK;
+  }
+  catch (const pj::CudaError& e) {
+    pj_status st = PJ_ECUDA;
+    delete ctx;
+    (void)e;
+    return st;
+  }
+  catch (const pj::ApiError& e) {
+    delete ctx;
+    return e.st;
+  }
+  catch (...) {
+    delete ctx;
+    return PJ_ECUDA;
+  }
+}
+
+void pj_destroy(pj_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->ws) cudaFree(b.p);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_counters);
+  cudaFree(ctx->mlp_w);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  delete ctx;
+}
+
+pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out) {
+  if (!ctx || !desc || !out) return PJ_EINVAL;
+  *out = nullptr;
+  pj_set* s = new (std::nothrow) pj_set();
+  if (!s) return fail(ctx, PJ_ENOMEM, "host allocation failed");
+  s->ctx = ctx;
+  try {
+    PJ_CK(cudaSetDevice(ctx->device));
+    load_set_impl(ctx, desc, s, ctx->stream);
+    *out = s;
+    return PJ_OK;
+  } catch (const pj::CudaError& e) {
+    free_set_storage(s);
+    delete s;
+    return fail(ctx, e.e == cudaErrorMemoryAllocation ? PJ_ENOMEM : PJ_ECUDA,
+                std::string(e.what) + ": " + cudaGetErrorString(e.e));
+  } catch (const pj::ApiError& e) {
+    free_set_storage(s);
+    delete s;
+    return fail(ctx, e.st, e.msg);
+  } catch (...) {
+    free_set_storage(s);
+    delete s;
+    return fail(ctx, PJ_ENOMEM, "host allocation failed");
+  }
+}
+
+pj_status pj_load_set_streamed(pj_ctx* ctx, int64_t n_objects, int n_chunks, pj_fill_fn fill, void* user,
+                               pj_set** out) {
+  if (!ctx || !out || !fill || n_objects < 0 || n_chunks < 1) return fail(ctx, PJ_EINVAL, "bad streamed set");
+  pj_set* s = new (std::nothrow) pj_set();
+  if (!s) return fail(ctx, PJ_ENOMEM, "host allocation failed");
+  s->ctx = ctx;
+  s->streamed = true;
+  s->n_total = n_objects;
+  s->n_chunks = n_chunks;
+  s->fill = fill;
+  s->user = user;
+  *out = s;
+  return PJ_OK;
+}
+
+void pj_free_set(pj_set* s) {
+  if (!s) return;
+  if (s->ctx) cudaSetDevice(s->ctx->device);
+  free_set_storage(s);
+  delete s;
+}
+
+pj_status pj_join_async(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, void* cuda_stream,
+                        pj_result* out) {
+  if (!ctx || !R || !S || !q || !out) return fail(ctx, PJ_EINVAL, "null argument");
+  memset(out, 0, sizeof(*out));
+  if (S->streamed) return fail(ctx, PJ_EINVAL, "only R may be a streamed set");
+  if (q->pred == PJ_WITHIN && !(q->tau >= 0.0 && std::isfinite(q->tau)))
+    return fail(ctx, PJ_EINVAL, "tau must be finite and >= 0");
+  if (q->pred == PJ_KNN && q->k < 1) return fail(ctx, PJ_EINVAL, "k must be >= 1");
+  if (q->pred != PJ_WITHIN && q->pred != PJ_INTERSECT && q->pred != PJ_KNN)
+    return fail(ctx, PJ_EINVAL, "unknown predicate");
+  if (q->prec != PJ_PREC_FP64 && q->prec != PJ_PREC_FP32_REDECIDE) return fail(ctx, PJ_EINVAL, "unknown precision");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  PJ_API_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  std::string stats;
+  pj_status rc;
+  if (R->streamed) rc = join_streamed(ctx, R, S, q, out, st, stats);
+  else if (q->pred == PJ_KNN) rc = join_knn(ctx, R, S, q, out, st, stats);
+  else rc = join_within(ctx, R, S, q, out, st, stats);
+  ctx->stats = stats;
+  if (rc != PJ_OK) {
+    if (out->priv) pj_result_free(out);
+    if (ctx->last_error.empty() || rc == PJ_ETIMEOUT)
+      ctx->last_error = rc == PJ_ETIMEOUT ? "deadline expired or a device wait hit its limit" : pj_status_str(rc);
+  }
+  return rc;
+  PJ_API_CATCH(ctx)
+}
+
+pj_status pj_join(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out) {
+  return pj_join_async(ctx, R, S, q, nullptr, out);
+}
+
+void pj_result_free(pj_result* res) {
+  if (!res) return;
+  if (res->priv) cudaFreeHost(res->priv);
+  memset(res, 0, sizeof(*res));
+}
+
+pj_status pj_get_stats(const pj_ctx* ctx, char* buf, size_t cap) {
+  if (!ctx || !buf || cap == 0) return PJ_EINVAL;
+  const std::string& s = ctx->stats.empty() ? std::string("{}") : ctx->stats;
+  if (s.size() + 1 > cap) return PJ_EINVAL;
+  memcpy(buf, s.c_str(), s.size() + 1);
+  return PJ_OK;
+}
+
+pj_status pj_tri_dist(pj_ctx* ctx, const float* P, const float* Q, int64_t n, pj_precision prec, double* out,
+                      double* err_out, void* cuda_stream) {
+  if (!ctx || n < 0 || (n > 0 && (!P || !Q || !out))) return fail(ctx, PJ_EINVAL, "bad tri_dist arguments");
+  PJ_API_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  tri_dist_batch(ctx, P, Q, n, prec == PJ_PREC_FP64, out, err_out, st);
+  PJ_CK(cudaStreamSynchronize(st));
+  return PJ_OK;
+  PJ_API_CATCH(ctx)
+}
+
+pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
+                         int64_t n, int lod, pj_precision prec, double* lb, double* ub) {
+  if (!ctx || !R || !S || n < 0 || (n > 0 && (!pr || !ps || !lb || !ub)))
+    return fail(ctx, PJ_EINVAL, "bad pair_bounds arguments");
+  if (R->streamed || S->streamed) return fail(ctx, PJ_EINVAL, "streamed sets are not addressable");
+  if (lod < 0 || lod >= R->L || lod >= S->L) return fail(ctx, PJ_EINVAL, "lod out of range");
+  for (int64_t i = 0; i < n; ++i)
+    if (pr[i] < 0 || pr[i] >= R->n || ps[i] < 0 || ps[i] >= S->n) return fail(ctx, PJ_EBOUNDS, "pair id out of range");
+  if (n == 0) return PJ_OK;
+  PJ_API_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  auto dpr = (int32_t*)ws_get(ctx, WS_PR, n * 4, st);
+  auto dps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);
+  PJ_CK(cudaMemcpyAsync(dpr, pr, n * 4, cudaMemcpyHostToDevice, st));
+  PJ_CK(cudaMemcpyAsync(dps, ps, n * 4, cudaMemcpyHostToDevice, st));
+  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  setup_pairs(ctx, R, S, n, 0.0, false, st);
+  StepSpec sp;
+  sp.lodR = lod;
+  sp.lodS = lod;
+  sp.full = (lod == R->L - 1) && (lod == S->L - 1);
+  sp.fp64 = prec == PJ_PREC_FP64;
+  sp.cull = false;
+  sp.want = UNDECIDED;
+  sp.step = 0;
+  init_bounds(ctx, n, sp, st);
+  int64_t nt = build_tiles(ctx, R, S, n, sp, st);
+  run_refine(ctx, R, S, nt, sp, st);
+  std::vector<unsigned char> blo(n * 8), bub(n * 8);
+  PJ_CK(cudaMemcpyAsync(blo.data(), ctx->ws[WS_LB].p, n * (sp.fp64 ? 8 : 4), cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaMemcpyAsync(bub.data(), ctx->ws[WS_UB].p, n * (sp.fp64 ? 8 : 4), cudaMemcpyDeviceToHost, st));
+  int herr = 0;
+  PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  if (herr & ERR_MBAR_TIMEOUT) return fail(ctx, PJ_ETIMEOUT, "a device wait hit its limit");
+  for (int64_t i = 0; i < n; ++i) {
+    if (sp.fp64) {
+      double a, b;
+      memcpy(&a, &blo[8 * i], 8);
+      memcpy(&b, &bub[8 * i], 8);
+      lb[i] = a;
+      ub[i] = b;
+    } else {
+      float a, b;
+      memcpy(&a, &blo[4 * i], 4);
+      memcpy(&b, &bub[4 * i], 4);
+      lb[i] = a;
+      ub[i] = b;
+    }
+  }
+  return PJ_OK;
+  PJ_API_CATCH(ctx)
+}
+
+}  // extern "C"

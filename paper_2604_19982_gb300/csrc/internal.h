@@ -1,0 +1,188 @@
+// Host-side internals of the join library: context, device-resident sets,
+// growable device buffers and the launchers each translation unit exports.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "../../include/pj.h"
+
+namespace pj {
+
+// Pair status codes (per candidate object pair).
+enum : uint8_t { UNDECIDED = 0, CONFIRMED = 1, REMOVED = 2, REDECIDE = 3 };
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+
+#define PJ_CK(call)                                                   \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) throw ::pj::CudaError{e_, #call};          \
+  } while (0)
+
+struct ApiError {
+  pj_status st;
+  std::string msg;
+};
+
+// Grow-only device buffer (stream-ordered allocation on the context stream).
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// One LoD of a device-resident set.
+struct LodData {
+  int64_t F = 0;                  // facets of all objects
+  float4* fac = nullptr;          // [3F]: (v0, hd), (v1, ph), (v2, 0)
+  int64_t* foff = nullptr;        // device [n+1] facet offsets
+  std::vector<int64_t> foff_h;    // host copy
+  int64_t C = 0;                  // chunks of <= CHUNK facets
+  float4* chunk = nullptr;        // [3C]: (lo, max hd), (hi, max ph), (max edge, min sine, 0, 0)
+  int64_t* coff = nullptr;        // device [n+1] chunk offsets
+  std::vector<int64_t> coff_h;
+  int64_t maxF = 0;               // largest facet count of one object
+};
+
+}  // namespace pj
+
+struct pj_set {
+  pj_ctx* ctx = nullptr;
+  int n = 0;
+  int L = 0;
+  pj::LodData lod[PJ_MAX_LODS];
+  float* mbb = nullptr;           // device [n][6] original-surface boxes
+  float* anchor = nullptr;        // device [n][3]
+  std::vector<float> mbb_h;       // host copy
+  // streamed R: the chunks are loaded inside pj_join
+  bool streamed = false;
+  int64_t n_total = 0;
+  int n_chunks = 0;
+  pj_fill_fn fill = nullptr;
+  void* user = nullptr;
+};
+
+struct pj_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  cudaStream_t stream = nullptr;   // default work stream
+  cudaStream_t copy_stream = nullptr;
+  int* d_err = nullptr;            // device error word
+  unsigned long long* d_counters = nullptr;  // [16] device counters
+  std::string last_error;
+  std::string stats;
+  int ctas_per_sm = 0;             // 0 = from occupancy
+  std::string autotune_cache;
+  // per-query workspace
+  pj::DevBuf ws[32];
+  // learned proposal (bf16 MLP), float master weights on the device
+  float* mlp_w = nullptr;          // packed: W1 64x16, b1 64, W2 64x64, b2 64, W3 64, b3 1
+  bool mlp_ready = false;
+  // autotuned launch choices (per workload key)
+  std::vector<std::pair<std::string, int>> tuned;
+};
+
+namespace pj {
+
+// Packed MLP weight layout (floats).
+constexpr int MLP_IN = 16, MLP_H = 64;
+constexpr int MLP_W1 = 0, MLP_B1 = MLP_W1 + MLP_H * MLP_IN, MLP_W2 = MLP_B1 + MLP_H,
+              MLP_B2 = MLP_W2 + MLP_H * MLP_H, MLP_W3 = MLP_B2 + MLP_H, MLP_B3 = MLP_W3 + MLP_H,
+              MLP_NW = MLP_B3 + 1;
+
+// workspace slots
+enum Slot {
+  WS_PR, WS_PS, WS_ORIGIN, WS_THR, WS_BOXLB, WS_ANCUB, WS_STATUS, WS_LOD0, WS_LB, WS_UB, WS_MID,
+  WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
+  WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5
+};
+
+void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st);
+
+// ---- set layout (api.cu)
+void free_set_storage(pj_set* s);
+
+// ---- scan (join.cu): exclusive prefix sum of n int64 values into out[0..n],
+// out[n] = total.  tmp is workspace.
+void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
+// ---- filter (filter.cu)
+struct FilterOut {
+  int64_t n_pairs = 0;
+};
+// Candidate pairs (r, s) with box MINDIST <= tau, grouped by r and sorted by
+// s; results land in WS_PR / WS_PS.
+FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, cudaStream_t st);
+// k-NN candidates: per r all s with MINDIST <= theta_r (theta_r = k-th
+// smallest anchor distance); roff (WS_ROFF, n_R+1) is the CSR of the result.
+FilterOut filter_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, int k, cudaStream_t st);
+
+// ---- refine (refine.cu)
+struct Tile {
+  int32_t pair, rb, sb;
+  uint16_t rl, sl;
+  float eps, eh, ew;
+  int32_t pad;
+};
+static_assert(sizeof(Tile) == 32, "tile is two int4");
+
+struct StepSpec {
+  int lodR, lodS;
+  bool full;        // both at the original surfaces (hd = ph = 0)
+  bool fp64;
+  bool cull;        // skip chunk pairs / blocks that cannot reach the threshold
+  uint8_t want;     // status of the pairs to refine (UNDECIDED or REDECIDE)
+  int step;         // LoD step index (pairs with lod0 > step wait)
+};
+
+// Count + emit tiles for the pairs in state `want`; returns tile count.
+int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, const StepSpec& sp,
+                    cudaStream_t st);
+// Reset the per-pair lb / ub words of the pairs being refined.
+void init_bounds(pj_ctx* ctx, int64_t n_pairs, const StepSpec& sp, cudaStream_t st);
+// Run the persistent refinement kernel over the built tiles.
+void run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+                cudaStream_t st);
+// Pair-setup: origin (pair-local frame), box MINDIST, anchor distance.
+void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, double tau, bool within,
+                 cudaStream_t st);
+
+// ---- decide (join.cu)
+void decide_within(pj_ctx* ctx, int64_t n_pairs, double tau, const StepSpec& sp, cudaStream_t st);
+
+// ---- triangle distance batch (refine.cu)
+void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool fp64, double* out,
+                    double* err, cudaStream_t st);
+
+// ---- kNN (knn.cu)
+void knn_prune(pj_ctx* ctx, int64_t n_r, int k, int64_t n_pairs, bool full, bool fp64, cudaStream_t st);
+void knn_theta(pj_ctx* ctx, int64_t n_r, int k, cudaStream_t st);
+
+// ---- MLP (mlp.cu)
+void mlp_forward(pj_ctx* ctx, const float* feats, int64_t n, float* out, cudaStream_t st);
+void mlp_grad(pj_ctx* ctx, const float* w, const float* feats, const float* target, int64_t n, float* loss,
+              float* grad, cudaStream_t st);
+void mlp_sgd(pj_ctx* ctx, float* w, float* mom, const float* grad, float lr, float beta, cudaStream_t st);
+void pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
+                   int64_t n, float* out, cudaStream_t st);
+
+// host timing helper
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace pj

@@ -1,0 +1,389 @@
+// Join orchestration on one GPU: MBB filter -> per-LoD [tile build ->
+// refine -> decide] from the coarsest LoD to the original surfaces (section
+// 3.1 overview: "after each LoD, resolve what is decidable, else go finer"),
+// an FP64 re-decide pass for the single-precision path, optional exact
+// distances, and the compaction of the result pairs.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pj {
+
+// ------------------------------------------------------------------ scan
+constexpr int SCAN_T = 512;
+constexpr int SCAN_I = 8;
+constexpr int SCAN_B = SCAN_T * SCAN_I;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  int64_t before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+  *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_block_sums(const int64_t* in, int64_t n, int64_t* bsum) {
+  __shared__ int64_t sh[32];
+  int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_I;
+  int64_t v = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_I; ++k)
+    if (base + k < n) v += in[base + k];
+  int64_t tot;
+  block_excl_scan(v, sh, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_apply(const int64_t* in, int64_t n, const int64_t* boff, int64_t nb, int64_t* out) {
+  __shared__ int64_t sh[32];
+  int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_I;
+  int64_t loc[SCAN_I];
+  int64_t v = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_I; ++k) {
+    loc[k] = base + k < n ? in[base + k] : 0;
+    v += loc[k];
+  }
+  int64_t tot;
+  int64_t run = block_excl_scan(v, sh, &tot) + (boff ? boff[blockIdx.x] : 0);
+#pragma unroll
+  for (int k = 0; k < SCAN_I; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += loc[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = boff ? boff[nb] : tot;
+}
+
+void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
+  if (n == 0) {
+    PJ_CK(cudaMemsetAsync(out, 0, 8, st));
+    return;
+  }
+  int64_t nb = (n + SCAN_B - 1) / SCAN_B;
+  if (nb == 1) {
+    k_scan_apply<<<1, SCAN_T, 0, st>>>(in, n, nullptr, 0, out);
+    PJ_CK(cudaGetLastError());
+    return;
+  }
+  int64_t* tmp = nullptr;
+  PJ_CK(cudaMallocAsync((void**)&tmp, (size_t)(2 * nb + 1) * 8, st));
+  int64_t* bsum = tmp;
+  int64_t* boff = tmp + nb;
+  k_block_sums<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum);
+  PJ_CK(cudaGetLastError());
+  scan_i64(ctx, bsum, boff, nb, st);
+  k_scan_apply<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, boff, nb, out);
+  PJ_CK(cudaGetLastError());
+  PJ_CK(cudaFreeAsync(tmp, st));
+}
+
+// ------------------------------------------------------------------ decide
+
+enum : uint8_t { MAKE_EXACT = 4 };
+
+template <bool F64>
+__device__ __forceinline__ double load_bound(const void* a, int64_t p) {
+  if (F64) return bits2d(((const unsigned long long*)a)[p]);
+  return (double)bits2f(((const unsigned*)a)[p]);
+}
+
+// within-tau / intersection decision of the refined pairs (section 3.1:
+// ub <= tau -> result, lb > tau -> pruned, else next LoD).  At the original
+// surfaces the FP64 bracket is a point; a single-precision bracket that
+// still straddles tau sends the pair to the FP64 re-decide pass.
+template <bool F64>
+__global__ void k_decide_within(int64_t n, uint8_t* status, const uint8_t* lod0, uint8_t want, int step, int full,
+                                double tau, const void* lb, const void* ub, const void* mid, double* dlo,
+                                double* dhi, double* d, uint8_t* exact, unsigned long long* cnt) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (!(status[p] == want && lod0[p] <= step)) return;
+  double l = load_bound<F64>(lb, p), u = load_bound<F64>(ub, p);
+  if (want == MAKE_EXACT) {
+    dlo[p] = l;
+    dhi[p] = u;
+    d[p] = u;
+    exact[p] = 1;
+    status[p] = CONFIRMED;
+    return;
+  }
+  if (u <= tau) {
+    status[p] = CONFIRMED;
+    dlo[p] = l;
+    dhi[p] = u;
+    if (full) {
+      exact[p] = F64 ? 1 : 2;
+      d[p] = F64 ? u : load_bound<F64>(mid, p);
+    } else {
+      exact[p] = 0;
+      d[p] = 0.5 * (l + u);
+    }
+    atomicAdd(&cnt[2], 1ULL);
+  } else if (l > tau || (full && F64)) {
+    status[p] = REMOVED;
+    atomicAdd(&cnt[3], 1ULL);
+  } else if (full) {
+    status[p] = REDECIDE;
+    atomicAdd(&cnt[4], 1ULL);
+  }
+}
+
+void decide_within(pj_ctx* ctx, int64_t n, double tau, const StepSpec& sp, cudaStream_t st) {
+  if (n == 0) return;
+  int th = 256;
+  unsigned g = (unsigned)((n + th - 1) / th);
+  auto status = (uint8_t*)ctx->ws[WS_STATUS].p;
+  auto lod0 = (const uint8_t*)ctx->ws[WS_LOD0].p;
+  if (sp.fp64)
+    k_decide_within<true><<<g, th, 0, st>>>(n, status, lod0, sp.want, sp.step, sp.full, tau, ctx->ws[WS_LB].p,
+                                             ctx->ws[WS_UB].p, ctx->ws[WS_MID].p, (double*)ctx->ws[WS_DLO].p,
+                                             (double*)ctx->ws[WS_DHI].p, (double*)ctx->ws[WS_D].p,
+                                             (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters);
+  else
+    k_decide_within<false><<<g, th, 0, st>>>(n, status, lod0, sp.want, sp.step, sp.full, tau, ctx->ws[WS_LB].p,
+                                              ctx->ws[WS_UB].p, ctx->ws[WS_MID].p, (double*)ctx->ws[WS_DLO].p,
+                                              (double*)ctx->ws[WS_DHI].p, (double*)ctx->ws[WS_D].p,
+                                              (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters);
+  PJ_CK(cudaGetLastError());
+}
+
+__global__ void k_mark_exact(int64_t n, uint8_t* status, const uint8_t* exact) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (status[p] == CONFIRMED && exact[p] != 1) status[p] = MAKE_EXACT;
+}
+
+// ------------------------------------------------------------------ results
+
+__global__ void k_flag_status(int64_t n, const uint8_t* status, uint8_t want, int64_t* flag) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n) flag[p] = status[p] == want ? 1 : 0;
+}
+
+struct ResultPack {
+  int32_t* r;
+  int32_t* s;
+  double* dlo;
+  double* dhi;
+  double* d;
+  uint8_t* exact;
+};
+
+__global__ void k_compact(int64_t n, const uint8_t* status, const int64_t* off, const int32_t* pr,
+                          const int32_t* ps, const double* dlo, const double* dhi, const double* d,
+                          const uint8_t* exact, ResultPack out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n || status[p] != CONFIRMED) return;
+  int64_t w = off[p];
+  out.r[w] = pr[p];
+  out.s[w] = ps[p];
+  out.dlo[w] = dlo[p];
+  out.dhi[w] = dhi[p];
+  out.d[w] = d[p];
+  out.exact[w] = exact[p];
+}
+
+struct HostResult {
+  void* block = nullptr;
+};
+
+// Allocate pinned host arrays for n results inside one block.
+void alloc_result(pj_result* res, int64_t n) {
+  size_t per = 4 + 4 + 8 + 8 + 8 + 1;
+  size_t bytes = std::max<size_t>(64, (size_t)n * per + 64);
+  void* blk = nullptr;
+  PJ_CK(cudaMallocHost(&blk, bytes));
+  char* c = (char*)blk;
+  res->n = n;
+  res->d_lo = (double*)c;
+  c += 8 * n;
+  res->d_hi = (double*)c;
+  c += 8 * n;
+  res->d = (double*)c;
+  c += 8 * n;
+  res->r = (int32_t*)c;
+  c += 4 * n;
+  res->s = (int32_t*)c;
+  c += 4 * n;
+  res->exact = (uint8_t*)c;
+  res->priv = blk;
+}
+
+// Copy the CONFIRMED pairs (in pair order = (r, s) order) to the host.
+int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) {
+  if (n == 0) {
+    alloc_result(res, 0);
+    return 0;
+  }
+  int th = 256;
+  unsigned g = (unsigned)((n + th - 1) / th);
+  auto flag = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
+  auto off = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
+  auto status = (const uint8_t*)ctx->ws[WS_STATUS].p;
+  k_flag_status<<<g, th, 0, st>>>(n, status, CONFIRMED, flag);
+  PJ_CK(cudaGetLastError());
+  scan_i64(ctx, flag, off, n, st);
+  int64_t m = 0;
+  PJ_CK(cudaMemcpyAsync(&m, off + n, 8, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  alloc_result(res, m);
+  if (m == 0) return 0;
+  size_t per = 4 + 4 + 8 + 8 + 8 + 1;
+  char* dev = (char*)ws_get(ctx, WS_RES, (size_t)m * per + 64, st);
+  ResultPack pk;
+  pk.dlo = (double*)dev;
+  pk.dhi = pk.dlo + m;
+  pk.d = pk.dhi + m;
+  pk.r = (int32_t*)(pk.d + m);
+  pk.s = pk.r + m;
+  pk.exact = (uint8_t*)(pk.s + m);
+  k_compact<<<g, th, 0, st>>>(n, status, off, (const int32_t*)ctx->ws[WS_PR].p, (const int32_t*)ctx->ws[WS_PS].p,
+                              (const double*)ctx->ws[WS_DLO].p, (const double*)ctx->ws[WS_DHI].p,
+                              (const double*)ctx->ws[WS_D].p, (const uint8_t*)ctx->ws[WS_EXACT].p, pk);
+  PJ_CK(cudaGetLastError());
+  // one contiguous copy: the device pack mirrors the host block layout
+  PJ_CK(cudaMemcpyAsync(res->d_lo, dev, (size_t)m * per, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  return m;
+}
+
+// ------------------------------------------------------------------ driver
+
+struct StepStat {
+  int step;
+  int64_t tiles;
+  double ms;
+};
+
+static unsigned long long read_counter(pj_ctx* ctx, int i, cudaStream_t st) {
+  unsigned long long v = 0;
+  PJ_CK(cudaMemcpyAsync(&v, ctx->d_counters + i, 8, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  return v;
+}
+
+pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                      cudaStream_t st, std::string& stats) {
+  Timer tall;
+  const double tau = q->pred == PJ_INTERSECT ? 0.0 : q->tau;
+  const bool fp64 = q->prec == PJ_PREC_FP64;
+  const bool cull = (q->flags & PJ_TILE_PRUNE) != 0;
+  PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
+  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  Timer tf;
+  FilterOut fo = filter_within(ctx, R, S, tau, st);
+  const int64_t n = fo.n_pairs;
+  setup_pairs(ctx, R, S, n, tau, true, st);
+  PJ_CK(cudaStreamSynchronize(st));
+  double ms_filter = tf.ms();
+  const int Lmax = std::max(R->L, S->L);
+  std::string steps = "[";
+  auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
+  int64_t tiles_total = 0;
+  for (int step = 0; step < Lmax && n > 0; ++step) {
+    if (deadline_hit()) return PJ_ETIMEOUT;
+    Timer ts;
+    StepSpec sp;
+    sp.lodR = std::max(0, step - (Lmax - R->L));
+    sp.lodS = std::max(0, step - (Lmax - S->L));
+    sp.full = step == Lmax - 1;
+    sp.fp64 = fp64;
+    sp.cull = cull;
+    sp.want = UNDECIDED;
+    sp.step = step;
+    init_bounds(ctx, n, sp, st);
+    int64_t nt = build_tiles(ctx, R, S, n, sp, st);
+    run_refine(ctx, R, S, nt, sp, st);
+    decide_within(ctx, n, tau, sp, st);
+    PJ_CK(cudaStreamSynchronize(st));
+    tiles_total += nt;
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s{\"step\":%d,\"tiles\":%lld,\"ms\":%.3f}", step ? "," : "", step, (long long)nt,
+             ts.ms());
+    steps += buf;
+  }
+  steps += "]";
+  int64_t n_redecide = 0;
+  double ms_redecide = 0;
+  if (!fp64 && n > 0) {
+    Timer tr;
+    n_redecide = (int64_t)read_counter(ctx, 4, st);
+    if (n_redecide > 0) {
+      StepSpec sp;
+      sp.lodR = R->L - 1;
+      sp.lodS = S->L - 1;
+      sp.full = true;
+      sp.fp64 = true;
+      sp.cull = false;
+      sp.want = REDECIDE;
+      sp.step = Lmax - 1;
+      init_bounds(ctx, n, sp, st);
+      int64_t nt = build_tiles(ctx, R, S, n, sp, st);
+      run_refine(ctx, R, S, nt, sp, st);
+      decide_within(ctx, n, tau, sp, st);
+      tiles_total += nt;
+    }
+    ms_redecide = tr.ms();
+  }
+  if ((q->flags & PJ_EXACT_DIST) && n > 0) {
+    int th = 256;
+    k_mark_exact<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_STATUS].p,
+                                                               (const uint8_t*)ctx->ws[WS_EXACT].p);
+    PJ_CK(cudaGetLastError());
+    StepSpec sp;
+    sp.lodR = R->L - 1;
+    sp.lodS = S->L - 1;
+    sp.full = true;
+    sp.fp64 = true;
+    sp.cull = false;
+    sp.want = MAKE_EXACT;
+    sp.step = Lmax - 1;
+    init_bounds(ctx, n, sp, st);
+    int64_t nt = build_tiles(ctx, R, S, n, sp, st);
+    run_refine(ctx, R, S, nt, sp, st);
+    decide_within(ctx, n, tau, sp, st);
+    tiles_total += nt;
+  }
+  Timer tg;
+  int64_t m = gather_results(ctx, n, out, st);
+  int herr = 0;
+  PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  unsigned long long cnt[8];
+  PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  char buf[640];
+  snprintf(buf, sizeof buf,
+           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"candidates\":%lld,\"results\":%lld,"
+           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%lld,"
+           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_redecide\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
+           "\"steps\":",
+           tau, fp64 ? "fp64" : "fp32", (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3],
+           (long long)n_redecide, (long long)tiles_total, ms_filter, ms_redecide, tg.ms(), tall.ms());
+  stats = std::string(buf) + steps + "}";
+  if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
+  if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
+  return PJ_OK;
+}
+
+}  // namespace pj
