@@ -233,6 +233,13 @@ pj_status pj_tri_dist(pj_ctx* ctx, const float* P, const float* Q, int64_t n, pj
 pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr,
                          const int32_t* ps, int64_t n, int lod, pj_precision prec, double* lb, double* ub);
 
+/* Measured fused-multiply-add throughput of the device (independent FMA
+ * chains on every SM), GFLOP/s with an FMA counted as 2 operations: the
+ * arithmetic peak the refinement kernels are compared against (their work
+ * is scalar ALU arithmetic, not a tensor-core contraction).  fp64 = 0 for
+ * single, 1 for double precision. */
+pj_status pj_fma_peak(pj_ctx* ctx, int fp64, double* gflops);
+
 const char* pj_last_error(const pj_ctx* ctx);
 const char* pj_status_str(pj_status s);
 

@@ -264,9 +264,11 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
       k_expand<<<(unsigned)((ld.F + th - 1) / th), th, 0, st>>>(ld.F, n, dv, dvo, dfa, ld.foff, nfs, dhd, dph,
                                                                 ld.fac, ctx->d_err);
       PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
       int64_t thr = ld.C * 32;
       k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, ld.coff, ld.foff, ld.fac, ld.chunk);
       PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
     }
     if (l == L - 1) {
       d_fin_verts = dv;
@@ -280,6 +282,7 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
     k_mbb<<<(unsigned)(((int64_t)n * 32 + th - 1) / th), th, 0, st>>>(n, d_fin_verts, d_fin_voff, s->anchor,
                                                                        s->mbb, ctx->d_err);
     PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   }
   s->mbb_h.resize((size_t)n * 6);
   if (n > 0) PJ_CK(cudaMemcpyAsync(s->mbb_h.data(), s->mbb, (size_t)n * 6 * 4, cudaMemcpyDeviceToHost, st));
@@ -380,6 +383,7 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
   PJ_CK(cudaMalloc((void**)&ctx->d_counters, 16 * sizeof(unsigned long long)));
   PJ_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   PJ_CK(cudaMemset(ctx->d_counters, 0, 16 * sizeof(unsigned long long)));
+  for (auto& e : ctx->ev) PJ_CK(cudaEventCreate(&e));
   std::string v = json_str(options_json, "persistent_ctas_per_sm");
   if (!v.empty()) ctx->ctas_per_sm = std::max(0, atoi(v.c_str()));
   ctx->autotune_cache = json_str(options_json, "autotune_cache");
@@ -410,6 +414,8 @@ void pj_destroy(pj_ctx* ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_counters);
   cudaFree(ctx->mlp_w);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   delete ctx;
@@ -421,8 +427,10 @@ pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out) {
   pj_set* s = new (std::nothrow) pj_set();
   if (!s) return fail(ctx, PJ_ENOMEM, "host allocation failed");
   s->ctx = ctx;
+  s->device = ctx->device;
   try {
     PJ_CK(cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();  // drop a stale non-sticky error of an unrelated call
     load_set_impl(ctx, desc, s, ctx->stream);
     *out = s;
     return PJ_OK;
@@ -448,6 +456,7 @@ pj_status pj_load_set_streamed(pj_ctx* ctx, int64_t n_objects, int n_chunks, pj_
   pj_set* s = new (std::nothrow) pj_set();
   if (!s) return fail(ctx, PJ_ENOMEM, "host allocation failed");
   s->ctx = ctx;
+  s->device = ctx->device;
   s->streamed = true;
   s->n_total = n_objects;
   s->n_chunks = n_chunks;
@@ -459,7 +468,7 @@ pj_status pj_load_set_streamed(pj_ctx* ctx, int64_t n_objects, int n_chunks, pj_
 
 void pj_free_set(pj_set* s) {
   if (!s) return;
-  if (s->ctx) cudaSetDevice(s->ctx->device);
+  cudaSetDevice(s->device);
   free_set_storage(s);
   delete s;
 }
@@ -478,6 +487,7 @@ pj_status pj_join_async(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
   PJ_API_TRY
   PJ_CK(cudaSetDevice(ctx->device));
+  (void)cudaGetLastError();
   std::string stats;
   pj_status rc;
   if (R->streamed) rc = join_streamed(ctx, R, S, q, out, st, stats);
@@ -516,6 +526,7 @@ pj_status pj_tri_dist(pj_ctx* ctx, const float* P, const float* Q, int64_t n, pj
   if (!ctx || n < 0 || (n > 0 && (!P || !Q || !out))) return fail(ctx, PJ_EINVAL, "bad tri_dist arguments");
   PJ_API_TRY
   PJ_CK(cudaSetDevice(ctx->device));
+  (void)cudaGetLastError();
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
   tri_dist_batch(ctx, P, Q, n, prec == PJ_PREC_FP64, out, err_out, st);
   PJ_CK(cudaStreamSynchronize(st));
@@ -534,6 +545,7 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
   if (n == 0) return PJ_OK;
   PJ_API_TRY
   PJ_CK(cudaSetDevice(ctx->device));
+  (void)cudaGetLastError();
   cudaStream_t st = ctx->stream;
   auto dpr = (int32_t*)ws_get(ctx, WS_PR, n * 4, st);
   auto dps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);

@@ -220,6 +220,7 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   int th = 256;
   k_grid_count<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, cnt);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   scan_i64(ctx, cnt, off, G.ncell, st);
   int64_t nids = 0;
   PJ_CK(cudaMemcpyAsync(&nids, off + G.ncell, 8, cudaMemcpyDeviceToHost, st));
@@ -228,6 +229,7 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
   k_grid_fill<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, off, cnt, ids);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   auto rcount = (int64_t*)ws_get(ctx, WS_RCOUNT, ((int64_t)R->n + 1) * 8, st);
   auto roff = (int64_t*)ws_get(ctx, WS_ROFF, ((int64_t)R->n + 1) * 8, st);
   int64_t warps_threads = (int64_t)R->n * 32;
@@ -235,6 +237,7 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   k_probe<false><<<g, th, 0, st>>>(R->n, R->mbb, S->mbb, ftau, lim2, G, off, ids, rcount, nullptr, nullptr,
                                    nullptr);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   scan_i64(ctx, rcount, roff, R->n, st);
   int64_t total = 0;
   PJ_CK(cudaMemcpyAsync(&total, roff + R->n, 8, cudaMemcpyDeviceToHost, st));
@@ -245,8 +248,10 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   auto ps = (int32_t*)ws_get(ctx, WS_PS, total * 4, st);
   k_probe<true><<<g, th, 0, st>>>(R->n, R->mbb, S->mbb, ftau, lim2, G, off, ids, nullptr, roff, pr, ps);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   k_seg_sort<<<R->n, 256, 0, st>>>(R->n, roff, ps);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   return out;
 }
 

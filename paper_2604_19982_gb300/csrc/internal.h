@@ -20,6 +20,8 @@ struct CudaError {
   const char* what;
 };
 
+#define PJ_COUNT_LAUNCH count_launch(ctx)
+
 #define PJ_CK(call)                                                   \
   do {                                                                \
     cudaError_t e_ = (call);                                          \
@@ -58,6 +60,7 @@ struct LodData {
 
 struct pj_set {
   pj_ctx* ctx = nullptr;
+  int device = 0;                 // CUDA device of the storage
   int n = 0;
   int L = 0;
   pj::LodData lod[PJ_MAX_LODS];
@@ -91,6 +94,11 @@ struct pj_ctx {
   bool mlp_ready = false;
   // autotuned launch choices (per workload key)
   std::vector<std::pair<std::string, int>> tuned;
+  // instrumentation: kernel launches issued by the library, and CUDA events
+  // bracketing the refinement launches of the current join
+  unsigned long long launches = 0;
+  cudaEvent_t ev[64] = {};
+  int ev_used = 0;
 };
 
 namespace pj {
@@ -151,9 +159,12 @@ int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pai
                     cudaStream_t st);
 // Reset the per-pair lb / ub words of the pairs being refined.
 void init_bounds(pj_ctx* ctx, int64_t n_pairs, const StepSpec& sp, cudaStream_t st);
-// Run the persistent refinement kernel over the built tiles.
-void run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
-                cudaStream_t st);
+// Run the persistent refinement kernel over the built tiles.  Returns the
+// index of the CUDA event pair (ctx->ev) bracketing the launch on `st`, or -1.
+int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+               cudaStream_t st);
+// Elapsed milliseconds of an event pair returned by run_refine (0 if -1).
+float refine_ms(pj_ctx* ctx, int ev);
 // Pair-setup: origin (pair-local frame), box MINDIST, anchor distance.
 void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, double tau, bool within,
                  cudaStream_t st);
@@ -176,6 +187,9 @@ void mlp_grad(pj_ctx* ctx, const float* w, const float* feats, const float* targ
 void mlp_sgd(pj_ctx* ctx, float* w, float* mom, const float* grad, float lr, float beta, cudaStream_t st);
 void pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
                    int64_t n, float* out, cudaStream_t st);
+
+// count a kernel launch of the library (for the benchmark's launch tally)
+inline void count_launch(pj_ctx* ctx, int n = 1) { ctx->launches += (unsigned long long)n; }
 
 // host timing helper
 struct Timer {

@@ -84,6 +84,7 @@ void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStrea
   if (nb == 1) {
     k_scan_apply<<<1, SCAN_T, 0, st>>>(in, n, nullptr, 0, out);
     PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
     return;
   }
   int64_t* tmp = nullptr;
@@ -92,9 +93,11 @@ void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStrea
   int64_t* boff = tmp + nb;
   k_block_sums<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   scan_i64(ctx, bsum, boff, nb, st);
   k_scan_apply<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, boff, nb, out);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   PJ_CK(cudaFreeAsync(tmp, st));
 }
 
@@ -166,6 +169,7 @@ void decide_within(pj_ctx* ctx, int64_t n, double tau, const StepSpec& sp, cudaS
                                               (double*)ctx->ws[WS_DHI].p, (double*)ctx->ws[WS_D].p,
                                               (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 __global__ void k_mark_exact(int64_t n, uint8_t* status, const uint8_t* exact) {
@@ -243,6 +247,7 @@ int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) 
   auto status = (const uint8_t*)ctx->ws[WS_STATUS].p;
   k_flag_status<<<g, th, 0, st>>>(n, status, CONFIRMED, flag);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   scan_i64(ctx, flag, off, n, st);
   int64_t m = 0;
   PJ_CK(cudaMemcpyAsync(&m, off + n, 8, cudaMemcpyDeviceToHost, st));
@@ -262,6 +267,7 @@ int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) 
                               (const double*)ctx->ws[WS_DLO].p, (const double*)ctx->ws[WS_DHI].p,
                               (const double*)ctx->ws[WS_D].p, (const uint8_t*)ctx->ws[WS_EXACT].p, pk);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   // one contiguous copy: the device pack mirrors the host block layout
   PJ_CK(cudaMemcpyAsync(res->d_lo, dev, (size_t)m * per, cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaStreamSynchronize(st));
@@ -286,6 +292,7 @@ static unsigned long long read_counter(pj_ctx* ctx, int i, cudaStream_t st) {
 pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                       cudaStream_t st, std::string& stats) {
   Timer tall;
+  const unsigned long long launches0 = ctx->launches;
   const double tau = q->pred == PJ_INTERSECT ? 0.0 : q->tau;
   const bool fp64 = q->prec == PJ_PREC_FP64;
   const bool cull = (q->flags & PJ_TILE_PRUNE) != 0;
@@ -301,6 +308,9 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   std::string steps = "[";
   auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
   int64_t tiles_total = 0;
+  ctx->ev_used = 0;
+  unsigned long long prev[2] = {0, 0};
+  double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
   for (int step = 0; step < Lmax && n > 0; ++step) {
     if (deadline_hit()) return PJ_ETIMEOUT;
     Timer ts;
@@ -314,13 +324,22 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     sp.step = step;
     init_bounds(ctx, n, sp, st);
     int64_t nt = build_tiles(ctx, R, S, n, sp, st);
-    run_refine(ctx, R, S, nt, sp, st);
+    int ev = run_refine(ctx, R, S, nt, sp, st);
     decide_within(ctx, n, tau, sp, st);
+    unsigned long long cur[2];
+    PJ_CK(cudaMemcpyAsync(cur, ctx->d_counters, sizeof cur, cudaMemcpyDeviceToHost, st));
     PJ_CK(cudaStreamSynchronize(st));
+    float kms = refine_ms(ctx, ev);
+    (fp64 ? refine_ms_fp64 : refine_ms_fp32) += kms;
     tiles_total += nt;
-    char buf[160];
-    snprintf(buf, sizeof buf, "%s{\"step\":%d,\"tiles\":%lld,\"ms\":%.3f}", step ? "," : "", step, (long long)nt,
-             ts.ms());
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tests\":%llu,\"refine_ms\":%.4f,"
+             "\"ms\":%.3f}",
+             step ? "," : "", step, fp64 ? "fp64" : "fp32", sp.full ? 1 : 0, (long long)nt,
+             (cur[0] - prev[0]) + (cur[1] - prev[1]), kms, ts.ms());
+    prev[0] = cur[0];
+    prev[1] = cur[1];
     steps += buf;
   }
   steps += "]";
@@ -340,8 +359,10 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
       sp.step = Lmax - 1;
       init_bounds(ctx, n, sp, st);
       int64_t nt = build_tiles(ctx, R, S, n, sp, st);
-      run_refine(ctx, R, S, nt, sp, st);
+      int ev = run_refine(ctx, R, S, nt, sp, st);
       decide_within(ctx, n, tau, sp, st);
+      PJ_CK(cudaStreamSynchronize(st));
+      refine_ms_fp64 += refine_ms(ctx, ev);
       tiles_total += nt;
     }
     ms_redecide = tr.ms();
@@ -351,6 +372,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     k_mark_exact<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_STATUS].p,
                                                                (const uint8_t*)ctx->ws[WS_EXACT].p);
     PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
     StepSpec sp;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
@@ -372,14 +394,15 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   unsigned long long cnt[8];
   PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaStreamSynchronize(st));
-  char buf[640];
+  char buf[900];
   snprintf(buf, sizeof buf,
            "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%lld,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_redecide\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
-           "\"steps\":",
+           "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
            tau, fp64 ? "fp64" : "fp32", (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3],
-           (long long)n_redecide, (long long)tiles_total, ms_filter, ms_redecide, tg.ms(), tall.ms());
+           (long long)n_redecide, (long long)tiles_total, ms_filter, ms_redecide, tg.ms(), tall.ms(),
+           refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;

@@ -88,6 +88,7 @@ void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, doubl
                                                               tau, within ? 1 : 0, origin, thr, box_lb, anc_ub,
                                                               status, lod0, exact, dlo, dhi, d);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 // ------------------------------------------------------------------ tiles
@@ -210,6 +211,7 @@ int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, co
   k_count_tiles<<<g, th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, cr, cs, origin, thr, sp.cull,
                                    sp.fp64, cnt);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   scan_i64(ctx, cnt, off, n, st);
   int64_t total = 0;
   PJ_CK(cudaMemcpyAsync(&total, off + n, 8, cudaMemcpyDeviceToHost, st));
@@ -219,6 +221,7 @@ int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, co
   k_emit_tiles<<<g, th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, cr, cs, origin, thr, sp.cull,
                                   sp.fp64, off, tiles);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
   return total;
 }
 
@@ -251,6 +254,7 @@ void init_bounds(pj_ctx* ctx, int64_t n, const StepSpec& sp, cudaStream_t st) {
   k_init_bounds<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, status, lod0, sp.want, sp.step, sp.fp64, lb,
                                                                ub, mid);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 // ------------------------------------------------------------------ refine
@@ -512,11 +516,24 @@ static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaSt
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
-void run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
-                cudaStream_t st) {
-  if (n_tiles == 0) return;
+float refine_ms(pj_ctx* ctx, int ev) {
+  if (ev < 0) return 0.f;
+  float ms = 0.f;
+  PJ_CK(cudaEventElapsedTime(&ms, ctx->ev[ev], ctx->ev[ev + 1]));
+  return ms;
+}
+
+int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+               cudaStream_t st) {
+  if (n_tiles == 0) return -1;
+  int ev = -1;
+  if (ctx->ev_used + 2 <= 64 && ctx->ev[ctx->ev_used]) {
+    ev = ctx->ev_used;
+    ctx->ev_used += 2;
+  }
   int64_t n = 1;
   RefineArgs a;
   a.tiles = (const Tile*)ctx->ws[WS_TILES].p;
@@ -533,6 +550,7 @@ void run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, 
   a.ntests = ctx->d_counters + (sp.fp64 ? 1 : 0);
   a.err = ctx->d_err;
   (void)n;
+  if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
   if (sp.fp64) {
     if (sp.full) {
       if (sp.cull) launch_refine<double, true, false>(ctx, a, n_tiles, st);
@@ -549,6 +567,8 @@ void run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, 
       else launch_refine<float, false, false>(ctx, a, n_tiles, st);
     }
   }
+  if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev + 1], st));
+  return ev;
 }
 
 // ------------------------------------------------------------------ batch
@@ -609,6 +629,7 @@ void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool
   if (fp64) k_tri_dist<double><<<g, th, 0, st>>>(P, Q, n, out, err);
   else k_tri_dist<float><<<g, th, 0, st>>>(P, Q, n, out, err);
   PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 }  // namespace pj

@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes as C
 import json
 import os
+import weakref
 
 import numpy as np
 
@@ -82,6 +83,7 @@ def lib():
             "pj_pair_features": (st, [vp, vp, vp, _i32p, _i32p, C.c_int64, vp]),
             "pj_tri_dist": (st, [vp, vp, vp, C.c_int64, C.c_int, vp, vp, vp]),
             "pj_pair_bounds": (st, [vp, vp, vp, _i32p, _i32p, C.c_int64, C.c_int, C.c_int, _dp, _dp]),
+            "pj_fma_peak": (st, [vp, C.c_int, _dp]),
             "pj_last_error": (C.c_char_p, [vp]),
             "pj_status_str": (C.c_char_p, [C.c_int]),
         }
@@ -163,6 +165,7 @@ class Set:
         self.handle = handle
         self.n = n
         self.n_lods = n_lods
+        ctx._sets.add(self)
 
     def free(self):
         if self.handle:
@@ -185,13 +188,17 @@ class Context:
             raise PJError(st, "pj_create failed (no usable sm_103 GPU?)")
         self.h = h.value
         self._keep = []
+        self._sets = weakref.WeakSet()
 
     def _check(self, st: int):
         if st != PJ_OK:
             raise PJError(st, (lib().pj_last_error(self.h) or b"").decode())
 
     def close(self):
+        """Free the sets loaded through this context, then the context."""
         if self.h:
+            for s in list(self._sets):
+                s.free()
             lib().pj_destroy(self.h)
             self.h = None
 
@@ -268,6 +275,12 @@ class Context:
         self._check(lib().pj_pair_bounds(self.h, R.handle, S.handle, _ptr(pr, C.c_int32), _ptr(ps, C.c_int32), n,
                                          int(lod), int(prec), _ptr(lb, C.c_double), _ptr(ub, C.c_double)))
         return lb, ub
+
+    def fma_peak(self, fp64: bool) -> float:
+        """Measured FMA throughput in GFLOP/s (FMA = 2 flops)."""
+        g = C.c_double()
+        self._check(lib().pj_fma_peak(self.h, 1 if fp64 else 0, C.byref(g)))
+        return g.value
 
     # ---- learned proposal
     def mlp_train(self, feats, target, epochs: int = 20, seed: int = 0):

@@ -43,7 +43,10 @@ def test_fp32_bounds_bracket_oracle(setup, lod):
     olb, oub = oracle.pair_bounds(w.R, w.S, pr, ps, lod)
     olb = np.maximum(olb, 0.0)
     assert (lb <= olb).all() and (oub <= ub).all()
-    assert (ub - oub < 2e-3).all() and (olb - lb < 2e-3).all()
+    # the bracket widens by the per-tile forward error bound, dominated by
+    # 8 sqrt(u) L with L the longest edge (~1.4 at the coarsest blob LoD)
+    tol = 5e-3 if lod == 0 else 2e-3
+    assert (ub - oub < tol).all() and (olb - lb < tol).all()
 
 
 def test_bounds_bracket_full_resolution_distance(setup):

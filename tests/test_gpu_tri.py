@@ -104,8 +104,10 @@ def test_fp32_within_reported_bound_random(ctx):
     d, err = run(ctx, P, Q, pj.FP32)
     ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
     assert (np.abs(d - ref) <= err).all()
-    # the bound is not vacuous: it is small against the coordinates
-    assert np.median(err) < 1e-3
+    # typical single-precision error is far inside the worst-case bound,
+    # whose 8 sqrt(u) L term covers nearly parallel edges
+    assert np.median(np.abs(d - ref)) < 1e-5
+    assert np.median(err) < 2e-2
 
 
 def test_fp32_within_reported_bound_near_parallel(ctx):
