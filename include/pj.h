@@ -233,6 +233,35 @@ pj_status pj_tri_dist(pj_ctx* ctx, const float* P, const float* Q, int64_t n, pj
 pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr,
                          const int32_t* ps, int64_t n, int lod, pj_precision prec, double* lb, double* ub);
 
+/* pj_pair_bounds for callers that cannot allocate device memory: the same
+ * bounds, computed without any cudaMalloc / cudaFree (nor any allocating
+ * library call).  Meant for code embedded in a host application that owns
+ * and budgets every device allocation itself (a database engine's or a
+ * renderer's memory manager) and forbids libraries from allocating, and for
+ * latency-critical loops that cannot afford the device-wide synchronization
+ * cudaMalloc / cudaFree imply.  The paper has no counterpart; it is a
+ * property of this library's interface.
+ *   pr, ps   DEVICE int32 [n] object ids in R and S (ids out of range give
+ *            PJ_EBOUNDS before any bound is computed);
+ *   lb, ub   DEVICE double [n] outputs, as for pj_pair_bounds;
+ *   cuda_stream  stream to work on (NULL = the context's stream); the call
+ *            returns when the results are written.
+ * Scratch: one fixed array of about 1.5 MB in the library's device code,
+ * held by every GPU that loads the library until the process exits.  Its
+ * device address is looked up on the first call on each device (with that
+ * device current).  Sizes beyond it are rejected with PJ_EINVAL:
+ * n <= PJ_STATIC_MAX_PAIRS, and n x (chunks of the largest R object) x
+ * (chunks of the largest S object) at `lod` <= PJ_STATIC_MAX_TILES, a chunk
+ * being 256 facets.  All calls share the array; it keeps the previous
+ * call's contents (the call clears what must start at zero), and calls that
+ * overlap on the GPU -- on two streams or from two host threads -- race on
+ * it and must be serialized by the caller. */
+#define PJ_STATIC_MAX_PAIRS 4096
+#define PJ_STATIC_MAX_TILES 32768
+pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr,
+                                const int32_t* ps, int64_t n, int lod, pj_precision prec, double* lb,
+                                double* ub, void* cuda_stream);
+
 /* Measured fused-multiply-add throughput of the device (independent FMA
  * chains on every SM), GFLOP/s with an FMA counted as 2 operations: the
  * arithmetic peak the refinement kernels are compared against (their work

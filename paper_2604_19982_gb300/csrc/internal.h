@@ -169,6 +169,41 @@ float refine_ms(pj_ctx* ctx, int ev);
 void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, double tau, bool within,
                  cudaStream_t st);
 
+// ---- explicit-buffer launchers (refine.cu / join.cu), used by entry points
+// that bring their own scratch instead of the context workspace
+struct PairBufs {
+  const int32_t* pr;
+  const int32_t* ps;
+  float4* origin;
+  float* thr;
+  double* box_lb;
+  double* anc_ub;
+  uint8_t* status;
+  uint8_t* lod0;
+  uint8_t* exact;
+  double* dlo;
+  double* dhi;
+  double* d;
+  void* lb;
+  void* ub;
+  void* mid;
+  int64_t* tcount;   // [n+1]
+  int64_t* toff;     // [n+1]
+  Tile* tiles;
+  unsigned long long* counters;  // [2]: tests, tile counter
+};
+void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const PairBufs& b,
+                      cudaStream_t st);
+void count_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                      const PairBufs& b, cudaStream_t st);
+void emit_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                     const PairBufs& b, cudaStream_t st);
+void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st);
+void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+                     const PairBufs& b, int* err, cudaStream_t st);
+// single-block exclusive scan, n <= 4096, no allocation
+void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
 // ---- decide (join.cu)
 void decide_within(pj_ctx* ctx, int64_t n_pairs, double tau, const StepSpec& sp, cudaStream_t st);
 

@@ -101,6 +101,17 @@ void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStrea
   PJ_CK(cudaFreeAsync(tmp, st));
 }
 
+void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
+  if (n > SCAN_B) throw ApiError{PJ_EINVAL, "scan_small_i64: n above one block"};
+  if (n == 0) {
+    PJ_CK(cudaMemsetAsync(out, 0, 8, st));
+    return;
+  }
+  k_scan_apply<<<1, SCAN_T, 0, st>>>(in, n, nullptr, 0, out);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
 // ------------------------------------------------------------------ decide
 
 enum : uint8_t { MAKE_EXACT = 4 };

@@ -571,6 +571,80 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, c
   return ev;
 }
 
+// ------------------------------------------------------------------ explicit buffers
+
+void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const PairBufs& b,
+                      cudaStream_t st) {
+  if (n == 0) return;
+  int th = 256;
+  k_setup_pairs<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.pr, b.ps, R->mbb, S->mbb, R->anchor, S->anchor,
+                                                              0.0, 0, b.origin, b.thr, b.box_lb, b.anc_ub, b.status,
+                                                              b.lod0, b.exact, b.dlo, b.dhi, b.d);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
+void count_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                      const PairBufs& b, cudaStream_t st) {
+  if (n == 0) return;
+  const LodData& LR = R->lod[sp.lodR];
+  const LodData& LS = S->lod[sp.lodS];
+  ChunkView cr{LR.chunk, LR.coff, LR.foff}, cs{LS.chunk, LS.coff, LS.foff};
+  int th = 128;
+  k_count_tiles<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.pr, b.ps, b.status, b.lod0, sp.want, sp.step, cr,
+                                                              cs, b.origin, b.thr, sp.cull, sp.fp64, b.tcount);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
+void emit_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                     const PairBufs& b, cudaStream_t st) {
+  if (n == 0) return;
+  const LodData& LR = R->lod[sp.lodR];
+  const LodData& LS = S->lod[sp.lodS];
+  ChunkView cr{LR.chunk, LR.coff, LR.foff}, cs{LS.chunk, LS.coff, LS.foff};
+  int th = 128;
+  k_emit_tiles<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.pr, b.ps, b.status, b.lod0, sp.want, sp.step, cr,
+                                                             cs, b.origin, b.thr, sp.cull, sp.fp64, b.toff, b.tiles);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
+void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st) {
+  if (n == 0) return;
+  int th = 256;
+  k_init_bounds<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.status, b.lod0, sp.want, sp.step, sp.fp64, b.lb,
+                                                               b.ub, b.mid);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
+void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+                     const PairBufs& b, int* err, cudaStream_t st) {
+  if (n_tiles == 0) return;
+  RefineArgs a;
+  a.tiles = b.tiles;
+  a.n_tiles = n_tiles;
+  a.counter = (int*)(b.counters + 1);
+  PJ_CK(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
+  a.facR = R->lod[sp.lodR].fac;
+  a.facS = S->lod[sp.lodS].fac;
+  a.origin = b.origin;
+  a.thr = b.thr;
+  a.lb = b.lb;
+  a.ub = b.ub;
+  a.mid = b.mid;
+  a.ntests = b.counters;
+  a.err = err;
+  if (sp.fp64) {
+    if (sp.full) launch_refine<double, true, false>(ctx, a, n_tiles, st);
+    else launch_refine<double, false, false>(ctx, a, n_tiles, st);
+  } else {
+    if (sp.full) launch_refine<float, true, false>(ctx, a, n_tiles, st);
+    else launch_refine<float, false, false>(ctx, a, n_tiles, st);
+  }
+}
+
 // ------------------------------------------------------------------ batch
 
 template <class T>

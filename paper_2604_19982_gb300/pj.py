@@ -84,6 +84,7 @@ def lib():
             "pj_tri_dist": (st, [vp, vp, vp, C.c_int64, C.c_int, vp, vp, vp]),
             "pj_pair_bounds": (st, [vp, vp, vp, _i32p, _i32p, C.c_int64, C.c_int, C.c_int, _dp, _dp]),
             "pj_fma_peak": (st, [vp, C.c_int, _dp]),
+            "pj_pair_bounds_static": (st, [vp, vp, vp, vp, vp, C.c_int64, C.c_int, C.c_int, vp, vp, vp]),
             "pj_last_error": (C.c_char_p, [vp]),
             "pj_status_str": (C.c_char_p, [C.c_int]),
         }
@@ -275,6 +276,13 @@ class Context:
         self._check(lib().pj_pair_bounds(self.h, R.handle, S.handle, _ptr(pr, C.c_int32), _ptr(ps, C.c_int32), n,
                                          int(lod), int(prec), _ptr(lb, C.c_double), _ptr(ub, C.c_double)))
         return lb, ub
+
+    def pair_bounds_static(self, R: Set, S: Set, pr_dev: int, ps_dev: int, n: int, lod: int, prec: int,
+                           lb_dev: int, ub_dev: int, stream: int | None = None):
+        """pj_pair_bounds_static: device buffers in and out, no allocation."""
+        self._check(lib().pj_pair_bounds_static(self.h, R.handle, S.handle, C.c_void_p(pr_dev), C.c_void_p(ps_dev),
+                                                int(n), int(lod), int(prec), C.c_void_p(lb_dev), C.c_void_p(ub_dev),
+                                                C.c_void_p(stream) if stream else None))
 
     def fma_peak(self, fp64: bool) -> float:
         """Measured FMA throughput in GFLOP/s (FMA = 2 flops)."""
