@@ -104,6 +104,9 @@ struct pj_ctx {
 namespace pj {
 
 // Packed MLP weight layout (floats).
+// capacity of the queue of straddling facet pairs per refine launch
+constexpr unsigned CROSS_QUEUE_CAP = 1u << 22;
+
 constexpr int MLP_IN = 16, MLP_H = 64;
 constexpr int MLP_W1 = 0, MLP_B1 = MLP_W1 + MLP_H * MLP_IN, MLP_W2 = MLP_B1 + MLP_H,
               MLP_B2 = MLP_W2 + MLP_H * MLP_H, MLP_W3 = MLP_B2 + MLP_H, MLP_B3 = MLP_W3 + MLP_H,
@@ -190,7 +193,9 @@ struct PairBufs {
   int64_t* tcount;   // [n+1]
   int64_t* toff;     // [n+1]
   Tile* tiles;
-  unsigned long long* counters;  // [2]: tests, tile counter
+  unsigned long long* counters;  // [3]: tests, tile counter, straddle-queue count
+  int4* queue;                   // straddling facet pairs (see k_cross_fix)
+  unsigned qcap;
 };
 void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const PairBufs& b,
                       cudaStream_t st);

@@ -272,6 +272,9 @@ struct RefineArgs {
   void* mid;
   unsigned long long* ntests;
   int* err;
+  int4* queue;       // straddling facet pairs: (pair, r facet, s facet, eps bits)
+  unsigned* qcount;
+  unsigned qcap;
 };
 
 template <class T>
@@ -430,23 +433,29 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
           load_rec(Q, srec[j]);
           bool maybe;
           T d2 = tri_d2(P, Q, eh, maybe);
-          if (FULL) {
-            d2m = min(d2m, d2);
-          } else {
-            T d = sqrt_test(d2);
-            lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
-            ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
-          }
-          if (maybe) {
-            bool poss = false, cert = false;
-            tri_cross(P, Q, eh, ew, poss, cert);
-            if (F64) poss = cert;   // double precision: the test as computed is the answer
+          if (!maybe) {
             if (FULL) {
-              anyposs |= poss;
-              anycert |= cert;
+              d2m = min(d2m, d2);
             } else {
-              if (poss) lbm = min(lbm, -add_ru(P.ph, Q.ph));
-              if (cert) ubc = min(ubc, add_ru(P.hd, Q.hd));
+              T d = sqrt_test(d2);
+              lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
+              ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
+            }
+          } else {
+            // rare: both triangles straddle each other's planes.  The pair is
+            // queued; k_cross_fix decides its meeting test in double
+            // precision and folds its bounds in.  A full queue falls back to
+            // "a crossing is possible" (lower bound 0), which stays valid.
+            unsigned qk = atomicAdd(a.qcount, 1u);
+            if (qk < a.qcap) {
+              a.queue[qk] = make_int4(tl.pair, tl.rb + i, tl.sb + j, __float_as_int(tl.eps));
+            } else if (FULL) {
+              anyposs = true;
+              d2m = min(d2m, d2);
+            } else {
+              T d = sqrt_test(d2);
+              lbm = min(lbm, -add_ru(P.ph, Q.ph));
+              ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
             }
           }
         }
@@ -503,6 +512,54 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
   }
 }
 
+// Bounds contribution of the queued straddling facet pairs: the 15-candidate
+// distance as in k_refine, the meeting test in double precision (exact
+// translation of the float vertices), then the same atomicMin updates.
+template <class T, bool FULL>
+__global__ void __launch_bounds__(256) k_cross_fix(RefineArgs a) {
+  const unsigned n = min(*a.qcount, a.qcap);
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int4 e = a.queue[k];
+    const int pair = e.x;
+    const float eps = __int_as_float(e.w);
+    const float4 o4 = a.origin[pair];
+    const float4* fr = a.facR + 3LL * e.y;
+    const float4* fs = a.facS + 3LL * e.z;
+    float4 r0 = fr[0], r1 = fr[1], r2 = fr[2], s0 = fs[0], s1 = fs[1], s2 = fs[2];
+    T va[3], vb[3], vc[3], wa[3], wb[3], wc[3];
+    translate(r0, o4, va);
+    translate(r1, o4, vb);
+    translate(r2, o4, vc);
+    translate(s0, o4, wa);
+    translate(s1, o4, wb);
+    translate(s2, o4, wc);
+    Rec<T> P, Q;
+    make_rec(P, va, vb, vc, T(r0.w), T(r1.w), true);
+    make_rec(Q, wa, wb, wc, T(s0.w), T(s1.w), false);
+    bool maybe;
+    T d2 = tri_d2(P, Q, T(0), maybe);
+    float4 rr[3] = {r0, r1, r2}, ss[3] = {s0, s1, s2};
+    const bool cert = cross_exact64(rr, ss, o4);
+    const T phs = add_ru(P.ph, Q.ph), hds = add_ru(P.hd, Q.hd);
+    T lb, ub, mid;
+    if (cert) {
+      lb = -phs;
+      ub = hds;
+      mid = T(0);
+    } else {
+      T d = FULL ? sqrt_rn(d2) : sqrt_test(d2);
+      lb = sub_rd(sub_rd(d, phs), T(eps));
+      ub = add_ru(add_ru(d, hds), T(eps));
+      mid = d;
+    }
+    lb = max(lb, T(0));
+    using B = Bits<T>;
+    atomicMin(&((typename B::U*)a.lb)[pair], B::enc(lb));
+    atomicMin(&((typename B::U*)a.ub)[pair], B::enc(ub));
+    if (FULL) atomicMin(&((typename B::U*)a.mid)[pair], B::enc(mid));
+  }
+}
+
 template <class T, bool FULL, bool CULL>
 static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaStream_t st) {
   auto kern = k_refine<T, FULL, CULL>;
@@ -517,6 +574,11 @@ static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaSt
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
+  if (args.qcap > 0) {
+    k_cross_fix<T, FULL><<<ctx->sm_count * 4, 256, 0, st>>>(args);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+  }
 }
 
 float refine_ms(pj_ctx* ctx, int ev) {
@@ -549,6 +611,10 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, c
   a.mid = ctx->ws[WS_MID].p;
   a.ntests = ctx->d_counters + (sp.fp64 ? 1 : 0);
   a.err = ctx->d_err;
+  a.qcap = CROSS_QUEUE_CAP;
+  a.queue = (int4*)ws_get(ctx, WS_MISC2, (size_t)a.qcap * sizeof(int4), st);
+  a.qcount = (unsigned*)(ctx->d_counters + 14);
+  PJ_CK(cudaMemsetAsync(a.qcount, 0, sizeof(unsigned), st));
   (void)n;
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
   if (sp.fp64) {
@@ -636,6 +702,10 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_ti
   a.mid = b.mid;
   a.ntests = b.counters;
   a.err = err;
+  a.queue = b.queue;
+  a.qcap = b.qcap;
+  a.qcount = (unsigned*)(b.counters + 2);
+  PJ_CK(cudaMemsetAsync(a.qcount, 0, sizeof(unsigned), st));
   if (sp.fp64) {
     if (sp.full) launch_refine<double, true, false>(ctx, a, n_tiles, st);
     else launch_refine<double, false, false>(ctx, a, n_tiles, st);
@@ -680,18 +750,15 @@ __global__ void k_tri_dist(const float* P, const float* Q, int64_t n, double* ou
   T eh = sizeof(T) == 8 ? T(0) : T(m.eh), ew = sizeof(T) == 8 ? T(0) : T(m.ew);
   bool maybe;
   T d2 = tri_d2(RP, RQ, eh, maybe);
-  bool poss = false, cert = false;
-  if (maybe) tri_cross(RP, RQ, eh, ew, poss, cert);
+  float4 fp[3] = {make_float4(a[0], a[1], a[2], 0.f), make_float4(a[3], a[4], a[5], 0.f),
+                  make_float4(a[6], a[7], a[8], 0.f)};
+  float4 fq[3] = {make_float4(b[0], b[1], b[2], 0.f), make_float4(b[3], b[4], b[5], 0.f),
+                  make_float4(b[6], b[7], b[8], 0.f)};
+  const bool cert = maybe && cross_exact64(fp, fq, make_float4(o[0], o[1], o[2], 0.f));
+  (void)ew;
   T d = sqrt_rn(d2);
-  if (sizeof(T) == 8) {
-    out[p] = cert ? 0.0 : double(d);
-    if (err) err[p] = 0.0;
-  } else {
-    out[p] = cert ? 0.0 : double(d);
-    double e = m.eps;
-    if (poss && !cert) e = fmax(e, double(d) + m.eps);
-    if (err) err[p] = cert ? 0.0 : e;
-  }
+  out[p] = cert ? 0.0 : double(d);
+  if (err) err[p] = (cert || sizeof(T) == 8) ? 0.0 : (double)m.eps;
 }
 
 void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool fp64, double* out, double* err,

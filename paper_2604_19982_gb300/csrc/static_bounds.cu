@@ -23,6 +23,7 @@ namespace {
 
 constexpr int64_t MAXP = PJ_STATIC_MAX_PAIRS;
 constexpr int64_t MAXT = PJ_STATIC_MAX_TILES;
+constexpr int64_t MAXQ = 65536;   // queued straddling facet pairs
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -43,13 +44,14 @@ constexpr size_t OFF_MID = OFF_UB + align256(MAXP * 8);
 constexpr size_t OFF_TCOUNT = OFF_MID + align256(MAXP * 8);
 constexpr size_t OFF_TOFF = OFF_TCOUNT + align256((MAXP + 1) * 8);
 constexpr size_t OFF_TILES = OFF_TOFF + align256((MAXP + 1) * 8);
-constexpr size_t OFF_COUNTERS = OFF_TILES + align256(MAXT * sizeof(Tile));
+constexpr size_t OFF_QUEUE = OFF_TILES + align256(MAXT * sizeof(Tile));
+constexpr size_t OFF_COUNTERS = OFF_QUEUE + align256(MAXQ * sizeof(int4));
 constexpr size_t OFF_ERR = OFF_COUNTERS + 256;
 constexpr size_t SCRATCH_BYTES = OFF_ERR + 256;
 
 }  // namespace
 
-// The scratch itself: about 1.5 MB per device.
+// The scratch itself: about 2.5 MB per device.
 static __device__ __align__(256) unsigned char g_bounds_scratch[SCRATCH_BYTES];
 
 namespace {
@@ -158,6 +160,8 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     b.toff = reinterpret_cast<int64_t*>(base + OFF_TOFF);
     b.tiles = reinterpret_cast<Tile*>(base + OFF_TILES);
     b.counters = reinterpret_cast<unsigned long long*>(base + OFF_COUNTERS);
+    b.queue = reinterpret_cast<int4*>(base + OFF_QUEUE);
+    b.qcap = (unsigned)MAXQ;
     StepSpec sp;
     sp.lodR = lod;
     sp.lodS = lod;

@@ -16,12 +16,10 @@
 //    (any s, t in [0, 1] is a true point pair, so the value never
 //    underestimates); the distance is taken from the difference vector
 //    r + s d1 - t d2 itself.
-//  * meeting: when both triangles straddle each other's planes, each edge is
-//    tested against the other triangle with the heights h and the in-plane
-//    dots g already formed above: the crossing point of edge (a, b) is inside
-//    iff every (h_b g_aj - h_a g_bj) sign(h_b - h_a) >= 0.  With error
-//    margins (single precision) the test yields `possible` (cannot be
-//    excluded) and `certain` (holds for the exact input).
+//  * meeting: only when both triangles straddle each other's planes (within
+//    the height error margin) can an edge cross the other triangle; that rare
+//    case is decided in double precision from the float vertices by signed
+//    volumes (cross_exact64), in both precisions of the path.
 //
 // The register-side record (P) stores n and m negated so that every dot
 // product reads the same difference vectors D_ij = p_i - q_j.
@@ -274,69 +272,57 @@ __device__ __forceinline__ T tri_d2(const Rec<T>& P, const Rec<T>& Q, T eh, bool
   return d2;
 }
 
-// Edge (a, b) with heights ha, hb over the other triangle's plane and the
-// in-plane dots ga[j], gb[j]: can it cross / does it certainly cross?
-template <class T>
-__device__ __forceinline__ void edge_cross(T ha, T hb, const T ga[3], const T gb[3], T eh, T ew, bool& possible,
-                                           bool& certain) {
-  bool same_pos = ha > eh && hb > eh;
-  bool same_neg = ha < -eh && hb < -eh;
-  if (same_pos || same_neg) return;
-  bool opposite = (ha > eh && hb < -eh) || (ha < -eh && hb > eh);
-  T dh = hb - ha;
-  bool sgn_known = dh > T(2) * eh || dh < -T(2) * eh;
-  T sg = dh > T(0) ? T(1) : T(-1);
-  bool all_nonneg = true, all_pos = true;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    T w = (hb * ga[j] - ha * gb[j]) * sg;
-    all_nonneg = all_nonneg && (w >= -ew);
-    all_pos = all_pos && (w > ew);
-  }
-  // with zero margins (double precision) "certain" reduces to the exact-
-  // arithmetic crossing test evaluated as computed
-  if (!sgn_known || all_nonneg) possible = true;
-  if (opposite && sgn_known && all_pos) certain = true;
+// Crossing decision in double precision from raw float vertices (the three
+// float4 of each facet, .w ignored) and a float origin: differences of
+// floats are exact in double, so this is the FP64 path's test, used by the
+// single-precision kernel in its rare branch.  Edge (a, b) of one triangle
+// crosses the other, (t0, t1, t2), when a and b lie strictly on opposite
+// sides of its plane and the line through them passes strictly inside all
+// three edges (signed volumes of (a, b, t_j, t_j+1) of one sign).
+__device__ __forceinline__ double orient64(const double a[3], const double b[3], const double c[3],
+                                           const double d[3]) {
+  double x0 = b[0] - a[0], x1 = b[1] - a[1], x2 = b[2] - a[2];
+  double y0 = c[0] - a[0], y1 = c[1] - a[1], y2 = c[2] - a[2];
+  double z0 = d[0] - a[0], z1 = d[1] - a[1], z2 = d[2] - a[2];
+  return x0 * (y1 * z2 - y2 * z1) + x1 * (y2 * z0 - y0 * z2) + x2 * (y0 * z1 - y1 * z0);
 }
 
-// The crossing test of all six edges (only run when `maybe`).  Recomputes
-// the heights and in-plane dots to keep the common path's registers low.
-template <class T>
-__device__ void tri_cross(const Rec<T>& P, const Rec<T>& Q, T eh, T ew, bool& possible, bool& certain) {
-  T D[3][3][3];
+static __device__ __noinline__ bool cross_exact64(const float4* fp, const float4* fq, float4 o) {
+  double P[3][3], Q[3][3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) D[i][j][k] = P.v[i][k] - Q.v[j][k];
-  T hP[3], hQ[3], gP[3][3], gQ[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    hP[i] = fma_(Q.n[2], D[i][0][2], fma_(Q.n[1], D[i][0][1], fma_(Q.n[0], D[i][0][0], Q.hoff)));
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gP[i][j] = dot3(Q.m[j], D[i][j]);      // m_Qj . (p_i - q_j)
+  for (int v = 0; v < 3; ++v) {
+    P[v][0] = (double)fp[v].x - (double)o.x;
+    P[v][1] = (double)fp[v].y - (double)o.y;
+    P[v][2] = (double)fp[v].z - (double)o.z;
+    Q[v][0] = (double)fq[v].x - (double)o.x;
+    Q[v][1] = (double)fq[v].y - (double)o.y;
+    Q[v][2] = (double)fq[v].z - (double)o.z;
   }
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    hQ[j] = fma_(P.n[2], D[0][j][2], fma_(P.n[1], D[0][j][1], fma_(P.n[0], D[0][j][0], P.hoff)));
-#pragma unroll
-    for (int i = 0; i < 3; ++i) gQ[j][i] = dot3(P.m[i], D[i][j]);      // m_Pi . (q_j - p_i)
+  for (int side = 0; side < 2; ++side) {
+    const double(*A)[3] = side ? Q : P;
+    const double(*B)[3] = side ? P : Q;
+    double h[3];
+    for (int i = 0; i < 3; ++i) h[i] = orient64(B[0], B[1], B[2], A[i]);
+    for (int i = 0; i < 3; ++i) {
+      int k = (i + 1) % 3;
+      if (!((h[i] > 0.0 && h[k] < 0.0) || (h[i] < 0.0 && h[k] > 0.0))) continue;
+      double o1 = orient64(A[i], A[k], B[0], B[1]);
+      double o2 = orient64(A[i], A[k], B[1], B[2]);
+      double o3 = orient64(A[i], A[k], B[2], B[0]);
+      if ((o1 > 0.0 && o2 > 0.0 && o3 > 0.0) || (o1 < 0.0 && o2 < 0.0 && o3 < 0.0)) return true;
+    }
   }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    int k = (i + 1) % 3;
-    edge_cross(hP[i], hP[k], gP[i], gP[k], eh, ew, possible, certain);
-    edge_cross(hQ[i], hQ[k], gQ[i], gQ[k], eh, ew, possible, certain);
-  }
+  return false;
 }
 
 // Forward error margins of the single-precision test for coordinates
 // bounded by rho (pair-local, per axis), maximal edge length L and minimal
-// facet sine smin (see the error analysis in the design notes):
-//   heights   |h~ - h| <= 128 u rho / smin
-//   crossing  |w~ - w| <= 2048 u rho^2 L / smin
+// facet sine smin:
+//   heights   |h~ - h| <= 128 u rho / smin   (straddle pre-filter)
 //   distance  |d~ - d| <= 256 u rho / smin + 8 sqrt(u) L
+// (u = 2^-24; the sqrt(u) L term covers nearly parallel edges, where the
+// segment parameter is ill-conditioned but any clamped value is a true
+// point pair).
 struct Margins {
   float eps, eh, ew;
 };
@@ -347,7 +333,7 @@ __host__ __device__ __forceinline__ Margins fp32_margins(float rho, float L, flo
   float s = smin > 1e-6f ? smin : 1e-6f;
   Margins m;
   m.eh = 128.0f * u * rho / s;
-  m.ew = 2048.0f * u * rho * rho * L / s;
+  m.ew = 0.0f;
   m.eps = 256.0f * u * rho / s + 8.0f * su * L;
   return m;
 }
