@@ -246,13 +246,13 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
  *   lb, ub   DEVICE double [n] outputs, as for pj_pair_bounds;
  *   cuda_stream  stream to work on (NULL = the context's stream); the call
  *            returns when the results are written.
- * Scratch: one fixed array of about 2.5 MB in the library's device code,
+ * Scratch: one fixed array of about 3.6 MB in the library's device code,
  * held by every GPU that loads the library until the process exits.  Its
  * device address is looked up on the first call on each device (with that
  * device current).  Sizes beyond it are rejected with PJ_EINVAL:
- * n <= PJ_STATIC_MAX_PAIRS, and n x (chunks of the largest R object) x
- * (chunks of the largest S object) at `lod` <= PJ_STATIC_MAX_TILES, a chunk
- * being 256 facets.  All calls share the array; it keeps the previous
+ * n <= PJ_STATIC_MAX_PAIRS, n x (blocks of the largest R object) x (blocks
+ * of the largest S object) at `lod` <= PJ_STATIC_MAX_TILES with a block of
+ * 32 facets, and n x (256-facet chunks of the largest R object) <= 65536.  All calls share the array; it keeps the previous
  * call's contents (the call clears what must start at zero), and calls that
  * overlap on the GPU -- on two streams or from two host threads -- race on
  * it and must be serialized by the caller. */

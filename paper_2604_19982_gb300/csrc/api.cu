@@ -93,14 +93,14 @@ __global__ void k_expand(int64_t F, int n, const float* verts, const int64_t* vo
 }
 
 // one warp per chunk: box, max hd / ph, max edge length, min facet sine
-__global__ void k_chunks(int64_t C, int n, const int64_t* coff, const int64_t* foff, const float4* fac,
+__global__ void k_chunks(int64_t C, int n, int size, const int64_t* coff, const int64_t* foff, const float4* fac,
                          float4* chunk) {
   int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (c >= C) return;
   int64_t o = upper_obj(coff, n, c);
   int64_t j = c - coff[o];
-  int64_t f0 = foff[o] + j * CHUNK, f1 = min(f0 + CHUNK, foff[o + 1]);
+  int64_t f0 = foff[o] + j * size, f1 = min(f0 + size, foff[o + 1]);
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   float mhd = 0.f, mph = 0.f, medge = 0.f, smin = 1.f;
   for (int64_t f = f0 + lane; f < f1; f += 32) {
@@ -172,6 +172,8 @@ void free_set_storage(pj_set* s) {
     cudaFree(s->lod[l].foff);
     cudaFree(s->lod[l].chunk);
     cudaFree(s->lod[l].coff);
+    cudaFree(s->lod[l].blk);
+    cudaFree(s->lod[l].boff);
     s->lod[l] = LodData();
   }
   cudaFree(s->mbb);
@@ -230,6 +232,12 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
       ld.coff_h[o + 1] = ld.coff_h[o] + (fo + CHUNK - 1) / CHUNK;
     }
     ld.C = ld.coff_h[n];
+    ld.boff_h.assign(n + 1, 0);
+    for (int o = 0; o < n; ++o) {
+      int64_t fo = ld.foff_h[o + 1] - ld.foff_h[o];
+      ld.boff_h[o + 1] = ld.boff_h[o] + (fo + BLK - 1) / BLK;
+    }
+    ld.B = ld.boff_h[n];
     // uploads
     float* dv;
     auto it = vcache.find(D->verts[l]);
@@ -247,6 +255,7 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
     temps.push_back(dfa);
     ld.foff = upload(ld.foff_h.data(), (size_t)n + 1, st);
     ld.coff = upload(ld.coff_h.data(), (size_t)n + 1, st);
+    ld.boff = upload(ld.boff_h.data(), (size_t)n + 1, st);
     float* dhd = nullptr;
     float* dph = nullptr;
     if (D->hd[l]) {
@@ -259,6 +268,7 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
     }
     PJ_CK(cudaMalloc((void**)&ld.fac, std::max<int64_t>(1, 3 * ld.F) * sizeof(float4)));
     PJ_CK(cudaMalloc((void**)&ld.chunk, std::max<int64_t>(1, 3 * ld.C) * sizeof(float4)));
+    PJ_CK(cudaMalloc((void**)&ld.blk, std::max<int64_t>(1, 3 * ld.B) * sizeof(float4)));
     if (ld.F > 0) {
       int th = 256;
       k_expand<<<(unsigned)((ld.F + th - 1) / th), th, 0, st>>>(ld.F, n, dv, dvo, dfa, ld.foff, nfs, dhd, dph,
@@ -266,7 +276,11 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
       PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
       int64_t thr = ld.C * 32;
-      k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, ld.coff, ld.foff, ld.fac, ld.chunk);
+      k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, CHUNK, ld.coff, ld.foff, ld.fac, ld.chunk);
+      PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+      thr = ld.B * 32;
+      k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.B, n, BLK, ld.boff, ld.foff, ld.fac, ld.blk);
       PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
     }

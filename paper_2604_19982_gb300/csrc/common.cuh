@@ -13,7 +13,8 @@ enum : int {
   ERR_CAPACITY = 8        // an output list would have overflowed its buffer
 };
 
-constexpr int CHUNK = 256;       // facets per chunk (tile side)
+constexpr int CHUNK = 256;       // facets per chunk (coarse pruning box)
+constexpr int BLK = 32;          // facets per block (side of a refinement unit)
 constexpr int REFINE_THREADS = 256;
 
 __device__ __forceinline__ void set_err(int* err, int bit) {

@@ -53,6 +53,10 @@ struct LodData {
   float4* chunk = nullptr;        // [3C]: (lo, max hd), (hi, max ph), (max edge, min sine, 0, 0)
   int64_t* coff = nullptr;        // device [n+1] chunk offsets
   std::vector<int64_t> coff_h;
+  int64_t B = 0;                  // blocks of <= BLK facets (same layout as chunks)
+  float4* blk = nullptr;          // [3B]
+  int64_t* boff = nullptr;        // device [n+1] block offsets
+  std::vector<int64_t> boff_h;
   int64_t maxF = 0;               // largest facet count of one object
 };
 
@@ -126,7 +130,10 @@ void free_set_storage(pj_set* s);
 
 // ---- scan (join.cu): exclusive prefix sum of n int64 values into out[0..n],
 // out[n] = total.  tmp is workspace.
-void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+// With tmp == nullptr the temporaries are allocated stream-ordered; otherwise
+// tmp must hold scan_tmp_words(n) words and nothing is allocated.
+void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, int64_t* tmp = nullptr);
+int64_t scan_tmp_words(int64_t n);
 
 // ---- filter (filter.cu)
 struct FilterOut {
@@ -190,8 +197,12 @@ struct PairBufs {
   void* lb;
   void* ub;
   void* mid;
-  int64_t* tcount;   // [n+1]
+  int64_t* tcount;   // [n+1] r chunks per pair
   int64_t* toff;     // [n+1]
+  int64_t* wcount;   // [wcap+1] units per (pair, r chunk)
+  int64_t* woff;     // [wcap+1]
+  int64_t wcap;
+  int64_t* scan_tmp; // scan temporaries (nullptr: allocate)
   Tile* tiles;
   unsigned long long* counters;  // [3]: tests, tile counter, straddle-queue count
   int4* queue;                   // straddling facet pairs (see k_cross_fix)
@@ -199,10 +210,8 @@ struct PairBufs {
 };
 void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const PairBufs& b,
                       cudaStream_t st);
-void count_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                      const PairBufs& b, cudaStream_t st);
-void emit_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                     const PairBufs& b, cudaStream_t st);
+int64_t build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                         const PairBufs& b, int64_t tiles_cap, cudaStream_t st);
 void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st);
 void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
                      const PairBufs& b, int* err, cudaStream_t st);

@@ -75,7 +75,18 @@ __global__ void k_scan_apply(const int64_t* in, int64_t n, const int64_t* boff, 
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = boff ? boff[nb] : tot;
 }
 
-void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
+// Temporary words needed by scan_i64 for n values (all recursion levels).
+int64_t scan_tmp_words(int64_t n) {
+  int64_t w = 0;
+  while (n > SCAN_B) {
+    int64_t nb = (n + SCAN_B - 1) / SCAN_B;
+    w += 2 * nb + 1;
+    n = nb;
+  }
+  return w;
+}
+
+void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, int64_t* tmp) {
   if (n == 0) {
     PJ_CK(cudaMemsetAsync(out, 0, 8, st));
     return;
@@ -84,21 +95,21 @@ void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStrea
   if (nb == 1) {
     k_scan_apply<<<1, SCAN_T, 0, st>>>(in, n, nullptr, 0, out);
     PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
+    PJ_COUNT_LAUNCH;
     return;
   }
-  int64_t* tmp = nullptr;
-  PJ_CK(cudaMallocAsync((void**)&tmp, (size_t)(2 * nb + 1) * 8, st));
+  bool own = tmp == nullptr;
+  if (own) PJ_CK(cudaMallocAsync((void**)&tmp, (size_t)scan_tmp_words(n) * 8, st));
   int64_t* bsum = tmp;
   int64_t* boff = tmp + nb;
   k_block_sums<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  scan_i64(ctx, bsum, boff, nb, st);
+  scan_i64(ctx, bsum, boff, nb, st, tmp + 2 * nb + 1);
   k_scan_apply<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, boff, nb, out);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  PJ_CK(cudaFreeAsync(tmp, st));
+  if (own) PJ_CK(cudaFreeAsync(tmp, st));
 }
 
 void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {

@@ -91,11 +91,19 @@ void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, doubl
   PJ_COUNT_LAUNCH;
 }
 
-// ------------------------------------------------------------------ tiles
+// ------------------------------------------------------------------ units
+// A refinement unit is one 32-facet block of r x one 32-facet block of s of
+// one candidate pair at one LoD.  The builder walks, for every (pair, r
+// chunk of 256 facets), the s chunks; a chunk pair whose box distance minus
+// the Hausdorff terms exceeds the pair's threshold is skipped whole, else its
+// 8 x 8 block pairs are tested the same way and only the live ones become
+// units (PJ_TILE_PRUNE; without it every block pair is a unit).
 
-struct ChunkView {
-  const float4* chunk;   // [3C]
+struct BoxView {
+  const float4* chunk;   // [3C] chunk boxes
   const int64_t* coff;   // [n+1]
+  const float4* blk;     // [3B] block boxes
+  const int64_t* boff;   // [n+1]
   const int64_t* foff;   // [n+1]
 };
 
@@ -113,8 +121,8 @@ __device__ __forceinline__ float absmax_rel(float4 lo, float4 hi, float4 o) {
   return fmaxf(m, fmaxf(fabsf(lo.z - o.z), fabsf(hi.z - o.z)));
 }
 
-// Margins of a chunk pair in the pair-local frame.
-__device__ __forceinline__ Margins chunk_margins(const float4* cr, const float4* cs, float4 o) {
+// Margins of a box pair (chunks or blocks) in the pair-local frame.
+__device__ __forceinline__ Margins box_margins(const float4* cr, const float4* cs, float4 o) {
   float rho = fmaxf(absmax_rel(cr[0], cr[1], o), absmax_rel(cs[0], cs[1], o));
   rho = rho * 1.0001f + 1e-30f;
   float L = fmaxf(cr[2].x, cs[2].x);
@@ -122,74 +130,132 @@ __device__ __forceinline__ Margins chunk_margins(const float4* cr, const float4*
   return fp32_margins(rho, L, smin);
 }
 
-// Can a facet pair of these two chunks reach the threshold?  Every facet
-// pair has true distance >= box gap; the single-precision lower bound adds
-// at most 2 eps of error; Eq. 2 subtracts at most max ph of each side.
-__device__ __forceinline__ bool chunk_pair_live(const float4* cr, const float4* cs, float thr, float eps) {
+// Can a facet pair of these two boxes reach the threshold?  Every facet pair
+// has true distance >= the box gap; the single-precision lower bound loses
+// at most 2 eps; Eq. 2 subtracts at most the max ph of each side.
+__device__ __forceinline__ bool box_pair_live(const float4* cr, const float4* cs, float thr, float eps) {
   float g = box_gap_rd(cr[0], cr[1], cs[0], cs[1]);
   float lb = __fsub_rd(__fsub_rd(__fsub_rd(g, cr[1].w), cs[1].w), 2.f * eps);
   return !(lb > thr);
 }
 
-__global__ void k_count_tiles(int64_t n, const int32_t* pr, const int32_t* ps, const uint8_t* status,
-                              const uint8_t* lod0, uint8_t want, int step, ChunkView R, ChunkView S,
-                              const float4* origin, const float* thr, int cull, int fp64, int64_t* count) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  int64_t c = 0;
-  if (status[p] == want && lod0[p] <= step) {
-    const int r = pr[p], s = ps[p];
-    int64_t r0 = R.coff[r], r1 = R.coff[r + 1], s0 = S.coff[s], s1 = S.coff[s + 1];
-    if (!cull) {
-      c = (r1 - r0) * (s1 - s0);
-    } else {
-      const float4 o = origin[p];
-      const float t = thr[p];
-      for (int64_t a = r0; a < r1; ++a)
-        for (int64_t b = s0; b < s1; ++b) {
-          const float4* ca = R.chunk + 3 * a;
-          const float4* cb = S.chunk + 3 * b;
-          float eps = fp64 ? 0.f : chunk_margins(ca, cb, o).eps;
-          c += chunk_pair_live(ca, cb, t, eps);
-        }
-    }
+__device__ __forceinline__ int64_t find_pair(const int64_t* off, int64_t n, int64_t w) {
+  // largest p with off[p] <= w
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= w) lo = mid;
+    else hi = mid;
   }
-  count[p] = c;
+  return lo;
 }
 
-__global__ void k_emit_tiles(int64_t n, const int32_t* pr, const int32_t* ps, const uint8_t* status,
-                             const uint8_t* lod0, uint8_t want, int step, ChunkView R, ChunkView S,
-                             const float4* origin, const float* thr, int cull, int fp64, const int64_t* off,
-                             Tile* tiles) {
+__global__ void k_rchunks(int64_t n, const int32_t* pr, const uint8_t* status, const uint8_t* lod0, uint8_t want,
+                          int step, const int64_t* coffR, int64_t* cnt) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
-  if (!(status[p] == want && lod0[p] <= step)) return;
-  const int r = pr[p], s = ps[p];
-  const int64_t r0 = R.coff[r], r1 = R.coff[r + 1], s0 = S.coff[s], s1 = S.coff[s + 1];
-  const int64_t fr0 = R.foff[r], fr1 = R.foff[r + 1], fs0 = S.foff[s], fs1 = S.foff[s + 1];
-  const float4 o = origin[p];
-  const float t = thr[p];
-  int64_t w = off[p];
-  for (int64_t a = r0; a < r1; ++a)
-    for (int64_t b = s0; b < s1; ++b) {
-      const float4* ca = R.chunk + 3 * a;
-      const float4* cb = S.chunk + 3 * b;
-      Margins m = chunk_margins(ca, cb, o);
-      if (fp64) m.eps = m.eh = m.ew = 0.f;
-      if (cull && !chunk_pair_live(ca, cb, t, m.eps)) continue;
-      Tile tl;
-      int64_t rb = fr0 + (a - r0) * CHUNK, sb = fs0 + (b - s0) * CHUNK;
-      tl.pair = (int32_t)p;
-      tl.rb = (int32_t)rb;
-      tl.sb = (int32_t)sb;
-      tl.rl = (uint16_t)(fr1 - rb < CHUNK ? fr1 - rb : CHUNK);
-      tl.sl = (uint16_t)(fs1 - sb < CHUNK ? fs1 - sb : CHUNK);
-      tl.eps = m.eps;
-      tl.eh = m.eh;
-      tl.ew = m.ew;
-      tl.pad = 0;
-      tiles[w++] = tl;
+  cnt[p] = (status[p] == want && lod0[p] <= step) ? coffR[pr[p] + 1] - coffR[pr[p]] : 0;
+}
+
+// EMIT = false: count the live units of every (pair, r chunk) work item;
+// EMIT = true: write them.  Work items w < off1[n] (read on the device).
+template <bool EMIT>
+__global__ void k_units(int64_t n, const int32_t* pr, const int32_t* ps, const int64_t* off1, BoxView R, BoxView S,
+                        const float4* origin, const float* thr, int cull, int fp64, int64_t* cnt2,
+                        const int64_t* off2, Tile* tiles) {
+  const int64_t W = off1[n];
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < W; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = find_pair(off1, n, w);
+    const int r = pr[p], s = ps[p];
+    const int64_t rc = R.coff[r] + (w - off1[p]);               // r chunk
+    const int64_t rb0 = R.boff[r] + (w - off1[p]) * (CHUNK / BLK);
+    const int64_t rb1 = min(rb0 + CHUNK / BLK, R.boff[r + 1]);    // r blocks of the chunk
+    const int64_t sc0 = S.coff[s], sc1 = S.coff[s + 1];
+    const float4 o = origin[p];
+    const float t = thr[p];
+    int64_t c = 0;
+    int64_t wpos = EMIT ? off2[w] : 0;
+    if (!cull && !EMIT) {
+      c = (rb1 - rb0) * (S.boff[s + 1] - S.boff[s]);
+    } else {
+      const float4* ca = R.chunk + 3 * rc;
+      for (int64_t sc = sc0; sc < sc1; ++sc) {
+        const float4* cb = S.chunk + 3 * sc;
+        if (cull && !box_pair_live(ca, cb, t, fp64 ? 0.f : box_margins(ca, cb, o).eps)) continue;
+        const int64_t sb0 = S.boff[s] + (sc - sc0) * (CHUNK / BLK);
+        const int64_t sb1 = min(sb0 + CHUNK / BLK, S.boff[s + 1]);
+        for (int64_t rb = rb0; rb < rb1; ++rb)
+          for (int64_t sb = sb0; sb < sb1; ++sb) {
+            const float4* ba = R.blk + 3 * rb;
+            const float4* bb = S.blk + 3 * sb;
+            Margins m = box_margins(ba, bb, o);
+            if (fp64) m.eps = m.eh = 0.f;
+            if (cull && !box_pair_live(ba, bb, t, m.eps)) continue;
+            if (EMIT) {
+              Tile tl;
+              const int64_t fr = R.foff[r] + (rb - R.boff[r]) * BLK, fs = S.foff[s] + (sb - S.boff[s]) * BLK;
+              tl.pair = (int32_t)p;
+              tl.rb = (int32_t)fr;
+              tl.sb = (int32_t)fs;
+              tl.rl = (uint16_t)(R.foff[r + 1] - fr < BLK ? R.foff[r + 1] - fr : BLK);
+              tl.sl = (uint16_t)(S.foff[s + 1] - fs < BLK ? S.foff[s + 1] - fs : BLK);
+              tl.eps = m.eps;
+              tl.eh = m.eh;
+              tl.ew = 0.f;
+              tl.pad = 0;
+              tiles[wpos++] = tl;
+            } else {
+              ++c;
+            }
+          }
+      }
     }
+    if (!EMIT) cnt2[w] = c;
+  }
+}
+
+static BoxView box_view(const LodData& L) { return BoxView{L.chunk, L.coff, L.blk, L.boff, L.foff}; }
+
+// Shared by the workspace path and the explicit-buffer path.
+static int64_t build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                           const int32_t* pr, const int32_t* ps, const uint8_t* status, const uint8_t* lod0,
+                           const float4* origin, const float* thr, int64_t* cnt1, int64_t* off1, int64_t* cnt2,
+                           int64_t* off2, int64_t wcap, Tile** tiles_io, int64_t tiles_cap, bool grow,
+                           int64_t* scan_tmp, cudaStream_t st) {
+  const LodData& LR = R->lod[sp.lodR];
+  const LodData& LS = S->lod[sp.lodS];
+  BoxView vr = box_view(LR), vs = box_view(LS);
+  int th = 256;
+  k_rchunks<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, status, lod0, sp.want, sp.step, LR.coff, cnt1);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  scan_i64(ctx, cnt1, off1, n, st, scan_tmp);
+  unsigned g = (unsigned)std::min<int64_t>((wcap + th - 1) / th + 1, (int64_t)ctx->sm_count * 32);
+  k_units<false><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, cnt2, nullptr, nullptr);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  int64_t W = 0;
+  PJ_CK(cudaMemcpyAsync(&W, off1 + n, 8, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  if (W == 0) return 0;
+  scan_i64(ctx, cnt2, off2, W, st, scan_tmp);
+  int64_t total = 0;
+  PJ_CK(cudaMemcpyAsync(&total, off2 + W, 8, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  if (total == 0) return 0;
+  if (total > tiles_cap) {
+    if (!grow) throw ApiError{PJ_EINVAL, "refinement units above the scratch capacity"};
+    *tiles_io = (Tile*)ws_get(ctx, WS_TILES, total * sizeof(Tile), st);
+  }
+  k_units<true><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, nullptr, off2, *tiles_io);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  return total;
+}
+
+static int64_t work_cap(const pj_set* R, const StepSpec& sp, int64_t n) {
+  const LodData& LR = R->lod[sp.lodR];
+  return n * std::max<int64_t>(1, (LR.maxF + CHUNK - 1) / CHUNK);
 }
 
 int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
@@ -201,28 +267,15 @@ int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, co
   auto lod0 = (uint8_t*)ws_get(ctx, WS_LOD0, n, st);
   auto origin = (float4*)ws_get(ctx, WS_ORIGIN, n * 16, st);
   auto thr = (float*)ws_get(ctx, WS_THR, n * 4, st);
-  auto cnt = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
-  auto off = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
-  const LodData& LR = R->lod[sp.lodR];
-  const LodData& LS = S->lod[sp.lodS];
-  ChunkView cr{LR.chunk, LR.coff, LR.foff}, cs{LS.chunk, LS.coff, LS.foff};
-  int th = 128;
-  unsigned g = (unsigned)((n + th - 1) / th);
-  k_count_tiles<<<g, th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, cr, cs, origin, thr, sp.cull,
-                                   sp.fp64, cnt);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-  scan_i64(ctx, cnt, off, n, st);
-  int64_t total = 0;
-  PJ_CK(cudaMemcpyAsync(&total, off + n, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
-  if (total == 0) return 0;
-  auto tiles = (Tile*)ws_get(ctx, WS_TILES, total * sizeof(Tile), st);
-  k_emit_tiles<<<g, th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, cr, cs, origin, thr, sp.cull,
-                                  sp.fp64, off, tiles);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-  return total;
+  const int64_t wcap = work_cap(R, sp, n);
+  auto cnt1 = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
+  auto off1 = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
+  auto cnt2 = (int64_t*)ws_get(ctx, WS_MISC3, (wcap + 1) * 8, st);
+  auto off2 = (int64_t*)ws_get(ctx, WS_MISC4, (wcap + 1) * 8, st);
+  Tile* tiles = (Tile*)ctx->ws[WS_TILES].p;
+  const int64_t cap = (int64_t)(ctx->ws[WS_TILES].cap / sizeof(Tile));
+  return build_units(ctx, R, S, n, sp, pr, ps, status, lod0, origin, thr, cnt1, off1, cnt2, off2, wcap, &tiles, cap,
+                     true, nullptr, st);
 }
 
 __global__ void k_init_bounds(int64_t n, const uint8_t* status, const uint8_t* lod0, uint8_t want, int step,
@@ -285,231 +338,174 @@ __device__ __forceinline__ void translate(const float4& A, const float4& o, T ou
 }
 
 constexpr uint32_t MBAR_POLL_LIMIT = 1u << 20;
+constexpr int REFINE_WARPS = REFINE_THREADS / 32;
 
 template <class T>
+constexpr size_t warp_smem_bytes() {
+  return (size_t)2 * BLK * 48 + (size_t)BLK * sizeof(RecSmem<T>);
+}
+template <class T>
 constexpr size_t refine_smem_bytes() {
-  return (size_t)CHUNK * 48 + (size_t)CHUNK * sizeof(RecSmem<T>) + 16 * sizeof(float4);
+  return REFINE_WARPS * warp_smem_bytes<T>();
 }
 
-template <class T, bool FULL, bool CULL>
+// Persistent, warp-granular refinement: every warp takes units from a global
+// counter, prefetches the next unit's 32 s facets with a TMA bulk copy into
+// its second buffer while it computes the current one, expands the s facets
+// into records in its own shared-memory slice, and keeps one r facet per
+// lane in registers.  No barrier couples the warps of a CTA.
+template <class T, bool FULL>
 __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_refine(RefineArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float4* raw = reinterpret_cast<float4*>(smem);
-  RecSmem<T>* srec = reinterpret_cast<RecSmem<T>*>(smem + CHUNK * 48);
-  float4* blk = reinterpret_cast<float4*>(smem + CHUNK * 48 + CHUNK * sizeof(RecSmem<T>));
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int s_tile;
-  __shared__ int s_fail;
-  __shared__ T red[4][REFINE_THREADS / 32];
-  __shared__ unsigned long long red_n[REFINE_THREADS / 32];
-  constexpr bool F64 = sizeof(T) == 8;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    mbar_init(&bar, 1);
+  __shared__ __align__(8) uint64_t bars[REFINE_WARPS][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wbase = smem + warp * warp_smem_bytes<T>();
+  float4* raw0 = reinterpret_cast<float4*>(wbase);
+  float4* raw1 = raw0 + 3 * BLK;
+  RecSmem<T>* rec = reinterpret_cast<RecSmem<T>*>(wbase + 2 * BLK * 48);
+  uint64_t* bar0 = &bars[warp][0];
+  uint64_t* bar1 = &bars[warp][1];
+  if (lane == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
     fence_mbar_init();
-    s_fail = 0;
   }
-  __syncthreads();
-  uint32_t phase = 0;
+  __syncwarp();
   const T INF = inf_(T(0));
+  const unsigned FULLM = 0xffffffffu;
+  uint32_t ph0 = 0, ph1 = 0;
+  int b = 0;
+  unsigned long long ntest = 0;
 
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int64_t t = s_tile;
-    if (t >= a.n_tiles) break;
-    const Tile tl = a.tiles[t];
-    const int rl = tl.rl, sl = tl.sl;
-    if (tid == 0) {
-      fence_proxy_async();
-      mbar_arrive_expect_tx(&bar, (uint32_t)sl * 48u);
-      tma_load_1d(raw, a.facS + 3LL * tl.sb, (uint32_t)sl * 48u, &bar);
+  int64_t cur = 0;
+  if (lane == 0) {
+    cur = atomicAdd(a.counter, 1);
+    if (cur < a.n_tiles) {
+      const Tile t0 = a.tiles[cur];
+      mbar_arrive_expect_tx(bar0, (uint32_t)t0.sl * 48u);
+      tma_load_1d(raw0, a.facS + 3LL * t0.sb, (uint32_t)t0.sl * 48u, bar0);
     }
+  }
+  cur = __shfl_sync(FULLM, cur, 0);
+  while (cur < a.n_tiles) {
+    // prefetch the next unit into the other buffer
+    int64_t nxt = 0;
+    if (lane == 0) {
+      nxt = atomicAdd(a.counter, 1);
+      if (nxt < a.n_tiles) {
+        const Tile tn = a.tiles[nxt];
+        fence_proxy_async();
+        uint64_t* bn = b ? bar0 : bar1;
+        mbar_arrive_expect_tx(bn, (uint32_t)tn.sl * 48u);
+        tma_load_1d(b ? raw0 : raw1, a.facS + 3LL * tn.sb, (uint32_t)tn.sl * 48u, bn);
+      }
+    }
+    nxt = __shfl_sync(FULLM, nxt, 0);
+    const Tile tl = a.tiles[cur];
+    const int rl = tl.rl, sl = tl.sl;
     const float4 o4 = a.origin[tl.pair];
-    const int nst = max(1, REFINE_THREADS / rl);
-    const bool active = tid < rl * nst;
-    const int i = active ? tid % rl : 0;
-    const int stripe = active ? tid / rl : 0;
-
-    // r facet -> register record (n, m negated)
+    const bool act = lane < rl;
     Rec<T> P;
-    float rlo[3], rhi[3];
     {
-      const float4* f = a.facR + 3LL * (tl.rb + i);
+      const float4* f = a.facR + 3LL * (tl.rb + (act ? lane : 0));
       float4 A = f[0], B = f[1], C = f[2];
       T va[3], vb[3], vc[3];
       translate(A, o4, va);
       translate(B, o4, vb);
       translate(C, o4, vc);
       make_rec(P, va, vb, vc, T(A.w), T(B.w), true);
-      if (CULL) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          float x0 = float(va[k]), x1 = float(vb[k]), x2 = float(vc[k]);
-          rlo[k] = fminf(x0, fminf(x1, x2));
-          rhi[k] = fmaxf(x0, fmaxf(x1, x2));
-        }
-      }
     }
-
-    if (!mbar_wait_bounded(&bar, phase, MBAR_POLL_LIMIT)) atomicOr(&s_fail, 1);
-    phase ^= 1u;
-    __syncthreads();
-    if (s_fail) {
-      if (tid == 0) set_err(a.err, ERR_MBAR_TIMEOUT);
-      // let the copy in flight land (bounded) before the CTA leaves
-      mbar_wait_bounded(&bar, phase ^ 1u, MBAR_POLL_LIMIT);
+    // wait for this unit's s facets, then expand them into records
+    const bool ok = mbar_wait_bounded(b ? bar1 : bar0, b ? ph1 : ph0, MBAR_POLL_LIMIT);
+    if (__any_sync(FULLM, !ok)) {
+      if (lane == 0) {
+        set_err(a.err, ERR_MBAR_TIMEOUT);
+        // let a prefetch in flight land (bounded) before the warp leaves
+        if (nxt < a.n_tiles) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
+      }
       break;
     }
-
-    // s chunk -> shared records
-    for (int k = tid; k < sl; k += REFINE_THREADS) {
-      float4 A = raw[3 * k], B = raw[3 * k + 1], C = raw[3 * k + 2];
+    if (b) ph1 ^= 1u;
+    else ph0 ^= 1u;
+    const float4* raw = b ? raw1 : raw0;
+    if (lane < sl) {
+      float4 A = raw[3 * lane], B = raw[3 * lane + 1], C = raw[3 * lane + 2];
       T va[3], vb[3], vc[3];
       translate(A, o4, va);
       translate(B, o4, vb);
       translate(C, o4, vc);
       Rec<T> Q;
       make_rec(Q, va, vb, vc, T(A.w), T(B.w), false);
-      store_rec(srec[k], Q);
+      store_rec(rec[lane], Q);
     }
-    if (CULL) {
-      // per 32-facet block: box (pair-local, float) with max ph / hd
-      const int nblk = (sl + 31) / 32;
-      if (warp < nblk) {
-        const int k = 32 * warp + lane;
-        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        float ph = 0.f, hd = 0.f;
-        if (k < sl) {
-          float4 A = raw[3 * k], B = raw[3 * k + 1], C = raw[3 * k + 2];
-          float xa[3] = {A.x - o4.x, A.y - o4.y, A.z - o4.z};
-          float xb[3] = {B.x - o4.x, B.y - o4.y, B.z - o4.z};
-          float xc[3] = {C.x - o4.x, C.y - o4.y, C.z - o4.z};
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            lo[q] = fminf(xa[q], fminf(xb[q], xc[q]));
-            hi[q] = fmaxf(xa[q], fmaxf(xb[q], xc[q]));
-          }
-          ph = B.w;
-          hd = A.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          lo[q] = warp_min(lo[q]);
-          hi[q] = -warp_min(-hi[q]);
-        }
-        ph = -warp_min(-ph);
-        hd = -warp_min(-hd);
-        if (lane == 0) {
-          blk[2 * warp] = make_float4(lo[0], lo[1], lo[2], ph);
-          blk[2 * warp + 1] = make_float4(hi[0], hi[1], hi[2], hd);
-        }
-      }
-    }
-    __syncthreads();
+    __syncwarp();
 
-    // ---- all facet pairs of this thread
-    T lbm = INF, ubu = INF, ubc = INF, d2m = INF;
-    bool anyposs = false, anycert = false;
-    unsigned long long ntest = 0;
-    const T eh = T(tl.eh), ew = T(tl.ew);
-    if (active) {
-      const int nblk = (sl + 31) / 32;
-      const float thr = CULL ? a.thr[tl.pair] : 0.f;
-      const float rph = CULL ? float(P.ph) : 0.f;
-      for (int b = stripe; b < nblk; b += nst) {
-        if (CULL) {
-          float4 blo = blk[2 * b], bhi = blk[2 * b + 1];
-          float4 mlo = make_float4(rlo[0], rlo[1], rlo[2], 0.f), mhi = make_float4(rhi[0], rhi[1], rhi[2], 0.f);
-          float g = box_gap_rd(mlo, mhi, blo, bhi);
-          float lbb = __fsub_rd(__fsub_rd(__fsub_rd(g, rph), blo.w), 2.f * tl.eps);
-          if (lbb > thr) continue;
-        }
-        const int j0 = 32 * b, j1 = min(j0 + 32, sl);
-        ntest += (unsigned long long)(j1 - j0);
-        for (int j = j0; j < j1; ++j) {
-          Rec<T> Q;
-          load_rec(Q, srec[j]);
-          bool maybe;
-          T d2 = tri_d2(P, Q, eh, maybe);
-          if (!maybe) {
-            if (FULL) {
-              d2m = min(d2m, d2);
-            } else {
-              T d = sqrt_test(d2);
-              lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
-              ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
-            }
+    T lbm = INF, ubu = INF, d2m = INF;
+    bool anyposs = false;
+    const T eh = T(tl.eh);
+    if (act) {
+      ntest += (unsigned long long)sl;
+      for (int j = 0; j < sl; ++j) {
+        Rec<T> Q;
+        load_rec(Q, rec[j]);
+        bool maybe;
+        T d2 = tri_d2(P, Q, eh, maybe);
+        if (!maybe) {
+          if (FULL) {
+            d2m = min(d2m, d2);
           } else {
-            // rare: both triangles straddle each other's planes.  The pair is
-            // queued; k_cross_fix decides its meeting test in double
-            // precision and folds its bounds in.  A full queue falls back to
-            // "a crossing is possible" (lower bound 0), which stays valid.
-            unsigned qk = atomicAdd(a.qcount, 1u);
-            if (qk < a.qcap) {
-              a.queue[qk] = make_int4(tl.pair, tl.rb + i, tl.sb + j, __float_as_int(tl.eps));
-            } else if (FULL) {
-              anyposs = true;
-              d2m = min(d2m, d2);
-            } else {
-              T d = sqrt_test(d2);
-              lbm = min(lbm, -add_ru(P.ph, Q.ph));
-              ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
-            }
+            T d = sqrt_test(d2);
+            lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
+            ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
+          }
+        } else {
+          // rare: both triangles straddle each other's planes.  The pair is
+          // queued; k_cross_fix decides its meeting test in double precision
+          // and folds its bounds in.  A full queue falls back to "a crossing
+          // is possible" (lower bound 0), which stays valid.
+          unsigned qk = atomicAdd(a.qcount, 1u);
+          if (qk < a.qcap) {
+            a.queue[qk] = make_int4(tl.pair, tl.rb + lane, tl.sb + j, __float_as_int(tl.eps));
+          } else if (FULL) {
+            anyposs = true;
+            d2m = min(d2m, d2);
+          } else {
+            T d = sqrt_test(d2);
+            lbm = min(lbm, -add_ru(P.ph, Q.ph));
+            ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
           }
         }
       }
     }
-    T lbv, ubv, ucv, midv = INF;
+    T lbv, ubv, midv = INF;
     if (FULL) {
       T d = d2m < INF ? sqrt_rn(d2m) : INF;
-      midv = anycert ? T(0) : d;
+      midv = d;
       lbv = anyposs ? T(0) : d;
       ubv = d;
-      ucv = anycert ? T(0) : INF;
     } else {
       lbv = lbm;
       ubv = ubu;
-      ucv = ubc;
     }
     lbv = warp_min(lbv);
     ubv = warp_min(ubv);
-    ucv = warp_min(ucv);
-    midv = warp_min(midv);
-    unsigned long long nt = warp_sum_u64(ntest);
+    if (FULL) midv = warp_min(midv);
     if (lane == 0) {
-      red[0][warp] = lbv;
-      red[1][warp] = ubv;
-      red[2][warp] = ucv;
-      red[3][warp] = midv;
-      red_n[warp] = nt;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      T L0 = red[0][0], U0 = red[1][0], C0 = red[2][0], M0 = red[3][0];
-      unsigned long long N0 = red_n[0];
-#pragma unroll
-      for (int w = 1; w < REFINE_THREADS / 32; ++w) {
-        L0 = min(L0, red[0][w]);
-        U0 = min(U0, red[1][w]);
-        C0 = min(C0, red[2][w]);
-        M0 = min(M0, red[3][w]);
-        N0 += red_n[w];
-      }
       const T eps = T(tl.eps);
-      T lb = L0 < INF ? sub_rd(L0, eps) : INF;
+      T lb = lbv < INF ? sub_rd(lbv, eps) : INF;
       lb = max(lb, T(0));
-      T ub = U0 < INF ? add_ru(U0, eps) : INF;
-      ub = min(ub, C0);
-      using B = Bits<T>;
-      atomicMin(&((typename B::U*)a.lb)[tl.pair], B::enc(lb));
-      atomicMin(&((typename B::U*)a.ub)[tl.pair], B::enc(ub));
-      if (FULL) atomicMin(&((typename B::U*)a.mid)[tl.pair], B::enc(M0));
-      if (N0) atomicAdd(a.ntests, N0);
+      T ub = ubv < INF ? add_ru(ubv, eps) : INF;
+      using Bt = Bits<T>;
+      if (lb < INF) atomicMin(&((typename Bt::U*)a.lb)[tl.pair], Bt::enc(lb));
+      if (ub < INF) atomicMin(&((typename Bt::U*)a.ub)[tl.pair], Bt::enc(ub));
+      if (FULL && midv < INF) atomicMin(&((typename Bt::U*)a.mid)[tl.pair], Bt::enc(midv));
     }
-    __syncthreads();
+    __syncwarp();   // records of this unit are read; the next unit overwrites them
+    cur = nxt;
+    b ^= 1;
   }
+  ntest = warp_sum_u64(ntest);
+  if (lane == 0 && ntest) atomicAdd(a.ntests, ntest);
 }
 
 // Bounds contribution of the queued straddling facet pairs: the 15-candidate
@@ -560,16 +556,16 @@ __global__ void __launch_bounds__(256) k_cross_fix(RefineArgs a) {
   }
 }
 
-template <class T, bool FULL, bool CULL>
+template <class T, bool FULL>
 static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaStream_t st) {
-  auto kern = k_refine<T, FULL, CULL>;
+  auto kern = k_refine<T, FULL>;
   const size_t smem = refine_smem_bytes<T>();
   PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, REFINE_THREADS, smem));
   if (occ < 1) occ = 1;
   if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
-  int64_t grid = std::min<int64_t>(n_tiles, (int64_t)occ * ctx->sm_count);
+  int64_t grid = std::min<int64_t>((n_tiles + REFINE_WARPS - 1) / REFINE_WARPS, (int64_t)occ * ctx->sm_count);
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
@@ -578,6 +574,16 @@ static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaSt
     k_cross_fix<T, FULL><<<ctx->sm_count * 4, 256, 0, st>>>(args);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
+  }
+}
+
+static void dispatch_refine(pj_ctx* ctx, RefineArgs& a, int64_t n_tiles, const StepSpec& sp, cudaStream_t st) {
+  if (sp.fp64) {
+    if (sp.full) launch_refine<double, true>(ctx, a, n_tiles, st);
+    else launch_refine<double, false>(ctx, a, n_tiles, st);
+  } else {
+    if (sp.full) launch_refine<float, true>(ctx, a, n_tiles, st);
+    else launch_refine<float, false>(ctx, a, n_tiles, st);
   }
 }
 
@@ -592,11 +598,10 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, c
                cudaStream_t st) {
   if (n_tiles == 0) return -1;
   int ev = -1;
-  if (ctx->ev_used + 2 <= 64 && ctx->ev[ctx->ev_used]) {
+  if (ctx->ev_used + 2 <= 60 && ctx->ev[ctx->ev_used]) {
     ev = ctx->ev_used;
     ctx->ev_used += 2;
   }
-  int64_t n = 1;
   RefineArgs a;
   a.tiles = (const Tile*)ctx->ws[WS_TILES].p;
   a.n_tiles = n_tiles;
@@ -615,24 +620,8 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, c
   a.queue = (int4*)ws_get(ctx, WS_MISC2, (size_t)a.qcap * sizeof(int4), st);
   a.qcount = (unsigned*)(ctx->d_counters + 14);
   PJ_CK(cudaMemsetAsync(a.qcount, 0, sizeof(unsigned), st));
-  (void)n;
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
-  if (sp.fp64) {
-    if (sp.full) {
-      if (sp.cull) launch_refine<double, true, false>(ctx, a, n_tiles, st);
-      else launch_refine<double, true, false>(ctx, a, n_tiles, st);
-    } else {
-      launch_refine<double, false, false>(ctx, a, n_tiles, st);
-    }
-  } else {
-    if (sp.full) {
-      if (sp.cull) launch_refine<float, true, true>(ctx, a, n_tiles, st);
-      else launch_refine<float, true, false>(ctx, a, n_tiles, st);
-    } else {
-      if (sp.cull) launch_refine<float, false, true>(ctx, a, n_tiles, st);
-      else launch_refine<float, false, false>(ctx, a, n_tiles, st);
-    }
-  }
+  dispatch_refine(ctx, a, n_tiles, sp, st);
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev + 1], st));
   return ev;
 }
@@ -650,30 +639,14 @@ void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
   PJ_COUNT_LAUNCH;
 }
 
-void count_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                      const PairBufs& b, cudaStream_t st) {
-  if (n == 0) return;
-  const LodData& LR = R->lod[sp.lodR];
-  const LodData& LS = S->lod[sp.lodS];
-  ChunkView cr{LR.chunk, LR.coff, LR.foff}, cs{LS.chunk, LS.coff, LS.foff};
-  int th = 128;
-  k_count_tiles<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.pr, b.ps, b.status, b.lod0, sp.want, sp.step, cr,
-                                                              cs, b.origin, b.thr, sp.cull, sp.fp64, b.tcount);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-}
-
-void emit_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                     const PairBufs& b, cudaStream_t st) {
-  if (n == 0) return;
-  const LodData& LR = R->lod[sp.lodR];
-  const LodData& LS = S->lod[sp.lodS];
-  ChunkView cr{LR.chunk, LR.coff, LR.foff}, cs{LS.chunk, LS.coff, LS.foff};
-  int th = 128;
-  k_emit_tiles<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.pr, b.ps, b.status, b.lod0, sp.want, sp.step, cr,
-                                                             cs, b.origin, b.thr, sp.cull, sp.fp64, b.toff, b.tiles);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
+int64_t build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                         const PairBufs& b, int64_t tiles_cap, cudaStream_t st) {
+  if (n == 0) return 0;
+  const int64_t wcap = work_cap(R, sp, n);
+  if (wcap > b.wcap) throw ApiError{PJ_EINVAL, "work items above the scratch capacity"};
+  Tile* tiles = b.tiles;
+  return build_units(ctx, R, S, n, sp, b.pr, b.ps, b.status, b.lod0, b.origin, b.thr, b.tcount, b.toff, b.wcount,
+                     b.woff, wcap, &tiles, tiles_cap, false, b.scan_tmp, st);
 }
 
 void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st) {
@@ -706,13 +679,7 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_ti
   a.qcap = b.qcap;
   a.qcount = (unsigned*)(b.counters + 2);
   PJ_CK(cudaMemsetAsync(a.qcount, 0, sizeof(unsigned), st));
-  if (sp.fp64) {
-    if (sp.full) launch_refine<double, true, false>(ctx, a, n_tiles, st);
-    else launch_refine<double, false, false>(ctx, a, n_tiles, st);
-  } else {
-    if (sp.full) launch_refine<float, true, false>(ctx, a, n_tiles, st);
-    else launch_refine<float, false, false>(ctx, a, n_tiles, st);
-  }
+  dispatch_refine(ctx, a, n_tiles, sp, st);
 }
 
 // ------------------------------------------------------------------ batch

@@ -24,6 +24,8 @@ namespace {
 constexpr int64_t MAXP = PJ_STATIC_MAX_PAIRS;
 constexpr int64_t MAXT = PJ_STATIC_MAX_TILES;
 constexpr int64_t MAXQ = 65536;   // queued straddling facet pairs
+constexpr int64_t MAXW = 65536;   // (pair, 256-facet chunk of r) work items
+constexpr int64_t SCANW = 64;     // scan temporaries (words), enough for MAXW
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -44,14 +46,17 @@ constexpr size_t OFF_MID = OFF_UB + align256(MAXP * 8);
 constexpr size_t OFF_TCOUNT = OFF_MID + align256(MAXP * 8);
 constexpr size_t OFF_TOFF = OFF_TCOUNT + align256((MAXP + 1) * 8);
 constexpr size_t OFF_TILES = OFF_TOFF + align256((MAXP + 1) * 8);
-constexpr size_t OFF_QUEUE = OFF_TILES + align256(MAXT * sizeof(Tile));
+constexpr size_t OFF_WCOUNT = OFF_TILES + align256(MAXT * sizeof(Tile));
+constexpr size_t OFF_WOFF = OFF_WCOUNT + align256((MAXW + 1) * 8);
+constexpr size_t OFF_SCANTMP = OFF_WOFF + align256((MAXW + 1) * 8);
+constexpr size_t OFF_QUEUE = OFF_SCANTMP + align256(SCANW * 8);
 constexpr size_t OFF_COUNTERS = OFF_QUEUE + align256(MAXQ * sizeof(int4));
 constexpr size_t OFF_ERR = OFF_COUNTERS + 256;
 constexpr size_t SCRATCH_BYTES = OFF_ERR + 256;
 
 }  // namespace
 
-// The scratch itself: about 2.5 MB per device.
+// The scratch itself: about 3.6 MB per device.
 static __device__ __align__(256) unsigned char g_bounds_scratch[SCRATCH_BYTES];
 
 namespace {
@@ -113,11 +118,15 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
                       std::to_string(MAXP) + ")";
     return PJ_EINVAL;
   }
-  // worst-case tile count: every pair of the largest objects at this LoD
-  const int64_t cr = (R->lod[lod].maxF + CHUNK - 1) / CHUNK, cs = (S->lod[lod].maxF + CHUNK - 1) / CHUNK;
-  if (n * cr * cs > MAXT) {
-    ctx->last_error = "pair_bounds_static: up to " + std::to_string(n * cr * cs) +
-                      " tiles needed, above PJ_STATIC_MAX_TILES (" + std::to_string(MAXT) + ")";
+  // worst-case unit count: every block pair of the largest objects at this LoD
+  const int64_t br = (R->lod[lod].maxF + BLK - 1) / BLK, bs = (S->lod[lod].maxF + BLK - 1) / BLK;
+  if (n * br * bs > MAXT) {
+    ctx->last_error = "pair_bounds_static: up to " + std::to_string(n * br * bs) +
+                      " units needed, above PJ_STATIC_MAX_TILES (" + std::to_string(MAXT) + ")";
+    return PJ_EINVAL;
+  }
+  if (n * ((R->lod[lod].maxF + CHUNK - 1) / CHUNK) > MAXW) {
+    ctx->last_error = "pair_bounds_static: too many (pair, 256-facet chunk) work items";
     return PJ_EINVAL;
   }
   if (n == 0) return PJ_OK;
@@ -170,18 +179,13 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     sp.cull = false;
     sp.want = UNDECIDED;
     sp.step = 0;
+    b.wcount = reinterpret_cast<int64_t*>(base + OFF_WCOUNT);
+    b.woff = reinterpret_cast<int64_t*>(base + OFF_WOFF);
+    b.wcap = MAXW;
+    b.scan_tmp = reinterpret_cast<int64_t*>(base + OFF_SCANTMP);
     setup_pairs_bufs(ctx, R, S, n, b, st);
     init_bounds_bufs(ctx, n, sp, b, st);
-    count_tiles_bufs(ctx, R, S, n, sp, b, st);
-    scan_small_i64(ctx, b.tcount, b.toff, n, st);
-    int64_t total = 0;
-    PJ_CK(cudaMemcpyAsync(&total, b.toff + n, 8, cudaMemcpyDeviceToHost, st));
-    PJ_CK(cudaStreamSynchronize(st));
-    if (total > MAXT) {
-      ctx->last_error = "pair_bounds_static: tile list above PJ_STATIC_MAX_TILES";
-      return PJ_EINVAL;
-    }
-    emit_tiles_bufs(ctx, R, S, n, sp, b, st);
+    const int64_t total = build_tiles_bufs(ctx, R, S, n, sp, b, MAXT, st);
     run_refine_bufs(ctx, R, S, total, sp, b, err, st);
     k_bits_out<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, sp.fp64 ? 1 : 0, b.lb, b.ub, lb, ub);
     PJ_CK(cudaGetLastError());
