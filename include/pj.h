@@ -114,8 +114,8 @@ typedef struct {
   double timeout_s;
 } pj_query;
 
-/* Result pairs, library-owned pinned host memory (free with
- * pj_result_free).  within/intersection: ordered by (r, s).  k-NN: for each
+/* Result pairs, library-owned host memory (free with pj_result_free); the
+ * device-to-host copy goes through the context's pinned staging buffer.  within/intersection: ordered by (r, s).  k-NN: for each
  * r in order, min(k, |S|) entries ordered by (d, s).
  *   d_lo <= d(r, s) <= d_hi always holds; d is the best estimate.
  *   exact[i] = 1: d_lo = d = d_hi is the FP64 full-resolution distance;

@@ -398,6 +398,7 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
   PJ_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   PJ_CK(cudaMemset(ctx->d_counters, 0, 16 * sizeof(unsigned long long)));
   for (auto& e : ctx->ev) PJ_CK(cudaEventCreate(&e));
+  PJ_CK(cudaMalloc((void**)&ctx->d_snap, 64 * 4 * sizeof(long long)));
   std::string v = json_str(options_json, "persistent_ctas_per_sm");
   if (!v.empty()) ctx->ctas_per_sm = std::max(0, atoi(v.c_str()));
   ctx->autotune_cache = json_str(options_json, "autotune_cache");
@@ -428,6 +429,8 @@ void pj_destroy(pj_ctx* ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_counters);
   cudaFree(ctx->mlp_w);
+  cudaFree(ctx->d_snap);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -523,7 +526,7 @@ pj_status pj_join(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query*
 
 void pj_result_free(pj_result* res) {
   if (!res) return;
-  if (res->priv) cudaFreeHost(res->priv);
+  free(res->priv);
   memset(res, 0, sizeof(*res));
 }
 
@@ -575,8 +578,9 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
   sp.cull = false;
   sp.want = UNDECIDED;
   sp.step = 0;
+  sp.exact_cross = true;
   init_bounds(ctx, n, sp, st);
-  int64_t nt = build_tiles(ctx, R, S, n, sp, st);
+  UnitCount nt = build_tiles(ctx, R, S, n, sp, st);
   run_refine(ctx, R, S, nt, sp, st);
   std::vector<unsigned char> blo(n * 8), bub(n * 8);
   PJ_CK(cudaMemcpyAsync(blo.data(), ctx->ws[WS_LB].p, n * (sp.fp64 ? 8 : 4), cudaMemcpyDeviceToHost, st));

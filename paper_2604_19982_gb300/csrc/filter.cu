@@ -222,9 +222,20 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   scan_i64(ctx, cnt, off, G.ncell, st);
+  // grid entries bounded on the host (one extra cell per axis absorbs
+  // host/device rounding of the cell index), so no synchronization here
   int64_t nids = 0;
-  PJ_CK(cudaMemcpyAsync(&nids, off + G.ncell, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
+  for (int o = 0; o < S->n; ++o) {
+    const float* b = &S->mbb_h[6 * o];
+    int64_t c = 1;
+    for (int k = 0; k < 3; ++k) {
+      double a0 = std::floor(((double)b[k] - tau - G.g0[k]) * G.inv_h);
+      double a1 = std::floor(((double)b[3 + k] + tau - G.g0[k]) * G.inv_h);
+      int64_t w = (int64_t)std::min<double>(G.dim[k], std::max(1.0, a1 - a0 + 3.0));
+      c *= w;
+    }
+    nids += c;
+  }
   auto ids = (int32_t*)ws_get(ctx, WS_GRIDIDS, std::max<int64_t>(1, nids) * 4, st);
   PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
   k_grid_fill<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, off, cnt, ids);

@@ -92,7 +92,7 @@ struct pj_ctx {
   int ctas_per_sm = 0;             // 0 = from occupancy
   std::string autotune_cache;
   // per-query workspace
-  pj::DevBuf ws[32];
+  pj::DevBuf ws[48];
   // learned proposal (bf16 MLP), float master weights on the device
   float* mlp_w = nullptr;          // packed: W1 64x16, b1 64, W2 64x64, b2 64, W3 64, b3 1
   bool mlp_ready = false;
@@ -103,6 +103,10 @@ struct pj_ctx {
   unsigned long long launches = 0;
   cudaEvent_t ev[64] = {};
   int ev_used = 0;
+  long long* d_snap = nullptr;     // [64][4] per-step counter snapshots
+  // pinned staging of result copies (grow-only)
+  void* h_stage = nullptr;
+  size_t h_stage_cap = 0;
 };
 
 namespace pj {
@@ -120,9 +124,12 @@ constexpr int MLP_W1 = 0, MLP_B1 = MLP_W1 + MLP_H * MLP_IN, MLP_W2 = MLP_B1 + ML
 enum Slot {
   WS_PR, WS_PS, WS_ORIGIN, WS_THR, WS_BOXLB, WS_ANCUB, WS_STATUS, WS_LOD0, WS_LB, WS_UB, WS_MID,
   WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
-  WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5
+  WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5,
+  WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3,
+  WS_COUNT
 };
 
+static_assert(WS_COUNT <= 48, "workspace slots");
 void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st);
 
 // ---- set layout (api.cu)
@@ -157,6 +164,8 @@ static_assert(sizeof(Tile) == 32, "tile is two int4");
 
 struct StepSpec {
   int lodR, lodS;
+  bool early = false;  // units of a pair already proven ub <= threshold are skipped
+  bool exact_cross = false;  // coarse single-precision steps also decide crossings exactly
   bool full;        // both at the original surfaces (hd = ph = 0)
   bool fp64;
   bool cull;        // skip chunk pairs / blocks that cannot reach the threshold
@@ -164,14 +173,20 @@ struct StepSpec {
   int step;         // LoD step index (pairs with lod0 > step wait)
 };
 
-// Count + emit tiles for the pairs in state `want`; returns tile count.
-int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, const StepSpec& sp,
-                    cudaStream_t st);
+// Count + emit refinement units for the pairs in state `want`.  count >= 0:
+// the host knows the number; count < 0: it stays on the device at *dev
+// (the unit buffer was sized for the worst case), nothing was synchronized.
+struct UnitCount {
+  int64_t count;
+  const int64_t* dev;
+};
+UnitCount build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, const StepSpec& sp,
+                      cudaStream_t st);
 // Reset the per-pair lb / ub words of the pairs being refined.
 void init_bounds(pj_ctx* ctx, int64_t n_pairs, const StepSpec& sp, cudaStream_t st);
 // Run the persistent refinement kernel over the built tiles.  Returns the
 // index of the CUDA event pair (ctx->ev) bracketing the launch on `st`, or -1.
-int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, const StepSpec& sp,
                cudaStream_t st);
 // Elapsed milliseconds of an event pair returned by run_refine (0 if -1).
 float refine_ms(pj_ctx* ctx, int ev);
@@ -207,13 +222,14 @@ struct PairBufs {
   unsigned long long* counters;  // [3]: tests, tile counter, straddle-queue count
   int4* queue;                   // straddling facet pairs (see k_cross_fix)
   unsigned qcap;
+  uint8_t* flag;                 // [n] pair proven (early exit), may be null
 };
 void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const PairBufs& b,
                       cudaStream_t st);
-int64_t build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                         const PairBufs& b, int64_t tiles_cap, cudaStream_t st);
+UnitCount build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                           const PairBufs& b, int64_t tiles_cap, cudaStream_t st);
 void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st);
-void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, const StepSpec& sp,
                      const PairBufs& b, int* err, cudaStream_t st);
 // single-block exclusive scan, n <= 4096, no allocation
 void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);

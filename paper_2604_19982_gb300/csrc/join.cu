@@ -140,11 +140,24 @@ __device__ __forceinline__ double load_bound(const void* a, int64_t p) {
 template <bool F64>
 __global__ void k_decide_within(int64_t n, uint8_t* status, const uint8_t* lod0, uint8_t want, int step, int full,
                                 double tau, const void* lb, const void* ub, const void* mid, double* dlo,
-                                double* dhi, double* d, uint8_t* exact, unsigned long long* cnt) {
+                                double* dhi, double* d, uint8_t* exact, unsigned long long* cnt,
+                                const uint8_t* flag, const double* box_lb, const double* anc_ub) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   if (!(status[p] == want && lod0[p] <= step)) return;
   double l = load_bound<F64>(lb, p), u = load_bound<F64>(ub, p);
+  if (flag && flag[p]) {
+    // Some units were skipped, and which ones depends on timing: report a
+    // bracket that does not (box distance .. threshold / anchor distance),
+    // or the exact 0 of a certified crossing.
+    if (u <= 0.0) {
+      l = 0.0;
+      u = 0.0;
+    } else {
+      l = box_lb[p];
+      u = fmin(tau, anc_ub[p]);
+    }
+  }
   if (want == MAKE_EXACT) {
     dlo[p] = l;
     dhi[p] = u;
@@ -157,7 +170,10 @@ __global__ void k_decide_within(int64_t n, uint8_t* status, const uint8_t* lod0,
     status[p] = CONFIRMED;
     dlo[p] = l;
     dhi[p] = u;
-    if (full) {
+    if (full && u == 0.0) {
+      exact[p] = 1;
+      d[p] = 0.0;
+    } else if (full && !(flag && flag[p])) {
       exact[p] = F64 ? 1 : 2;
       d[p] = F64 ? u : load_bound<F64>(mid, p);
     } else {
@@ -180,16 +196,19 @@ void decide_within(pj_ctx* ctx, int64_t n, double tau, const StepSpec& sp, cudaS
   unsigned g = (unsigned)((n + th - 1) / th);
   auto status = (uint8_t*)ctx->ws[WS_STATUS].p;
   auto lod0 = (const uint8_t*)ctx->ws[WS_LOD0].p;
+  const uint8_t* flag = sp.early ? (const uint8_t*)ctx->ws[WS_FLAG].p : nullptr;
+  const double* box_lb = (const double*)ctx->ws[WS_BOXLB].p;
+  const double* anc_ub = (const double*)ctx->ws[WS_ANCUB].p;
   if (sp.fp64)
     k_decide_within<true><<<g, th, 0, st>>>(n, status, lod0, sp.want, sp.step, sp.full, tau, ctx->ws[WS_LB].p,
                                              ctx->ws[WS_UB].p, ctx->ws[WS_MID].p, (double*)ctx->ws[WS_DLO].p,
                                              (double*)ctx->ws[WS_DHI].p, (double*)ctx->ws[WS_D].p,
-                                             (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters);
+                                             (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters, flag, box_lb, anc_ub);
   else
     k_decide_within<false><<<g, th, 0, st>>>(n, status, lod0, sp.want, sp.step, sp.full, tau, ctx->ws[WS_LB].p,
                                               ctx->ws[WS_UB].p, ctx->ws[WS_MID].p, (double*)ctx->ws[WS_DLO].p,
                                               (double*)ctx->ws[WS_DHI].p, (double*)ctx->ws[WS_D].p,
-                                              (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters);
+                                              (uint8_t*)ctx->ws[WS_EXACT].p, ctx->d_counters, flag, box_lb, anc_ub);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
@@ -234,12 +253,13 @@ struct HostResult {
   void* block = nullptr;
 };
 
-// Allocate pinned host arrays for n results inside one block.
+// Host arrays for n results inside one block (pageable; the copy from the
+// device goes through the context's pinned staging buffer).
 void alloc_result(pj_result* res, int64_t n) {
   size_t per = 4 + 4 + 8 + 8 + 8 + 1;
   size_t bytes = std::max<size_t>(64, (size_t)n * per + 64);
-  void* blk = nullptr;
-  PJ_CK(cudaMallocHost(&blk, bytes));
+  void* blk = malloc(bytes);
+  if (!blk) throw ApiError{PJ_ENOMEM, "host allocation of the result failed"};
   char* c = (char*)blk;
   res->n = n;
   res->d_lo = (double*)c;
@@ -256,7 +276,20 @@ void alloc_result(pj_result* res, int64_t n) {
   res->priv = blk;
 }
 
-// Copy the CONFIRMED pairs (in pair order = (r, s) order) to the host.
+static void* stage(pj_ctx* ctx, size_t bytes) {
+  if (ctx->h_stage_cap < bytes) {
+    if (ctx->h_stage) PJ_CK(cudaFreeHost(ctx->h_stage));
+    ctx->h_stage = nullptr;
+    size_t cap = std::max(bytes, ctx->h_stage_cap * 2);
+    PJ_CK(cudaMallocHost(&ctx->h_stage, cap));
+    ctx->h_stage_cap = cap;
+  }
+  return ctx->h_stage;
+}
+
+// Copy the CONFIRMED pairs (in pair order = (r, s) order) to the host: the
+// compacted arrays (capacity n) and their count come back in one copy and
+// one synchronization.
 int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) {
   if (n == 0) {
     alloc_result(res, 0);
@@ -271,28 +304,33 @@ int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) 
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   scan_i64(ctx, flag, off, n, st);
-  int64_t m = 0;
-  PJ_CK(cudaMemcpyAsync(&m, off + n, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
-  alloc_result(res, m);
-  if (m == 0) return 0;
-  size_t per = 4 + 4 + 8 + 8 + 8 + 1;
-  char* dev = (char*)ws_get(ctx, WS_RES, (size_t)m * per + 64, st);
+  const size_t per = 4 + 4 + 8 + 8 + 8 + 1;
+  char* dev = (char*)ws_get(ctx, WS_RES, (size_t)n * per + 64, st);
   ResultPack pk;
   pk.dlo = (double*)dev;
-  pk.dhi = pk.dlo + m;
-  pk.d = pk.dhi + m;
-  pk.r = (int32_t*)(pk.d + m);
-  pk.s = pk.r + m;
-  pk.exact = (uint8_t*)(pk.s + m);
+  pk.dhi = pk.dlo + n;
+  pk.d = pk.dhi + n;
+  pk.r = (int32_t*)(pk.d + n);
+  pk.s = pk.r + n;
+  pk.exact = (uint8_t*)(pk.s + n);
   k_compact<<<g, th, 0, st>>>(n, status, off, (const int32_t*)ctx->ws[WS_PR].p, (const int32_t*)ctx->ws[WS_PS].p,
                               (const double*)ctx->ws[WS_DLO].p, (const double*)ctx->ws[WS_DHI].p,
                               (const double*)ctx->ws[WS_D].p, (const uint8_t*)ctx->ws[WS_EXACT].p, pk);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  // one contiguous copy: the device pack mirrors the host block layout
-  PJ_CK(cudaMemcpyAsync(res->d_lo, dev, (size_t)m * per, cudaMemcpyDeviceToHost, st));
+  char* h = (char*)stage(ctx, (size_t)n * per + 64);
+  PJ_CK(cudaMemcpyAsync(h, dev, (size_t)n * per, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaMemcpyAsync(h + (size_t)n * per, off + n, 8, cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaStreamSynchronize(st));
+  int64_t m = 0;
+  memcpy(&m, h + (size_t)n * per, 8);
+  alloc_result(res, m);
+  memcpy(res->d_lo, h, (size_t)m * 8);
+  memcpy(res->d_hi, h + (size_t)n * 8, (size_t)m * 8);
+  memcpy(res->d, h + (size_t)n * 16, (size_t)m * 8);
+  memcpy(res->r, h + (size_t)n * 24, (size_t)m * 4);
+  memcpy(res->s, h + (size_t)n * 28, (size_t)m * 4);
+  memcpy(res->exact, h + (size_t)n * 32, (size_t)m);
   return m;
 }
 
@@ -304,12 +342,6 @@ struct StepStat {
   double ms;
 };
 
-static unsigned long long read_counter(pj_ctx* ctx, int i, cudaStream_t st) {
-  unsigned long long v = 0;
-  PJ_CK(cudaMemcpyAsync(&v, ctx->d_counters + i, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
-  return v;
-}
 
 pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                       cudaStream_t st, std::string& stats) {
@@ -324,18 +356,22 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   FilterOut fo = filter_within(ctx, R, S, tau, st);
   const int64_t n = fo.n_pairs;
   setup_pairs(ctx, R, S, n, tau, true, st);
-  PJ_CK(cudaStreamSynchronize(st));
   double ms_filter = tf.ms();
   const int Lmax = std::max(R->L, S->L);
-  std::string steps = "[";
   auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
-  int64_t tiles_total = 0;
   ctx->ev_used = 0;
-  unsigned long long prev[2] = {0, 0};
-  double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
+  int evs[PJ_MAX_LODS + 2];
+  int64_t host_units[PJ_MAX_LODS + 2];
+  int nsteps = 0;
+  // per-step snapshot of (units, fp32 tests, fp64 tests) taken on the device
+  auto snapshot = [&](int i, const UnitCount& uc) {
+    long long* d = ctx->d_snap + 4 * i;
+    if (uc.count < 0) PJ_CK(cudaMemcpyAsync(d, uc.dev, 8, cudaMemcpyDeviceToDevice, st));
+    PJ_CK(cudaMemcpyAsync(d + 1, ctx->d_counters, 16, cudaMemcpyDeviceToDevice, st));
+    host_units[i] = uc.count;
+  };
   for (int step = 0; step < Lmax && n > 0; ++step) {
     if (deadline_hit()) return PJ_ETIMEOUT;
-    Timer ts;
     StepSpec sp;
     sp.lodR = std::max(0, step - (Lmax - R->L));
     sp.lodS = std::max(0, step - (Lmax - S->L));
@@ -344,57 +380,38 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     sp.cull = cull;
     sp.want = UNDECIDED;
     sp.step = step;
+    // early exit (with pruning on): coarse steps only report a bracket, and
+    // at full resolution an intersection test's answer is exactly 0
+    sp.early = cull && (!sp.full || tau == 0.0);
     init_bounds(ctx, n, sp, st);
-    int64_t nt = build_tiles(ctx, R, S, n, sp, st);
-    int ev = run_refine(ctx, R, S, nt, sp, st);
+    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
+    evs[nsteps] = run_refine(ctx, R, S, uc, sp, st);
     decide_within(ctx, n, tau, sp, st);
-    unsigned long long cur[2];
-    PJ_CK(cudaMemcpyAsync(cur, ctx->d_counters, sizeof cur, cudaMemcpyDeviceToHost, st));
-    PJ_CK(cudaStreamSynchronize(st));
-    float kms = refine_ms(ctx, ev);
-    (fp64 ? refine_ms_fp64 : refine_ms_fp32) += kms;
-    tiles_total += nt;
-    char buf[256];
-    snprintf(buf, sizeof buf,
-             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tests\":%llu,\"refine_ms\":%.4f,"
-             "\"ms\":%.3f}",
-             step ? "," : "", step, fp64 ? "fp64" : "fp32", sp.full ? 1 : 0, (long long)nt,
-             (cur[0] - prev[0]) + (cur[1] - prev[1]), kms, ts.ms());
-    prev[0] = cur[0];
-    prev[1] = cur[1];
-    steps += buf;
+    snapshot(nsteps++, uc);
   }
-  steps += "]";
-  int64_t n_redecide = 0;
-  double ms_redecide = 0;
   if (!fp64 && n > 0) {
-    Timer tr;
-    n_redecide = (int64_t)read_counter(ctx, 4, st);
-    if (n_redecide > 0) {
-      StepSpec sp;
-      sp.lodR = R->L - 1;
-      sp.lodS = S->L - 1;
-      sp.full = true;
-      sp.fp64 = true;
-      sp.cull = false;
-      sp.want = REDECIDE;
-      sp.step = Lmax - 1;
-      init_bounds(ctx, n, sp, st);
-      int64_t nt = build_tiles(ctx, R, S, n, sp, st);
-      int ev = run_refine(ctx, R, S, nt, sp, st);
-      decide_within(ctx, n, tau, sp, st);
-      PJ_CK(cudaStreamSynchronize(st));
-      refine_ms_fp64 += refine_ms(ctx, ev);
-      tiles_total += nt;
-    }
-    ms_redecide = tr.ms();
+    // pairs whose single-precision bracket still straddles tau at full
+    // resolution (status REDECIDE) are refined again in double precision
+    StepSpec sp;
+    sp.lodR = R->L - 1;
+    sp.lodS = S->L - 1;
+    sp.full = true;
+    sp.fp64 = true;
+    sp.cull = false;
+    sp.want = REDECIDE;
+    sp.step = Lmax - 1;
+    init_bounds(ctx, n, sp, st);
+    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
+    evs[nsteps] = run_refine(ctx, R, S, uc, sp, st);
+    decide_within(ctx, n, tau, sp, st);
+    snapshot(nsteps++, uc);
   }
   if ((q->flags & PJ_EXACT_DIST) && n > 0) {
     int th = 256;
     k_mark_exact<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_STATUS].p,
                                                                (const uint8_t*)ctx->ws[WS_EXACT].p);
     PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
+    PJ_COUNT_LAUNCH;
     StepSpec sp;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
@@ -404,27 +421,50 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     sp.want = MAKE_EXACT;
     sp.step = Lmax - 1;
     init_bounds(ctx, n, sp, st);
-    int64_t nt = build_tiles(ctx, R, S, n, sp, st);
-    run_refine(ctx, R, S, nt, sp, st);
+    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
+    evs[nsteps] = run_refine(ctx, R, S, uc, sp, st);
     decide_within(ctx, n, tau, sp, st);
-    tiles_total += nt;
+    snapshot(nsteps++, uc);
   }
   Timer tg;
   int64_t m = gather_results(ctx, n, out, st);
+  // after the one synchronization of gather_results everything is readable
   int herr = 0;
-  PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   unsigned long long cnt[8];
-  PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
+  PJ_CK(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
+  long long snap[64 * 4];
+  if (nsteps) PJ_CK(cudaMemcpy(snap, ctx->d_snap, sizeof(long long) * 4 * nsteps, cudaMemcpyDeviceToHost));
+  std::string steps = "[";
+  long long prev32 = 0, prev64 = 0;
+  double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
+  int64_t tiles_total = 0;
+  for (int i = 0; i < nsteps; ++i) {
+    const bool s64 = fp64 || i >= Lmax;
+    float kms = refine_ms(ctx, evs[i]);
+    (s64 ? refine_ms_fp64 : refine_ms_fp32) += kms;
+    long long units = host_units[i] >= 0 ? host_units[i] : snap[4 * i];
+    if (evs[i] < 0 && host_units[i] < 0) units = snap[4 * i];
+    tiles_total += units;
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tests\":%lld,\"refine_ms\":%.4f}",
+             i ? "," : "", i, s64 ? "fp64" : "fp32", (i >= Lmax - 1) ? 1 : 0, units,
+             (snap[4 * i + 1] - prev32) + (snap[4 * i + 2] - prev64), kms);
+    prev32 = snap[4 * i + 1];
+    prev64 = snap[4 * i + 2];
+    steps += buf;
+  }
+  steps += "]";
   char buf[900];
   snprintf(buf, sizeof buf,
            "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"candidates\":%lld,\"results\":%lld,"
-           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%lld,"
-           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_redecide\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
+           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%llu,"
+           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
-           tau, fp64 ? "fp64" : "fp32", (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3],
-           (long long)n_redecide, (long long)tiles_total, ms_filter, ms_redecide, tg.ms(), tall.ms(),
-           refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
+           tau, fp64 ? "fp64" : "fp32", (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], cnt[4],
+           (long long)tiles_total, ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64,
+           ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;

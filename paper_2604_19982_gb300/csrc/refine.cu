@@ -162,8 +162,12 @@ __global__ void k_rchunks(int64_t n, const int32_t* pr, const uint8_t* status, c
 template <bool EMIT>
 __global__ void k_units(int64_t n, const int32_t* pr, const int32_t* ps, const int64_t* off1, BoxView R, BoxView S,
                         const float4* origin, const float* thr, int cull, int fp64, int64_t* cnt2,
-                        const int64_t* off2, Tile* tiles) {
+                        const int64_t* off2, Tile* tiles, int64_t wcap) {
   const int64_t W = off1[n];
+  if (!EMIT)  // entries past the live work items count zero units
+    for (int64_t w = W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w <= wcap;
+         w += (int64_t)gridDim.x * blockDim.x)
+      cnt2[w] = 0;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < W; w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = find_pair(off1, n, w);
     const int r = pr[p], s = ps[p];
@@ -217,11 +221,13 @@ __global__ void k_units(int64_t n, const int32_t* pr, const int32_t* ps, const i
 static BoxView box_view(const LodData& L) { return BoxView{L.chunk, L.coff, L.blk, L.boff, L.foff}; }
 
 // Shared by the workspace path and the explicit-buffer path.
-static int64_t build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                           const int32_t* pr, const int32_t* ps, const uint8_t* status, const uint8_t* lod0,
-                           const float4* origin, const float* thr, int64_t* cnt1, int64_t* off1, int64_t* cnt2,
-                           int64_t* off2, int64_t wcap, Tile** tiles_io, int64_t tiles_cap, bool grow,
-                           int64_t* scan_tmp, cudaStream_t st) {
+constexpr size_t UNIT_BUDGET_BYTES = size_t(512) << 20;
+
+static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                             const int32_t* pr, const int32_t* ps, const uint8_t* status, const uint8_t* lod0,
+                             const float4* origin, const float* thr, int64_t* cnt1, int64_t* off1, int64_t* cnt2,
+                             int64_t* off2, int64_t wcap, Tile** tiles_io, int64_t tiles_cap, bool grow,
+                             int64_t* scan_tmp, cudaStream_t st) {
   const LodData& LR = R->lod[sp.lodR];
   const LodData& LS = S->lod[sp.lodS];
   BoxView vr = box_view(LR), vs = box_view(LS);
@@ -231,26 +237,31 @@ static int64_t build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_
   PJ_COUNT_LAUNCH;
   scan_i64(ctx, cnt1, off1, n, st, scan_tmp);
   unsigned g = (unsigned)std::min<int64_t>((wcap + th - 1) / th + 1, (int64_t)ctx->sm_count * 32);
-  k_units<false><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, cnt2, nullptr, nullptr);
+  k_units<false><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, cnt2, nullptr, nullptr,
+                                   wcap);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  int64_t W = 0;
-  PJ_CK(cudaMemcpyAsync(&W, off1 + n, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
-  if (W == 0) return 0;
-  scan_i64(ctx, cnt2, off2, W, st, scan_tmp);
-  int64_t total = 0;
-  PJ_CK(cudaMemcpyAsync(&total, off2 + W, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
-  if (total == 0) return 0;
-  if (total > tiles_cap) {
-    if (!grow) throw ApiError{PJ_EINVAL, "refinement units above the scratch capacity"};
-    *tiles_io = (Tile*)ws_get(ctx, WS_TILES, total * sizeof(Tile), st);
+  scan_i64(ctx, cnt2, off2, wcap, st, scan_tmp);   // off2[wcap] = number of units
+  const int64_t worst = n * ((LR.maxF + BLK - 1) / BLK) * ((LS.maxF + BLK - 1) / BLK);
+  UnitCount uc{-1, off2 + wcap};
+  if (worst <= tiles_cap || (grow && (size_t)worst * sizeof(Tile) <= UNIT_BUDGET_BYTES)) {
+    if (worst > tiles_cap) *tiles_io = (Tile*)ws_get(ctx, WS_TILES, worst * sizeof(Tile), st);
+  } else {
+    int64_t total = 0;
+    PJ_CK(cudaMemcpyAsync(&total, off2 + wcap, 8, cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaStreamSynchronize(st));
+    uc.count = total;
+    if (total == 0) return uc;
+    if (total > tiles_cap) {
+      if (!grow) throw ApiError{PJ_EINVAL, "refinement units above the scratch capacity"};
+      *tiles_io = (Tile*)ws_get(ctx, WS_TILES, total * sizeof(Tile), st);
+    }
   }
-  k_units<true><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, nullptr, off2, *tiles_io);
+  k_units<true><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, nullptr, off2, *tiles_io,
+                                  wcap);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  return total;
+  return uc;
 }
 
 static int64_t work_cap(const pj_set* R, const StepSpec& sp, int64_t n) {
@@ -258,9 +269,9 @@ static int64_t work_cap(const pj_set* R, const StepSpec& sp, int64_t n) {
   return n * std::max<int64_t>(1, (LR.maxF + CHUNK - 1) / CHUNK);
 }
 
-int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                    cudaStream_t st) {
-  if (n == 0) return 0;
+UnitCount build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                      cudaStream_t st) {
+  if (n == 0) return UnitCount{0, nullptr};
   auto pr = (int32_t*)ws_get(ctx, WS_PR, n * 4, st);
   auto ps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);
   auto status = (uint8_t*)ws_get(ctx, WS_STATUS, n, st);
@@ -272,17 +283,19 @@ int64_t build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, co
   auto off1 = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
   auto cnt2 = (int64_t*)ws_get(ctx, WS_MISC3, (wcap + 1) * 8, st);
   auto off2 = (int64_t*)ws_get(ctx, WS_MISC4, (wcap + 1) * 8, st);
+  auto tmp = (int64_t*)ws_get(ctx, WS_MISC5, (scan_tmp_words(wcap + 1) + scan_tmp_words(n) + 8) * 8, st);
   Tile* tiles = (Tile*)ctx->ws[WS_TILES].p;
   const int64_t cap = (int64_t)(ctx->ws[WS_TILES].cap / sizeof(Tile));
   return build_units(ctx, R, S, n, sp, pr, ps, status, lod0, origin, thr, cnt1, off1, cnt2, off2, wcap, &tiles, cap,
-                     true, nullptr, st);
+                     true, tmp, st);
 }
 
 __global__ void k_init_bounds(int64_t n, const uint8_t* status, const uint8_t* lod0, uint8_t want, int step,
-                              int fp64, void* lb, void* ub, void* mid) {
+                              int fp64, void* lb, void* ub, void* mid, uint8_t* flag) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   if (!(status[p] == want && lod0[p] <= step)) return;
+  if (flag) flag[p] = 0;
   if (fp64) {
     const unsigned long long inf = 0x7ff0000000000000ULL;
     ((unsigned long long*)lb)[p] = inf;
@@ -303,9 +316,10 @@ void init_bounds(pj_ctx* ctx, int64_t n, const StepSpec& sp, cudaStream_t st) {
   auto lb = ws_get(ctx, WS_LB, n * 8, st);
   auto ub = ws_get(ctx, WS_UB, n * 8, st);
   auto mid = ws_get(ctx, WS_MID, n * 8, st);
+  auto flag = (uint8_t*)ws_get(ctx, WS_FLAG, n, st);
   int th = 256;
   k_init_bounds<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, status, lod0, sp.want, sp.step, sp.fp64, lb,
-                                                               ub, mid);
+                                                               ub, mid, flag);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
@@ -315,6 +329,7 @@ void init_bounds(pj_ctx* ctx, int64_t n, const StepSpec& sp, cudaStream_t st) {
 struct RefineArgs {
   const Tile* tiles;
   int64_t n_tiles;
+  const int64_t* n_tiles_dev;   // if set, the unit count lives here
   int* counter;
   const float4* facR;
   const float4* facS;
@@ -328,6 +343,9 @@ struct RefineArgs {
   int4* queue;       // straddling facet pairs: (pair, r facet, s facet, eps bits)
   unsigned* qcount;
   unsigned qcap;
+  uint8_t* flag;     // per pair: a unit proved ub <= threshold (early exit)
+  int early;         // skip the units of flagged pairs
+  int exact_cross;   // decide every straddling pair's meeting test (bounds entry points)
 };
 
 template <class T>
@@ -340,13 +358,55 @@ __device__ __forceinline__ void translate(const float4& A, const float4& o, T ou
 constexpr uint32_t MBAR_POLL_LIMIT = 1u << 20;
 constexpr int REFINE_WARPS = REFINE_THREADS / 32;
 
+constexpr int WARP_LIST = 128;   // straddling facet pairs kept per warp and unit
+
 template <class T>
 constexpr size_t warp_smem_bytes() {
-  return (size_t)2 * BLK * 48 + (size_t)BLK * sizeof(RecSmem<T>);
+  return (size_t)2 * BLK * 48 + (size_t)BLK * sizeof(RecSmem<T>) + (size_t)WARP_LIST * 8;
 }
 template <class T>
 constexpr size_t refine_smem_bytes() {
   return REFINE_WARPS * warp_smem_bytes<T>();
+}
+
+template <class T>
+struct ListOut {
+  T lbm, ubu, ubc, d2m;
+  bool anyposs;
+};
+
+// Contributions of the straddling facet pairs a warp listed during one
+// unit: lane k takes entries k, k+32, ...; the meeting test is decided in
+// double precision (cross_exact64).  Out of line so that its double-precision
+// registers do not weigh on the unit's inner loop; called only when the
+// warp's list is non-empty.
+template <class T, bool FULL>
+__device__ __noinline__ ListOut<T> process_list(const uint2* list, unsigned nl, int lane, const float4* fr0,
+                                                const float4* raw, float4 o4) {
+  const T INF = inf_(T(0));
+  ListOut<T> out{INF, INF, INF, INF, false};
+  for (unsigned k = lane; k < nl; k += 32) {
+    const uint2 e = list[k];
+    const int li = e.x & 255, lj = e.x >> 8;
+    const float4* fr = fr0 + 3 * li;
+    const bool cert = cross_exact64(fr, raw + 3 * lj, o4);
+    const T phs = add_ru(T(fr[1].w), T(raw[3 * lj + 1].w)), hds = add_ru(T(fr[0].w), T(raw[3 * lj].w));
+    if (cert) {
+      out.lbm = min(out.lbm, -phs);
+      out.ubc = min(out.ubc, hds);
+      if (FULL) out.anyposs = true;
+    } else {
+      const T d2e = T(__uint_as_float(e.y));
+      if (FULL) {
+        out.d2m = min(out.d2m, d2e);
+      } else {
+        T d = sqrt_test(d2e);
+        out.lbm = min(out.lbm, sub_rd(d, phs));
+        out.ubu = min(out.ubu, add_ru(d, hds));
+      }
+    }
+  }
+  return out;
 }
 
 // Persistent, warp-granular refinement: every warp takes units from a global
@@ -363,16 +423,20 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
   float4* raw0 = reinterpret_cast<float4*>(wbase);
   float4* raw1 = raw0 + 3 * BLK;
   RecSmem<T>* rec = reinterpret_cast<RecSmem<T>*>(wbase + 2 * BLK * 48);
+  uint2* list = reinterpret_cast<uint2*>(wbase + 2 * BLK * 48 + BLK * sizeof(RecSmem<T>));
+  __shared__ unsigned list_n[REFINE_WARPS];
   uint64_t* bar0 = &bars[warp][0];
   uint64_t* bar1 = &bars[warp][1];
   if (lane == 0) {
     mbar_init(bar0, 1);
     mbar_init(bar1, 1);
     fence_mbar_init();
+    list_n[warp] = 0;
   }
   __syncwarp();
   const T INF = inf_(T(0));
   const unsigned FULLM = 0xffffffffu;
+  const int64_t NT = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
   uint32_t ph0 = 0, ph1 = 0;
   int b = 0;
   unsigned long long ntest = 0;
@@ -380,19 +444,19 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
   int64_t cur = 0;
   if (lane == 0) {
     cur = atomicAdd(a.counter, 1);
-    if (cur < a.n_tiles) {
+    if (cur < NT) {
       const Tile t0 = a.tiles[cur];
       mbar_arrive_expect_tx(bar0, (uint32_t)t0.sl * 48u);
       tma_load_1d(raw0, a.facS + 3LL * t0.sb, (uint32_t)t0.sl * 48u, bar0);
     }
   }
   cur = __shfl_sync(FULLM, cur, 0);
-  while (cur < a.n_tiles) {
+  while (cur < NT) {
     // prefetch the next unit into the other buffer
     int64_t nxt = 0;
     if (lane == 0) {
       nxt = atomicAdd(a.counter, 1);
-      if (nxt < a.n_tiles) {
+      if (nxt < NT) {
         const Tile tn = a.tiles[nxt];
         fence_proxy_async();
         uint64_t* bn = b ? bar0 : bar1;
@@ -421,13 +485,19 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
       if (lane == 0) {
         set_err(a.err, ERR_MBAR_TIMEOUT);
         // let a prefetch in flight land (bounded) before the warp leaves
-        if (nxt < a.n_tiles) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
+        if (nxt < NT) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
       }
       break;
     }
     if (b) ph1 ^= 1u;
     else ph0 ^= 1u;
     const float4* raw = b ? raw1 : raw0;
+    if (a.early && __ldcg(a.flag + tl.pair)) {   // the pair is already decided
+      __syncwarp();
+      cur = nxt;
+      b ^= 1;
+      continue;
+    }
     if (lane < sl) {
       float4 A = raw[3 * lane], B = raw[3 * lane + 1], C = raw[3 * lane + 2];
       T va[3], vb[3], vc[3];
@@ -450,6 +520,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
         load_rec(Q, rec[j]);
         bool maybe;
         T d2 = tri_d2(P, Q, eh, maybe);
+        if (maybe && boxes_apart(P, Q)) maybe = false;   // straddling planes, but apart
         if (!maybe) {
           if (FULL) {
             d2m = min(d2m, d2);
@@ -458,29 +529,53 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
             lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
             ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
           }
+        } else if (!FULL && sizeof(T) == 4 && !a.exact_cross) {
+          // coarse LoD: a crossing is taken as possible (lower term -ph-ph,
+          // upper term d+hd+hd); both stay valid and are only ~d looser
+          T d = sqrt_test(d2);
+          lbm = min(lbm, -add_ru(P.ph, Q.ph));
+          ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
         } else {
-          // rare: both triangles straddle each other's planes.  The pair is
-          // queued; k_cross_fix decides its meeting test in double precision
-          // and folds its bounds in.  A full queue falls back to "a crossing
-          // is possible" (lower bound 0), which stays valid.
-          unsigned qk = atomicAdd(a.qcount, 1u);
-          if (qk < a.qcap) {
-            a.queue[qk] = make_int4(tl.pair, tl.rb + lane, tl.sb + j, __float_as_int(tl.eps));
-          } else if (FULL) {
-            anyposs = true;
-            d2m = min(d2m, d2);
+          // rare at full resolution: both triangles straddle each other's
+          // planes; decided after the loop (warp list), or by k_cross_fix
+          // when the list is full
+          unsigned li = atomicAdd(&list_n[warp], 1u);
+          if (li < WARP_LIST) {
+            list[li] = make_uint2((unsigned)(lane | (j << 8)), __float_as_uint((float)d2));
           } else {
-            T d = sqrt_test(d2);
-            lbm = min(lbm, -add_ru(P.ph, Q.ph));
-            ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
+            unsigned qk = atomicAdd(a.qcount, 1u);
+            if (qk < a.qcap) {
+              a.queue[qk] = make_int4(tl.pair, tl.rb + lane, tl.sb + j, __float_as_int(tl.eps));
+            } else if (FULL) {
+              anyposs = true;   // a crossing is possible: lower bound 0 stays valid
+              d2m = min(d2m, d2);
+            } else {
+              T d = sqrt_test(d2);
+              lbm = min(lbm, -add_ru(P.ph, Q.ph));
+              ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
+            }
           }
         }
       }
     }
+    // the warp's straddling pairs: meeting test in double precision
+    __syncwarp();
+    const unsigned nl = min(list_n[warp], (unsigned)WARP_LIST);
+    T ubc = INF;
+    if (nl) {
+      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, a.facR + 3LL * tl.rb, raw, o4);
+      lbm = min(lbm, lo.lbm);
+      ubu = min(ubu, lo.ubu);
+      ubc = lo.ubc;
+      d2m = min(d2m, lo.d2m);
+      anyposs = anyposs || lo.anyposs;
+    }
+    __syncwarp();
+    if (lane == 0) list_n[warp] = 0;
     T lbv, ubv, midv = INF;
     if (FULL) {
       T d = d2m < INF ? sqrt_rn(d2m) : INF;
-      midv = d;
+      midv = ubc < INF ? T(0) : d;
       lbv = anyposs ? T(0) : d;
       ubv = d;
     } else {
@@ -489,16 +584,19 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     }
     lbv = warp_min(lbv);
     ubv = warp_min(ubv);
+    ubc = warp_min(ubc);
     if (FULL) midv = warp_min(midv);
     if (lane == 0) {
       const T eps = T(tl.eps);
       T lb = lbv < INF ? sub_rd(lbv, eps) : INF;
       lb = max(lb, T(0));
       T ub = ubv < INF ? add_ru(ubv, eps) : INF;
+      ub = min(ub, ubc);
       using Bt = Bits<T>;
       if (lb < INF) atomicMin(&((typename Bt::U*)a.lb)[tl.pair], Bt::enc(lb));
       if (ub < INF) atomicMin(&((typename Bt::U*)a.ub)[tl.pair], Bt::enc(ub));
       if (FULL && midv < INF) atomicMin(&((typename Bt::U*)a.mid)[tl.pair], Bt::enc(midv));
+      if (a.early && ub <= a.thr[tl.pair]) a.flag[tl.pair] = 1;
     }
     __syncwarp();   // records of this unit are read; the next unit overwrites them
     cur = nxt;
@@ -565,7 +663,8 @@ static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaSt
   PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, REFINE_THREADS, smem));
   if (occ < 1) occ = 1;
   if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
-  int64_t grid = std::min<int64_t>((n_tiles + REFINE_WARPS - 1) / REFINE_WARPS, (int64_t)occ * ctx->sm_count);
+  int64_t grid = (int64_t)occ * ctx->sm_count;
+  if (n_tiles >= 0) grid = std::min<int64_t>((n_tiles + REFINE_WARPS - 1) / REFINE_WARPS, grid);
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
@@ -594,8 +693,9 @@ float refine_ms(pj_ctx* ctx, int ev) {
   return ms;
 }
 
-int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, const StepSpec& sp,
                cudaStream_t st) {
+  const int64_t n_tiles = units.count;
   if (n_tiles == 0) return -1;
   int ev = -1;
   if (ctx->ev_used + 2 <= 60 && ctx->ev[ctx->ev_used]) {
@@ -605,6 +705,7 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, c
   RefineArgs a;
   a.tiles = (const Tile*)ctx->ws[WS_TILES].p;
   a.n_tiles = n_tiles;
+  a.n_tiles_dev = n_tiles < 0 ? units.dev : nullptr;
   a.counter = (int*)(ctx->d_counters + 15);
   PJ_CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
   a.facR = R->lod[sp.lodR].fac;
@@ -620,6 +721,9 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, c
   a.queue = (int4*)ws_get(ctx, WS_MISC2, (size_t)a.qcap * sizeof(int4), st);
   a.qcount = (unsigned*)(ctx->d_counters + 14);
   PJ_CK(cudaMemsetAsync(a.qcount, 0, sizeof(unsigned), st));
+  a.flag = (uint8_t*)ctx->ws[WS_FLAG].p;
+  a.early = sp.early ? 1 : 0;
+  a.exact_cross = sp.exact_cross ? 1 : 0;
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
   dispatch_refine(ctx, a, n_tiles, sp, st);
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev + 1], st));
@@ -639,9 +743,9 @@ void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
   PJ_COUNT_LAUNCH;
 }
 
-int64_t build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
-                         const PairBufs& b, int64_t tiles_cap, cudaStream_t st) {
-  if (n == 0) return 0;
+UnitCount build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
+                           const PairBufs& b, int64_t tiles_cap, cudaStream_t st) {
+  if (n == 0) return UnitCount{0, nullptr};
   const int64_t wcap = work_cap(R, sp, n);
   if (wcap > b.wcap) throw ApiError{PJ_EINVAL, "work items above the scratch capacity"};
   Tile* tiles = b.tiles;
@@ -653,17 +757,19 @@ void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs
   if (n == 0) return;
   int th = 256;
   k_init_bounds<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.status, b.lod0, sp.want, sp.step, sp.fp64, b.lb,
-                                                               b.ub, b.mid);
+                                                               b.ub, b.mid, b.flag);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
 
-void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_tiles, const StepSpec& sp,
+void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, const StepSpec& sp,
                      const PairBufs& b, int* err, cudaStream_t st) {
+  const int64_t n_tiles = units.count;
   if (n_tiles == 0) return;
   RefineArgs a;
   a.tiles = b.tiles;
   a.n_tiles = n_tiles;
+  a.n_tiles_dev = n_tiles < 0 ? units.dev : nullptr;
   a.counter = (int*)(b.counters + 1);
   PJ_CK(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
   a.facR = R->lod[sp.lodR].fac;
@@ -679,6 +785,9 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_ti
   a.qcap = b.qcap;
   a.qcount = (unsigned*)(b.counters + 2);
   PJ_CK(cudaMemsetAsync(a.qcount, 0, sizeof(unsigned), st));
+  a.flag = b.flag;
+  a.early = 0;
+  a.exact_cross = sp.exact_cross ? 1 : 0;
   dispatch_refine(ctx, a, n_tiles, sp, st);
 }
 

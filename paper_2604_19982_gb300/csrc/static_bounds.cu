@@ -170,6 +170,7 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     b.tiles = reinterpret_cast<Tile*>(base + OFF_TILES);
     b.counters = reinterpret_cast<unsigned long long*>(base + OFF_COUNTERS);
     b.queue = reinterpret_cast<int4*>(base + OFF_QUEUE);
+    b.flag = nullptr;
     b.qcap = (unsigned)MAXQ;
     StepSpec sp;
     sp.lodR = lod;
@@ -179,13 +180,14 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     sp.cull = false;
     sp.want = UNDECIDED;
     sp.step = 0;
+    sp.exact_cross = true;
     b.wcount = reinterpret_cast<int64_t*>(base + OFF_WCOUNT);
     b.woff = reinterpret_cast<int64_t*>(base + OFF_WOFF);
     b.wcap = MAXW;
     b.scan_tmp = reinterpret_cast<int64_t*>(base + OFF_SCANTMP);
     setup_pairs_bufs(ctx, R, S, n, b, st);
     init_bounds_bufs(ctx, n, sp, b, st);
-    const int64_t total = build_tiles_bufs(ctx, R, S, n, sp, b, MAXT, st);
+    const UnitCount total = build_tiles_bufs(ctx, R, S, n, sp, b, MAXT, st);
     run_refine_bufs(ctx, R, S, total, sp, b, err, st);
     k_bits_out<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, sp.fp64 ? 1 : 0, b.lb, b.ub, lb, ub);
     PJ_CK(cudaGetLastError());

@@ -272,6 +272,21 @@ __device__ __forceinline__ T tri_d2(const Rec<T>& P, const Rec<T>& Q, T eh, bool
   return d2;
 }
 
+// Are the boxes of the two facets strictly apart on some axis?  Then they
+// cannot meet.  Rounding of the pair-local translation is monotone, so a
+// strict separation of the computed coordinates implies one of the exact.
+template <class T>
+__device__ __forceinline__ bool boxes_apart(const Rec<T>& P, const Rec<T>& Q) {
+  bool apart = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T pmin = min(P.v[0][k], min(P.v[1][k], P.v[2][k])), pmax = max(P.v[0][k], max(P.v[1][k], P.v[2][k]));
+    T qmin = min(Q.v[0][k], min(Q.v[1][k], Q.v[2][k])), qmax = max(Q.v[0][k], max(Q.v[1][k], Q.v[2][k]));
+    apart = apart || (pmax < qmin) || (qmax < pmin);
+  }
+  return apart;
+}
+
 // Crossing decision in double precision from raw float vertices (the three
 // float4 of each facet, .w ignored) and a float origin: differences of
 // floats are exact in double, so this is the FP64 path's test, used by the
@@ -287,7 +302,7 @@ __device__ __forceinline__ double orient64(const double a[3], const double b[3],
   return x0 * (y1 * z2 - y2 * z1) + x1 * (y2 * z0 - y0 * z2) + x2 * (y0 * z1 - y1 * z0);
 }
 
-static __device__ __noinline__ bool cross_exact64(const float4* fp, const float4* fq, float4 o) {
+static __device__ __forceinline__ bool cross_exact64(const float4* fp, const float4* fq, float4 o) {
   double P[3][3], Q[3][3];
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
