@@ -234,6 +234,11 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount un
 // single-block exclusive scan, n <= 4096, no allocation
 void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
 
+// ---- results (join.cu)
+void alloc_result(pj_result* res, int64_t n);
+int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st);
+void mark_exact(pj_ctx* ctx, int64_t n, cudaStream_t st);
+
 // ---- decide (join.cu)
 void decide_within(pj_ctx* ctx, int64_t n_pairs, double tau, const StepSpec& sp, cudaStream_t st);
 

@@ -219,6 +219,14 @@ __global__ void k_mark_exact(int64_t n, uint8_t* status, const uint8_t* exact) {
   if (status[p] == CONFIRMED && exact[p] != 1) status[p] = MAKE_EXACT;
 }
 
+void mark_exact(pj_ctx* ctx, int64_t n, cudaStream_t st) {
+  int th = 256;
+  k_mark_exact<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_STATUS].p,
+                                                             (const uint8_t*)ctx->ws[WS_EXACT].p);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
 // ------------------------------------------------------------------ results
 
 __global__ void k_flag_status(int64_t n, const uint8_t* status, uint8_t want, int64_t* flag) {

@@ -5,11 +5,6 @@
 
 namespace pj {
 
-pj_status join_knn(pj_ctx* ctx, const pj_set*, const pj_set*, const pj_query*, pj_result*, cudaStream_t,
-                   std::string&) {
-  ctx->last_error = "k-NN join not built yet";
-  return PJ_EINVAL;
-}
 pj_status join_streamed(pj_ctx* ctx, const pj_set*, const pj_set*, const pj_query*, pj_result*, cudaStream_t,
                         std::string&) {
   ctx->last_error = "streamed join not built yet";
