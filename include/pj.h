@@ -182,9 +182,30 @@ pj_status pj_get_stats(const pj_ctx* ctx, char* json_buf, size_t cap);
  * never changes a result.
  * ------------------------------------------------------------------ */
 
+/* With PJ_USE_MLP a join first predicts y = log(1 + d) for every candidate
+ * pair.  k-NN: each step's first wave (the k candidates of every r refined
+ * before the rest, section 3.4) is picked by smallest prediction at the
+ * coarsest step, by bracket midpoint after that.  within-tau / intersection:
+ * a pair starts at the coarsest step whose per-object Hausdorff terms w_l
+ * (max hd + max ph of r plus those of s at that LoD) satisfy
+ * max |x - tau| >= 0.5 * w_l over x in [expm1(y - 0.15), expm1(y + 0.15)],
+ * else at full resolution.  The join fails with PJ_EINVAL if no weights
+ * were trained, fitted or loaded. */
+
+/* Fit the proposal to a workload: run q's candidate filter on R x S, take a
+ * seeded sample of at most max_pairs candidates, label them with their
+ * full-resolution distances (the refinement kernel), and train fresh weights
+ * for `epochs` passes (Adam, mini-batches of 2048) on 90 % of them.  *rmse
+ * (may be NULL) receives the prediction error in log(1 + d) on the other
+ * 10 %.  PJ_EINVAL if q is malformed, max_pairs < 16, or the filter yields
+ * fewer than 16 candidates. */
+pj_status pj_mlp_fit(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, int64_t max_pairs,
+                     int epochs, uint64_t seed, double* rmse);
+
 /* Train on n examples: feats HOST float32 [n][16], target HOST float32 [n]
- * (log(1 + d)).  Mini-batch SGD with momentum, `epochs` passes, shuffled
- * with `seed`; forward and backward run in the library's kernels. */
+ * (log(1 + d)).  Adam over shuffled mini-batches of 2048, `epochs` passes,
+ * shuffled with `seed`; forward and backward run in the library's kernels.
+ * Continues from the current weights (He-initialized from `seed` if none). */
 pj_status pj_mlp_train(pj_ctx* ctx, const float* feats, const float* target, int64_t n, int epochs,
                        uint64_t seed);
 pj_status pj_mlp_save(const pj_ctx* ctx, const char* path);

@@ -13,7 +13,11 @@
 namespace pj {
 
 // Pair status codes (per candidate object pair).
-enum : uint8_t { UNDECIDED = 0, CONFIRMED = 1, REMOVED = 2, REDECIDE = 3 };
+// MAKE_EXACT (4): a result pair queued for its FP64 distance; WAVE (5): a
+// k-NN candidate in the current step's first wave.
+enum : uint8_t { UNDECIDED = 0, CONFIRMED = 1, REMOVED = 2, REDECIDE = 3, MAKE_EXACT = 4, WAVE = 5 };
+// lod0 gate value that admits every pair (passes after the LoD loop).
+constexpr int STEP_ALL = 255;
 
 struct CudaError {
   cudaError_t e;
@@ -190,6 +194,20 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
                cudaStream_t st);
 // Elapsed milliseconds of an event pair returned by run_refine (0 if -1).
 float refine_ms(pj_ctx* ctx, int ev);
+// Per-step record of a join: units, tests and refinement time of every
+// refinement launch, read back once after the join's final synchronization.
+struct StepLog {
+  static constexpr int MAX = 16;
+  int n = 0;
+  int ev[MAX];
+  int64_t units[MAX];
+  bool f64[MAX];
+  bool full[MAX];
+  // Record one refinement step (after run_refine on `st`).
+  void add(pj_ctx* ctx, const UnitCount& uc, int event, const StepSpec& sp, cudaStream_t st);
+  // JSON array of the steps; also sums refinement ms per precision and units.
+  std::string json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total) const;
+};
 // Pair-setup: origin (pair-local frame), box MINDIST, anchor distance.
 void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, double tau, bool within,
                  cudaStream_t st);
@@ -247,14 +265,18 @@ void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool
                     double* err, cudaStream_t st);
 
 // ---- kNN (knn.cu)
-void knn_prune(pj_ctx* ctx, int64_t n_r, int k, int64_t n_pairs, bool full, bool fp64, cudaStream_t st);
-void knn_theta(pj_ctx* ctx, int64_t n_r, int k, cudaStream_t st);
 
 // ---- MLP (mlp.cu)
 void mlp_forward(pj_ctx* ctx, const float* feats, int64_t n, float* out, cudaStream_t st);
-void mlp_grad(pj_ctx* ctx, const float* w, const float* feats, const float* target, int64_t n, float* loss,
-              float* grad, cudaStream_t st);
-void mlp_sgd(pj_ctx* ctx, float* w, float* mom, const float* grad, float lr, float beta, cudaStream_t st);
+// Predicted log1p(d) of the candidate pairs in WS_PR / WS_PS (into WS_PRED).
+const float* propose(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, cudaStream_t st);
+// lod0 of the undecided pairs from the predictions (within-tau start LoD).
+void start_lod(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const float* pred, double tau,
+               cudaStream_t st);
+// start LoD rule: the band half-width of a prediction in log1p units and the
+// fraction of the Hausdorff terms a distance gap must reach
+constexpr float PRED_BAND = 0.15f;
+constexpr float START_MARGIN = 0.5f;
 void pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
                    int64_t n, float* out, cudaStream_t st);
 

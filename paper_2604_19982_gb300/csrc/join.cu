@@ -125,7 +125,6 @@ void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cud
 
 // ------------------------------------------------------------------ decide
 
-enum : uint8_t { MAKE_EXACT = 4 };
 
 template <bool F64>
 __device__ __forceinline__ double load_bound(const void* a, int64_t p) {
@@ -344,11 +343,41 @@ int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) 
 
 // ------------------------------------------------------------------ driver
 
-struct StepStat {
-  int step;
-  int64_t tiles;
-  double ms;
-};
+void StepLog::add(pj_ctx* ctx, const UnitCount& uc, int event, const StepSpec& sp, cudaStream_t st) {
+  if (n >= MAX) return;
+  long long* d = ctx->d_snap + 4 * n;
+  if (uc.count < 0) PJ_CK(cudaMemcpyAsync(d, uc.dev, 8, cudaMemcpyDeviceToDevice, st));
+  PJ_CK(cudaMemcpyAsync(d + 1, ctx->d_counters, 16, cudaMemcpyDeviceToDevice, st));
+  ev[n] = event;
+  units[n] = uc.count;
+  f64[n] = sp.fp64;
+  full[n] = sp.full;
+  ++n;
+}
+
+std::string StepLog::json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total) const {
+  long long snap[MAX * 4];
+  if (n) PJ_CK(cudaMemcpy(snap, ctx->d_snap, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost));
+  std::string out = "[";
+  long long prev32 = 0, prev64 = 0;
+  *ms32 = *ms64 = 0;
+  *units_total = 0;
+  for (int i = 0; i < n; ++i) {
+    const float kms = refine_ms(ctx, ev[i]);
+    (f64[i] ? *ms64 : *ms32) += kms;
+    const long long u = units[i] >= 0 ? units[i] : snap[4 * i];
+    *units_total += u;
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tests\":%lld,\"refine_ms\":%.4f}",
+             i ? "," : "", i, f64[i] ? "fp64" : "fp32", full[i] ? 1 : 0, u,
+             (snap[4 * i + 1] - prev32) + (snap[4 * i + 2] - prev64), kms);
+    prev32 = snap[4 * i + 1];
+    prev64 = snap[4 * i + 2];
+    out += buf;
+  }
+  return out + "]";
+}
 
 
 pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
@@ -364,20 +393,14 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   FilterOut fo = filter_within(ctx, R, S, tau, st);
   const int64_t n = fo.n_pairs;
   setup_pairs(ctx, R, S, n, tau, true, st);
+  const bool use_mlp = (q->flags & PJ_USE_MLP) != 0;
+  if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
+  if (use_mlp && n > 0) start_lod(ctx, R, S, n, propose(ctx, R, S, n, st), tau, st);
   double ms_filter = tf.ms();
   const int Lmax = std::max(R->L, S->L);
   auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
   ctx->ev_used = 0;
-  int evs[PJ_MAX_LODS + 2];
-  int64_t host_units[PJ_MAX_LODS + 2];
-  int nsteps = 0;
-  // per-step snapshot of (units, fp32 tests, fp64 tests) taken on the device
-  auto snapshot = [&](int i, const UnitCount& uc) {
-    long long* d = ctx->d_snap + 4 * i;
-    if (uc.count < 0) PJ_CK(cudaMemcpyAsync(d, uc.dev, 8, cudaMemcpyDeviceToDevice, st));
-    PJ_CK(cudaMemcpyAsync(d + 1, ctx->d_counters, 16, cudaMemcpyDeviceToDevice, st));
-    host_units[i] = uc.count;
-  };
+  StepLog log;
   for (int step = 0; step < Lmax && n > 0; ++step) {
     if (deadline_hit()) return PJ_ETIMEOUT;
     StepSpec sp;
@@ -393,9 +416,9 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     sp.early = cull && (!sp.full || tau == 0.0);
     init_bounds(ctx, n, sp, st);
     UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    evs[nsteps] = run_refine(ctx, R, S, uc, sp, st);
+    const int ev = run_refine(ctx, R, S, uc, sp, st);
     decide_within(ctx, n, tau, sp, st);
-    snapshot(nsteps++, uc);
+    log.add(ctx, uc, ev, sp, st);
   }
   if (!fp64 && n > 0) {
     // pairs whose single-precision bracket still straddles tau at full
@@ -410,9 +433,9 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     sp.step = Lmax - 1;
     init_bounds(ctx, n, sp, st);
     UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    evs[nsteps] = run_refine(ctx, R, S, uc, sp, st);
+    const int ev = run_refine(ctx, R, S, uc, sp, st);
     decide_within(ctx, n, tau, sp, st);
-    snapshot(nsteps++, uc);
+    log.add(ctx, uc, ev, sp, st);
   }
   if ((q->flags & PJ_EXACT_DIST) && n > 0) {
     int th = 256;
@@ -430,9 +453,9 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     sp.step = Lmax - 1;
     init_bounds(ctx, n, sp, st);
     UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    evs[nsteps] = run_refine(ctx, R, S, uc, sp, st);
+    const int ev = run_refine(ctx, R, S, uc, sp, st);
     decide_within(ctx, n, tau, sp, st);
-    snapshot(nsteps++, uc);
+    log.add(ctx, uc, ev, sp, st);
   }
   Timer tg;
   int64_t m = gather_results(ctx, n, out, st);
@@ -441,36 +464,16 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   PJ_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   unsigned long long cnt[8];
   PJ_CK(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
-  long long snap[64 * 4];
-  if (nsteps) PJ_CK(cudaMemcpy(snap, ctx->d_snap, sizeof(long long) * 4 * nsteps, cudaMemcpyDeviceToHost));
-  std::string steps = "[";
-  long long prev32 = 0, prev64 = 0;
   double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
   int64_t tiles_total = 0;
-  for (int i = 0; i < nsteps; ++i) {
-    const bool s64 = fp64 || i >= Lmax;
-    float kms = refine_ms(ctx, evs[i]);
-    (s64 ? refine_ms_fp64 : refine_ms_fp32) += kms;
-    long long units = host_units[i] >= 0 ? host_units[i] : snap[4 * i];
-    if (evs[i] < 0 && host_units[i] < 0) units = snap[4 * i];
-    tiles_total += units;
-    char buf[256];
-    snprintf(buf, sizeof buf,
-             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tests\":%lld,\"refine_ms\":%.4f}",
-             i ? "," : "", i, s64 ? "fp64" : "fp32", (i >= Lmax - 1) ? 1 : 0, units,
-             (snap[4 * i + 1] - prev32) + (snap[4 * i + 2] - prev64), kms);
-    prev32 = snap[4 * i + 1];
-    prev64 = snap[4 * i + 2];
-    steps += buf;
-  }
-  steps += "]";
+  const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total);
   char buf[900];
   snprintf(buf, sizeof buf,
-           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"candidates\":%lld,\"results\":%lld,"
+           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%llu,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
-           tau, fp64 ? "fp64" : "fp32", (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], cnt[4],
+           tau, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], cnt[4],
            (long long)tiles_total, ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64,
            ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";

@@ -308,9 +308,16 @@ FilterOut filter_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, int k, cudaS
 
 // ------------------------------------------------------------------ prune
 
+// Pruning thresholds sit strictly above theta_r: a unit skipped against one
+// holds no facet pair at distance <= theta_r, and a pair whose lower bound
+// is clamped to one is certainly beyond the k-th neighbour.
+__device__ __forceinline__ float thr_above(double t) {
+  return nextafterf(__double2float_ru(t), INFINITY);
+}
+
 __global__ void k_theta_to_pairs(int64_t n, const int32_t* pr, const double* theta, float* thr) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p < n) thr[p] = __double2float_ru(theta[pr[p]]);
+  if (p < n) thr[p] = thr_above(theta[pr[p]]);
 }
 
 template <bool F64>
@@ -321,63 +328,84 @@ __device__ __forceinline__ double kload(const void* a, int64_t p) {
 
 constexpr int KPRUNE_SMEM = 2048;   // candidates of one r kept in shared memory
 
-// Algorithm 6 (corrected) for one r per CTA, then the shrinking bound.
-// refined: the pairs in `want` state were refined at this step (their lb/ub
-// words are fresh); pairs decided earlier keep their recorded bracket.
+struct PruneArgs {
+  const int64_t* roff;
+  const int32_t* ps;
+  uint8_t* status;
+  uint8_t* stnew;
+  uint8_t* lod0;
+  const void* lbw;
+  const void* ubw;
+  const void* midw;
+  float* thr;
+  double* theta;
+  double* dlo;
+  double* dhi;
+  double* d;
+  uint8_t* exact;
+  unsigned long long* cnt;
+  int nR;
+  int k;
+  int fresh_st;    // status whose pairs were refined now (with lod0 <= step); -1: none
+  int step;
+  int clamp;       // the refinement pruned units against thr
+  int full;        // the refinement ran at full resolution
+};
+
+// Algorithm 6 (corrected) for one r per CTA, then the shrinking bound.  The
+// candidates in state UNDECIDED or WAVE compete; the ones refined at this
+// step take their fresh lb / ub words, the others keep their bracket.  A
+// first-wave candidate left undecided returns to UNDECIDED with lod0 =
+// step + 1, so the second wave of the same step does not refine it again.
 template <bool F64>
-__global__ void __launch_bounds__(256) k_knn_prune(int nR, const int64_t* roff, const int32_t* ps, uint8_t* status,
-                                                   uint8_t* stnew, const void* lbw, const void* ubw,
-                                                   const void* midw, int fresh, int clamp, float* thr, double* theta,
-                                                   double* dlo, double* dhi, double* d, uint8_t* exact, int k,
-                                                   int full, int fp64_exact, unsigned long long* cnt) {
+__global__ void __launch_bounds__(256) k_knn_prune(PruneArgs A) {
   __shared__ double s_lb[KPRUNE_SMEM], s_ub[KPRUNE_SMEM];
   __shared__ int s_id[KPRUNE_SMEM];
   __shared__ uint8_t s_st[KPRUNE_SMEM];
   __shared__ int s_conf;
   const int r = blockIdx.x;
-  if (r >= nR) return;
-  const int64_t a = roff[r], C = roff[r + 1] - a;
+  if (r >= A.nR) return;
+  const int64_t a = A.roff[r], C = A.roff[r + 1] - a;
   if (C == 0) return;
   if (threadIdx.x == 0) s_conf = 0;
   __syncthreads();
   const bool in_smem = C <= KPRUNE_SMEM;
-  // bracket of every candidate: fresh bounds for the undecided ones when
-  // they were refined at this step (clamped by the pruning threshold, below
-  // which no skipped unit can lie), recorded brackets otherwise
+  auto fresh_at = [&](int64_t p, uint8_t stt) { return (int)stt == A.fresh_st && (int)A.lod0[p] <= A.step; };
   for (int64_t i = threadIdx.x; i < C; i += blockDim.x) {
     const int64_t p = a + i;
-    const uint8_t stt = status[p];
+    const uint8_t stt = A.status[p];
     double l, u;
-    if (stt == UNDECIDED && fresh) {
-      l = kload<F64>(lbw, p);
-      if (clamp) l = fmin(l, (double)thr[p]);   // pruned units lie above thr
-      u = kload<F64>(ubw, p);
-      dlo[p] = l;
-      dhi[p] = u;
+    if (fresh_at(p, stt)) {
+      l = kload<F64>(A.lbw, p);
+      if (A.clamp) l = fmin(l, (double)A.thr[p]);   // pruned units lie above thr
+      u = kload<F64>(A.ubw, p);
+      A.dlo[p] = l;
+      A.dhi[p] = u;
     } else {
-      l = dlo[p];
-      u = dhi[p];
+      l = A.dlo[p];
+      u = A.dhi[p];
     }
     if (stt == CONFIRMED) atomicAdd(&s_conf, 1);
     if (in_smem) {
       s_lb[i] = l;
       s_ub[i] = u;
-      s_id[i] = ps[p];
+      s_id[i] = A.ps[p];
       s_st[i] = stt;
     }
   }
   __syncthreads();
-  const int k_left = k - s_conf;
-  auto LB = [&](int64_t i) { return in_smem ? s_lb[i] : dlo[a + i]; };
-  auto UB = [&](int64_t i) { return in_smem ? s_ub[i] : dhi[a + i]; };
-  auto ID = [&](int64_t i) { return in_smem ? s_id[i] : ps[a + i]; };
-  auto ST = [&](int64_t i) { return in_smem ? s_st[i] : status[a + i]; };
+  const int k_left = A.k - s_conf;
+  auto LB = [&](int64_t i) { return in_smem ? s_lb[i] : A.dlo[a + i]; };
+  auto UB = [&](int64_t i) { return in_smem ? s_ub[i] : A.dhi[a + i]; };
+  auto ID = [&](int64_t i) { return in_smem ? s_id[i] : A.ps[a + i]; };
+  auto ST = [&](int64_t i) { return in_smem ? s_st[i] : A.status[a + i]; };
+  auto live = [](uint8_t x) { return x == UNDECIDED || x == WAVE; };
   // (xv, xi) < (yv, yi) lexicographically
   auto before = [](double xv, int xi, double yv, int yi) { return xv < yv || (xv == yv && xi < yi); };
   // decisions against the statuses at the start of the round
   for (int64_t m = threadIdx.x; m < C; m += blockDim.x) {
     uint8_t ns = ST(m);
-    if (ns == UNDECIDED) {
+    if (live(ns)) {
       if (k_left <= 0) {
         ns = REMOVED;
       } else {
@@ -385,7 +413,7 @@ __global__ void __launch_bounds__(256) k_knn_prune(int nR, const int64_t* roff, 
         const int im = ID(m);
         int64_t prec = 0, maybe = 0;
         for (int64_t j = 0; j < C; ++j) {
-          if (j == m || ST(j) != UNDECIDED) continue;
+          if (j == m || !live(ST(j))) continue;
           const double lj = LB(j), uj = UB(j);
           const int ij = ID(j);
           if (before(uj, ij, lm, im)) ++prec;     // j certainly before m
@@ -395,25 +423,31 @@ __global__ void __launch_bounds__(256) k_knn_prune(int nR, const int64_t* roff, 
         else if (maybe < k_left) ns = CONFIRMED;
       }
     }
-    stnew[a + m] = ns;
+    A.stnew[a + m] = ns;
   }
   __syncthreads();
   for (int64_t m = threadIdx.x; m < C; m += blockDim.x) {
     const int64_t p = a + m;
-    const uint8_t old = ST(m), ns = stnew[p];
+    const uint8_t old = ST(m), ns = A.stnew[p];
+    const bool fr = fresh_at(p, old);
+    if (ns == WAVE) {   // first wave, still undecided
+      A.status[p] = UNDECIDED;
+      A.lod0[p] = (uint8_t)min(A.step + 1, STEP_ALL);
+      continue;
+    }
     if (ns == old) continue;
-    status[p] = ns;
+    A.status[p] = ns;
     if (ns == CONFIRMED) {
-      atomicAdd(&cnt[2], 1ULL);
-      if (full && fresh) {
-        exact[p] = fp64_exact ? 1 : 2;
-        d[p] = fp64_exact ? UB(m) : kload<F64>(midw, p);
+      atomicAdd(&A.cnt[2], 1ULL);
+      if (A.full && fr) {
+        A.exact[p] = F64 ? 1 : 2;
+        A.d[p] = F64 ? UB(m) : kload<F64>(A.midw, p);
       } else {
-        exact[p] = 0;
-        d[p] = 0.5 * (LB(m) + UB(m));
+        A.exact[p] = 0;
+        A.d[p] = 0.5 * (LB(m) + UB(m));
       }
     } else if (ns == REMOVED) {
-      atomicAdd(&cnt[3], 1ULL);
+      atomicAdd(&A.cnt[3], 1ULL);
     }
   }
   __syncthreads();
@@ -421,10 +455,10 @@ __global__ void __launch_bounds__(256) k_knn_prune(int nR, const int64_t* roff, 
   if (threadIdx.x == 0) {
     double top[KMAX];
     int nt = 0;
-    const int kk = min(k, KMAX);
+    const int kk = min(A.k, KMAX);
     for (int64_t i = 0; i < C; ++i) {
-      if (status[a + i] == REMOVED) continue;
-      const double u = dhi[a + i];
+      if (A.status[a + i] == REMOVED) continue;
+      const double u = A.dhi[a + i];
       if (nt < kk || u < top[nt - 1]) {
         int pos = nt < kk ? nt++ : kk - 1;
         while (pos > 0 && top[pos - 1] > u) {
@@ -435,48 +469,101 @@ __global__ void __launch_bounds__(256) k_knn_prune(int nR, const int64_t* roff, 
       }
     }
     double t = nt >= kk ? top[kk - 1] : INFINITY;
-    t = fmin(t, theta[r]);
-    theta[r] = t;
-    for (int64_t i = 0; i < C; ++i) thr[a + i] = __double2float_ru(t);
+    t = fmin(t, A.theta[r]);
+    A.theta[r] = t;
+    const float th = thr_above(t);
+    for (int64_t i = 0; i < C; ++i) A.thr[a + i] = th;
   }
 }
 
-static void knn_prune_launch(pj_ctx* ctx, int nR, int k, bool full, bool fp64, int fresh, int clamp,
+// First wave of a step: per r (one warp), the k_left undecided candidates
+// with the smallest key become WAVE; the key is the proposal's predicted
+// distance when one is given (step 0), else the midpoint of the current
+// bracket.  Ties go to the smaller s id.
+__global__ void k_knn_wave(int nR, const int64_t* roff, const int32_t* ps, uint8_t* status, const uint8_t* lod0,
+                           int step, const float* pred, const double* dlo, const double* dhi, int k) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nR) return;
+  const int64_t a = roff[r], C = roff[r + 1] - a;
+  int conf = 0;
+  for (int64_t i = lane; i < C; i += 32) conf += status[a + i] == CONFIRMED;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) conf += __shfl_xor_sync(0xffffffffu, conf, o);
+  const int k_left = k - conf;
+  for (int t = 0; t < k_left; ++t) {
+    double bk = INFINITY;
+    int bid = INT_MAX;
+    int64_t bi = -1;
+    for (int64_t i = lane; i < C; i += 32) {
+      const int64_t p = a + i;
+      if (status[p] != UNDECIDED || (int)lod0[p] > step) continue;
+      const double key = pred ? (double)pred[p] : 0.5 * (dlo[p] + dhi[p]);
+      const int id = ps[p];
+      if (key < bk || (key == bk && id < bid)) {
+        bk = key;
+        bid = id;
+        bi = p;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oid = __shfl_xor_sync(0xffffffffu, bid, o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
+      if (ok < bk || (ok == bk && oid < bid)) {
+        bk = ok;
+        bid = oid;
+        bi = oi;
+      }
+    }
+    if (bi < 0) break;
+    if (lane == 0) status[bi] = WAVE;
+    __syncwarp();
+  }
+}
+
+static void knn_prune_launch(pj_ctx* ctx, int nR, int k, bool full, bool fp64, int fresh_st, int step, bool clamp,
                              cudaStream_t st) {
-  auto roff = (const int64_t*)ctx->ws[WS_ROFF].p;
-  auto ps = (const int32_t*)ctx->ws[WS_PS].p;
-  auto status = (uint8_t*)ctx->ws[WS_STATUS].p;
-  auto stnew = (uint8_t*)ctx->ws[WS_KNN2].p;
-  auto thr = (float*)ctx->ws[WS_THR].p;
-  auto theta = (double*)ctx->ws[WS_KNN].p;
-  auto dlo = (double*)ctx->ws[WS_DLO].p;
-  auto dhi = (double*)ctx->ws[WS_DHI].p;
-  auto d = (double*)ctx->ws[WS_D].p;
-  auto exact = (uint8_t*)ctx->ws[WS_EXACT].p;
-  if (fp64)
-    k_knn_prune<true><<<nR, 256, 0, st>>>(nR, roff, ps, status, stnew, ctx->ws[WS_LB].p, ctx->ws[WS_UB].p,
-                                          ctx->ws[WS_MID].p, fresh, clamp, thr, theta, dlo, dhi, d, exact, k, full, 1,
-                                          ctx->d_counters);
-  else
-    k_knn_prune<false><<<nR, 256, 0, st>>>(nR, roff, ps, status, stnew, ctx->ws[WS_LB].p, ctx->ws[WS_UB].p,
-                                           ctx->ws[WS_MID].p, fresh, clamp, thr, theta, dlo, dhi, d, exact, k, full, 0,
-                                           ctx->d_counters);
+  PruneArgs A;
+  A.roff = (const int64_t*)ctx->ws[WS_ROFF].p;
+  A.ps = (const int32_t*)ctx->ws[WS_PS].p;
+  A.status = (uint8_t*)ctx->ws[WS_STATUS].p;
+  A.stnew = (uint8_t*)ctx->ws[WS_KNN2].p;
+  A.lod0 = (uint8_t*)ctx->ws[WS_LOD0].p;
+  A.lbw = ctx->ws[WS_LB].p;
+  A.ubw = ctx->ws[WS_UB].p;
+  A.midw = ctx->ws[WS_MID].p;
+  A.thr = (float*)ctx->ws[WS_THR].p;
+  A.theta = (double*)ctx->ws[WS_KNN].p;
+  A.dlo = (double*)ctx->ws[WS_DLO].p;
+  A.dhi = (double*)ctx->ws[WS_DHI].p;
+  A.d = (double*)ctx->ws[WS_D].p;
+  A.exact = (uint8_t*)ctx->ws[WS_EXACT].p;
+  A.cnt = ctx->d_counters;
+  A.nR = nR;
+  A.k = k;
+  A.fresh_st = fresh_st;
+  A.step = step;
+  A.clamp = clamp ? 1 : 0;
+  A.full = full ? 1 : 0;
+  if (fp64) k_knn_prune<true><<<nR, 256, 0, st>>>(A);
+  else k_knn_prune<false><<<nR, 256, 0, st>>>(A);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
 
-// first round: the box MINDIST / anchor-distance brackets of the filter
-void knn_prune_round_boxes(pj_ctx* ctx, int nR, int k, int64_t n, cudaStream_t st) {
-  ws_get(ctx, WS_KNN2, (size_t)std::max<int64_t>(1, n), st);
-  knn_prune_launch(ctx, nR, k, false, false, 0, 0, st);
-}
-
-void knn_prune_round(pj_ctx* ctx, int nR, int k, bool full, bool fp64, bool pruned, cudaStream_t st) {
-  knn_prune_launch(ctx, nR, k, full, fp64, 1, pruned ? 1 : 0, st);
+static void knn_wave(pj_ctx* ctx, int nR, int k, int step, const float* pred, cudaStream_t st) {
+  const int wpb = 8;
+  k_knn_wave<<<(nR + wpb - 1) / wpb, wpb * 32, 0, st>>>(
+      nR, (const int64_t*)ctx->ws[WS_ROFF].p, (const int32_t*)ctx->ws[WS_PS].p, (uint8_t*)ctx->ws[WS_STATUS].p,
+      (const uint8_t*)ctx->ws[WS_LOD0].p, step, pred, (const double*)ctx->ws[WS_DLO].p,
+      (const double*)ctx->ws[WS_DHI].p, k);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 // ------------------------------------------------------------------ driver
-
 
 pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                    cudaStream_t st, std::string& stats) {
@@ -486,12 +573,15 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
   if (k > KMAX) throw ApiError{PJ_EINVAL, "k above 32 is not supported by the GPU k-NN join"};
   const bool fp64 = q->prec == PJ_PREC_FP64;
   const bool cull = (q->flags & PJ_TILE_PRUNE) != 0;
+  const bool use_mlp = (q->flags & PJ_USE_MLP) != 0;
+  if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
   PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
   PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   Timer tf;
   FilterOut fo = filter_knn(ctx, R, S, k, st);
   const int64_t n = fo.n_pairs;
   setup_pairs(ctx, R, S, n, 0.0, false, st);
+  const float* pred = nullptr;
   if (n > 0) {
     int th = 256;
     k_theta_to_pairs<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (const int32_t*)ctx->ws[WS_PR].p,
@@ -500,13 +590,21 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
     // the box / anchor bracket is the first round of Algorithm 6
-    knn_prune_round_boxes(ctx, R->n, k, n, st);
+    ws_get(ctx, WS_KNN2, (size_t)n, st);
+    knn_prune_launch(ctx, R->n, k, false, false, -1, 0, false, st);
+    if (use_mlp) pred = propose(ctx, R, S, n, st);
   }
   const double ms_filter = tf.ms();
   const int Lmax = std::max(R->L, S->L);
   ctx->ev_used = 0;
-  int evs[PJ_MAX_LODS + 2];
-  int nsteps = 0;
+  StepLog log;
+  // one refinement pass over the pairs in state `want` and its pruning round
+  auto pass = [&](StepSpec sp, int fresh_st) {
+    init_bounds(ctx, n, sp, st);
+    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
+    log.add(ctx, uc, run_refine(ctx, R, S, uc, sp, st), sp, st);
+    knn_prune_launch(ctx, R->n, k, sp.full, sp.fp64, fresh_st, sp.step, sp.cull, st);
+  };
   for (int step = 0; step < Lmax && n > 0; ++step) {
     if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
     StepSpec sp;
@@ -515,28 +613,28 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     sp.full = step == Lmax - 1;
     sp.fp64 = fp64;
     sp.cull = cull;
-    sp.want = UNDECIDED;
     sp.step = step;
-    init_bounds(ctx, n, sp, st);
-    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    evs[nsteps++] = run_refine(ctx, R, S, uc, sp, st);
-    knn_prune_round(ctx, R->n, k, sp.full, fp64, sp.cull, st);
+    // first wave: the k most promising candidates of every r tighten theta_r
+    // before the others are refined against it
+    knn_wave(ctx, R->n, k, step, step == 0 ? pred : nullptr, st);
+    sp.want = WAVE;
+    pass(sp, WAVE);
+    sp.want = UNDECIDED;
+    pass(sp, UNDECIDED);
   }
   if (!fp64 && n > 0) {
     // candidates whose single-precision brackets still tie: FP64 at full
-    // resolution, then the last pruning round resolves everything
+    // resolution, units pruned against the strict threshold, then the last
+    // pruning round resolves everything
     StepSpec sp;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
     sp.full = true;
     sp.fp64 = true;
-    sp.cull = false;
+    sp.cull = true;
     sp.want = UNDECIDED;
-    sp.step = Lmax - 1;
-    init_bounds(ctx, n, sp, st);
-    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    evs[nsteps++] = run_refine(ctx, R, S, uc, sp, st);
-    knn_prune_round(ctx, R->n, k, true, true, false, st);
+    sp.step = STEP_ALL;
+    pass(sp, UNDECIDED);
   }
   if ((q->flags & PJ_EXACT_DIST) && n > 0) {
     mark_exact(ctx, n, st);
@@ -546,11 +644,11 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     sp.full = true;
     sp.fp64 = true;
     sp.cull = false;
-    sp.want = 4;   // MAKE_EXACT
-    sp.step = Lmax - 1;
+    sp.want = MAKE_EXACT;
+    sp.step = STEP_ALL;
     init_bounds(ctx, n, sp, st);
     UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    evs[nsteps++] = run_refine(ctx, R, S, uc, sp, st);
+    log.add(ctx, uc, run_refine(ctx, R, S, uc, sp, st), sp, st);
     decide_within(ctx, n, 0.0, sp, st);
   }
   Timer tg;
@@ -583,15 +681,17 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
   unsigned long long cnt[8];
   PJ_CK(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
   double rms32 = 0, rms64 = 0;
-  for (int i = 0; i < nsteps; ++i) ((fp64 || i >= Lmax) ? rms64 : rms32) += refine_ms(ctx, evs[i]);
+  int64_t units = 0;
+  const std::string steps = log.json(ctx, &rms32, &rms64, &units);
   char buf[700];
   snprintf(buf, sizeof buf,
-           "{\"pred\":\"knn\",\"k\":%d,\"prec\":\"%s\",\"candidates\":%lld,\"results\":%lld,\"tests_fp32\":%llu,"
-           "\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"ms_filter\":%.3f,\"ms_gather\":%.3f,"
-           "\"ms_total\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu}",
-           k, fp64 ? "fp64" : "fp32", (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], ms_filter, tg.ms(),
-           tall.ms(), rms32, rms64, ctx->launches - launches0);
-  stats = buf;
+           "{\"pred\":\"knn\",\"k\":%d,\"prec\":\"%s\",\"mlp\":%d,\"candidates\":%lld,\"results\":%lld,\"tests_fp32\":%llu,"
+           "\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,\"ms_filter\":%.3f,"
+           "\"ms_gather\":%.3f,\"ms_total\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,"
+           "\"launches\":%llu,\"steps\":",
+           k, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], (long long)units,
+           ms_filter, tg.ms(), tall.ms(), rms32, rms64, ctx->launches - launches0);
+  stats = std::string(buf) + steps + "}";
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   return PJ_OK;
 }

@@ -495,6 +495,135 @@ static void ensure_weights(pj_ctx* ctx) {
   if (!ctx->mlp_w) PJ_CK(cudaMalloc((void**)&ctx->mlp_w, MLP_NW * sizeof(float)));
 }
 
+// Adam over shuffled mini-batches of device-resident features X [n][16] and
+// targets T [n].  The per-epoch permutation is drawn on the host.
+static void mlp_train_dev(pj_ctx* ctx, const float* X, const float* T, int64_t n, int epochs, uint64_t seed,
+                          cudaStream_t st) {
+  ensure_weights(ctx);
+  if (!ctx->mlp_ready) {
+    std::vector<float> W;
+    mlp_init_host(W, seed);
+    PJ_CK(cudaMemcpyAsync(ctx->mlp_w, W.data(), MLP_NW * 4, cudaMemcpyHostToDevice, st));
+    PJ_CK(cudaStreamSynchronize(st));
+    ctx->mlp_ready = true;
+  }
+  float* opt = (float*)ws_get(ctx, WS_MLP3, (3 * MLP_NW + 1) * sizeof(float), st);
+  float* grad = opt;
+  float* m = opt + MLP_NW;
+  float* v = opt + 2 * MLP_NW;
+  PJ_CK(cudaMemsetAsync(m, 0, 2 * MLP_NW * sizeof(float), st));
+  int32_t* idx = (int32_t*)ws_get(ctx, WS_FEAT, (size_t)n * 4, st);
+  std::vector<int32_t> perm(n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+  std::mt19937_64 rng(seed ^ 0x9e3779b97f4a7c15ULL);
+  const int64_t batch = std::min<int64_t>(n, 2048);
+  const float lr = 3e-3f, b1 = 0.9f, b2 = 0.999f;
+  int64_t step = 0;
+  for (int e = 0; e < epochs; ++e) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    PJ_CK(cudaMemcpyAsync(idx, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+    PJ_CK(cudaStreamSynchronize(st));   // perm is reused by the next epoch
+    for (int64_t b0 = 0; b0 < n; b0 += batch) {
+      const int64_t cnt = std::min(batch, n - b0);
+      PJ_CK(cudaMemsetAsync(grad, 0, MLP_NW * sizeof(float), st));
+      mlp_grad_launch(ctx, ctx->mlp_w, X, T, idx + b0, cnt, 1.f / (float)cnt, grad, nullptr, st);
+      ++step;
+      const float c1 = 1.f / (1.f - std::pow(b1, (float)step)), c2 = 1.f / (1.f - std::pow(b2, (float)step));
+      k_adam<<<(MLP_NW + 255) / 256, 256, 0, st>>>(ctx->mlp_w, m, v, grad, lr, b1, b2, c1, c2, MLP_NW);
+      PJ_CK(cudaGetLastError());
+      count_launch(ctx);
+    }
+  }
+  PJ_CK(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ proposal
+// The network predicts y = log1p(d) of a candidate pair from its features.
+
+const float* propose(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, cudaStream_t st) {
+  float* X = (float*)ws_get(ctx, WS_FEAT, (size_t)n * 64, st);
+  float* y = (float*)ws_get(ctx, WS_PRED, (size_t)n * 4, st);
+  pair_features(ctx, R, S, (const int32_t*)ctx->ws[WS_PR].p, (const int32_t*)ctx->ws[WS_PS].p, n, X, st);
+  mlp_forward(ctx, X, n, y, st);
+  return y;
+}
+
+struct LodMax {
+  const float4* chunkR[PJ_MAX_LODS];
+  const int64_t* coffR[PJ_MAX_LODS];
+  const float4* chunkS[PJ_MAX_LODS];
+  const int64_t* coffS[PJ_MAX_LODS];
+};
+
+__device__ __forceinline__ float obj_hd_ph(const float4* ch, const int64_t* coff, int o) {
+  float m = 0.f;
+  for (int64_t c = coff[o]; c < coff[o + 1]; ++c) m = fmaxf(m, ch[3 * c].w + ch[3 * c + 1].w);
+  return m;
+}
+
+// Start LoD of the undecided pairs (section 3.2, reading): step l can decide
+// a pair only when its distance is far enough from tau compared with the
+// Hausdorff terms of that LoD; with the per-object maxima w_l (hd + ph of r
+// plus hd + ph of s), |d - tau| > w_l decides it for certain.  The pair
+// starts at the coarsest step with max |x - tau| >= margin * w_l over the
+// prediction interval x in [expm1(y - u), expm1(y + u)], else at full
+// resolution.  Skipping steps never changes a result.
+__global__ void k_start_lod(int64_t n, const int32_t* pr, const int32_t* ps, const uint8_t* status,
+                            const float* pred, double tau, LodMax M, int offR, int offS, int Lmax, float margin,
+                            float u, uint8_t* lod0) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (status[p] != UNDECIDED) return;
+  const double y = pred[p];
+  const double lo = fmax(0.0, expm1(y - u)), hi = expm1(y + u);
+  const double gap = fmax(fabs(lo - tau), fabs(hi - tau));
+  const int r = pr[p], s = ps[p];
+  int start = Lmax - 1;
+  for (int l = 0; l < Lmax - 1; ++l) {
+    const int lr = max(0, l - offR), ls = max(0, l - offS);
+    const float w = obj_hd_ph(M.chunkR[lr], M.coffR[lr], r) + obj_hd_ph(M.chunkS[ls], M.coffS[ls], s);
+    if (gap >= (double)margin * w) {
+      start = l;
+      break;
+    }
+  }
+  lod0[p] = (uint8_t)start;
+}
+
+void start_lod(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const float* pred, double tau,
+               cudaStream_t st) {
+  if (n == 0) return;
+  LodMax M;
+  for (int l = 0; l < PJ_MAX_LODS; ++l) {
+    M.chunkR[l] = l < R->L ? R->lod[l].chunk : nullptr;
+    M.coffR[l] = l < R->L ? R->lod[l].coff : nullptr;
+    M.chunkS[l] = l < S->L ? S->lod[l].chunk : nullptr;
+    M.coffS[l] = l < S->L ? S->lod[l].coff : nullptr;
+  }
+  const int Lmax = std::max(R->L, S->L);
+  int th = 256;
+  k_start_lod<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(
+      n, (const int32_t*)ctx->ws[WS_PR].p, (const int32_t*)ctx->ws[WS_PS].p, (const uint8_t*)ctx->ws[WS_STATUS].p,
+      pred, tau, M, Lmax - R->L, Lmax - S->L, Lmax, START_MARGIN, PRED_BAND, (uint8_t*)ctx->ws[WS_LOD0].p);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
+// Training targets: y = log1p of the full-resolution distance (midpoint of
+// the single-precision bracket, whose width is a few ulps).
+__global__ void k_targets(int64_t n, const float* lb, const float* ub, float* t) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n) t[p] = log1pf(0.5f * (lb[p] + ub[p]));
+}
+
+__global__ void k_sq_err(int64_t n, const float* y, const float* t, double* acc) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double e = 0;
+  if (p < n) e = (double)(y[p] - t[p]) * (y[p] - t[p]);
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0 && e != 0) atomicAdd(acc, e);
+}
+
 }  // namespace pj
 
 using namespace pj;
@@ -620,41 +749,86 @@ pj_status pj_mlp_train(pj_ctx* ctx, const float* feats, const float* target, int
   float* T = (float*)ws_get(ctx, WS_MLP2, (size_t)n * 4, st);
   PJ_CK(cudaMemcpyAsync(X, feats, (size_t)n * 64, cudaMemcpyHostToDevice, st));
   PJ_CK(cudaMemcpyAsync(T, target, (size_t)n * 4, cudaMemcpyHostToDevice, st));
-  ensure_weights(ctx);
-  if (!ctx->mlp_ready) {
-    std::vector<float> W;
-    mlp_init_host(W, seed);
-    PJ_CK(cudaMemcpyAsync(ctx->mlp_w, W.data(), MLP_NW * 4, cudaMemcpyHostToDevice, st));
-    ctx->mlp_ready = true;
-  }
-  float* opt = (float*)ws_get(ctx, WS_MLP3, (3 * MLP_NW + 1) * sizeof(float), st);
-  float* grad = opt;
-  float* m = opt + MLP_NW;
-  float* v = opt + 2 * MLP_NW;
-  PJ_CK(cudaMemsetAsync(m, 0, 2 * MLP_NW * sizeof(float), st));
-  int32_t* idx = (int32_t*)ws_get(ctx, WS_FEAT, (size_t)n * 4, st);
-  std::vector<int32_t> perm(n);
-  for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
-  std::mt19937_64 rng(seed ^ 0x9e3779b97f4a7c15ULL);
-  const int64_t batch = std::min<int64_t>(n, 2048);
-  const float lr = 3e-3f, b1 = 0.9f, b2 = 0.999f;
-  int64_t step = 0;
-  for (int e = 0; e < epochs; ++e) {
-    std::shuffle(perm.begin(), perm.end(), rng);
-    PJ_CK(cudaMemcpyAsync(idx, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
-    PJ_CK(cudaStreamSynchronize(st));   // perm is reused by the next epoch
-    for (int64_t b0 = 0; b0 < n; b0 += batch) {
-      const int64_t cnt = std::min(batch, n - b0);
-      PJ_CK(cudaMemsetAsync(grad, 0, MLP_NW * sizeof(float), st));
-      mlp_grad_launch(ctx, ctx->mlp_w, X, T, idx + b0, cnt, 1.f / (float)cnt, grad, nullptr, st);
-      ++step;
-      const float c1 = 1.f / (1.f - std::pow(b1, (float)step)), c2 = 1.f / (1.f - std::pow(b2, (float)step));
-      k_adam<<<(MLP_NW + 255) / 256, 256, 0, st>>>(ctx->mlp_w, m, v, grad, lr, b1, b2, c1, c2, MLP_NW);
-      PJ_CK(cudaGetLastError());
-      count_launch(ctx);
-    }
-  }
+  mlp_train_dev(ctx, X, T, n, epochs, seed, st);
+  return PJ_OK;
+  MLP_CATCH(ctx)
+}
+
+pj_status pj_mlp_fit(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, int64_t max_pairs,
+                     int epochs, uint64_t seed, double* rmse) {
+  if (!ctx || !R || !S || !q || max_pairs < 16 || epochs < 1) return mlp_fail(ctx, PJ_EINVAL, "bad mlp_fit arguments");
+  if (R->streamed || S->streamed) return mlp_fail(ctx, PJ_EINVAL, "streamed sets are not addressable");
+  if (q->pred == PJ_KNN && (q->k < 1 || q->k > 32)) return mlp_fail(ctx, PJ_EINVAL, "k out of range");
+  if (q->pred == PJ_WITHIN && !(q->tau >= 0.0)) return mlp_fail(ctx, PJ_EINVAL, "tau must be >= 0");
+  MLP_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  (void)cudaGetLastError();
+  cudaStream_t st = ctx->stream;
+  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  FilterOut fo = q->pred == PJ_KNN ? filter_knn(ctx, R, S, q->k, st)
+                                   : filter_within(ctx, R, S, q->pred == PJ_INTERSECT ? 0.0 : q->tau, st);
+  const int64_t nc = fo.n_pairs;
+  if (nc < 16) return mlp_fail(ctx, PJ_EINVAL, "the query has fewer than 16 candidate pairs to learn from");
+  // a seeded sample of the candidates (all of them when they fit)
+  std::vector<int32_t> hr(nc), hs(nc);
+  PJ_CK(cudaMemcpyAsync(hr.data(), ctx->ws[WS_PR].p, nc * 4, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaMemcpyAsync(hs.data(), ctx->ws[WS_PS].p, nc * 4, cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaStreamSynchronize(st));
+  std::mt19937_64 rng(seed * 0x2545f4914f6cdd1dULL + 1);
+  std::vector<int64_t> pick(nc);
+  for (int64_t i = 0; i < nc; ++i) pick[i] = i;
+  std::shuffle(pick.begin(), pick.end(), rng);
+  const int64_t n = std::min(nc, max_pairs);
+  std::vector<int32_t> sr(n), ss(n);
+  for (int64_t i = 0; i < n; ++i) {
+    sr[i] = hr[pick[i]];
+    ss[i] = hs[pick[i]];
+  }
+  auto dpr = (int32_t*)ws_get(ctx, WS_PR, n * 4, st);
+  auto dps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);
+  PJ_CK(cudaMemcpyAsync(dpr, sr.data(), n * 4, cudaMemcpyHostToDevice, st));
+  PJ_CK(cudaMemcpyAsync(dps, ss.data(), n * 4, cudaMemcpyHostToDevice, st));
+  // labels: full-resolution distances from the refinement kernel
+  setup_pairs(ctx, R, S, n, 0.0, false, st);
+  StepSpec sp;
+  sp.lodR = R->L - 1;
+  sp.lodS = S->L - 1;
+  sp.full = true;
+  sp.fp64 = false;
+  sp.cull = false;
+  sp.want = UNDECIDED;
+  sp.step = STEP_ALL;
+  sp.exact_cross = true;
+  init_bounds(ctx, n, sp, st);
+  UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
+  run_refine(ctx, R, S, uc, sp, st);
+  float* X = (float*)ws_get(ctx, WS_MLP, (size_t)n * 64, st);
+  float* T = (float*)ws_get(ctx, WS_MLP2, (size_t)n * 4, st);
+  pair_features(ctx, R, S, dpr, dps, n, X, st);
+  int th = 256;
+  k_targets<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (const float*)ctx->ws[WS_LB].p,
+                                                          (const float*)ctx->ws[WS_UB].p, T);
+  PJ_CK(cudaGetLastError());
+  count_launch(ctx);
+  int herr = 0;
+  PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  if (herr & ERR_MBAR_TIMEOUT) return mlp_fail(ctx, PJ_ETIMEOUT, "a device wait hit its limit");
+  // train on the first 90 %, report the RMSE (log1p units) on the rest
+  const int64_t nv = std::max<int64_t>(1, n / 10), ntr = n - nv;
+  ctx->mlp_ready = false;   // fresh weights for this workload
+  mlp_train_dev(ctx, X, T, ntr, epochs, seed, st);
+  float* yv = (float*)ws_get(ctx, WS_PRED, (size_t)nv * 4, st);
+  mlp_forward(ctx, X + 16 * ntr, nv, yv, st);
+  double* acc = (double*)ws_get(ctx, WS_MISC5, 8, st);
+  PJ_CK(cudaMemsetAsync(acc, 0, 8, st));
+  k_sq_err<<<(unsigned)((nv + th - 1) / th), th, 0, st>>>(nv, yv, T + ntr, acc);
+  PJ_CK(cudaGetLastError());
+  count_launch(ctx);
+  double se = 0;
+  PJ_CK(cudaMemcpyAsync(&se, acc, 8, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  if (rmse) *rmse = std::sqrt(se / (double)nv);
   return PJ_OK;
   MLP_CATCH(ctx)
 }

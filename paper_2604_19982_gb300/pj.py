@@ -74,6 +74,7 @@ def lib():
             "pj_result_free": (None, [C.POINTER(ResultC)]),
             "pj_get_stats": (st, [vp, C.c_char_p, C.c_size_t]),
             "pj_mlp_train": (st, [vp, _fp, _fp, C.c_int64, C.c_int, C.c_uint64]),
+            "pj_mlp_fit": (st, [vp, vp, vp, C.POINTER(Query), C.c_int64, C.c_int, C.c_uint64, _dp]),
             "pj_mlp_save": (st, [vp, C.c_char_p]),
             "pj_mlp_load": (st, [vp, C.c_char_p]),
             "pj_mlp_set_weights": (st, [vp, _fp, _fp, _fp, _fp, _fp, _fp]),
@@ -291,6 +292,16 @@ class Context:
         return g.value
 
     # ---- learned proposal
+    def mlp_fit(self, R: Set, S: Set, pred: int = KNN, tau: float = 0.0, k: int = 0, max_pairs: int = 200000,
+                epochs: int = 30, seed: int = 1) -> float:
+        """pj_mlp_fit: train fresh proposal weights on a sample of the
+        query's candidates; returns the held-out RMSE in log(1 + d)."""
+        q = Query(pred, float(tau), int(k), FP32, 0, 0.0)
+        rmse = C.c_double()
+        self._check(lib().pj_mlp_fit(self.h, R.handle, S.handle, C.byref(q), int(max_pairs), int(epochs), int(seed),
+                                     C.byref(rmse)))
+        return rmse.value
+
     def mlp_train(self, feats, target, epochs: int = 20, seed: int = 0):
         feats = np.ascontiguousarray(feats, np.float32)
         target = np.ascontiguousarray(target, np.float32)
