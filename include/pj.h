@@ -267,7 +267,7 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
  *   lb, ub   DEVICE double [n] outputs, as for pj_pair_bounds;
  *   cuda_stream  stream to work on (NULL = the context's stream); the call
  *            returns when the results are written.
- * Scratch: one fixed array of about 3.6 MB in the library's device code,
+ * Scratch: one fixed array of about 2.4 MB in the library's device code,
  * held by every GPU that loads the library until the process exits.  Its
  * device address is looked up on the first call on each device (with that
  * device current).  Sizes beyond it are rejected with PJ_EINVAL:

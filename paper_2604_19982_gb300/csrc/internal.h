@@ -230,12 +230,11 @@ struct PairBufs {
   void* lb;
   void* ub;
   void* mid;
-  int64_t* tcount;   // [n+1] r chunks per pair
+  int64_t* tcount;   // [n+1] builder work items per pair
   int64_t* toff;     // [n+1]
-  int64_t* wcount;   // [wcap+1] units per (pair, r chunk)
-  int64_t* woff;     // [wcap+1]
-  int64_t wcap;
+  int64_t* ucount;   // [1] unit counter of the builder
   int64_t* scan_tmp; // scan temporaries (nullptr: allocate)
+  int* err;          // device error word
   Tile* tiles;
   unsigned long long* counters;  // [3]: tests, tile counter, straddle-queue count
   int4* queue;                   // straddling facet pairs (see k_cross_fix)

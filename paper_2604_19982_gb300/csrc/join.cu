@@ -478,6 +478,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
            ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
+  if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
   return PJ_OK;
 }

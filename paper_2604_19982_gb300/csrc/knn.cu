@@ -693,6 +693,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
            ms_filter, tg.ms(), tall.ms(), rms32, rms64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
+  if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   return PJ_OK;
 }
 

@@ -93,11 +93,12 @@ void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, doubl
 
 // ------------------------------------------------------------------ units
 // A refinement unit is one 32-facet block of r x one 32-facet block of s of
-// one candidate pair at one LoD.  The builder walks, for every (pair, r
-// chunk of 256 facets), the s chunks; a chunk pair whose box distance minus
-// the Hausdorff terms exceeds the pair's threshold is skipped whole, else its
-// 8 x 8 block pairs are tested the same way and only the live ones become
-// units (PJ_TILE_PRUNE; without it every block pair is a unit).
+// one candidate pair at one LoD.  A work item of the builder is one (pair,
+// r block, 256-facet s chunk): the r block's box is tested against the s
+// chunk's box, then against each of the chunk's (up to 8) s blocks; a box
+// pair whose distance minus the Hausdorff terms exceeds the pair's
+// threshold is skipped (PJ_TILE_PRUNE; without it every block pair is a
+// unit).  The live units of a warp are appended with one atomic add.
 
 struct BoxView {
   const float4* chunk;   // [3C] chunk boxes
@@ -150,71 +151,119 @@ __device__ __forceinline__ int64_t find_pair(const int64_t* off, int64_t n, int6
   return lo;
 }
 
-__global__ void k_rchunks(int64_t n, const int32_t* pr, const uint8_t* status, const uint8_t* lod0, uint8_t want,
-                          int step, const int64_t* coffR, int64_t* cnt) {
+// Work items of every selected pair: r blocks x s chunks.  Also clears the
+// unit counter that k_emit_units appends to.
+__global__ void k_items(int64_t n, const int32_t* pr, const int32_t* ps, const uint8_t* status,
+                        const uint8_t* lod0, uint8_t want, int step, const int64_t* boffR, const int64_t* coffS,
+                        int64_t* cnt, int64_t* ucount) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p == 0) *ucount = 0;
   if (p >= n) return;
-  cnt[p] = (status[p] == want && lod0[p] <= step) ? coffR[pr[p] + 1] - coffR[pr[p]] : 0;
+  const bool sel = status[p] == want && lod0[p] <= step;
+  cnt[p] = sel ? (boffR[pr[p] + 1] - boffR[pr[p]]) * (coffS[ps[p] + 1] - coffS[ps[p]]) : 0;
 }
 
-// EMIT = false: count the live units of every (pair, r chunk) work item;
-// EMIT = true: write them.  Work items w < off1[n] (read on the device).
+// EMIT = false: only count the live units into *ucount; EMIT = true: also
+// write them (at most cap; more sets ERR_CAPACITY and drops the excess).
+// Work items w < off1[n] (read on the device), walked in warp-uniform
+// strides so the warp-wide append is safe.
 template <bool EMIT>
-__global__ void k_units(int64_t n, const int32_t* pr, const int32_t* ps, const int64_t* off1, BoxView R, BoxView S,
-                        const float4* origin, const float* thr, int cull, int fp64, int64_t* cnt2,
-                        const int64_t* off2, Tile* tiles, int64_t wcap) {
+__global__ void __launch_bounds__(256) k_emit_units(int64_t n, const int32_t* pr, const int32_t* ps,
+                                                    const int64_t* off1, BoxView R, BoxView S,
+                                                    const float4* origin, const float* thr, int cull, int fp64,
+                                                    Tile* tiles, int64_t cap, int64_t* ucount, int* err) {
+  constexpr int SB = CHUNK / BLK;
   const int64_t W = off1[n];
-  if (!EMIT)  // entries past the live work items count zero units
-    for (int64_t w = W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w <= wcap;
-         w += (int64_t)gridDim.x * blockDim.x)
-      cnt2[w] = 0;
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < W; w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = find_pair(off1, n, w);
-    const int r = pr[p], s = ps[p];
-    const int64_t rc = R.coff[r] + (w - off1[p]);               // r chunk
-    const int64_t rb0 = R.boff[r] + (w - off1[p]) * (CHUNK / BLK);
-    const int64_t rb1 = min(rb0 + CHUNK / BLK, R.boff[r + 1]);    // r blocks of the chunk
-    const int64_t sc0 = S.coff[s], sc1 = S.coff[s + 1];
-    const float4 o = origin[p];
-    const float t = thr[p];
-    int64_t c = 0;
-    int64_t wpos = EMIT ? off2[w] : 0;
-    if (!cull && !EMIT) {
-      c = (rb1 - rb0) * (S.boff[s + 1] - S.boff[s]);
-    } else {
-      const float4* ca = R.chunk + 3 * rc;
-      for (int64_t sc = sc0; sc < sc1; ++sc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); w0 < W; w0 += stride) {
+    const int64_t w = w0 + lane;
+    unsigned mask = 0;
+    float eps[SB], eh[SB];
+    int sl[SB];
+    int32_t pair = 0, fr = 0, fs0 = 0;
+    int rl = 0;
+#pragma unroll
+    for (int j = 0; j < SB; ++j) {
+      eps[j] = eh[j] = 0.f;
+      sl[j] = 0;
+    }
+    if (w < W) {
+      const int64_t p = find_pair(off1, n, w);
+      const int r = pr[p], s = ps[p];
+      const int64_t loc = w - off1[p];
+      const int64_t nsc = S.coff[s + 1] - S.coff[s];
+      const int64_t rb = R.boff[r] + loc / nsc;
+      const int64_t sc = S.coff[s] + loc % nsc;
+      const int64_t sb0 = S.boff[s] + (sc - S.coff[s]) * SB;
+      const int nsb = (int)min((int64_t)SB, S.boff[s + 1] - sb0);
+      const float4 o = origin[p];
+      const float t = thr[p];
+      const float4* ba = R.blk + 3 * rb;
+      const int64_t fr64 = R.foff[r] + (rb - R.boff[r]) * BLK;
+      const int64_t fs64 = S.foff[s] + (sb0 - S.boff[s]) * BLK;
+      pair = (int32_t)p;
+      fr = (int32_t)fr64;
+      fs0 = (int32_t)fs64;
+      rl = (int)min((int64_t)BLK, R.foff[r + 1] - fr64);
+      const int64_t send = S.foff[s + 1];
+      bool live = true;
+      if (cull) {
         const float4* cb = S.chunk + 3 * sc;
-        if (cull && !box_pair_live(ca, cb, t, fp64 ? 0.f : box_margins(ca, cb, o).eps)) continue;
-        const int64_t sb0 = S.boff[s] + (sc - sc0) * (CHUNK / BLK);
-        const int64_t sb1 = min(sb0 + CHUNK / BLK, S.boff[s + 1]);
-        for (int64_t rb = rb0; rb < rb1; ++rb)
-          for (int64_t sb = sb0; sb < sb1; ++sb) {
-            const float4* ba = R.blk + 3 * rb;
-            const float4* bb = S.blk + 3 * sb;
+        live = box_pair_live(ba, cb, t, fp64 ? 0.f : box_margins(ba, cb, o).eps);
+      }
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+          if (j < nsb) {
+            const float4* bb = S.blk + 3 * (sb0 + j);
             Margins m = box_margins(ba, bb, o);
             if (fp64) m.eps = m.eh = 0.f;
-            if (cull && !box_pair_live(ba, bb, t, m.eps)) continue;
-            if (EMIT) {
-              Tile tl;
-              const int64_t fr = R.foff[r] + (rb - R.boff[r]) * BLK, fs = S.foff[s] + (sb - S.boff[s]) * BLK;
-              tl.pair = (int32_t)p;
-              tl.rb = (int32_t)fr;
-              tl.sb = (int32_t)fs;
-              tl.rl = (uint16_t)(R.foff[r + 1] - fr < BLK ? R.foff[r + 1] - fr : BLK);
-              tl.sl = (uint16_t)(S.foff[s + 1] - fs < BLK ? S.foff[s + 1] - fs : BLK);
-              tl.eps = m.eps;
-              tl.eh = m.eh;
-              tl.ew = 0.f;
-              tl.pad = 0;
-              tiles[wpos++] = tl;
-            } else {
-              ++c;
+            if (!cull || box_pair_live(ba, bb, t, m.eps)) {
+              mask |= 1u << j;
+              eps[j] = m.eps;
+              eh[j] = m.eh;
+              sl[j] = (int)min((int64_t)BLK, send - (fs64 + (int64_t)j * BLK));
             }
           }
+        }
       }
     }
-    if (!EMIT) cnt2[w] = c;
+    const int c = __popc(mask);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total)
+      base = atomicAdd(reinterpret_cast<unsigned long long*>(ucount), (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (EMIT && mask) {
+      int64_t pos = (int64_t)base + incl - c;
+      if (pos + c > cap) {
+        set_err(err, ERR_CAPACITY);
+      } else {
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+          if (mask & (1u << j)) {
+            Tile tl;
+            tl.pair = pair;
+            tl.rb = fr;
+            tl.sb = fs0 + j * BLK;
+            tl.rl = (uint16_t)rl;
+            tl.sl = (uint16_t)sl[j];
+            tl.eps = eps[j];
+            tl.eh = eh[j];
+            tl.ew = 0.f;
+            tl.pad = 0;
+            tiles[pos++] = tl;
+          }
+        }
+      }
+    }
   }
 }
 
@@ -225,48 +274,54 @@ constexpr size_t UNIT_BUDGET_BYTES = size_t(512) << 20;
 
 static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
                              const int32_t* pr, const int32_t* ps, const uint8_t* status, const uint8_t* lod0,
-                             const float4* origin, const float* thr, int64_t* cnt1, int64_t* off1, int64_t* cnt2,
-                             int64_t* off2, int64_t wcap, Tile** tiles_io, int64_t tiles_cap, bool grow,
-                             int64_t* scan_tmp, cudaStream_t st) {
+                             const float4* origin, const float* thr, int64_t* cnt1, int64_t* off1, int64_t* ucount,
+                             Tile** tiles_io, int64_t tiles_cap, bool grow, int64_t* scan_tmp, int* err,
+                             cudaStream_t st) {
   const LodData& LR = R->lod[sp.lodR];
   const LodData& LS = S->lod[sp.lodS];
   BoxView vr = box_view(LR), vs = box_view(LS);
   int th = 256;
-  k_rchunks<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, status, lod0, sp.want, sp.step, LR.coff, cnt1);
+  k_items<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, LR.boff, LS.coff,
+                                                        cnt1, ucount);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  scan_i64(ctx, cnt1, off1, n, st, scan_tmp);
-  unsigned g = (unsigned)std::min<int64_t>((wcap + th - 1) / th + 1, (int64_t)ctx->sm_count * 32);
-  k_units<false><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, cnt2, nullptr, nullptr,
-                                   wcap);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-  scan_i64(ctx, cnt2, off2, wcap, st, scan_tmp);   // off2[wcap] = number of units
-  const int64_t worst = n * ((LR.maxF + BLK - 1) / BLK) * ((LS.maxF + BLK - 1) / BLK);
-  UnitCount uc{-1, off2 + wcap};
+  scan_i64(ctx, cnt1, off1, n, st, scan_tmp);   // off1[n] = work items
+  const int64_t bR = (LR.maxF + BLK - 1) / BLK, bS = (LS.maxF + BLK - 1) / BLK;
+  const int64_t cS = std::max<int64_t>(1, (LS.maxF + CHUNK - 1) / CHUNK);
+  const int64_t items_max = n * bR * cS;
+  const unsigned g =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((items_max + th - 1) / th, (int64_t)ctx->sm_count * 16));
+  const int64_t worst = n * bR * bS;
+  UnitCount uc{-1, ucount};
+  int64_t cap = tiles_cap;
   if (worst <= tiles_cap || (grow && (size_t)worst * sizeof(Tile) <= UNIT_BUDGET_BYTES)) {
-    if (worst > tiles_cap) *tiles_io = (Tile*)ws_get(ctx, WS_TILES, worst * sizeof(Tile), st);
+    if (worst > tiles_cap) {
+      *tiles_io = (Tile*)ws_get(ctx, WS_TILES, worst * sizeof(Tile), st);
+      cap = worst;
+    }
   } else {
+    // the worst case does not fit: count first, then size the buffer
+    k_emit_units<false><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, nullptr, 0,
+                                          ucount, err);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
     int64_t total = 0;
-    PJ_CK(cudaMemcpyAsync(&total, off2 + wcap, 8, cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaMemcpyAsync(&total, ucount, 8, cudaMemcpyDeviceToHost, st));
     PJ_CK(cudaStreamSynchronize(st));
     uc.count = total;
     if (total == 0) return uc;
     if (total > tiles_cap) {
       if (!grow) throw ApiError{PJ_EINVAL, "refinement units above the scratch capacity"};
       *tiles_io = (Tile*)ws_get(ctx, WS_TILES, total * sizeof(Tile), st);
+      cap = total;
     }
+    PJ_CK(cudaMemsetAsync(ucount, 0, 8, st));
   }
-  k_units<true><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, nullptr, off2, *tiles_io,
-                                  wcap);
+  k_emit_units<true><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, *tiles_io, cap,
+                                       ucount, err);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   return uc;
-}
-
-static int64_t work_cap(const pj_set* R, const StepSpec& sp, int64_t n) {
-  const LodData& LR = R->lod[sp.lodR];
-  return n * std::max<int64_t>(1, (LR.maxF + CHUNK - 1) / CHUNK);
 }
 
 UnitCount build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
@@ -278,16 +333,14 @@ UnitCount build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
   auto lod0 = (uint8_t*)ws_get(ctx, WS_LOD0, n, st);
   auto origin = (float4*)ws_get(ctx, WS_ORIGIN, n * 16, st);
   auto thr = (float*)ws_get(ctx, WS_THR, n * 4, st);
-  const int64_t wcap = work_cap(R, sp, n);
   auto cnt1 = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
   auto off1 = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
-  auto cnt2 = (int64_t*)ws_get(ctx, WS_MISC3, (wcap + 1) * 8, st);
-  auto off2 = (int64_t*)ws_get(ctx, WS_MISC4, (wcap + 1) * 8, st);
-  auto tmp = (int64_t*)ws_get(ctx, WS_MISC5, (scan_tmp_words(wcap + 1) + scan_tmp_words(n) + 8) * 8, st);
+  auto ucount = (int64_t*)ws_get(ctx, WS_MISC4, 64, st);
+  auto tmp = (int64_t*)ws_get(ctx, WS_MISC5, (scan_tmp_words(n) + 8) * 8, st);
   Tile* tiles = (Tile*)ctx->ws[WS_TILES].p;
   const int64_t cap = (int64_t)(ctx->ws[WS_TILES].cap / sizeof(Tile));
-  return build_units(ctx, R, S, n, sp, pr, ps, status, lod0, origin, thr, cnt1, off1, cnt2, off2, wcap, &tiles, cap,
-                     true, tmp, st);
+  return build_units(ctx, R, S, n, sp, pr, ps, status, lod0, origin, thr, cnt1, off1, ucount, &tiles, cap, true,
+                     tmp, ctx->d_err, st);
 }
 
 __global__ void k_init_bounds(int64_t n, const uint8_t* status, const uint8_t* lod0, uint8_t want, int step,
@@ -746,11 +799,9 @@ void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
 UnitCount build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
                            const PairBufs& b, int64_t tiles_cap, cudaStream_t st) {
   if (n == 0) return UnitCount{0, nullptr};
-  const int64_t wcap = work_cap(R, sp, n);
-  if (wcap > b.wcap) throw ApiError{PJ_EINVAL, "work items above the scratch capacity"};
   Tile* tiles = b.tiles;
-  return build_units(ctx, R, S, n, sp, b.pr, b.ps, b.status, b.lod0, b.origin, b.thr, b.tcount, b.toff, b.wcount,
-                     b.woff, wcap, &tiles, tiles_cap, false, b.scan_tmp, st);
+  return build_units(ctx, R, S, n, sp, b.pr, b.ps, b.status, b.lod0, b.origin, b.thr, b.tcount, b.toff, b.ucount,
+                     &tiles, tiles_cap, false, b.scan_tmp, b.err, st);
 }
 
 void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st) {

@@ -24,8 +24,7 @@ namespace {
 constexpr int64_t MAXP = PJ_STATIC_MAX_PAIRS;
 constexpr int64_t MAXT = PJ_STATIC_MAX_TILES;
 constexpr int64_t MAXQ = 65536;   // queued straddling facet pairs
-constexpr int64_t MAXW = 65536;   // (pair, 256-facet chunk of r) work items
-constexpr int64_t SCANW = 64;     // scan temporaries (words), enough for MAXW
+constexpr int64_t SCANW = 64;     // scan temporaries (words), enough for MAXP + 1
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -46,9 +45,8 @@ constexpr size_t OFF_MID = OFF_UB + align256(MAXP * 8);
 constexpr size_t OFF_TCOUNT = OFF_MID + align256(MAXP * 8);
 constexpr size_t OFF_TOFF = OFF_TCOUNT + align256((MAXP + 1) * 8);
 constexpr size_t OFF_TILES = OFF_TOFF + align256((MAXP + 1) * 8);
-constexpr size_t OFF_WCOUNT = OFF_TILES + align256(MAXT * sizeof(Tile));
-constexpr size_t OFF_WOFF = OFF_WCOUNT + align256((MAXW + 1) * 8);
-constexpr size_t OFF_SCANTMP = OFF_WOFF + align256((MAXW + 1) * 8);
+constexpr size_t OFF_UCOUNT = OFF_TILES + align256(MAXT * sizeof(Tile));
+constexpr size_t OFF_SCANTMP = OFF_UCOUNT + 256;
 constexpr size_t OFF_QUEUE = OFF_SCANTMP + align256(SCANW * 8);
 constexpr size_t OFF_COUNTERS = OFF_QUEUE + align256(MAXQ * sizeof(int4));
 constexpr size_t OFF_ERR = OFF_COUNTERS + 256;
@@ -56,7 +54,7 @@ constexpr size_t SCRATCH_BYTES = OFF_ERR + 256;
 
 }  // namespace
 
-// The scratch itself: about 3.6 MB per device.
+// The scratch itself: about 2.4 MB per device.
 static __device__ __align__(256) unsigned char g_bounds_scratch[SCRATCH_BYTES];
 
 namespace {
@@ -125,10 +123,6 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
                       " units needed, above PJ_STATIC_MAX_TILES (" + std::to_string(MAXT) + ")";
     return PJ_EINVAL;
   }
-  if (n * ((R->lod[lod].maxF + CHUNK - 1) / CHUNK) > MAXW) {
-    ctx->last_error = "pair_bounds_static: too many (pair, 256-facet chunk) work items";
-    return PJ_EINVAL;
-  }
   if (n == 0) return PJ_OK;
   try {
     PJ_CK(cudaSetDevice(ctx->device));
@@ -181,9 +175,8 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     sp.want = UNDECIDED;
     sp.step = 0;
     sp.exact_cross = true;
-    b.wcount = reinterpret_cast<int64_t*>(base + OFF_WCOUNT);
-    b.woff = reinterpret_cast<int64_t*>(base + OFF_WOFF);
-    b.wcap = MAXW;
+    b.ucount = reinterpret_cast<int64_t*>(base + OFF_UCOUNT);
+    b.err = err;
     b.scan_tmp = reinterpret_cast<int64_t*>(base + OFF_SCANTMP);
     setup_pairs_bufs(ctx, R, S, n, b, st);
     init_bounds_bufs(ctx, n, sp, b, st);
