@@ -190,6 +190,33 @@ static T* upload(const T* h, size_t count, cudaStream_t st) {
 }
 
 // Lay a described set out on the device (see pj_load_set).
+void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st) {
+  const int n = s->n, L = s->L;
+  int th = 256;
+  for (int l = 0; l < L; ++l) {
+    LodData& ld = s->lod[l];
+    if (ld.F == 0) continue;
+    k_expand<<<(unsigned)((ld.F + th - 1) / th), th, 0, st>>>(ld.F, n, raw[l].verts, raw[l].voff, raw[l].faces, ld.foff,
+                                                              raw[l].nfs, raw[l].hd, raw[l].ph, ld.fac, ctx->d_err);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+    int64_t thr = ld.C * 32;
+    k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, CHUNK, ld.coff, ld.foff, ld.fac, ld.chunk);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+    thr = ld.B * 32;
+    k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.B, n, BLK, ld.boff, ld.foff, ld.fac, ld.blk);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+  }
+  if (n > 0) {
+    k_mbb<<<(unsigned)(((int64_t)n * 32 + th - 1) / th), th, 0, st>>>(n, raw[L - 1].verts, raw[L - 1].voff, s->anchor,
+                                                                       s->mbb, ctx->d_err);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+  }
+}
+
 pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaStream_t st) {
   const int n = D->n_objects, L = D->n_lods;
   if (n < 0 || L < 1 || L > PJ_MAX_LODS) throw ApiError{PJ_EINVAL, "n_objects < 0 or n_lods outside [1, 8]"};
@@ -199,8 +226,7 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
   std::map<const void*, float*> vcache;
   std::vector<void*> temps;
   PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
-  float* d_fin_verts = nullptr;
-  int64_t* d_fin_voff = nullptr;
+  RawLod raw[PJ_MAX_LODS];
   for (int l = 0; l < L; ++l) {
     if (!D->verts[l] || !D->vert_off[l] || !D->faces[l])
       throw ApiError{PJ_EINVAL, "verts / vert_off / faces of a LoD is NULL"};
@@ -269,35 +295,11 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
     PJ_CK(cudaMalloc((void**)&ld.fac, std::max<int64_t>(1, 3 * ld.F) * sizeof(float4)));
     PJ_CK(cudaMalloc((void**)&ld.chunk, std::max<int64_t>(1, 3 * ld.C) * sizeof(float4)));
     PJ_CK(cudaMalloc((void**)&ld.blk, std::max<int64_t>(1, 3 * ld.B) * sizeof(float4)));
-    if (ld.F > 0) {
-      int th = 256;
-      k_expand<<<(unsigned)((ld.F + th - 1) / th), th, 0, st>>>(ld.F, n, dv, dvo, dfa, ld.foff, nfs, dhd, dph,
-                                                                ld.fac, ctx->d_err);
-      PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-      int64_t thr = ld.C * 32;
-      k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, CHUNK, ld.coff, ld.foff, ld.fac, ld.chunk);
-      PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-      thr = ld.B * 32;
-      k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.B, n, BLK, ld.boff, ld.foff, ld.fac, ld.blk);
-      PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-    }
-    if (l == L - 1) {
-      d_fin_verts = dv;
-      d_fin_voff = dvo;
-    }
+    raw[l] = RawLod{dv, dvo, dfa, nfs, dhd, dph};
   }
   PJ_CK(cudaMalloc((void**)&s->mbb, std::max(1, n) * 6 * sizeof(float)));
   s->anchor = upload(D->anchor, (size_t)n * 3, st);
-  if (n > 0) {
-    int th = 256;
-    k_mbb<<<(unsigned)(((int64_t)n * 32 + th - 1) / th), th, 0, st>>>(n, d_fin_verts, d_fin_voff, s->anchor,
-                                                                       s->mbb, ctx->d_err);
-    PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-  }
+  build_set_kernels(ctx, s, raw, st);
   s->mbb_h.resize((size_t)n * 6);
   if (n > 0) PJ_CK(cudaMemcpyAsync(s->mbb_h.data(), s->mbb, (size_t)n * 6 * 4, cudaMemcpyDeviceToHost, st));
   int herr = 0;
@@ -431,6 +433,8 @@ void pj_destroy(pj_ctx* ctx) {
   cudaFree(ctx->mlp_w);
   cudaFree(ctx->d_snap);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  for (void* hp : ctx->stream_pinned)
+    if (hp) cudaFreeHost(hp);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -64,6 +64,14 @@ struct LodData {
   int64_t maxF = 0;               // largest facet count of one object
 };
 
+// Totals of the last join (also in its JSON stats).
+struct JoinSummary {
+  int64_t candidates = 0, results = 0, units = 0;
+  unsigned long long tests32 = 0, tests64 = 0, confirmed = 0, removed = 0;
+  double ms_filter = 0, ms_total = 0, refine_ms32 = 0, refine_ms64 = 0;
+  unsigned long long launches = 0;
+};
+
 }  // namespace pj
 
 struct pj_set {
@@ -93,6 +101,7 @@ struct pj_ctx {
   unsigned long long* d_counters = nullptr;  // [16] device counters
   std::string last_error;
   std::string stats;
+  pj::JoinSummary last_sum;
   int ctas_per_sm = 0;             // 0 = from occupancy
   std::string autotune_cache;
   // per-query workspace
@@ -111,6 +120,8 @@ struct pj_ctx {
   // pinned staging of result copies (grow-only)
   void* h_stage = nullptr;
   size_t h_stage_cap = 0;
+  void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
+  size_t stream_pinned_cap[2] = {};
 };
 
 namespace pj {
@@ -129,7 +140,7 @@ enum Slot {
   WS_PR, WS_PS, WS_ORIGIN, WS_THR, WS_BOXLB, WS_ANCUB, WS_STATUS, WS_LOD0, WS_LB, WS_UB, WS_MID,
   WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
   WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5,
-  WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3,
+  WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3, WS_STREAM4, WS_STREAM5,
   WS_COUNT
 };
 
@@ -258,6 +269,22 @@ void mark_exact(pj_ctx* ctx, int64_t n, cudaStream_t st);
 
 // ---- decide (join.cu)
 void decide_within(pj_ctx* ctx, int64_t n_pairs, double tau, const StepSpec& sp, cudaStream_t st);
+
+// ---- set building (api.cu)
+// Raw device arrays of one LoD as given by the caller (faces: shared
+// template of nfs rows when nfs > 0, else per-object rows).
+struct RawLod {
+  const float* verts;
+  const int64_t* voff;
+  const int32_t* faces;
+  int nfs;
+  const float* hd;
+  const float* ph;
+};
+// Facet records, chunk and block boxes of every LoD and the object boxes,
+// into the set's allocated buffers (foff / coff / boff already on the
+// device); kernel errors go to ctx->d_err.
+void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st);
 
 // ---- triangle distance batch (refine.cu)
 void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool fp64, double* out,

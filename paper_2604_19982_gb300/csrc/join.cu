@@ -477,6 +477,19 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
            (long long)tiles_total, ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64,
            ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
+  JoinSummary& js = ctx->last_sum;
+  js.candidates = n;
+  js.results = m;
+  js.units = tiles_total;
+  js.tests32 = cnt[0];
+  js.tests64 = cnt[1];
+  js.confirmed = cnt[2];
+  js.removed = cnt[3];
+  js.ms_filter = ms_filter;
+  js.ms_total = tall.ms();
+  js.refine_ms32 = refine_ms_fp32;
+  js.refine_ms64 = refine_ms_fp64;
+  js.launches = ctx->launches - launches0;
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;

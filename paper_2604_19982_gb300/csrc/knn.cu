@@ -692,6 +692,19 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
            k, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], (long long)units,
            ms_filter, tg.ms(), tall.ms(), rms32, rms64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
+  JoinSummary& js = ctx->last_sum;
+  js.candidates = n;
+  js.results = m;
+  js.units = units;
+  js.tests32 = cnt[0];
+  js.tests64 = cnt[1];
+  js.confirmed = cnt[2];
+  js.removed = cnt[3];
+  js.ms_filter = ms_filter;
+  js.ms_total = tall.ms();
+  js.refine_ms32 = rms32;
+  js.refine_ms64 = rms64;
+  js.launches = ctx->launches - launches0;
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   return PJ_OK;

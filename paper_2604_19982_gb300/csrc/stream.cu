@@ -1,0 +1,431 @@
+// Streamed join: R arrives in chunks, S stays resident (section 4,
+// Algorithm 3 and the pipelined refinement of Algorithm 5).
+//
+// A loader thread asks the caller's fill callback for chunk c, checks it,
+// and packs its raw arrays (vertices once per distinct host array, vertex
+// and face offsets, faces, hd / ph, anchors, and the facet / chunk / block
+// offsets computed on the host) into one of two pinned host slots.  The
+// calling thread copies a packed chunk to the matching device slot with one
+// host-to-device copy on the context's copy stream, builds the chunk's
+// facet records and boxes on the compute stream once that copy is done, and
+// joins the chunk against S with the resident-set join.  The copy of chunk
+// c + 1 is issued before the join of chunk c starts, so it overlaps that
+// join; the loader packs chunk c + 2 meanwhile.  Results carry global R ids
+// (the ids of chunk c continue those of chunk c - 1).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pj {
+
+pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                      cudaStream_t st, std::string& stats);
+pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                   cudaStream_t st, std::string& stats);
+
+namespace {
+
+constexpr size_t PACK_ALIGN = 256;
+size_t pad(size_t x) { return (x + PACK_ALIGN - 1) & ~(PACK_ALIGN - 1); }
+
+// Where each array of one chunk sits inside its packed slot (byte offsets).
+struct Plan {
+  int index = -1;
+  int n = 0;
+  int L = 0;
+  int64_t first_id = 0;
+  int vsrc[PJ_MAX_LODS];           // LoD whose packed vertex array this LoD uses
+  size_t o_verts[PJ_MAX_LODS], o_voff[PJ_MAX_LODS], o_faces[PJ_MAX_LODS];
+  size_t o_hd[PJ_MAX_LODS], o_ph[PJ_MAX_LODS];
+  size_t o_foff[PJ_MAX_LODS], o_coff[PJ_MAX_LODS], o_boff[PJ_MAX_LODS];
+  int nfs[PJ_MAX_LODS];
+  bool has_hd[PJ_MAX_LODS], has_ph[PJ_MAX_LODS];
+  int64_t F[PJ_MAX_LODS], C[PJ_MAX_LODS], B[PJ_MAX_LODS], maxF[PJ_MAX_LODS];
+  size_t o_anchor = 0;
+  size_t bytes = 0;
+};
+
+struct ChunkSlot {
+  enum State { FREE, FILLED, COPYING };
+  State state = FREE;
+  Plan plan;
+  cudaEvent_t copied = nullptr;
+};
+
+struct Piece {
+  const void* src;
+  size_t off;
+  size_t bytes;
+};
+
+// Check one chunk description (the rules of pj_load_set) and lay it out.
+// Host offset arrays are computed into `offs` (kept alive until packed).
+void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Piece>& pieces,
+                std::vector<std::vector<int64_t>>& offs) {
+  const int n = D->n_objects, L = D->n_lods;
+  if (n < 0 || L < 1 || L > PJ_MAX_LODS) throw ApiError{PJ_EINVAL, "chunk: n_objects < 0 or n_lods outside [1, 8]"};
+  if (L_expect > 0 && L != L_expect) throw ApiError{PJ_EINVAL, "chunk: n_lods differs from the first chunk"};
+  if (n > 0 && !D->anchor) throw ApiError{PJ_EINVAL, "chunk: anchor is NULL"};
+  P.n = n;
+  P.L = L;
+  size_t at = 0;
+  auto put = [&](const void* src, size_t bytes) {
+    const size_t off = at;
+    if (bytes) pieces.push_back(Piece{src, off, bytes});
+    at = pad(at + bytes);
+    return off;
+  };
+  offs.assign(3 * L, {});
+  for (int l = 0; l < L; ++l) {
+    if (!D->verts[l] || !D->vert_off[l] || !D->faces[l])
+      throw ApiError{PJ_EINVAL, "chunk: verts / vert_off / faces of a LoD is NULL"};
+    if (l == L - 1 && (D->hd[l] || D->ph[l])) throw ApiError{PJ_EINVAL, "chunk: hd / ph of the original LoD must be NULL"};
+    const int64_t* vo = D->vert_off[l];
+    if (n > 0 && vo[0] != 0) throw ApiError{PJ_EINVAL, "chunk: vert_off must start at 0"};
+    for (int o = 0; o < n; ++o)
+      if (vo[o + 1] < vo[o]) throw ApiError{PJ_EINVAL, "chunk: vert_off not non-decreasing"};
+    const int64_t nv = n > 0 ? vo[n] : 0;
+    const bool shared = D->face_off[l] == nullptr;
+    const int nfs = shared ? D->n_faces_shared[l] : 0;
+    if (shared && nfs <= 0 && n > 0) throw ApiError{PJ_EINVAL, "chunk: shared topology needs n_faces_shared > 0"};
+    if (!shared && n > 0 && D->face_off[l][0] != 0) throw ApiError{PJ_EINVAL, "chunk: face_off must start at 0"};
+    std::vector<int64_t>& fo = offs[3 * l];
+    std::vector<int64_t>& co = offs[3 * l + 1];
+    std::vector<int64_t>& bo = offs[3 * l + 2];
+    fo.assign(n + 1, 0);
+    co.assign(n + 1, 0);
+    bo.assign(n + 1, 0);
+    int64_t maxF = 0;
+    for (int o = 0; o < n; ++o) {
+      const int64_t c = shared ? nfs : D->face_off[l][o + 1] - D->face_off[l][o];
+      if (c < 0) throw ApiError{PJ_EINVAL, "chunk: face_off not non-decreasing"};
+      fo[o + 1] = fo[o] + c;
+      co[o + 1] = co[o] + (c + CHUNK - 1) / CHUNK;
+      bo[o + 1] = bo[o] + (c + BLK - 1) / BLK;
+      maxF = std::max(maxF, c);
+    }
+    if (fo[n] >= (1LL << 31)) throw ApiError{PJ_EINVAL, "chunk: more than 2^31 facets in one LoD"};
+    P.F[l] = fo[n];
+    P.C[l] = co[n];
+    P.B[l] = bo[n];
+    P.maxF[l] = maxF;
+    P.nfs[l] = nfs;
+    P.vsrc[l] = l;
+    for (int m = 0; m < l; ++m)
+      if (D->verts[m] == D->verts[l] && P.vsrc[m] == m && D->vert_off[m][n] == nv) {
+        P.vsrc[l] = m;
+        break;
+      }
+    P.o_verts[l] = P.vsrc[l] == l ? put(D->verts[l], (size_t)nv * 12) : P.o_verts[P.vsrc[l]];
+    P.o_voff[l] = put(vo, (size_t)(n + 1) * 8);
+    P.o_faces[l] = put(D->faces[l], (size_t)(shared ? nfs : P.F[l]) * 12);
+    P.has_hd[l] = D->hd[l] != nullptr;
+    P.has_ph[l] = D->ph[l] != nullptr;
+    P.o_hd[l] = P.has_hd[l] ? put(D->hd[l], (size_t)P.F[l] * 4) : 0;
+    P.o_ph[l] = P.has_ph[l] ? put(D->ph[l], (size_t)P.F[l] * 4) : 0;
+    P.o_foff[l] = put(fo.data(), (size_t)(n + 1) * 8);
+    P.o_coff[l] = put(co.data(), (size_t)(n + 1) * 8);
+    P.o_boff[l] = put(bo.data(), (size_t)(n + 1) * 8);
+  }
+  P.o_anchor = put(D->anchor, (size_t)n * 12);
+  P.bytes = at;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                        cudaStream_t st, std::string& stats) {
+  Timer tall;
+  const int N = R->n_chunks;
+  ChunkSlot slots[2];
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  pj_status lerr = PJ_OK;
+  std::string lmsg;
+  double ms_fill = 0, ms_pack = 0;
+  int L_first = 0;
+  struct Events {
+    cudaEvent_t e[6] = {};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } evs;
+  for (int i = 0; i < 6; ++i) PJ_CK(cudaEventCreateWithFlags(&evs.e[i], i < 2 ? cudaEventDisableTiming : 0));
+  slots[0].copied = evs.e[0];
+  slots[1].copied = evs.e[1];
+  cudaEvent_t h2d0[2] = {evs.e[2], evs.e[3]}, h2d1[2] = {evs.e[4], evs.e[5]};
+  Plan plans[2];   // the calling thread's copy of the plan of each slot in flight
+  const int device = ctx->device;
+
+  // ---- loader thread: fill, check, pack
+  std::thread loader([&]() {
+    cudaSetDevice(device);
+    int64_t first = 0;
+    std::vector<Piece> pieces;
+    std::vector<std::vector<int64_t>> offs;
+    for (int c = 0; c < N; ++c) {
+      ChunkSlot& sl = slots[c & 1];
+      bool copying;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || sl.state != ChunkSlot::FILLED; });
+        if (stop) return;
+        copying = sl.state == ChunkSlot::COPYING;
+      }
+      // the pinned slot is reused once its previous copy has landed
+      if (copying && cudaEventSynchronize(sl.copied) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        lerr = PJ_ECUDA;
+        lmsg = "loader: waiting for a chunk copy failed";
+        stop = true;
+        cv.notify_all();
+        return;
+      }
+      pj_mesh_set_desc d;
+      memset(&d, 0, sizeof d);
+      auto t0 = std::chrono::steady_clock::now();
+      const pj_status rc = R->fill(R->user, c, &d);
+      ms_fill += ms_since(t0);
+      Plan P;
+      pj_status err = PJ_OK;
+      std::string msg;
+      if (rc != PJ_OK) {
+        err = rc == PJ_ECANCELLED ? PJ_ECANCELLED : PJ_ESOURCE;
+        msg = "the fill callback returned " + std::to_string((int)rc) + " for chunk " + std::to_string(c);
+      } else {
+        try {
+          pieces.clear();
+          plan_chunk(&d, L_first, P, pieces, offs);
+          if (c == 0) L_first = P.L;
+          P.index = c;
+          P.first_id = first;
+          first += P.n;
+          if (first > R->n_total) throw ApiError{PJ_EINVAL, "the chunks hold more objects than the streamed set"};
+          t0 = std::chrono::steady_clock::now();
+          void*& hp = ctx->stream_pinned[c & 1];
+          size_t& hc = ctx->stream_pinned_cap[c & 1];
+          if (hc < P.bytes) {
+            if (hp) cudaFreeHost(hp);
+            hp = nullptr;
+            hc = 0;
+            if (cudaHostAlloc(&hp, P.bytes, cudaHostAllocDefault) != cudaSuccess)
+              throw ApiError{PJ_ENOMEM, "pinned staging allocation failed"};
+            hc = P.bytes;
+          }
+          for (const Piece& pc : pieces) memcpy(static_cast<unsigned char*>(hp) + pc.off, pc.src, pc.bytes);
+          ms_pack += ms_since(t0);
+        } catch (const ApiError& e) {
+          err = e.st;
+          msg = e.msg;
+        }
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      if (err != PJ_OK) {
+        lerr = err;
+        lmsg = msg;
+        stop = true;
+        cv.notify_all();
+        return;
+      }
+      sl.plan = P;
+      sl.state = ChunkSlot::FILLED;
+      cv.notify_all();
+    }
+  });
+  struct Joiner {
+    std::thread& t;
+    std::mutex& mu;
+    std::condition_variable& cv;
+    bool& stop;
+    ~Joiner() {
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        stop = true;
+      }
+      cv.notify_all();
+      if (t.joinable()) t.join();
+    }
+  } joiner{loader, mu, cv, stop};
+
+  // ---- calling thread: copy, build, join
+  int enqueued = 0;   // chunks whose copy has been issued
+  double ms_h2d = 0, ms_wait = 0;
+  size_t bytes_h2d = 0;
+  // issue the copy of chunk c if it is packed (or wait for it when `block`)
+  auto enqueue = [&](int c, bool block) -> bool {
+    ChunkSlot& sl = slots[c & 1];
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (block) {
+        auto t0 = std::chrono::steady_clock::now();
+        cv.wait(lk, [&] { return stop || (sl.state == ChunkSlot::FILLED && sl.plan.index == c); });
+        ms_wait += ms_since(t0);
+      }
+      if (lerr != PJ_OK) throw ApiError{lerr, lmsg};
+      if (!(sl.state == ChunkSlot::FILLED && sl.plan.index == c)) {
+        if (stop) throw ApiError{PJ_ECANCELLED, "streamed join stopped"};
+        return false;
+      }
+    }
+    const size_t bytes = sl.plan.bytes;
+    void* dev = ws_get(ctx, (c & 1) ? WS_STREAM5 : WS_STREAM4, bytes, ctx->copy_stream);
+    PJ_CK(cudaEventRecord(h2d0[c & 1], ctx->copy_stream));
+    PJ_CK(cudaMemcpyAsync(dev, ctx->stream_pinned[c & 1], bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    PJ_CK(cudaEventRecord(h2d1[c & 1], ctx->copy_stream));
+    PJ_CK(cudaEventRecord(sl.copied, ctx->copy_stream));
+    bytes_h2d += bytes;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      plans[c & 1] = sl.plan;
+      sl.state = ChunkSlot::COPYING;
+    }
+    cv.notify_all();
+    return true;
+  };
+
+  std::vector<int32_t> rr, ss;
+  std::vector<double> dlo, dhi, dd;
+  std::vector<uint8_t> ex;
+  JoinSummary tot;
+  int64_t objects = 0;
+  for (int c = 0; c < N; ++c) {
+    if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
+    if (enqueued <= c) {
+      enqueue(c, true);
+      enqueued = c + 1;
+    }
+    ChunkSlot& sl = slots[c & 1];
+    const Plan P = plans[c & 1];
+    // the copy of the next chunk overlaps this chunk's build and join
+    if (c + 1 < N && enqueued == c + 1 && enqueue(c + 1, false)) enqueued = c + 2;
+    PJ_CK(cudaStreamWaitEvent(st, sl.copied, 0));
+    unsigned char* dev = (unsigned char*)ctx->ws[(c & 1) ? WS_STREAM5 : WS_STREAM4].p;
+    // device view of the chunk
+    pj_set view;
+    view.ctx = ctx;
+    view.device = ctx->device;
+    view.n = P.n;
+    view.L = P.L;
+    int64_t fac_n = 0, box_n = 0;
+    for (int l = 0; l < P.L; ++l) {
+      fac_n += 3 * std::max<int64_t>(1, P.F[l]);
+      box_n += 3 * (std::max<int64_t>(1, P.C[l]) + std::max<int64_t>(1, P.B[l]));
+    }
+    float4* fac = (float4*)ws_get(ctx, WS_STREAM, fac_n * sizeof(float4), st);
+    float4* box = (float4*)ws_get(ctx, WS_STREAM2, box_n * sizeof(float4), st);
+    view.mbb = (float*)ws_get(ctx, WS_STREAM3, (size_t)std::max(1, P.n) * 6 * sizeof(float), st);
+    view.anchor = (float*)(dev + P.o_anchor);
+    RawLod raw[PJ_MAX_LODS];
+    for (int l = 0; l < P.L; ++l) {
+      LodData& ld = view.lod[l];
+      ld.F = P.F[l];
+      ld.C = P.C[l];
+      ld.B = P.B[l];
+      ld.maxF = P.maxF[l];
+      ld.fac = fac;
+      fac += 3 * std::max<int64_t>(1, P.F[l]);
+      ld.chunk = box;
+      box += 3 * std::max<int64_t>(1, P.C[l]);
+      ld.blk = box;
+      box += 3 * std::max<int64_t>(1, P.B[l]);
+      ld.foff = (int64_t*)(dev + P.o_foff[l]);
+      ld.coff = (int64_t*)(dev + P.o_coff[l]);
+      ld.boff = (int64_t*)(dev + P.o_boff[l]);
+      raw[l] = RawLod{(const float*)(dev + P.o_verts[l]), (const int64_t*)(dev + P.o_voff[l]),
+                      (const int32_t*)(dev + P.o_faces[l]), P.nfs[l],
+                      P.has_hd[l] ? (const float*)(dev + P.o_hd[l]) : nullptr,
+                      P.has_ph[l] ? (const float*)(dev + P.o_ph[l]) : nullptr};
+    }
+    PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+    build_set_kernels(ctx, &view, raw, st);
+    view.mbb_h.resize((size_t)P.n * 6);
+    int herr = 0;
+    if (P.n > 0) PJ_CK(cudaMemcpyAsync(view.mbb_h.data(), view.mbb, (size_t)P.n * 24, cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaStreamSynchronize(st));
+    if (herr & ERR_BOUNDS) throw ApiError{PJ_EBOUNDS, "chunk " + std::to_string(c) + ": a face index lies outside its object's vertices"};
+    if (herr & ERR_NONFINITE) throw ApiError{PJ_ENONFINITE, "chunk " + std::to_string(c) + ": non-finite vertex, anchor, hd or ph"};
+    float h2d = 0;
+    if (cudaEventElapsedTime(&h2d, h2d0[c & 1], h2d1[c & 1]) == cudaSuccess) ms_h2d += h2d;
+    // the join of this chunk against S
+    pj_query qc = *q;
+    if (q->timeout_s > 0) qc.timeout_s = std::max(1e-3, q->timeout_s - tall.ms() / 1000.0);
+    pj_result part;
+    memset(&part, 0, sizeof part);
+    std::string st_chunk;
+    pj_status rc = q->pred == PJ_KNN ? join_knn(ctx, &view, S, &qc, &part, st, st_chunk)
+                                     : join_within(ctx, &view, S, &qc, &part, st, st_chunk);
+    if (rc != PJ_OK) {
+      free(part.priv);
+      return rc;
+    }
+    const JoinSummary& js = ctx->last_sum;
+    tot.candidates += js.candidates;
+    tot.results += js.results;
+    tot.units += js.units;
+    tot.tests32 += js.tests32;
+    tot.tests64 += js.tests64;
+    tot.confirmed += js.confirmed;
+    tot.removed += js.removed;
+    tot.ms_filter += js.ms_filter;
+    tot.refine_ms32 += js.refine_ms32;
+    tot.refine_ms64 += js.refine_ms64;
+    tot.launches += js.launches;
+    for (int64_t i = 0; i < part.n; ++i) {
+      rr.push_back((int32_t)(part.r[i] + P.first_id));
+      ss.push_back(part.s[i]);
+      dlo.push_back(part.d_lo[i]);
+      dhi.push_back(part.d_hi[i]);
+      dd.push_back(part.d[i]);
+      ex.push_back(part.exact[i]);
+    }
+    free(part.priv);
+    objects += P.n;
+  }
+  if (objects != R->n_total)
+    throw ApiError{PJ_ESOURCE, "the chunks hold " + std::to_string(objects) + " objects, the streamed set " +
+                                   std::to_string(R->n_total)};
+  const int64_t m = (int64_t)rr.size();
+  alloc_result(out, m);
+  if (m) {
+    memcpy(out->r, rr.data(), m * 4);
+    memcpy(out->s, ss.data(), m * 4);
+    memcpy(out->d_lo, dlo.data(), m * 8);
+    memcpy(out->d_hi, dhi.data(), m * 8);
+    memcpy(out->d, dd.data(), m * 8);
+    memcpy(out->exact, ex.data(), m);
+  }
+  const double ms_total = tall.ms();
+  char buf[1024];
+  snprintf(buf, sizeof buf,
+           "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
+           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,"
+           "\"bytes_h2d\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
+           "\"ms_wait_loader\":%.3f,\"ms_filter\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,"
+           "\"ms_total\":%.3f,\"launches\":%llu}",
+           q->pred == PJ_KNN ? "knn" : "within", N, (long long)objects, (long long)tot.candidates, (long long)m,
+           tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, ms_h2d,
+           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, tot.ms_filter, tot.refine_ms32,
+           tot.refine_ms64, ms_total, tot.launches);
+  stats = buf;
+  tot.results = m;
+  tot.ms_total = ms_total;
+  ctx->last_sum = tot;
+  return PJ_OK;
+}
+
+}  // namespace pj

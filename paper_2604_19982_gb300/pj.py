@@ -97,6 +97,10 @@ def lib():
     return _lib
 
 
+class Cancel(Exception):
+    """Raised by a streamed set's chunk function to cancel the join."""
+
+
 class PJError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{lib().pj_status_str(status).decode()} ({status}): {msg}")
@@ -219,7 +223,10 @@ class Context:
         return Set(self, h.value, int(ms.n), int(ms.n_lods))
 
     def load_set_streamed(self, n_objects: int, n_chunks: int, chunk_fn) -> Set:
-        """``chunk_fn(c)`` returns the mesh-set object of chunk ``c``."""
+        """``chunk_fn(c)`` returns the mesh-set object of chunk ``c`` (called
+        from the library's loader thread during a join); raising
+        :class:`Cancel` stops the join with PJ_ECANCELLED, any other
+        exception with PJ_ESOURCE."""
         keep_box = {}
 
         def fill(user, chunk, out):
@@ -230,6 +237,8 @@ class Context:
                 keep_box["cur"] = (keep, d)
                 C.memmove(out, C.byref(d), C.sizeof(MeshSetDesc))
                 return PJ_OK
+            except Cancel:
+                return PJ_ECANCELLED
             except Exception:   # any failure of the source
                 return PJ_ESOURCE
 

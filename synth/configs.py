@@ -69,14 +69,17 @@ def blob_set(n: int, side: float, seed: int, set_id: int, subs=BLOB_SUBS,
 
 
 def tube_set(n: int, side: float, seed: int, set_id: int, start: int = 0,
-             count: int | None = None) -> MeshSet:
+             count: int | None = None, length_range=(50.0, 800.0)) -> MeshSet:
+    """Tubes with centres uniform in the cube and arc lengths uniform in
+    ``length_range`` (the workload's range by default; tests use shorter
+    tubes to keep the oracle fast)."""
     count = n - start if count is None else count
     centres = np.empty((count, 3))
     lengths = np.empty(count)
     for i in range(count):
         rng = _rng(seed, set_id, start + i, 29)
         centres[i] = rng.uniform(0.0, side, size=3)
-        lengths[i] = rng.uniform(50.0, 800.0)
+        lengths[i] = rng.uniform(*length_range)
     return make_tubes(lambda i: _rng(seed, set_id, start + i, 31), centres, lengths)
 
 
