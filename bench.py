@@ -157,14 +157,28 @@ def h2d_bytes(ms) -> int:
 RESULT_BYTES_PER_PAIR = 4 + 4 + 8 + 8 + 8 + 1
 
 
-def dist_init():
+def dist_init(backend: str | None = None):
+    """Process group of a multi-rank run (one replica of the join per rank,
+    no data-path collective).  NCCL on GPUs; gloo when asked (CPU tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(backend or "nccl")
     return world, rank, local
+
+
+def _reduce(x: float, world: int, op_name: str) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op_name))
+    return float(t.item())
 
 
 def barrier(world):
@@ -174,23 +188,13 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    """The slowest rank's time: the job finishes when every replica has."""
+    return _reduce(x, world, "MAX")
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    """Units processed by all ranks together."""
+    return _reduce(x, world, "SUM")
 
 
 # ----------------------------------------------------------------- oracle sample

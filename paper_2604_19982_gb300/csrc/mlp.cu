@@ -561,7 +561,9 @@ __device__ __forceinline__ float obj_hd_ph(const float4* ch, const int64_t* coff
   return m;
 }
 
-// Start LoD of the undecided pairs (section 3.2, reading): step l can decide
+// Start LoD of the undecided pairs.  Section 3.1 refines every pair LoD by
+// LoD from the coarsest; skipping the coarse steps a pair cannot pass is
+// this library's addition, driven by the prediction.  Step l can decide
 // a pair only when its distance is far enough from tau compared with the
 // Hausdorff terms of that LoD; with the per-object maxima w_l (hd + ph of r
 // plus hd + ph of s), |d - tau| > w_l decides it for certain.  The pair

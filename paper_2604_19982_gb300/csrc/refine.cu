@@ -1,20 +1,23 @@
 // Facet-level refinement (section 3.3, Algorithm 4 and Eq. 1 / Eq. 2),
 // re-designed for sm_103a:
-//  * work unit = tile: one 256-facet chunk of r x one 256-facet chunk of s of
-//    one candidate pair at one LoD (replaces the paper's block per voxel
-//    pair); tiles are built on the device and consumed by a persistent
-//    kernel through an atomic counter (one launch per LoD step);
-//  * the s chunk is staged into shared memory with a TMA bulk copy
-//    (cp.async.bulk, mbarrier completion, bounded wait), then expanded once
-//    into per-facet records; r facets live in registers (one per thread,
-//    several s stripes when the r chunk is short), s records are read by
-//    warp-wide broadcast;
-//  * per-thread running minima, warp-shuffle + one shared word per warp,
-//    then one atomicMin per tile and pair on the order-preserving bits
-//    (replaces the block-wide Hillis-Steele scan of section 2.2);
-//  * optional pruning (PJ_TILE_PRUNE): chunk pairs and 32-facet blocks whose
-//    box distance minus the Hausdorff terms exceeds the pair's threshold are
-//    skipped; they cannot change the decision (see build_tiles).
+//  * unit = one 32-facet block of r x one 32-facet block of s of one
+//    candidate pair at one LoD (replaces the paper's thread block per voxel
+//    pair); units are built on the device (k_items / k_emit_units) and
+//    consumed by a persistent kernel through an atomic counter, one launch
+//    per LoD step;
+//  * every warp works alone: lane 0 prefetches the next unit's s block with
+//    a TMA bulk copy (cp.async.bulk, mbarrier completion, bounded wait) into
+//    the warp's other buffer; the 32 s facets are expanded once into
+//    shared-memory records; each lane holds one r facet in registers and
+//    runs its 32 tests against the broadcast s records;
+//  * per-lane running minima, a warp-shuffle min and one atomicMin per unit
+//    and pair on the order-preserving bits (replaces the block-wide
+//    Hillis-Steele scan and shared-memory aggregation of section 2.2);
+//  * facet pairs whose planes straddle each other are decided by an exact
+//    double-precision meeting test after the loop (warp list, overflow to a
+//    global queue and k_cross_fix);
+//  * optional pruning (PJ_TILE_PRUNE): block pairs whose box distance minus
+//    the Hausdorff terms exceeds the pair's threshold are never built.
 #include <algorithm>
 #include <stdexcept>
 

@@ -1,5 +1,6 @@
-// Streamed join: R arrives in chunks, S stays resident (section 4,
-// Algorithm 3 and the pipelined refinement of Algorithm 5).
+// Streamed join: R arrives in chunks, S stays resident (the double-stream
+// chunked streaming of section 3.2, Algorithm 3, and the copy / compute
+// overlap of section 3.3, Algorithm 5).
 //
 // A loader thread asks the caller's fill callback for chunk c, checks it,
 // and packs its raw arrays (vertices once per distinct host array, vertex

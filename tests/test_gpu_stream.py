@@ -1,4 +1,4 @@
-"""Streamed joins (section 4, Algorithms 3 and 5): R arrives in chunks
+"""Streamed joins (section 3.2, Algorithm 3; section 3.3, Algorithm 5): R arrives in chunks
 through a fill callback while S stays resident.  A streamed join must
 return exactly the pairs, brackets and distances of the same join over the
 resident concatenation of the chunks (the per-pair schedule does not
