@@ -135,9 +135,12 @@ typedef struct {
 } pj_result;
 
 /* Create a context on CUDA device `device`.  options_json may be NULL or a
- * JSON object with optional keys "persistent_ctas_per_sm" (int),
- * "autotune_cache" (path string).  Fails with PJ_ECUDA when no GPU of
- * compute capability 10.x is usable. */
+ * JSON object with optional keys "persistent_ctas_per_sm" (int, 0 = from
+ * occupancy), "refine_variant" (1: scalar single-precision refinement, one
+ * triangle test per lane and instruction; 2, the default: packed FP32x2
+ * refinement, two tests per lane and instruction; anything else gives
+ * PJ_EINVAL) and "autotune_cache" (path string).  Fails with PJ_ECUDA when
+ * the device is not compute capability 10.3 (GB300). */
 pj_status pj_create(pj_ctx** out, int device, const char* options_json);
 void pj_destroy(pj_ctx* ctx);
 

@@ -403,6 +403,15 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
   PJ_CK(cudaMalloc((void**)&ctx->d_snap, 64 * 4 * sizeof(long long)));
   std::string v = json_str(options_json, "persistent_ctas_per_sm");
   if (!v.empty()) ctx->ctas_per_sm = std::max(0, atoi(v.c_str()));
+  v = json_str(options_json, "refine_variant");
+  if (!v.empty()) {
+    const int rv = atoi(v.c_str());
+    if (rv != 1 && rv != 2) {
+      pj_destroy(ctx);
+      return PJ_EINVAL;
+    }
+    ctx->refine_variant = rv;
+  }
   ctx->autotune_cache = json_str(options_json, "autotune_cache");
   *out = ctx;
   return PJ_OK;

@@ -103,6 +103,7 @@ struct pj_ctx {
   std::string stats;
   pj::JoinSummary last_sum;
   int ctas_per_sm = 0;             // 0 = from occupancy
+  int refine_variant = 2;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
   std::string autotune_cache;
   // per-query workspace
   pj::DevBuf ws[48];

@@ -23,6 +23,7 @@
 
 #include "internal.h"
 #include "tritri.cuh"
+#include "tritri2.cuh"
 
 namespace pj {
 
@@ -418,7 +419,7 @@ constexpr int WARP_LIST = 128;   // straddling facet pairs kept per warp and uni
 
 template <class T>
 constexpr size_t warp_smem_bytes() {
-  return (size_t)2 * BLK * 48 + (size_t)BLK * sizeof(RecSmem<T>) + (size_t)WARP_LIST * 8;
+  return (size_t)2 * BLK * 48 + (size_t)BLK * sizeof(typename RecOf<T>::S) + (size_t)WARP_LIST * 8;
 }
 template <class T>
 constexpr size_t refine_smem_bytes() {
@@ -478,8 +479,10 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
   unsigned char* wbase = smem + warp * warp_smem_bytes<T>();
   float4* raw0 = reinterpret_cast<float4*>(wbase);
   float4* raw1 = raw0 + 3 * BLK;
-  RecSmem<T>* rec = reinterpret_cast<RecSmem<T>*>(wbase + 2 * BLK * 48);
-  uint2* list = reinterpret_cast<uint2*>(wbase + 2 * BLK * 48 + BLK * sizeof(RecSmem<T>));
+  using RecT = typename RecOf<T>::R;
+  using RecS = typename RecOf<T>::S;
+  RecS* rec = reinterpret_cast<RecS*>(wbase + 2 * BLK * 48);
+  uint2* list = reinterpret_cast<uint2*>(wbase + 2 * BLK * 48 + BLK * sizeof(RecS));
   __shared__ unsigned list_n[REFINE_WARPS];
   uint64_t* bar0 = &bars[warp][0];
   uint64_t* bar1 = &bars[warp][1];
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     const int rl = tl.rl, sl = tl.sl;
     const float4 o4 = a.origin[tl.pair];
     const bool act = lane < rl;
-    Rec<T> P;
+    RecT P;
     {
       const float4* f = a.facR + 3LL * (tl.rb + (act ? lane : 0));
       float4 A = f[0], B = f[1], C = f[2];
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
       translate(A, o4, va);
       translate(B, o4, vb);
       translate(C, o4, vc);
-      Rec<T> Q;
+      RecT Q;
       make_rec(Q, va, vb, vc, T(A.w), T(B.w), false);
       store_rec(rec[lane], Q);
     }
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     if (act) {
       ntest += (unsigned long long)sl;
       for (int j = 0; j < sl; ++j) {
-        Rec<T> Q;
+        RecT Q;
         load_rec(Q, rec[j]);
         bool maybe;
         T d2 = tri_d2(P, Q, eh, maybe);
@@ -665,6 +668,216 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
 // Bounds contribution of the queued straddling facet pairs: the 15-candidate
 // distance as in k_refine, the meeting test in double precision (exact
 // translation of the float vertices), then the same atomicMin updates.
+// ---------------------------------------------------------------- packed FP32
+// k_refine2: the single-precision refinement with two s facets per lane and
+// loop iteration (tritri2.cuh).  The s block is expanded into 16 paired
+// records; an odd last facet is paired with a copy of itself and the copy's
+// half is masked.  Unit scheduling, staging, the straddle list and the
+// reductions are those of k_refine.
+constexpr size_t warp_smem_bytes2() {
+  return (size_t)2 * BLK * 48 + (size_t)(BLK / 2) * sizeof(RecSmem2) + (size_t)WARP_LIST * 8;
+}
+constexpr size_t refine_smem_bytes2() { return REFINE_WARPS * warp_smem_bytes2(); }
+
+template <bool FULL>
+__global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
+  using T = float;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[REFINE_WARPS][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wbase = smem + warp * warp_smem_bytes2();
+  float4* raw0 = reinterpret_cast<float4*>(wbase);
+  float4* raw1 = raw0 + 3 * BLK;
+  RecSmem2* rec = reinterpret_cast<RecSmem2*>(wbase + 2 * BLK * 48);
+  uint2* list = reinterpret_cast<uint2*>(wbase + 2 * BLK * 48 + (BLK / 2) * sizeof(RecSmem2));
+  __shared__ unsigned list_n[REFINE_WARPS];
+  uint64_t* bar0 = &bars[warp][0];
+  uint64_t* bar1 = &bars[warp][1];
+  if (lane == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    fence_mbar_init();
+    list_n[warp] = 0;
+  }
+  __syncwarp();
+  const T INF = inf_(T(0));
+  const unsigned FULLM = 0xffffffffu;
+  const int64_t NT = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
+  uint32_t ph0 = 0, ph1 = 0;
+  int b = 0;
+  unsigned long long ntest = 0;
+
+  int64_t cur = 0;
+  if (lane == 0) {
+    cur = atomicAdd(a.counter, 1);
+    if (cur < NT) {
+      const Tile t0 = a.tiles[cur];
+      mbar_arrive_expect_tx(bar0, (uint32_t)t0.sl * 48u);
+      tma_load_1d(raw0, a.facS + 3LL * t0.sb, (uint32_t)t0.sl * 48u, bar0);
+    }
+  }
+  cur = __shfl_sync(FULLM, cur, 0);
+  while (cur < NT) {
+    int64_t nxt = 0;
+    if (lane == 0) {
+      nxt = atomicAdd(a.counter, 1);
+      if (nxt < NT) {
+        const Tile tn = a.tiles[nxt];
+        fence_proxy_async();
+        uint64_t* bn = b ? bar0 : bar1;
+        mbar_arrive_expect_tx(bn, (uint32_t)tn.sl * 48u);
+        tma_load_1d(b ? raw0 : raw1, a.facS + 3LL * tn.sb, (uint32_t)tn.sl * 48u, bn);
+      }
+    }
+    nxt = __shfl_sync(FULLM, nxt, 0);
+    const Tile tl = a.tiles[cur];
+    const int rl = tl.rl, sl = tl.sl;
+    const float4 o4 = a.origin[tl.pair];
+    const bool act = lane < rl;
+    RecL2 P;
+    T Pph, Phd;
+    {
+      const float4* f = a.facR + 3LL * (tl.rb + (act ? lane : 0));
+      float4 A = f[0], B = f[1], C = f[2];
+      T va[3], vb[3], vc[3];
+      translate(A, o4, va);
+      translate(B, o4, vb);
+      translate(C, o4, vc);
+      RecL R;
+      make_rec(R, va, vb, vc, T(A.w), T(B.w), true);
+      dup_rec(P, R);
+      Pph = R.ph;
+      Phd = R.hd;
+    }
+    const bool ok = mbar_wait_bounded(b ? bar1 : bar0, b ? ph1 : ph0, MBAR_POLL_LIMIT);
+    if (__any_sync(FULLM, !ok)) {
+      if (lane == 0) {
+        set_err(a.err, ERR_MBAR_TIMEOUT);
+        if (nxt < NT) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
+      }
+      break;
+    }
+    if (b) ph1 ^= 1u;
+    else ph0 ^= 1u;
+    const float4* raw = b ? raw1 : raw0;
+    if (a.early && __ldcg(a.flag + tl.pair)) {
+      __syncwarp();
+      cur = nxt;
+      b ^= 1;
+      continue;
+    }
+    const int sl2 = (sl + 1) & ~1;   // facets in paired records (odd: last one twice)
+    if (lane < sl2) {
+      const int fi = min(lane, sl - 1);
+      float4 A = raw[3 * fi], B = raw[3 * fi + 1], C = raw[3 * fi + 2];
+      T va[3], vb[3], vc[3];
+      translate(A, o4, va);
+      translate(B, o4, vb);
+      translate(C, o4, vc);
+      RecL Q;
+      make_rec(Q, va, vb, vc, T(A.w), T(B.w), false);
+      store_half(rec[lane >> 1], lane & 1, Q);
+    }
+    __syncwarp();
+
+    T lbm = INF, ubu = INF, d2m = INF;
+    bool anyposs = false;
+    const T eh = T(tl.eh);
+    if (act) {
+      ntest += (unsigned long long)sl;
+      for (int jp = 0; jp < (sl2 >> 1); ++jp) {
+        RecL2 Q;
+        load_pair(Q, rec[jp]);
+        bool m0, m1;
+        const f2 d2p = tri_d2x2(P, Q, eh, m0, m1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * jp + h;
+          if (j >= sl) continue;
+          const T d2 = h ? hi2(d2p) : lo2(d2p);
+          bool maybe = h ? m1 : m0;
+          if (maybe && boxes_apart_half(P, rec[jp], h)) maybe = false;
+          const T qph = rec[jp].x[2 * F_PH + h], qhd = rec[jp].x[2 * F_HD + h];
+          if (!maybe) {
+            if (FULL) {
+              d2m = min(d2m, d2);
+            } else {
+              T d = sqrt_test(d2);
+              lbm = min(lbm, sub_rd(d, add_ru(Pph, qph)));
+              ubu = min(ubu, add_ru(d, add_ru(Phd, qhd)));
+            }
+          } else if (!FULL && !a.exact_cross) {
+            T d = sqrt_test(d2);
+            lbm = min(lbm, -add_ru(Pph, qph));
+            ubu = min(ubu, add_ru(d, add_ru(Phd, qhd)));
+          } else {
+            unsigned li = atomicAdd(&list_n[warp], 1u);
+            if (li < WARP_LIST) {
+              list[li] = make_uint2((unsigned)(lane | (j << 8)), __float_as_uint((float)d2));
+            } else {
+              unsigned qk = atomicAdd(a.qcount, 1u);
+              if (qk < a.qcap) {
+                a.queue[qk] = make_int4(tl.pair, tl.rb + lane, tl.sb + j, __float_as_int(tl.eps));
+              } else if (FULL) {
+                anyposs = true;
+                d2m = min(d2m, d2);
+              } else {
+                T d = sqrt_test(d2);
+                lbm = min(lbm, -add_ru(Pph, qph));
+                ubu = min(ubu, add_ru(d, add_ru(Phd, qhd)));
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+    const unsigned nl = min(list_n[warp], (unsigned)WARP_LIST);
+    T ubc = INF;
+    if (nl) {
+      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, a.facR + 3LL * tl.rb, raw, o4);
+      lbm = min(lbm, lo.lbm);
+      ubu = min(ubu, lo.ubu);
+      ubc = lo.ubc;
+      d2m = min(d2m, lo.d2m);
+      anyposs = anyposs || lo.anyposs;
+    }
+    __syncwarp();
+    if (lane == 0) list_n[warp] = 0;
+    T lbv, ubv, midv = INF;
+    if (FULL) {
+      T d = d2m < INF ? sqrt_rn(d2m) : INF;
+      midv = ubc < INF ? T(0) : d;
+      lbv = anyposs ? T(0) : d;
+      ubv = d;
+    } else {
+      lbv = lbm;
+      ubv = ubu;
+    }
+    lbv = warp_min(lbv);
+    ubv = warp_min(ubv);
+    ubc = warp_min(ubc);
+    if (FULL) midv = warp_min(midv);
+    if (lane == 0) {
+      const T eps = T(tl.eps);
+      T lb = lbv < INF ? sub_rd(lbv, eps) : INF;
+      lb = max(lb, T(0));
+      T ub = ubv < INF ? add_ru(ubv, eps) : INF;
+      ub = min(ub, ubc);
+      using Bt = Bits<T>;
+      if (lb < INF) atomicMin(&((typename Bt::U*)a.lb)[tl.pair], Bt::enc(lb));
+      if (ub < INF) atomicMin(&((typename Bt::U*)a.ub)[tl.pair], Bt::enc(ub));
+      if (FULL && midv < INF) atomicMin(&((typename Bt::U*)a.mid)[tl.pair], Bt::enc(midv));
+      if (a.early && ub <= a.thr[tl.pair]) a.flag[tl.pair] = 1;
+    }
+    __syncwarp();
+    cur = nxt;
+    b ^= 1;
+  }
+  ntest = warp_sum_u64(ntest);
+  if (lane == 0 && ntest) atomicAdd(a.ntests, ntest);
+}
+
 template <class T, bool FULL>
 __global__ void __launch_bounds__(256) k_cross_fix(RefineArgs a) {
   const unsigned n = min(*a.qcount, a.qcap);
@@ -683,7 +896,7 @@ __global__ void __launch_bounds__(256) k_cross_fix(RefineArgs a) {
     translate(s0, o4, wa);
     translate(s1, o4, wb);
     translate(s2, o4, wc);
-    Rec<T> P, Q;
+    typename RecOf<T>::R P, Q;
     make_rec(P, va, vb, vc, T(r0.w), T(r1.w), true);
     make_rec(Q, wa, wb, wc, T(s0.w), T(s1.w), false);
     bool maybe;
@@ -732,13 +945,40 @@ static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaSt
   }
 }
 
+template <bool FULL>
+static void launch_refine2(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaStream_t st) {
+  auto kern = k_refine2<FULL>;
+  const size_t smem = refine_smem_bytes2();
+  PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, REFINE_THREADS, smem));
+  if (occ < 1) occ = 1;
+  if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
+  int64_t grid = (int64_t)occ * ctx->sm_count;
+  if (n_tiles >= 0) grid = std::min<int64_t>((n_tiles + REFINE_WARPS - 1) / REFINE_WARPS, grid);
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  if (args.qcap > 0) {
+    k_cross_fix<float, FULL><<<ctx->sm_count * 4, 256, 0, st>>>(args);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+  }
+}
+
+// FP64 steps use k_refine<double>; FP32 steps the packed kernel (variant 2,
+// default) or the scalar one (variant 1), chosen per context.
 static void dispatch_refine(pj_ctx* ctx, RefineArgs& a, int64_t n_tiles, const StepSpec& sp, cudaStream_t st) {
   if (sp.fp64) {
     if (sp.full) launch_refine<double, true>(ctx, a, n_tiles, st);
     else launch_refine<double, false>(ctx, a, n_tiles, st);
-  } else {
+  } else if (ctx->refine_variant == 1) {
     if (sp.full) launch_refine<float, true>(ctx, a, n_tiles, st);
     else launch_refine<float, false>(ctx, a, n_tiles, st);
+  } else {
+    if (sp.full) launch_refine2<true>(ctx, a, n_tiles, st);
+    else launch_refine2<false>(ctx, a, n_tiles, st);
   }
 }
 
@@ -870,7 +1110,7 @@ __global__ void k_tri_dist(const float* P, const float* Q, int64_t n, double* ou
       qv[v][k] = T(b[3 * v + k]) - T(o[k]);
       rho = fmaxf(rho, fmaxf(fabsf(a[3 * v + k] - o[k]), fabsf(b[3 * v + k] - o[k])));
     }
-  Rec<T> RP, RQ;
+  typename RecOf<T>::R RP, RQ;
   make_rec(RP, pv[0], pv[1], pv[2], T(0), T(0), true);
   make_rec(RQ, qv[0], qv[1], qv[2], T(0), T(0), false);
 #pragma unroll

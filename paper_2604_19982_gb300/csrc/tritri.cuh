@@ -275,17 +275,182 @@ __device__ __forceinline__ T tri_d2(const Rec<T>& P, const Rec<T>& Q, T eh, bool
 // Are the boxes of the two facets strictly apart on some axis?  Then they
 // cannot meet.  Rounding of the pair-local translation is monotone, so a
 // strict separation of the computed coordinates implies one of the exact.
-template <class T>
-__device__ __forceinline__ bool boxes_apart(const Rec<T>& P, const Rec<T>& Q) {
+template <class R>
+__device__ __forceinline__ bool boxes_apart(const R& P, const R& Q) {
   bool apart = false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    T pmin = min(P.v[0][k], min(P.v[1][k], P.v[2][k])), pmax = max(P.v[0][k], max(P.v[1][k], P.v[2][k]));
-    T qmin = min(Q.v[0][k], min(Q.v[1][k], Q.v[2][k])), qmax = max(Q.v[0][k], max(Q.v[1][k], Q.v[2][k]));
+    auto pmin = min(P.v[0][k], min(P.v[1][k], P.v[2][k])), pmax = max(P.v[0][k], max(P.v[1][k], P.v[2][k]));
+    auto qmin = min(Q.v[0][k], min(Q.v[1][k], Q.v[2][k])), qmax = max(Q.v[0][k], max(Q.v[1][k], Q.v[2][k]));
     apart = apart || (pmax < qmin) || (qmax < pmin);
   }
   return apart;
 }
+
+// ---------------------------------------------------------------- FP32 form
+// The single-precision kernels evaluate the same 15 candidates without the
+// 27 vertex differences: every plane, inside and edge product against a
+// vertex x of the other facet is taken as (a . x) - k with the constant k
+// of the record, so that only the three differences an edge pair's closest
+// points need are formed, when they are needed.  Record constants:
+//   c = n . v0 - hoff,   mc_i = m_i . v_i,   ev_i = e_i . v_i.
+// Both sides use the same orientation (n, m_i = n x e_i, not negated).  The
+// rounding of (a . x) - k is a few u rho (rho: coordinate bound of the pair
+// frame), far inside the margins eh / eps of fp32_margins.
+struct RecL {
+  float v[3][3];
+  float e[3][3];
+  float ee[3], iee[3];
+  float n[3];
+  float m[3][3];
+  float c, mc[3], ev[3];
+  float hd, ph;
+};
+
+__device__ __forceinline__ void make_rec(RecL& R, const float a[3], const float b[3], const float c[3], float hd,
+                                         float ph, bool) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    R.v[0][k] = a[k];
+    R.v[1][k] = b[k];
+    R.v[2][k] = c[k];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) R.e[i][k] = R.v[(i + 1) % 3][k] - R.v[i][k];
+    R.ee[i] = dot3(R.e[i], R.e[i]);
+    R.iee[i] = R.ee[i] > 0.f ? 1.f / R.ee[i] : 0.f;
+  }
+  float cx = R.e[0][1] * R.e[1][2] - R.e[0][2] * R.e[1][1];
+  float cy = R.e[0][2] * R.e[1][0] - R.e[0][0] * R.e[1][2];
+  float cz = R.e[0][0] * R.e[1][1] - R.e[0][1] * R.e[1][0];
+  float c2 = cx * cx + cy * cy + cz * cz;
+  float hoff;
+  if (c2 > 0.f) {
+    float inv = 1.f / sqrt_rn(c2);
+    R.n[0] = cx * inv;
+    R.n[1] = cy * inv;
+    R.n[2] = cz * inv;
+    hoff = 0.f;
+  } else {
+    R.n[0] = R.n[1] = R.n[2] = 0.f;
+    hoff = inf_(0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R.m[i][0] = R.n[1] * R.e[i][2] - R.n[2] * R.e[i][1];
+    R.m[i][1] = R.n[2] * R.e[i][0] - R.n[0] * R.e[i][2];
+    R.m[i][2] = R.n[0] * R.e[i][1] - R.n[1] * R.e[i][0];
+    R.mc[i] = dot3(R.m[i], R.v[i]);
+    R.ev[i] = dot3(R.e[i], R.v[i]);
+  }
+  R.c = dot3(R.n, R.v[0]) - hoff;
+  R.hd = hd;
+  R.ph = ph;
+}
+
+// Shared-memory image of a RecL: 48 floats, 12 float4 loads.
+struct RecSmemL {
+  float x[48];
+};
+
+__device__ __forceinline__ void store_rec(RecSmemL& S, const RecL& R) {
+  float4* q = reinterpret_cast<float4*>(S.x);
+  q[0] = make_float4(R.v[0][0], R.v[0][1], R.v[0][2], R.hd);
+  q[1] = make_float4(R.v[1][0], R.v[1][1], R.v[1][2], R.ph);
+  q[2] = make_float4(R.v[2][0], R.v[2][1], R.v[2][2], R.c);
+  q[3] = make_float4(R.e[0][0], R.e[0][1], R.e[0][2], R.ee[0]);
+  q[4] = make_float4(R.e[1][0], R.e[1][1], R.e[1][2], R.ee[1]);
+  q[5] = make_float4(R.e[2][0], R.e[2][1], R.e[2][2], R.ee[2]);
+  q[6] = make_float4(R.n[0], R.n[1], R.n[2], R.iee[0]);
+  q[7] = make_float4(R.m[0][0], R.m[0][1], R.m[0][2], R.iee[1]);
+  q[8] = make_float4(R.m[1][0], R.m[1][1], R.m[1][2], R.iee[2]);
+  q[9] = make_float4(R.m[2][0], R.m[2][1], R.m[2][2], R.mc[0]);
+  q[10] = make_float4(R.ev[0], R.ev[1], R.ev[2], R.mc[1]);
+  q[11] = make_float4(R.mc[2], 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void load_rec(RecL& R, const RecSmemL& S) {
+  const float4* q = reinterpret_cast<const float4*>(S.x);
+  float4 a[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a[k] = q[k];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R.v[i][0] = a[i].x; R.v[i][1] = a[i].y; R.v[i][2] = a[i].z;
+    R.e[i][0] = a[3 + i].x; R.e[i][1] = a[3 + i].y; R.e[i][2] = a[3 + i].z; R.ee[i] = a[3 + i].w;
+    R.m[i][0] = a[7 + i].x; R.m[i][1] = a[7 + i].y; R.m[i][2] = a[7 + i].z;
+  }
+  R.hd = a[0].w; R.ph = a[1].w; R.c = a[2].w;
+  R.n[0] = a[6].x; R.n[1] = a[6].y; R.n[2] = a[6].z;
+  R.iee[0] = a[6].w; R.iee[1] = a[7].w; R.iee[2] = a[8].w;
+  R.mc[0] = a[9].w; R.mc[1] = a[10].w; R.mc[2] = a[11].x;
+  R.ev[0] = a[10].x; R.ev[1] = a[10].y; R.ev[2] = a[10].z;
+}
+
+// (a . x) - k as one FMA chain
+__device__ __forceinline__ float affine3(const float a[3], const float x[3], float k) {
+  return fmaf(a[2], x[2], fmaf(a[1], x[1], fmaf(a[0], x[0], -k)));
+}
+
+// Squared minimum over the 15 candidate distances of P and Q (as tri_d2),
+// with `maybe` set when both facets straddle the other's plane within eh.
+__device__ __forceinline__ float tri_d2(const RecL& P, const RecL& Q, float eh, bool& maybe) {
+  const float INF = inf_(0.f);
+  float d2 = INF;
+  float hP[3], hQ[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {   // vertices of P against Q's interior
+    hP[i] = affine3(Q.n, P.v[i], Q.c);
+    const float g = min(affine3(Q.m[0], P.v[i], Q.mc[0]),
+                        min(affine3(Q.m[1], P.v[i], Q.mc[1]), affine3(Q.m[2], P.v[i], Q.mc[2])));
+    d2 = min(d2, g >= 0.f ? hP[i] * hP[i] : INF);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {   // vertices of Q against P's interior
+    hQ[j] = affine3(P.n, Q.v[j], P.c);
+    const float g = min(affine3(P.m[0], Q.v[j], P.mc[0]),
+                        min(affine3(P.m[1], Q.v[j], P.mc[1]), affine3(P.m[2], Q.v[j], P.mc[2])));
+    d2 = min(d2, g >= 0.f ? hQ[j] * hQ[j] : INF);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)     // edge i of P against edge j of Q
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float* d1 = P.e[i];
+      const float* dq = Q.e[j];
+      const float b = dot3(d1, dq);
+      const float c = -affine3(d1, Q.v[j], P.ev[i]);   // d1 . (p_i - q_j)
+      const float f = affine3(dq, P.v[i], Q.ev[j]);    // dq . (p_i - q_j)
+      const float den = fmaf(P.ee[i], Q.ee[j], -b * b);
+      const float num = fmaf(b, f, -c * Q.ee[j]);
+      float s = __saturatef(__fdividef(num, den));
+      const float t = __saturatef(fmaf(b, s, f) * Q.iee[j]);
+      s = __saturatef(fmaf(b, t, -c) * P.iee[i]);
+      const float wx = fmaf(s, d1[0], P.v[i][0]) - fmaf(t, dq[0], Q.v[j][0]);
+      const float wy = fmaf(s, d1[1], P.v[i][1]) - fmaf(t, dq[1], Q.v[j][1]);
+      const float wz = fmaf(s, d1[2], P.v[i][2]) - fmaf(t, dq[2], Q.v[j][2]);
+      d2 = min(d2, fmaf(wz, wz, fmaf(wy, wy, wx * wx)));
+    }
+  const float pmin = min(hP[0], min(hP[1], hP[2])), pmax = max(hP[0], max(hP[1], hP[2]));
+  const float qmin = min(hQ[0], min(hQ[1], hQ[2])), qmax = max(hQ[0], max(hQ[1], hQ[2]));
+  maybe = (pmin <= eh) && (pmax >= -eh) && (qmin <= eh) && (qmax >= -eh);
+  return d2;
+}
+
+// Record types per precision: FP32 kernels use the form above, FP64 the
+// difference form (which reproduces the oracle's arithmetic).
+template <class T>
+struct RecOf {
+  using R = Rec<T>;
+  using S = RecSmem<T>;
+};
+template <>
+struct RecOf<float> {
+  using R = RecL;
+  using S = RecSmemL;
+};
 
 // Crossing decision in double precision from raw float vertices (the three
 // float4 of each facet, .w ignored) and a float origin: differences of
