@@ -422,13 +422,15 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   }
   if (!fp64 && n > 0) {
     // pairs whose single-precision bracket still straddles tau at full
-    // resolution (status REDECIDE) are refined again in double precision
+    // resolution (status REDECIDE) are refined again in double precision;
+    // the decision only asks d <= tau, so units farther apart than tau may
+    // be skipped
     StepSpec sp;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
     sp.full = true;
     sp.fp64 = true;
-    sp.cull = false;
+    sp.cull = cull;
     sp.want = REDECIDE;
     sp.step = Lmax - 1;
     init_bounds(ctx, n, sp, st);
@@ -443,12 +445,14 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
                                                                (const uint8_t*)ctx->ws[WS_EXACT].p);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
+    // every result pair has d <= tau, so its closest facet pair lies in a
+    // unit within tau: pruned units cannot hold the minimum
     StepSpec sp;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
     sp.full = true;
     sp.fp64 = true;
-    sp.cull = false;
+    sp.cull = cull;
     sp.want = MAKE_EXACT;
     sp.step = Lmax - 1;
     init_bounds(ctx, n, sp, st);

@@ -631,7 +631,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     sp.lodS = S->L - 1;
     sp.full = true;
     sp.fp64 = true;
-    sp.cull = true;
+    sp.cull = cull;
     sp.want = UNDECIDED;
     sp.step = STEP_ALL;
     pass(sp, UNDECIDED);
@@ -643,7 +643,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     sp.lodS = S->L - 1;
     sp.full = true;
     sp.fp64 = true;
-    sp.cull = false;
+    sp.cull = cull;   // result pairs lie within theta_r < thr
     sp.want = MAKE_EXACT;
     sp.step = STEP_ALL;
     init_bounds(ctx, n, sp, st);
