@@ -54,7 +54,17 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-path measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="blobs20k", choices=["blobs20k", "knn50k", "tubes2k", "stream"],
+                    help="blobs20k (default) is the benchmark line; the others measure the k-NN, "
+                         "tubes-vs-blobs and streamed workloads for the profiles")
+    ap.add_argument("--stream-chunks", type=int, default=8,
+                    help="stream workload: chunks of 31,250 blobs streamed against 20,000 tubes (64 = full size)")
     return ap.parse_args()
+
+
+def alu_peak(nsm: int, mhz: float = 2070.0) -> float:
+    """FP32 ALU peak in TFLOP/s: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return nsm * 128 * 2 * mhz * 1e6 / 1e12
 
 
 # ----------------------------------------------------------------- clocks
@@ -307,9 +317,10 @@ def ours_arm(args):
     results = sum(n for _, n in stats) // max(1, args.steps)
 
     # roofline of the dominant kernel: the single-precision refine kernel
-    peak32 = ctx.fma_peak(False) / 1000.0          # TFLOP/s measured now
+    # against the ALU peak derived from unit counts and the maximum clock
+    measured32 = ctx.fma_peak(False) / 1000.0      # FMA-chain micro-benchmark, TFLOP/s
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    nominal = nsm * 128 * 2 * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
+    peak32 = alu_peak(nsm)
     achieved = tests_fp32 * FLOPS_PER_TEST / (kms_fp32 / 1000.0) / 1e12 if kms_fp32 > 0 else 0.0
     traffic = None
     prof = os.path.join(ROOT, "profiles", "refine_fp32_traffic.json")
@@ -320,9 +331,10 @@ def ours_arm(args):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                 "frac": achieved / peak32 if peak32 else None, "traffic": traffic,
-                "kernel": "k_refine<float> (tile refinement, FP32)",
-                "peak_kind": "measured FMA-chain throughput (pj_fma_peak), FMA = 2 flops",
-                "nominal_peak_at_median_clock": nominal, "flops_per_test": FLOPS_PER_TEST,
+                "kernel": "k_refine2 (single-precision refinement, packed FP32x2)",
+                "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x 2.070 GHz",
+                "measured_fma_peak": measured32, "frac_of_measured": achieved / measured32 if measured32 else None,
+                "flops_per_test": FLOPS_PER_TEST,
                 "kernel_ms_per_step": kms_fp32 / args.steps, "tests_per_step": tests_fp32 // args.steps}
 
     plain = None
@@ -409,10 +421,142 @@ def ours_arm(args):
         dist.destroy_process_group()
 
 
+def extra_arm(args):
+    """k-NN, tubes-vs-blobs and streamed workloads (one GPU): tuned path, the
+    plain FP64 path on the same inputs (tubes: on a 100-tube subset, the full
+    plain join being hours of FP64 work), refine-kernel roofline."""
+    from synth import configs
+    if args.workload == "stream":
+        # host-side generation in spawned processes, before any CUDA call
+        procs = max(1, min(16, os.cpu_count() or 1))
+        S_stream = configs.tube_set_parallel(20000, 5000.0, 0, 1, procs=procs)
+        chunks = configs.stream_chunks_parallel(range(args.stream_chunks), procs=procs)
+    import torch
+    from paper_2604_19982_gb300 import pj
+
+    torch.cuda.set_device(0)
+    ctx = pj.Context(0)
+    stream = torch.cuda.Stream()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    extra = {}
+    if args.workload == "knn50k":
+        desc = ("knn50k: R, S = 50,000 sub-3 blobs each, 20-cluster Gaussian mixture (sigma 15) in a cube of "
+                "side 1000, k = 3; proposal fitted on the seed-1 run")
+        w1 = configs.knn50k(seed=1)
+        a, b = ctx.load_set(w1.R), ctx.load_set(w1.S)
+        extra["proposal_rmse_log1p"] = ctx.mlp_fit(a, b, pj.KNN, k=3, max_pairs=200000, epochs=30, seed=1)
+        a.free()
+        b.free()
+        w = configs.knn50k()
+        gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
+        q = dict(pred=pj.KNN, k=3)
+        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.USE_MLP)
+        untrained = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
+        plain = dict(prec=pj.FP64, flags=0)
+        gP = gR
+    elif args.workload == "tubes2k":
+        desc = "tubes2k: 2,000 tubes (2k-50k facets) x 200,000 sub-3 blobs, side 2,320, within tau = 2"
+        w = configs.tubes2k()
+        gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
+        q = dict(pred=pj.WITHIN, tau=2.0)
+        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
+        untrained = None
+        plain = dict(prec=pj.FP64, flags=0)
+        gP = ctx.load_set(configs.tube_set(2000, 2320.0, 0, 0, start=0, count=100))
+        extra["plain_inputs"] = "the first 100 tubes of R against all of S"
+    else:
+        n_ch = args.stream_chunks
+        desc = (f"stream: {n_ch} chunks of 31,250 sub-3 blobs ({n_ch * 31250:,} objects) streamed against "
+                "20,000 tubes, side 5,000, within tau = 1")
+        gS = ctx.load_set(S_stream)
+        gR = ctx.load_set_streamed(31250 * n_ch, n_ch, lambda c: chunks[c])
+        q = dict(pred=pj.WITHIN, tau=1.0)
+        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
+        untrained = None
+        plain = None
+        gP = None
+        # pinned host-to-device copy peak: 1 GiB, best of 5
+        h = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+        d = torch.empty_like(h, device="cuda")
+        best = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            d.copy_(h, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, h.numel() * 4 / (e0.elapsed_time(e1) / 1000.0) / 1e9)
+        extra["h2d_peak_gbs"] = best
+        del h, d
+
+    def run(R, mode):
+        ctx.join(R, gS, stream=stream.cuda_stream, **q, **mode)
+        return ctx.stats()
+
+    for _ in range(max(1, args.warmup)):
+        run(gR, tuned)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    stats = []
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        stats.append(run(gR, tuned))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1000.0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) if args.workload != "stream" else wall
+    pairs = sum(st["candidates"] for st in stats)
+    tests32 = sum(st["tests_fp32"] for st in stats)
+    kms32 = sum(st["refine_ms_fp32"] for st in stats)
+    value = pairs / (ms / 1000.0)
+    achieved = tests32 * FLOPS_PER_TEST / (kms32 / 1000.0) / 1e12 if kms32 > 0 else 0.0
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": max(1, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": desc, "flags": tuned["flags"], "candidate_pairs_per_step": pairs // args.steps,
+                      "results_per_step": stats[-1]["results"]},
+           "tri_tests_per_s": sum(st["tests_fp32"] + st["tests_fp64"] for st in stats) / (ms / 1000.0),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak(nsm), "unit": "TFLOP/s",
+                        "frac": achieved / alu_peak(nsm), "kernel": "k_refine2 (single-precision refinement)",
+                        "kernel_ms_per_step": kms32 / args.steps},
+           "last_step_stats": {k: v for k, v in stats[-1].items() if k != "steps"},
+           "clocks": clk}
+    out.update(extra)
+    if untrained is not None:
+        st = run(gR, untrained)
+        t = time.perf_counter()
+        st = run(gR, untrained)
+        out["without_proposal"] = {"ms": (time.perf_counter() - t) * 1000.0, "tests": st["tests_fp32"] + st["tests_fp64"]}
+        out["with_proposal_tests"] = stats[-1]["tests_fp32"] + stats[-1]["tests_fp64"]
+    if plain is not None and not args.no_plain:
+        t = time.perf_counter()
+        st = run(gP, plain)
+        pms = (time.perf_counter() - t) * 1000.0
+        if gP is not gR:
+            t = time.perf_counter()
+            st2 = run(gP, tuned)
+            tms = (time.perf_counter() - t) * 1000.0
+            out["plain"] = {"value": st["candidates"] / (pms / 1000.0), "ms": pms, "dtype": "f64",
+                            "tuned_same_inputs": {"value": st2["candidates"] / (tms / 1000.0), "ms": tms}}
+            out["speedup_vs_plain"] = (st2["candidates"] / tms) / (st["candidates"] / pms)
+        else:
+            out["plain"] = {"value": st["candidates"] / (pms / 1000.0), "ms": pms, "dtype": "f64"}
+            out["speedup_vs_plain"] = value / out["plain"]["value"]
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload != "blobs20k":
+        extra_arm(args)
     else:
         ours_arm(args)
 

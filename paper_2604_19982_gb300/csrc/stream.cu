@@ -140,6 +140,32 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
   P.bytes = at;
 }
 
+// Copy the pieces into the pinned slot with several host threads (the
+// chunk is hundreds of MB; one thread's memcpy would pace the pipeline).
+void pack_parallel(const std::vector<Piece>& pieces, unsigned char* dst) {
+  constexpr size_t SLICE = size_t(4) << 20;
+  struct Job {
+    const unsigned char* src;
+    size_t off, bytes;
+  };
+  std::vector<Job> jobs;
+  for (const Piece& pc : pieces)
+    for (size_t a = 0; a < pc.bytes; a += SLICE)
+      jobs.push_back(Job{static_cast<const unsigned char*>(pc.src) + a, pc.off + a, std::min(SLICE, pc.bytes - a)});
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const unsigned T = (unsigned)std::min<size_t>(std::min(8u, hw), jobs.size());
+  if (T <= 1) {
+    for (const Job& j : jobs) memcpy(dst + j.off, j.src, j.bytes);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < T; ++t)
+    th.emplace_back([&, t]() {
+      for (size_t k = t; k < jobs.size(); k += T) memcpy(dst + jobs[k].off, jobs[k].src, jobs[k].bytes);
+    });
+  for (auto& x : th) x.join();
+}
+
 double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -227,7 +253,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
               throw ApiError{PJ_ENOMEM, "pinned staging allocation failed"};
             hc = P.bytes;
           }
-          for (const Piece& pc : pieces) memcpy(static_cast<unsigned char*>(hp) + pc.off, pc.src, pc.bytes);
+          pack_parallel(pieces, static_cast<unsigned char*>(hp));
           ms_pack += ms_since(t0);
         } catch (const ApiError& e) {
           err = e.st;

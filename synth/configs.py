@@ -21,7 +21,7 @@ import dataclasses
 
 import numpy as np
 
-from .mesh import MeshSet, _blob_params, make_blobs, make_tubes
+from .mesh import MeshSet, _blob_params, concat, make_blobs, make_tubes
 
 BLOCK = 1024  # objects per random-stream block
 
@@ -139,3 +139,30 @@ def stream2m_R_chunk(chunk: int, seed: int = 0, n: int = 2_000_000, chunks: int 
     start = chunk * per
     count = max(0, min(n, start + per) - start)
     return blob_set(n, side, seed, 0, start=start, count=count)
+
+
+def _tube_part(args):
+    n, side, seed, set_id, start, count, lr = args
+    return tube_set(n, side, seed, set_id, start=start, count=count, length_range=lr)
+
+
+def tube_set_parallel(n: int, side: float, seed: int, set_id: int, procs: int = 16,
+                      length_range=(50.0, 800.0)) -> MeshSet:
+    """tube_set generated in ``procs`` spawned processes (same objects: each
+    tube has its own random stream).  Start it before any CUDA call."""
+    import multiprocessing as mp
+    step = (n + procs - 1) // procs
+    parts = [(n, side, seed, set_id, a, min(step, n - a), length_range) for a in range(0, n, step)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return concat(pool.map(_tube_part, parts))
+
+
+def _stream_chunk(args):
+    return stream2m_R_chunk(*args)
+
+
+def stream_chunks_parallel(chunks, procs: int = 16, seed: int = 0):
+    """Chunks of the streamed workload's R, generated in spawned processes."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_stream_chunk, [(c, seed) for c in chunks])

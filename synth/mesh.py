@@ -128,6 +128,40 @@ class MeshSet:
         return int(self.face_off[lod][-1])
 
 
+def concat(sets) -> MeshSet:
+    """One MeshSet holding the objects of ``sets`` in order (same LoD count;
+    a LoD with shared topology must use one template in every part)."""
+    sets = list(sets)
+    L = sets[0].n_lods
+    verts, voff, faces, foff, hd, ph = [], [], [], [], [], []
+    for l in range(L):
+        shared = sets[0].face_off[l] is None
+        # LoDs that share one vertex array in every part keep sharing it
+        same_v = [next((m for m in range(l) if x.verts[m] is x.verts[l]), None) for x in sets]
+        if same_v[0] is not None and all(v == same_v[0] for v in same_v):
+            verts.append(verts[same_v[0]])
+            voff.append(voff[same_v[0]])
+        else:
+            verts.append(np.concatenate([x.verts[l] for x in sets]))
+            offs = [np.asarray(sets[0].vert_off[l], np.int64)]
+            for x in sets[1:]:
+                offs.append(np.asarray(x.vert_off[l][1:], np.int64) + offs[-1][-1])
+            voff.append(np.concatenate(offs))
+        if shared:
+            faces.append(sets[0].faces[l])
+            foff.append(None)
+        else:
+            faces.append(np.concatenate([x.faces[l] for x in sets]))
+            offs = [np.asarray(sets[0].face_off[l], np.int64)]
+            for x in sets[1:]:
+                offs.append(np.asarray(x.face_off[l][1:], np.int64) + offs[-1][-1])
+            foff.append(np.concatenate(offs))
+        hd.append(None if sets[0].hd[l] is None else np.concatenate([x.hd[l] for x in sets]))
+        ph.append(None if sets[0].ph[l] is None else np.concatenate([x.ph[l] for x in sets]))
+    return MeshSet(n=sum(x.n for x in sets), n_lods=L, verts=verts, vert_off=voff, faces=faces, face_off=foff,
+                   hd=hd, ph=ph, anchor=np.concatenate([x.anchor for x in sets]), kind=sets[0].kind)
+
+
 # --------------------------------------------------------------------------
 # icosphere with a hierarchical face order (children of face f are 4f..4f+3)
 
