@@ -1,6 +1,7 @@
 // C ABI of the join library (declared in include/pj.h): contexts, device
 // resident mesh sets and the entry points.  No exception crosses the ABI.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +19,8 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
                       cudaStream_t st, std::string& stats);
 pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                    cudaStream_t st, std::string& stats);
+pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                         cudaStream_t st, std::string& stats);
 pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                         cudaStream_t st, std::string& stats);
 void alloc_result(pj_result* res, int64_t n);
@@ -462,6 +465,8 @@ pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out) {
     PJ_CK(cudaSetDevice(ctx->device));
     (void)cudaGetLastError();  // drop a stale non-sticky error of an unrelated call
     load_set_impl(ctx, desc, s, ctx->stream);
+    static std::atomic<uint64_t> next_uid{1};
+    s->uid = next_uid.fetch_add(1);
     *out = s;
     return PJ_OK;
   } catch (const pj::CudaError& e) {
@@ -521,6 +526,7 @@ pj_status pj_join_async(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   std::string stats;
   pj_status rc;
   if (R->streamed) rc = join_streamed(ctx, R, S, q, out, st, stats);
+  else if (q->flags & PJ_AUTOTUNE) rc = join_autotuned(ctx, R, S, q, out, st, stats);
   else if (q->pred == PJ_KNN) rc = join_knn(ctx, R, S, q, out, st, stats);
   else rc = join_within(ctx, R, S, q, out, st, stats);
   ctx->stats = stats;

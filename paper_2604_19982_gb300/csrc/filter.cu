@@ -6,6 +6,7 @@
 // at most tau (a lower bound of d, so no result is lost).  Output: pairs
 // grouped by r, each group sorted by s.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 
 #include "internal.h"
@@ -187,7 +188,11 @@ static Grid make_grid(const pj_set* R, const pj_set* S, double tau) {
     lo[k] -= (float)tau + 1.f;
     hi[k] += (float)tau + 1.f;
   }
-  double h = std::max({extS + 2 * tau, extR, 1e-3});
+  // cells at least one S box (+tau) and one R box wide, and about four
+  // cells per S object (sparser grids only add empty cells to clear and scan)
+  double vol = 1.0;
+  for (int k = 0; k < 3; ++k) vol *= std::max(1e-3, (double)hi[k] - lo[k]);
+  double h = std::max({extS + 2 * tau, extR, std::cbrt(vol / (4.0 * std::max(1, S->n))), 1e-3});
   Grid G;
   for (;;) {
     int64_t tot = 1;
@@ -206,10 +211,40 @@ static Grid make_grid(const pj_set* R, const pj_set* S, double tau) {
   return G;
 }
 
+// Grid parameters and the bound on grid entries depend only on the two
+// sets and tau: kept per (R, S, tau) for repeated joins (sets are
+// immutable once loaded; streamed chunk views have uid 0 and are not kept).
+static bool grid_cached(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, Grid* G, int64_t* nids) {
+  if (!R->uid || !S->uid) return false;
+  for (auto& e : ctx->grid_cache)
+    if (e.rid == R->uid && e.sid == S->uid && e.tau == tau) {
+      memcpy(G, e.grid, sizeof(Grid));
+      *nids = e.nids;
+      return true;
+    }
+  return false;
+}
+
+static void grid_keep(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, const Grid& G, int64_t nids) {
+  if (!R->uid || !S->uid) return;
+  static_assert(sizeof(Grid) <= sizeof(GridCacheEntry::grid), "grid cache entry");
+  if (ctx->grid_cache.size() >= 8) ctx->grid_cache.erase(ctx->grid_cache.begin());
+  GridCacheEntry e;
+  e.rid = R->uid;
+  e.sid = S->uid;
+  e.tau = tau;
+  memcpy(e.grid, &G, sizeof(Grid));
+  e.nids = nids;
+  ctx->grid_cache.push_back(e);
+}
+
 FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, cudaStream_t st) {
   FilterOut out;
   if (R->n == 0 || S->n == 0) return out;
-  Grid G = make_grid(R, S, tau);
+  Grid G;
+  int64_t nids = 0;
+  const bool cached = grid_cached(ctx, R, S, tau, &G, &nids);
+  if (!cached) G = make_grid(R, S, tau);
   float ftau = (float)tau;
   if ((double)ftau < tau) ftau = nextafterf(ftau, INFINITY);
   double lim = tau * (1.0 + 1e-9);
@@ -224,17 +259,19 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   scan_i64(ctx, cnt, off, G.ncell, st);
   // grid entries bounded on the host (one extra cell per axis absorbs
   // host/device rounding of the cell index), so no synchronization here
-  int64_t nids = 0;
-  for (int o = 0; o < S->n; ++o) {
-    const float* b = &S->mbb_h[6 * o];
-    int64_t c = 1;
-    for (int k = 0; k < 3; ++k) {
-      double a0 = std::floor(((double)b[k] - tau - G.g0[k]) * G.inv_h);
-      double a1 = std::floor(((double)b[3 + k] + tau - G.g0[k]) * G.inv_h);
-      int64_t w = (int64_t)std::min<double>(G.dim[k], std::max(1.0, a1 - a0 + 3.0));
-      c *= w;
+  if (!cached) {
+    for (int o = 0; o < S->n; ++o) {
+      const float* b = &S->mbb_h[6 * o];
+      int64_t c = 1;
+      for (int k = 0; k < 3; ++k) {
+        double a0 = std::floor(((double)b[k] - tau - G.g0[k]) * G.inv_h);
+        double a1 = std::floor(((double)b[3 + k] + tau - G.g0[k]) * G.inv_h);
+        int64_t w = (int64_t)std::min<double>(G.dim[k], std::max(1.0, a1 - a0 + 3.0));
+        c *= w;
+      }
+      nids += c;
     }
-    nids += c;
+    grid_keep(ctx, R, S, tau, G, nids);
   }
   auto ids = (int32_t*)ws_get(ctx, WS_GRIDIDS, std::max<int64_t>(1, nids) * 4, st);
   PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));

@@ -64,6 +64,14 @@ struct LodData {
   int64_t maxF = 0;               // largest facet count of one object
 };
 
+// Host-side grid parameters of the within filter for one (R, S, tau).
+struct GridCacheEntry {
+  uint64_t rid = 0, sid = 0;
+  double tau = 0;
+  unsigned char grid[64];
+  int64_t nids = 0;
+};
+
 // Totals of the last join (also in its JSON stats).
 struct JoinSummary {
   int64_t candidates = 0, results = 0, units = 0;
@@ -83,6 +91,7 @@ struct pj_set {
   float* mbb = nullptr;           // device [n][6] original-surface boxes
   float* anchor = nullptr;        // device [n][3]
   std::vector<float> mbb_h;       // host copy
+  uint64_t uid = 0;               // unique per loaded set (0: a temporary view)
   // streamed R: the chunks are loaded inside pj_join
   bool streamed = false;
   int64_t n_total = 0;
@@ -102,8 +111,10 @@ struct pj_ctx {
   std::string last_error;
   std::string stats;
   pj::JoinSummary last_sum;
+  std::vector<pj::GridCacheEntry> grid_cache;
   int ctas_per_sm = 0;             // 0 = from occupancy
   int refine_variant = 2;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
+  int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
   std::string autotune_cache;
   // per-query workspace
   pj::DevBuf ws[48];

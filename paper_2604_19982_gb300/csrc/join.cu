@@ -380,6 +380,11 @@ std::string StepLog::json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* unit
 }
 
 
+__global__ void k_lod0_floor(int64_t n, uint8_t* lod0, uint8_t s) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n && lod0[p] < s) lod0[p] = s;
+}
+
 pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                       cudaStream_t st, std::string& stats) {
   Timer tall;
@@ -396,6 +401,14 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   const bool use_mlp = (q->flags & PJ_USE_MLP) != 0;
   if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
   if (use_mlp && n > 0) start_lod(ctx, R, S, n, propose(ctx, R, S, n, st), tau, st);
+  if (ctx->sched_start > 0 && n > 0) {
+    // autotuned schedule: no pair is refined before this step
+    int th = 256;
+    k_lod0_floor<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_LOD0].p,
+                                                               (uint8_t)ctx->sched_start);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+  }
   double ms_filter = tf.ms();
   const int Lmax = std::max(R->L, S->L);
   auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };

@@ -31,6 +31,8 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
                       cudaStream_t st, std::string& stats);
 pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                    cudaStream_t st, std::string& stats);
+pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                         cudaStream_t st, std::string& stats);
 
 namespace {
 
@@ -290,7 +292,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
 
   // ---- calling thread: copy, build, join
   int enqueued = 0;   // chunks whose copy has been issued
-  double ms_h2d = 0, ms_wait = 0;
+  double ms_h2d = 0, ms_wait = 0, ms_build = 0, ms_join = 0;
   size_t bytes_h2d = 0;
   // issue the copy of chunk c if it is packed (or wait for it when `block`)
   auto enqueue = [&](int c, bool block) -> bool {
@@ -377,6 +379,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
                       P.has_hd[l] ? (const float*)(dev + P.o_hd[l]) : nullptr,
                       P.has_ph[l] ? (const float*)(dev + P.o_ph[l]) : nullptr};
     }
+    Timer tb;
     PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
     build_set_kernels(ctx, &view, raw, st);
     view.mbb_h.resize((size_t)P.n * 6);
@@ -386,6 +389,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     PJ_CK(cudaStreamSynchronize(st));
     if (herr & ERR_BOUNDS) throw ApiError{PJ_EBOUNDS, "chunk " + std::to_string(c) + ": a face index lies outside its object's vertices"};
     if (herr & ERR_NONFINITE) throw ApiError{PJ_ENONFINITE, "chunk " + std::to_string(c) + ": non-finite vertex, anchor, hd or ph"};
+    ms_build += tb.ms();
     float h2d = 0;
     if (cudaEventElapsedTime(&h2d, h2d0[c & 1], h2d1[c & 1]) == cudaSuccess) ms_h2d += h2d;
     // the join of this chunk against S
@@ -394,8 +398,11 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     pj_result part;
     memset(&part, 0, sizeof part);
     std::string st_chunk;
-    pj_status rc = q->pred == PJ_KNN ? join_knn(ctx, &view, S, &qc, &part, st, st_chunk)
-                                     : join_within(ctx, &view, S, &qc, &part, st, st_chunk);
+    Timer tj;
+    pj_status rc = (q->flags & PJ_AUTOTUNE) ? join_autotuned(ctx, &view, S, &qc, &part, st, st_chunk)
+                   : q->pred == PJ_KNN         ? join_knn(ctx, &view, S, &qc, &part, st, st_chunk)
+                                               : join_within(ctx, &view, S, &qc, &part, st, st_chunk);
+    ms_join += tj.ms();
     if (rc != PJ_OK) {
       free(part.priv);
       return rc;
@@ -442,11 +449,12 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
            "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,"
            "\"bytes_h2d\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
-           "\"ms_wait_loader\":%.3f,\"ms_filter\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,"
-           "\"ms_total\":%.3f,\"launches\":%llu}",
+           "\"ms_wait_loader\":%.3f,\"ms_build\":%.3f,\"ms_join\":%.3f,\"ms_filter\":%.3f,"
+           "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"ms_total\":%.3f,\"launches\":%llu}",
            q->pred == PJ_KNN ? "knn" : "within", N, (long long)objects, (long long)tot.candidates, (long long)m,
            tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, ms_h2d,
-           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, tot.ms_filter, tot.refine_ms32,
+           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, ms_build, ms_join, tot.ms_filter,
+           tot.refine_ms32,
            tot.refine_ms64, ms_total, tot.launches);
   stats = buf;
   tot.results = m;

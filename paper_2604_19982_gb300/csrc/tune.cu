@@ -1,0 +1,184 @@
+// Autotuning of the join (PJ_AUTOTUNE): per workload key -- predicate,
+// precision, flags, tau or k, and the shapes of R and S (objects, LoDs,
+// largest facet count per LoD) -- the first join runs every candidate
+// configuration, keeps the fastest, and later joins with the same key use
+// it.  Candidates: the single-precision refinement variant (scalar, one
+// triangle test per lane and instruction, or packed FP32x2, two), and for
+// within-tau / intersection joins the LoD schedule (every pair starts at
+// step 0, 1, ... or at full resolution; with PJ_USE_MLP also the learned
+// per-pair start).  Configurations only change how the work is scheduled,
+// never a result.  Choices persist across contexts in the "autotune_cache"
+// file of pj_create, one "key choice" line each.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace pj {
+
+pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                      cudaStream_t st, std::string& stats);
+pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                   cudaStream_t st, std::string& stats);
+
+namespace {
+
+struct Choice {
+  int variant;   // 1 scalar, 2 packed
+  int start;     // -1: the query's own schedule; >= 0: every pair starts at that step
+  int encode() const { return variant * 64 + (start + 1); }
+  static Choice decode(int c) { return Choice{c / 64, c % 64 - 1}; }
+};
+
+std::string key_of(const pj_set* R, const pj_set* S, const pj_query* q) {
+  std::ostringstream k;
+  k.precision(17);
+  k << "p" << (int)q->pred << ".x" << (int)q->prec << ".f" << (q->flags & ~(uint32_t)PJ_AUTOTUNE);
+  if (q->pred == PJ_KNN) k << ".k" << q->k;
+  else k << ".t" << q->tau;
+  for (const pj_set* X : {R, S}) {
+    k << ".n" << X->n << ".L" << X->L;
+    for (int l = 0; l < X->L; ++l) k << "." << X->lod[l].maxF;
+  }
+  return k.str();
+}
+
+bool lookup(pj_ctx* ctx, const std::string& key, Choice* c) {
+  for (auto& e : ctx->tuned)
+    if (e.first == key) {
+      *c = Choice::decode(e.second);
+      return true;
+    }
+  if (!ctx->autotune_cache.empty()) {
+    std::ifstream f(ctx->autotune_cache);
+    std::string k;
+    int v;
+    while (f >> k >> v)
+      if (k == key) {
+        ctx->tuned.emplace_back(k, v);
+        *c = Choice::decode(v);
+        return true;
+      }
+  }
+  return false;
+}
+
+void store(pj_ctx* ctx, const std::string& key, const Choice& c) {
+  ctx->tuned.emplace_back(key, c.encode());
+  if (!ctx->autotune_cache.empty()) {
+    std::ofstream f(ctx->autotune_cache, std::ios::app);
+    if (f) f << key << " " << c.encode() << "\n";
+  }
+}
+
+pj_status run_with(pj_ctx* ctx, const Choice& c, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                   cudaStream_t st, std::string& stats) {
+  const int v0 = ctx->refine_variant, s0 = ctx->sched_start;
+  ctx->refine_variant = c.variant;
+  ctx->sched_start = c.start;
+  pj_status rc;
+  try {
+    rc = q->pred == PJ_KNN ? join_knn(ctx, R, S, q, out, st, stats) : join_within(ctx, R, S, q, out, st, stats);
+  } catch (...) {
+    ctx->refine_variant = v0;
+    ctx->sched_start = s0;
+    throw;
+  }
+  ctx->refine_variant = v0;
+  ctx->sched_start = s0;
+  return rc;
+}
+
+std::string with_tuning(const std::string& stats, const std::string& extra) {
+  if (stats.size() < 2 || stats.back() != '}') return stats;
+  return stats.substr(0, stats.size() - 1) + ",\"autotune\":" + extra + "}";
+}
+
+}  // namespace
+
+// A join of a resident R (or one streamed chunk) with PJ_AUTOTUNE.
+pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                         cudaStream_t st, std::string& stats) {
+  const std::string key = key_of(R, S, q);
+  Choice best;
+  if (lookup(ctx, key, &best)) {
+    pj_status rc = run_with(ctx, best, R, S, q, out, st, stats);
+    char buf[128];
+    snprintf(buf, sizeof buf, "{\"cached\":1,\"variant\":%d,\"start\":%d}", best.variant, best.start);
+    stats = with_tuning(stats, buf);
+    return rc;
+  }
+  std::vector<Choice> cand;
+  const int Lmax = std::max(R->L, S->L);
+  const std::vector<int> variants = q->prec == PJ_PREC_FP64 ? std::vector<int>{2} : std::vector<int>{2, 1};
+  for (int v : variants) {
+    if (q->pred == PJ_KNN) {
+      cand.push_back(Choice{v, -1});
+    } else {
+      for (int s = 0; s < Lmax; ++s) cand.push_back(Choice{v, s});
+      if (q->flags & PJ_USE_MLP) cand.push_back(Choice{v, -1});
+    }
+  }
+  std::string tried = "[";
+  double best_ms = 1e300;
+  pj_result keep;
+  memset(&keep, 0, sizeof keep);
+  std::string keep_stats;
+  JoinSummary keep_sum;
+  {
+    // one untimed run first: workspace growth would bias the first candidate
+    pj_result warm;
+    memset(&warm, 0, sizeof warm);
+    std::string st_w;
+    pj_status rc = run_with(ctx, cand[0], R, S, q, &warm, st, st_w);
+    free(warm.priv);
+    if (rc != PJ_OK) return rc;
+  }
+  for (size_t i = 0; i < cand.size(); ++i) {
+    pj_result res;
+    memset(&res, 0, sizeof res);
+    std::string st_i;
+    Timer t;
+    pj_status rc = run_with(ctx, cand[i], R, S, q, &res, st, st_i);
+    const double ms = t.ms();
+    if (rc != PJ_OK) {
+      free(res.priv);
+      free(keep.priv);
+      return rc;
+    }
+    char buf[96];
+    snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"ms\":%.3f}", i ? "," : "", cand[i].variant,
+             cand[i].start, ms);
+    tried += buf;
+    if (keep.priv && res.n != keep.n) {
+      free(res.priv);
+      free(keep.priv);
+      throw ApiError{PJ_ECUDA, "autotuning: configurations disagree on the number of results"};
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand[i];
+      free(keep.priv);
+      keep = res;
+      keep_stats = st_i;
+      keep_sum = ctx->last_sum;
+    } else {
+      free(res.priv);
+    }
+  }
+  tried += "]";
+  store(ctx, key, best);
+  *out = keep;
+  ctx->last_sum = keep_sum;
+  char buf[96];
+  snprintf(buf, sizeof buf, "{\"cached\":0,\"variant\":%d,\"start\":%d,\"tried\":", best.variant, best.start);
+  stats = with_tuning(keep_stats, std::string(buf) + tried + "}");
+  return PJ_OK;
+}
+
+}  // namespace pj

@@ -1,0 +1,108 @@
+"""PJ_AUTOTUNE: the first join of a workload key tries every candidate
+configuration (refinement variant x LoD schedule) and keeps the fastest;
+later joins reuse it, also from another context through the cache file.
+Configurations only reschedule work, so the pairs must equal those of the
+untuned join, and with PJ_EXACT_DIST every field (a pair confirmed at
+another LoD step reports that step's bracket otherwise); both refinement
+variants are also pinned directly through the "refine_variant" option."""
+
+import numpy as np
+import pytest
+
+from synth import configs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sets():
+    w = configs.blobs20k(n=2000)
+    return w
+
+
+def key(res):
+    o = np.lexsort((res.s, res.r))
+    return tuple(x[o] for x in (res.r, res.s, res.d_lo, res.d_hi, res.d, res.exact))
+
+
+def same(a, b, exact=True):
+    ka, kb = key(a), key(b)
+    n = len(ka) if exact else 2
+    for x, y in zip(ka[:n], kb[:n]):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_within_and_cache_file(sets, tmp_path):
+    from paper_2604_19982_gb300 import pj
+    path = str(tmp_path / "tune.txt")
+    ctx = pj.Context(0, {"autotune_cache": path})
+    gR, gS = ctx.load_set(sets.R), ctx.load_set(sets.S)
+    for tau, fl in ((0.0, pj.TILE_PRUNE), (1.0, pj.TILE_PRUNE | pj.EXACT_DIST)):
+        ref = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=pj.FP32, flags=fl)
+        a = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
+        st = ctx.stats()["autotune"]
+        assert st["cached"] == 0 and len(st["tried"]) == 6   # 2 variants x 3 start steps
+        same(ref, a, fl & pj.EXACT_DIST)
+        b = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
+        assert ctx.stats()["autotune"]["cached"] == 1
+        same(ref, b, fl & pj.EXACT_DIST)
+    ctx.close()
+    lines = open(path).read().split("\n")
+    assert len([x for x in lines if x.strip()]) == 2
+    ctx2 = pj.Context(0, {"autotune_cache": path})
+    gR, gS = ctx2.load_set(sets.R), ctx2.load_set(sets.S)
+    c = ctx2.join(gR, gS, pj.WITHIN, tau=0.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
+    assert ctx2.stats()["autotune"]["cached"] == 1
+    assert c.n > 0
+    ctx2.close()
+
+
+def test_autotune_knn_and_fp64(sets):
+    from paper_2604_19982_gb300 import pj
+    ctx = pj.Context(0)
+    gR, gS = ctx.load_set(sets.R), ctx.load_set(sets.S)
+    ref = ctx.join(gR, gS, pj.KNN, k=3, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+    a = ctx.join(gR, gS, pj.KNN, k=3, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.AUTOTUNE)
+    assert len(ctx.stats()["autotune"]["tried"]) == 2
+    same(ref, a)
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP64)
+    a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP64, flags=pj.AUTOTUNE)
+    assert len(ctx.stats()["autotune"]["tried"]) == 3   # FP64: schedules only
+    same(ref, a, exact=False)
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_refine_variants_agree(sets, variant):
+    from paper_2604_19982_gb300 import pj
+    base = pj.Context(0)
+    ctx = pj.Context(0, {"refine_variant": variant})
+    out = []
+    for c in (base, ctx):
+        gR, gS = c.load_set(sets.R), c.load_set(sets.S)
+        out.append([c.join(gR, gS, pj.WITHIN, tau=t, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+                    for t in (0.0, 1.0)])
+    for a, b in zip(*out):
+        assert np.array_equal(np.sort(a.r * 100000 + a.s), np.sort(b.r * 100000 + b.s))
+        same(a, b)
+    base.close()
+    ctx.close()
+    with pytest.raises(pj.PJError):
+        pj.Context(0, {"refine_variant": 3})
+
+
+def test_autotune_streamed(sets):
+    from paper_2604_19982_gb300 import pj
+    ctx = pj.Context(0)
+    gR, gS = ctx.load_set(sets.R), ctx.load_set(sets.S)
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+    parts = [(0, 1000), (1000, 1000)]
+    g = ctx.load_set_streamed(2000, 2, lambda c: configs.blob_set(2000, sets_side(), 0, 0, start=parts[c][0],
+                                                                  count=parts[c][1]))
+    a = ctx.join(g, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.AUTOTUNE)
+    same(ref, a)
+    ctx.close()
+
+
+def sets_side():
+    return configs.scaled_side(400.0, 20_000, 2000)
