@@ -56,75 +56,63 @@ __device__ __forceinline__ int64_t upper_obj(const int64_t* off, int n, int64_t 
   return lo;
 }
 
-__global__ void k_expand(int64_t F, int n, const float* verts, const int64_t* voff, const int32_t* faces,
-                         const int64_t* foff, int nf_shared, const float* hd, const float* ph, float4* fac,
-                         int* err) {
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  int64_t o, row;
-  if (nf_shared > 0) {
-    o = f / nf_shared;
-    row = f - o * nf_shared;
-  } else {
-    o = upper_obj(foff, n, f);
-    row = f;
-  }
-  const int64_t v0 = voff[o], nv = voff[o + 1] - v0;
-  float x[3][3];
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    int id = faces[3 * row + k];
-    if (id < 0 || id >= nv) {
-      ok = false;
-      id = 0;
-    }
-    const float* v = verts + 3 * (v0 + id);
-    x[k][0] = v[0];
-    x[k][1] = v[1];
-    x[k][2] = v[2];
-  }
-  float h = hd ? hd[f] : 0.f, p = ph ? ph[f] : 0.f;
-  bool fin = isfinite(h) && isfinite(p) && h >= 0.f && p >= 0.f;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) fin = fin && isfinite(x[k][0]) && isfinite(x[k][1]) && isfinite(x[k][2]);
-  if (!ok) set_err(err, ERR_BOUNDS);
-  if (!fin) set_err(err, ERR_NONFINITE);
-  fac[3 * f + 0] = make_float4(x[0][0], x[0][1], x[0][2], h);
-  fac[3 * f + 1] = make_float4(x[1][0], x[1][1], x[1][2], p);
-  fac[3 * f + 2] = make_float4(x[2][0], x[2][1], x[2][2], 0.f);
-}
-
-// one warp per chunk: box, max hd / ph, max edge length, min facet sine
-__global__ void k_chunks(int64_t C, int n, int size, const int64_t* coff, const int64_t* foff, const float4* fac,
-                         float4* chunk) {
-  int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (c >= C) return;
-  int64_t o = upper_obj(coff, n, c);
-  int64_t j = c - coff[o];
-  int64_t f0 = foff[o] + j * size, f1 = min(f0 + size, foff[o + 1]);
+// One warp per 32-facet block: each lane expands one facet into its
+// record (v0, hd), (v1, ph), (v2, 0); the warp reduces the block's box, max
+// hd / ph, max edge length and min facet sine from registers, so the
+// records are written once and never read back.
+__global__ void k_expand_blocks(int64_t B, int n, const float* verts, const int64_t* voff, const int32_t* faces,
+                                const int64_t* foff, const int64_t* boff, int nf_shared, const float* hd,
+                                const float* ph, float4* fac, float4* blk, int* err) {
+  const int64_t bi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (bi >= B) return;
+  const int64_t o = upper_obj(boff, n, bi);
+  const int64_t f = foff[o] + (bi - boff[o]) * BLK + lane;
+  const bool act = f < foff[o + 1];
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   float mhd = 0.f, mph = 0.f, medge = 0.f, smin = 1.f;
-  for (int64_t f = f0 + lane; f < f1; f += 32) {
-    float4 A = fac[3 * f], B = fac[3 * f + 1], Cc = fac[3 * f + 2];
-    float a[3] = {A.x, A.y, A.z}, b[3] = {B.x, B.y, B.z}, cc[3] = {Cc.x, Cc.y, Cc.z};
+  if (act) {
+    const int64_t row = nf_shared > 0 ? f - o * nf_shared : f;
+    const int64_t v0 = voff[o], nv = voff[o + 1] - v0;
+    float x[3][3];
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      lo[k] = fminf(lo[k], fminf(a[k], fminf(b[k], cc[k])));
-      hi[k] = fmaxf(hi[k], fmaxf(a[k], fmaxf(b[k], cc[k])));
+      int id = faces[3 * row + k];
+      if (id < 0 || id >= nv) {
+        ok = false;
+        id = 0;
+      }
+      const float* v = verts + 3 * (v0 + id);
+      x[k][0] = v[0];
+      x[k][1] = v[1];
+      x[k][2] = v[2];
     }
-    mhd = fmaxf(mhd, A.w);
-    mph = fmaxf(mph, B.w);
+    const float h = hd ? hd[f] : 0.f, p = ph ? ph[f] : 0.f;
+    bool fin = isfinite(h) && isfinite(p) && h >= 0.f && p >= 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fin = fin && isfinite(x[k][0]) && isfinite(x[k][1]) && isfinite(x[k][2]);
+    if (!ok) set_err(err, ERR_BOUNDS);
+    if (!fin) set_err(err, ERR_NONFINITE);
+    fac[3 * f + 0] = make_float4(x[0][0], x[0][1], x[0][2], h);
+    fac[3 * f + 1] = make_float4(x[1][0], x[1][1], x[1][2], p);
+    fac[3 * f + 2] = make_float4(x[2][0], x[2][1], x[2][2], 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(x[0][k], fminf(x[1][k], x[2][k]));
+      hi[k] = fmaxf(x[0][k], fmaxf(x[1][k], x[2][k]));
+    }
+    mhd = h;
+    mph = p;
     float e0 = 0, e1 = 0, e2 = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      e0 += (b[k] - a[k]) * (b[k] - a[k]);
-      e1 += (cc[k] - b[k]) * (cc[k] - b[k]);
-      e2 += (a[k] - cc[k]) * (a[k] - cc[k]);
+      e0 += (x[1][k] - x[0][k]) * (x[1][k] - x[0][k]);
+      e1 += (x[2][k] - x[1][k]) * (x[2][k] - x[1][k]);
+      e2 += (x[0][k] - x[2][k]) * (x[0][k] - x[2][k]);
     }
-    medge = fmaxf(medge, sqrtf(fmaxf(e0, fmaxf(e1, e2))) * 1.0001f);
-    smin = fminf(smin, facet_sin<float>(a, b, cc) * 0.999f);
+    medge = sqrtf(fmaxf(e0, fmaxf(e1, e2))) * 1.0001f;
+    smin = facet_sin<float>(x[0], x[1], x[2]) * 0.999f;
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -136,10 +124,29 @@ __global__ void k_chunks(int64_t C, int n, int size, const int64_t* coff, const 
   medge = -warp_min(-medge);
   smin = warp_min(smin);
   if (lane == 0) {
-    chunk[3 * c + 0] = make_float4(lo[0], lo[1], lo[2], mhd);
-    chunk[3 * c + 1] = make_float4(hi[0], hi[1], hi[2], mph);
-    chunk[3 * c + 2] = make_float4(medge, smin, 0.f, 0.f);
+    blk[3 * bi + 0] = make_float4(lo[0], lo[1], lo[2], mhd);
+    blk[3 * bi + 1] = make_float4(hi[0], hi[1], hi[2], mph);
+    blk[3 * bi + 2] = make_float4(medge, smin, 0.f, 0.f);
   }
+}
+
+// One thread per 256-facet chunk: the reduction of its (up to 8) blocks.
+__global__ void k_chunks_from_blocks(int64_t C, int n, const int64_t* coff, const int64_t* boff, const float4* blk,
+                                     float4* chunk) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int64_t o = upper_obj(coff, n, c);
+  const int64_t b0 = boff[o] + (c - coff[o]) * (CHUNK / BLK), b1 = min(b0 + CHUNK / BLK, boff[o + 1]);
+  float4 lo = blk[3 * b0], hi = blk[3 * b0 + 1], ex = blk[3 * b0 + 2];
+  for (int64_t b = b0 + 1; b < b1; ++b) {
+    const float4 l = blk[3 * b], h = blk[3 * b + 1], e = blk[3 * b + 2];
+    lo = make_float4(fminf(lo.x, l.x), fminf(lo.y, l.y), fminf(lo.z, l.z), fmaxf(lo.w, l.w));
+    hi = make_float4(fmaxf(hi.x, h.x), fmaxf(hi.y, h.y), fmaxf(hi.z, h.z), fmaxf(hi.w, h.w));
+    ex = make_float4(fmaxf(ex.x, e.x), fminf(ex.y, e.y), 0.f, 0.f);
+  }
+  chunk[3 * c + 0] = lo;
+  chunk[3 * c + 1] = hi;
+  chunk[3 * c + 2] = ex;
 }
 
 // one warp per object: box of its original-surface vertices
@@ -184,10 +191,12 @@ void free_set_storage(pj_set* s) {
   s->mbb = s->anchor = nullptr;
 }
 
+// Set storage and load temporaries are stream-ordered allocations from the
+// device's memory pool (no device-wide synchronization per buffer).
 template <class T>
 static T* upload(const T* h, size_t count, cudaStream_t st) {
   T* d = nullptr;
-  PJ_CK(cudaMalloc((void**)&d, std::max<size_t>(1, count) * sizeof(T)));
+  PJ_CK(cudaMallocAsync((void**)&d, std::max<size_t>(1, count) * sizeof(T), st));
   if (count) PJ_CK(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
   return d;
 }
@@ -199,16 +208,13 @@ void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t s
   for (int l = 0; l < L; ++l) {
     LodData& ld = s->lod[l];
     if (ld.F == 0) continue;
-    k_expand<<<(unsigned)((ld.F + th - 1) / th), th, 0, st>>>(ld.F, n, raw[l].verts, raw[l].voff, raw[l].faces, ld.foff,
-                                                              raw[l].nfs, raw[l].hd, raw[l].ph, ld.fac, ctx->d_err);
+    k_expand_blocks<<<(unsigned)((ld.B * 32 + th - 1) / th), th, 0, st>>>(
+        ld.B, n, raw[l].verts, raw[l].voff, raw[l].faces, ld.foff, ld.boff, raw[l].nfs, raw[l].hd, raw[l].ph, ld.fac,
+        ld.blk, ctx->d_err);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
-    int64_t thr = ld.C * 32;
-    k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.C, n, CHUNK, ld.coff, ld.foff, ld.fac, ld.chunk);
-    PJ_CK(cudaGetLastError());
-    PJ_COUNT_LAUNCH;
-    thr = ld.B * 32;
-    k_chunks<<<(unsigned)((thr + th - 1) / th), th, 0, st>>>(ld.B, n, BLK, ld.boff, ld.foff, ld.fac, ld.blk);
+    k_chunks_from_blocks<<<(unsigned)((ld.C + th - 1) / th), th, 0, st>>>(ld.C, n, ld.coff, ld.boff, ld.blk,
+                                                                         ld.chunk);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
   }
@@ -227,7 +233,14 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
   s->n = n;
   s->L = L;
   std::map<const void*, float*> vcache;
-  std::vector<void*> temps;
+  struct Temps {
+    std::vector<void*> v;
+    cudaStream_t st;
+    void push_back(void* p) { v.push_back(p); }
+    ~Temps() {
+      for (void* p : v) cudaFreeAsync(p, st);
+    }
+  } temps{{}, st};
   PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   RawLod raw[PJ_MAX_LODS];
   for (int l = 0; l < L; ++l) {
@@ -295,20 +308,21 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
       dph = upload(D->ph[l], (size_t)ld.F, st);
       temps.push_back(dph);
     }
-    PJ_CK(cudaMalloc((void**)&ld.fac, std::max<int64_t>(1, 3 * ld.F) * sizeof(float4)));
-    PJ_CK(cudaMalloc((void**)&ld.chunk, std::max<int64_t>(1, 3 * ld.C) * sizeof(float4)));
-    PJ_CK(cudaMalloc((void**)&ld.blk, std::max<int64_t>(1, 3 * ld.B) * sizeof(float4)));
+    PJ_CK(cudaMallocAsync((void**)&ld.fac, std::max<int64_t>(1, 3 * ld.F) * sizeof(float4), st));
+    PJ_CK(cudaMallocAsync((void**)&ld.chunk, std::max<int64_t>(1, 3 * ld.C) * sizeof(float4), st));
+    PJ_CK(cudaMallocAsync((void**)&ld.blk, std::max<int64_t>(1, 3 * ld.B) * sizeof(float4), st));
     raw[l] = RawLod{dv, dvo, dfa, nfs, dhd, dph};
   }
-  PJ_CK(cudaMalloc((void**)&s->mbb, std::max(1, n) * 6 * sizeof(float)));
+  PJ_CK(cudaMallocAsync((void**)&s->mbb, std::max(1, n) * 6 * sizeof(float), st));
   s->anchor = upload(D->anchor, (size_t)n * 3, st);
   build_set_kernels(ctx, s, raw, st);
   s->mbb_h.resize((size_t)n * 6);
   if (n > 0) PJ_CK(cudaMemcpyAsync(s->mbb_h.data(), s->mbb, (size_t)n * 6 * 4, cudaMemcpyDeviceToHost, st));
   int herr = 0;
   PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  for (void* p : temps.v) PJ_CK(cudaFreeAsync(p, st));
+  temps.v.clear();
   PJ_CK(cudaStreamSynchronize(st));
-  for (void* p : temps) cudaFree(p);
   if (herr & ERR_BOUNDS) throw ApiError{PJ_EBOUNDS, "a face index lies outside its object's vertices"};
   if (herr & ERR_NONFINITE) throw ApiError{PJ_ENONFINITE, "non-finite vertex, anchor, hd or ph (or negative hd/ph)"};
   return PJ_OK;
@@ -397,6 +411,15 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
     throw ApiError{PJ_ECUDA, "this library is built for sm_103a (GB300); device is sm_" +
                                  std::to_string(prop.major) + std::to_string(prop.minor)};
   PJ_CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+  {
+    // keep freed pool memory for the next set instead of returning it
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    (void)cudaGetLastError();
+  }
   PJ_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   PJ_CK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
   PJ_CK(cudaMalloc((void**)&ctx->d_counters, 16 * sizeof(unsigned long long)));
