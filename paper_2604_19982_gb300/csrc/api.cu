@@ -462,6 +462,7 @@ void pj_destroy(pj_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  graphs_clear(ctx);
   for (auto& b : ctx->ws) cudaFree(b.p);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_counters);

@@ -292,8 +292,12 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   PJ_CK(cudaStreamSynchronize(st));
   out.n_pairs = total;
   if (total == 0) return out;
-  auto pr = (int32_t*)ws_get(ctx, WS_PR, total * 4, st);
-  auto ps = (int32_t*)ws_get(ctx, WS_PS, total * 4, st);
+  // capacity of the pair arrays: the next power of two (a fixed-capacity
+  // join pads to it without reallocating the filter's output)
+  int64_t cap = 256;
+  while (cap < total) cap <<= 1;
+  auto pr = (int32_t*)ws_get(ctx, WS_PR, cap * 4, st);
+  auto ps = (int32_t*)ws_get(ctx, WS_PS, cap * 4, st);
   k_probe<true><<<g, th, 0, st>>>(R->n, R->mbb, S->mbb, ftau, lim2, G, off, ids, nullptr, roff, pr, ps);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;

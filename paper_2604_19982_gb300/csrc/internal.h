@@ -72,6 +72,15 @@ struct GridCacheEntry {
   int64_t nids = 0;
 };
 
+// The host-side record of a join's refinement steps (see StepLog).
+struct StepLogData {
+  int n = 0;
+  int ev[16];
+  int64_t units[16];
+  bool f64[16];
+  bool full[16];
+};
+
 // Totals of the last join (also in its JSON stats).
 struct JoinSummary {
   int64_t candidates = 0, results = 0, units = 0;
@@ -112,6 +121,14 @@ struct pj_ctx {
   std::string stats;
   pj::JoinSummary last_sum;
   std::vector<pj::GridCacheEntry> grid_cache;
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t cap = 0;
+    unsigned long long kernels = 0;   // library kernels in the graph
+    pj::StepLogData log;
+  };
+  std::vector<GraphEntry> graphs;   // captured joins (PJ_USE_GRAPH), oldest first
   int ctas_per_sm = 0;             // 0 = from occupancy
   int refine_variant = 2;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
   int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
@@ -219,21 +236,18 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
 float refine_ms(pj_ctx* ctx, int ev);
 // Per-step record of a join: units, tests and refinement time of every
 // refinement launch, read back once after the join's final synchronization.
-struct StepLog {
+struct StepLog : StepLogData {
   static constexpr int MAX = 16;
-  int n = 0;
-  int ev[MAX];
-  int64_t units[MAX];
-  bool f64[MAX];
-  bool full[MAX];
   // Record one refinement step (after run_refine on `st`).
   void add(pj_ctx* ctx, const UnitCount& uc, int event, const StepSpec& sp, cudaStream_t st);
   // JSON array of the steps; also sums refinement ms per precision and units.
   std::string json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total) const;
 };
 // Pair-setup: origin (pair-local frame), box MINDIST, anchor distance.
+// n_live (device, may be null): pairs at or past *n_live are padding of a
+// fixed-capacity join and are marked REMOVED.
 void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n_pairs, double tau, bool within,
-                 cudaStream_t st);
+                 cudaStream_t st, const int64_t* n_live = nullptr);
 
 // ---- explicit-buffer launchers (refine.cu / join.cu), used by entry points
 // that bring their own scratch instead of the context workspace
@@ -277,6 +291,13 @@ void scan_small_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cud
 // ---- results (join.cu)
 void alloc_result(pj_result* res, int64_t n);
 int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st);
+// gather_results in two halves: the device part (compaction and the copy of
+// capacity n into pinned staging, no synchronization) and, after the
+// stream is synchronized, the host part.
+void gather_device(pj_ctx* ctx, int64_t n, cudaStream_t st);
+// Destroy the captured join graphs of a context.
+void graphs_clear(pj_ctx* ctx);
+int64_t gather_host(pj_ctx* ctx, int64_t n, pj_result* res);
 void mark_exact(pj_ctx* ctx, int64_t n, cudaStream_t st);
 
 // ---- decide (join.cu)

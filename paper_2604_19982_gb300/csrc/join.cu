@@ -294,23 +294,18 @@ static void* stage(pj_ctx* ctx, size_t bytes) {
   return ctx->h_stage;
 }
 
-// Copy the CONFIRMED pairs (in pair order = (r, s) order) to the host: the
-// compacted arrays (capacity n) and their count come back in one copy and
-// one synchronization.
-int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) {
-  if (n == 0) {
-    alloc_result(res, 0);
-    return 0;
-  }
+void gather_device(pj_ctx* ctx, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
   int th = 256;
   unsigned g = (unsigned)((n + th - 1) / th);
   auto flag = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
   auto off = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
+  auto tmp = (int64_t*)ws_get(ctx, WS_TMP, (scan_tmp_words(n) + 8) * 8, st);
   auto status = (const uint8_t*)ctx->ws[WS_STATUS].p;
   k_flag_status<<<g, th, 0, st>>>(n, status, CONFIRMED, flag);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  scan_i64(ctx, flag, off, n, st);
+  scan_i64(ctx, flag, off, n, st, tmp);
   const size_t per = 4 + 4 + 8 + 8 + 8 + 1;
   char* dev = (char*)ws_get(ctx, WS_RES, (size_t)n * per + 64, st);
   ResultPack pk;
@@ -328,7 +323,15 @@ int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) 
   char* h = (char*)stage(ctx, (size_t)n * per + 64);
   PJ_CK(cudaMemcpyAsync(h, dev, (size_t)n * per, cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaMemcpyAsync(h + (size_t)n * per, off + n, 8, cudaMemcpyDeviceToHost, st));
-  PJ_CK(cudaStreamSynchronize(st));
+}
+
+int64_t gather_host(pj_ctx* ctx, int64_t n, pj_result* res) {
+  if (n == 0) {
+    alloc_result(res, 0);
+    return 0;
+  }
+  const size_t per = 4 + 4 + 8 + 8 + 8 + 1;
+  const char* h = (const char*)ctx->h_stage;
   int64_t m = 0;
   memcpy(&m, h + (size_t)n * per, 8);
   alloc_result(res, m);
@@ -339,6 +342,15 @@ int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) 
   memcpy(res->s, h + (size_t)n * 28, (size_t)m * 4);
   memcpy(res->exact, h + (size_t)n * 32, (size_t)m);
   return m;
+}
+
+// Copy the CONFIRMED pairs (in pair order = (r, s) order) to the host: the
+// compacted arrays (capacity n) and their count come back in one copy and
+// one synchronization.
+int64_t gather_results(pj_ctx* ctx, int64_t n, pj_result* res, cudaStream_t st) {
+  gather_device(ctx, n, st);
+  if (n) PJ_CK(cudaStreamSynchronize(st));
+  return gather_host(ctx, n, res);
 }
 
 // ------------------------------------------------------------------ driver
@@ -385,6 +397,63 @@ __global__ void k_lod0_floor(int64_t n, uint8_t* lod0, uint8_t s) {
   if (p < n && lod0[p] < s) lod0[p] = s;
 }
 
+// ------------------------------------------------------------------ graphs
+// PJ_USE_GRAPH: everything after the filter's one synchronization -- pair
+// setup, every LoD step, the FP64 passes, compaction and the result copy --
+// is a fixed sequence for a given capacity (the candidate list is padded to
+// the next power of two with pairs marked REMOVED, whose work is empty).
+// It is captured into a CUDA graph once per key and replayed afterwards;
+// the key holds every host-side launch parameter (set shapes and device
+// pointers, workspace addresses, query, capacity, kernel choices), so a
+// replay issues exactly the launches a direct run would.
+
+static uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
+  return h;
+}
+
+static std::string graph_key(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, int64_t cap) {
+  uint64_t h = 1469598103934665603ULL;
+  for (const pj_set* X : {R, S}) {
+    h = fnv(h, &X->n, sizeof X->n);
+    h = fnv(h, &X->L, sizeof X->L);
+    h = fnv(h, &X->mbb, sizeof X->mbb);
+    h = fnv(h, &X->anchor, sizeof X->anchor);
+    for (int l = 0; l < X->L; ++l) {
+      const LodData& d = X->lod[l];
+      const void* ptrs[6] = {d.fac, d.foff, d.chunk, d.coff, d.blk, d.boff};
+      const int64_t sz[4] = {d.F, d.C, d.B, d.maxF};
+      h = fnv(h, ptrs, sizeof ptrs);
+      h = fnv(h, sz, sizeof sz);
+    }
+  }
+  for (int i = 0; i < WS_COUNT; ++i) {
+    h = fnv(h, &ctx->ws[i].p, sizeof(void*));
+    h = fnv(h, &ctx->ws[i].cap, sizeof(size_t));
+  }
+  h = fnv(h, &ctx->h_stage, sizeof(void*));
+  h = fnv(h, &ctx->h_stage_cap, sizeof(size_t));
+  const int knobs[3] = {ctx->refine_variant, ctx->sched_start, ctx->ctas_per_sm};
+  h = fnv(h, knobs, sizeof knobs);
+  char buf[200];
+  snprintf(buf, sizeof buf, "%016llx.p%d.t%.17g.x%d.f%u.c%lld", (unsigned long long)h, (int)q->pred, q->tau,
+           (int)q->prec, q->flags, (long long)cap);
+  return buf;
+}
+
+static pj_ctx::GraphEntry* graph_find(pj_ctx* ctx, const std::string& key) {
+  for (auto& g : ctx->graphs)
+    if (g.key == key) return &g;
+  return nullptr;
+}
+
+void graphs_clear(pj_ctx* ctx) {
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+}
+
 pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                       cudaStream_t st, std::string& stats) {
   Timer tall;
@@ -392,91 +461,139 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   const double tau = q->pred == PJ_INTERSECT ? 0.0 : q->tau;
   const bool fp64 = q->prec == PJ_PREC_FP64;
   const bool cull = (q->flags & PJ_TILE_PRUNE) != 0;
+  const bool use_mlp = (q->flags & PJ_USE_MLP) != 0;
+  if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
   PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
   PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   Timer tf;
   FilterOut fo = filter_within(ctx, R, S, tau, st);
   const int64_t n = fo.n_pairs;
-  setup_pairs(ctx, R, S, n, tau, true, st);
-  const bool use_mlp = (q->flags & PJ_USE_MLP) != 0;
-  if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
-  if (use_mlp && n > 0) start_lod(ctx, R, S, n, propose(ctx, R, S, n, st), tau, st);
-  if (ctx->sched_start > 0 && n > 0) {
-    // autotuned schedule: no pair is refined before this step
-    int th = 256;
-    k_lod0_floor<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_LOD0].p,
-                                                               (uint8_t)ctx->sched_start);
-    PJ_CK(cudaGetLastError());
-    PJ_COUNT_LAUNCH;
-  }
-  double ms_filter = tf.ms();
   const int Lmax = std::max(R->L, S->L);
   auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
-  ctx->ev_used = 0;
+
+  // fixed-capacity graph mode: not with the learned start (its features
+  // read every pair id), nor when a step would have to size its unit buffer
+  // on the host, nor on the legacy default stream
+  bool graph = (q->flags & PJ_USE_GRAPH) && !use_mlp && n > 0 && st != nullptr;
+  int64_t cap = n;
+  if (graph) {
+    cap = 256;
+    while (cap < n) cap <<= 1;
+    for (int l = 0; l < Lmax && graph; ++l) {
+      const int lr = std::max(0, l - (Lmax - R->L)), ls = std::max(0, l - (Lmax - S->L));
+      const int64_t worst = cap * ((R->lod[lr].maxF + BLK - 1) / BLK) * ((S->lod[ls].maxF + BLK - 1) / BLK);
+      if ((size_t)worst * sizeof(Tile) > (size_t(512) << 20)) graph = false;
+    }
+    if (!graph) cap = n;
+  }
+  const int64_t nn = cap;
+  const int64_t* n_live = graph ? (const int64_t*)ctx->ws[WS_ROFF].p + R->n : nullptr;
+
+  // the whole device sequence after the filter; false on an expired deadline
+  auto enqueue = [&](StepLog& log) -> bool {
+    setup_pairs(ctx, R, S, nn, tau, true, st, n_live);
+    if (use_mlp) start_lod(ctx, R, S, nn, propose(ctx, R, S, nn, st), tau, st);
+    if (ctx->sched_start > 0) {
+      // autotuned schedule: no pair is refined before this step
+      int th = 256;
+      k_lod0_floor<<<(unsigned)((nn + th - 1) / th), th, 0, st>>>(nn, (uint8_t*)ctx->ws[WS_LOD0].p,
+                                                                  (uint8_t)ctx->sched_start);
+      PJ_CK(cudaGetLastError());
+      PJ_COUNT_LAUNCH;
+    }
+    ctx->ev_used = 0;
+    for (int step = 0; step < Lmax; ++step) {
+      if (deadline_hit()) return false;
+      StepSpec sp;
+      sp.lodR = std::max(0, step - (Lmax - R->L));
+      sp.lodS = std::max(0, step - (Lmax - S->L));
+      sp.full = step == Lmax - 1;
+      sp.fp64 = fp64;
+      sp.cull = cull;
+      sp.want = UNDECIDED;
+      sp.step = step;
+      // early exit (with pruning on): coarse steps only report a bracket, and
+      // at full resolution an intersection test's answer is exactly 0
+      sp.early = cull && (!sp.full || tau == 0.0);
+      init_bounds(ctx, nn, sp, st);
+      UnitCount uc = build_tiles(ctx, R, S, nn, sp, st);
+      const int ev = run_refine(ctx, R, S, uc, sp, st);
+      decide_within(ctx, nn, tau, sp, st);
+      log.add(ctx, uc, ev, sp, st);
+    }
+    if (!fp64) {
+      // pairs whose single-precision bracket still straddles tau at full
+      // resolution (status REDECIDE) are refined again in double precision;
+      // the decision only asks d <= tau, so units farther apart than tau may
+      // be skipped
+      StepSpec sp;
+      sp.lodR = R->L - 1;
+      sp.lodS = S->L - 1;
+      sp.full = true;
+      sp.fp64 = true;
+      sp.cull = cull;
+      sp.want = REDECIDE;
+      sp.step = Lmax - 1;
+      init_bounds(ctx, nn, sp, st);
+      UnitCount uc = build_tiles(ctx, R, S, nn, sp, st);
+      const int ev = run_refine(ctx, R, S, uc, sp, st);
+      decide_within(ctx, nn, tau, sp, st);
+      log.add(ctx, uc, ev, sp, st);
+    }
+    if (q->flags & PJ_EXACT_DIST) {
+      int th = 256;
+      k_mark_exact<<<(unsigned)((nn + th - 1) / th), th, 0, st>>>(nn, (uint8_t*)ctx->ws[WS_STATUS].p,
+                                                                  (const uint8_t*)ctx->ws[WS_EXACT].p);
+      PJ_CK(cudaGetLastError());
+      PJ_COUNT_LAUNCH;
+      // every result pair has d <= tau, so its closest facet pair lies in a
+      // unit within tau: pruned units cannot hold the minimum
+      StepSpec sp;
+      sp.lodR = R->L - 1;
+      sp.lodS = S->L - 1;
+      sp.full = true;
+      sp.fp64 = true;
+      sp.cull = cull;
+      sp.want = MAKE_EXACT;
+      sp.step = Lmax - 1;
+      init_bounds(ctx, nn, sp, st);
+      UnitCount uc = build_tiles(ctx, R, S, nn, sp, st);
+      const int ev = run_refine(ctx, R, S, uc, sp, st);
+      decide_within(ctx, nn, tau, sp, st);
+      log.add(ctx, uc, ev, sp, st);
+    }
+    gather_device(ctx, nn, st);
+    return true;
+  };
+
   StepLog log;
-  for (int step = 0; step < Lmax && n > 0; ++step) {
-    if (deadline_hit()) return PJ_ETIMEOUT;
-    StepSpec sp;
-    sp.lodR = std::max(0, step - (Lmax - R->L));
-    sp.lodS = std::max(0, step - (Lmax - S->L));
-    sp.full = step == Lmax - 1;
-    sp.fp64 = fp64;
-    sp.cull = cull;
-    sp.want = UNDECIDED;
-    sp.step = step;
-    // early exit (with pruning on): coarse steps only report a bracket, and
-    // at full resolution an intersection test's answer is exactly 0
-    sp.early = cull && (!sp.full || tau == 0.0);
-    init_bounds(ctx, n, sp, st);
-    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    const int ev = run_refine(ctx, R, S, uc, sp, st);
-    decide_within(ctx, n, tau, sp, st);
-    log.add(ctx, uc, ev, sp, st);
-  }
-  if (!fp64 && n > 0) {
-    // pairs whose single-precision bracket still straddles tau at full
-    // resolution (status REDECIDE) are refined again in double precision;
-    // the decision only asks d <= tau, so units farther apart than tau may
-    // be skipped
-    StepSpec sp;
-    sp.lodR = R->L - 1;
-    sp.lodS = S->L - 1;
-    sp.full = true;
-    sp.fp64 = true;
-    sp.cull = cull;
-    sp.want = REDECIDE;
-    sp.step = Lmax - 1;
-    init_bounds(ctx, n, sp, st);
-    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    const int ev = run_refine(ctx, R, S, uc, sp, st);
-    decide_within(ctx, n, tau, sp, st);
-    log.add(ctx, uc, ev, sp, st);
-  }
-  if ((q->flags & PJ_EXACT_DIST) && n > 0) {
-    int th = 256;
-    k_mark_exact<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (uint8_t*)ctx->ws[WS_STATUS].p,
-                                                               (const uint8_t*)ctx->ws[WS_EXACT].p);
-    PJ_CK(cudaGetLastError());
-    PJ_COUNT_LAUNCH;
-    // every result pair has d <= tau, so its closest facet pair lies in a
-    // unit within tau: pruned units cannot hold the minimum
-    StepSpec sp;
-    sp.lodR = R->L - 1;
-    sp.lodS = S->L - 1;
-    sp.full = true;
-    sp.fp64 = true;
-    sp.cull = cull;
-    sp.want = MAKE_EXACT;
-    sp.step = Lmax - 1;
-    init_bounds(ctx, n, sp, st);
-    UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
-    const int ev = run_refine(ctx, R, S, uc, sp, st);
-    decide_within(ctx, n, tau, sp, st);
-    log.add(ctx, uc, ev, sp, st);
+  const char* gmode = "off";
+  double ms_filter = 0;
+  bool need_capture = false;
+  if (nn > 0) {
+    pj_ctx::GraphEntry* ge = graph ? graph_find(ctx, graph_key(ctx, R, S, q, cap)) : nullptr;
+    ms_filter = tf.ms();
+    if (ge) {
+      // replay: one launch for the whole sequence
+      if (deadline_hit()) return PJ_ETIMEOUT;
+      PJ_CK(cudaEventRecord(ctx->ev[60], st));
+      PJ_CK(cudaGraphLaunch(ge->exec, st));
+      PJ_CK(cudaEventRecord(ctx->ev[61], st));
+      ctx->launches += ge->kernels;
+      static_cast<StepLogData&>(log) = ge->log;
+      gmode = "replay";
+    } else {
+      if (!enqueue(log)) return PJ_ETIMEOUT;
+      if (graph) gmode = "captured";
+    }
+    PJ_CK(cudaStreamSynchronize(st));
+    need_capture = graph && !ge;
+  } else {
+    ms_filter = tf.ms();
   }
   Timer tg;
-  int64_t m = gather_results(ctx, n, out, st);
-  // after the one synchronization of gather_results everything is readable
+  const int64_t m = gather_host(ctx, nn, out);
+  // after the synchronization everything is readable
   int herr = 0;
   PJ_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   unsigned long long cnt[8];
@@ -484,15 +601,20 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
   int64_t tiles_total = 0;
   const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total);
-  char buf[900];
+  float graph_ms = 0.f;
+  if (!strcmp(gmode, "replay")) PJ_CK(cudaEventElapsedTime(&graph_ms, ctx->ev[60], ctx->ev[61]));
+  char buf[1000];
   snprintf(buf, sizeof buf,
-           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"candidates\":%lld,\"results\":%lld,"
+           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"graph_ms\":%.4f,"
+           "\"capacity\":%lld,"
+           "\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%llu,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
-           tau, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, (long long)n, (long long)m, cnt[0], cnt[1], cnt[2], cnt[3], cnt[4],
-           (long long)tiles_total, ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64,
-           ctx->launches - launches0);
+           tau, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, gmode, graph_ms, (long long)nn, (long long)n, (long long)m,
+           cnt[0],
+           cnt[1], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
+           ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   JoinSummary& js = ctx->last_sum;
   js.candidates = n;
@@ -510,6 +632,44 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
+  if (need_capture) {
+    // the direct run sized every buffer: capture the same sequence now
+    // (recorded, not executed) under a key taken after it
+    const std::string key = graph_key(ctx, R, S, q, cap);
+    const unsigned long long l0 = ctx->launches;
+    StepLog glog;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        ok = enqueue(glog);
+      } catch (...) {
+        ok = false;   // not capturable: keep the direct run's results
+      }
+      if (cudaStreamEndCapture(st, &g) != cudaSuccess) ok = false;
+    }
+    (void)cudaGetLastError();
+    const unsigned long long kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    if (ok && g) {
+      cudaGraphExec_t ex = nullptr;
+      if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+        if (ctx->graphs.size() >= 16) {
+          cudaGraphExecDestroy(ctx->graphs.front().exec);
+          ctx->graphs.erase(ctx->graphs.begin());
+        }
+        pj_ctx::GraphEntry e;
+        e.key = key;
+        e.exec = ex;
+        e.cap = cap;
+        e.kernels = kernels;
+        e.log = glog;
+        ctx->graphs.push_back(e);
+      }
+      (void)cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+  }
   return PJ_OK;
 }
 

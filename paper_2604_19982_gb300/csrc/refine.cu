@@ -32,9 +32,15 @@ namespace pj {
 __global__ void k_setup_pairs(int64_t n, const int32_t* pr, const int32_t* ps, const float* mbbR,
                               const float* mbbS, const float* ancR, const float* ancS, double tau, int within,
                               float4* origin, float* thr, double* box_lb, double* anc_ub, uint8_t* status,
-                              uint8_t* lod0, uint8_t* exact, double* dlo, double* dhi, double* d) {
+                              uint8_t* lod0, uint8_t* exact, double* dlo, double* dhi, double* d,
+                              const int64_t* n_live) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  if (n_live && p >= *n_live) {   // padding of a fixed-capacity (graph) join
+    status[p] = REMOVED;
+    lod0[p] = 0;
+    return;
+  }
   const int r = pr[p], s = ps[p];
   const float* a = mbbR + 6LL * r;
   const float* b = mbbS + 6LL * s;
@@ -73,7 +79,7 @@ __global__ void k_setup_pairs(int64_t n, const int32_t* pr, const int32_t* ps, c
 }
 
 void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, double tau, bool within,
-                 cudaStream_t st) {
+                 cudaStream_t st, const int64_t* n_live) {
   if (n == 0) return;
   auto pr = (int32_t*)ws_get(ctx, WS_PR, n * 4, st);
   auto ps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);
@@ -90,7 +96,7 @@ void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, doubl
   int th = 256;
   k_setup_pairs<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, ps, R->mbb, S->mbb, R->anchor, S->anchor,
                                                               tau, within ? 1 : 0, origin, thr, box_lb, anc_ub,
-                                                              status, lod0, exact, dlo, dhi, d);
+                                                              status, lod0, exact, dlo, dhi, d, n_live);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
@@ -994,7 +1000,10 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
   const int64_t n_tiles = units.count;
   if (n_tiles == 0) return -1;
   int ev = -1;
-  if (ctx->ev_used + 2 <= 60 && ctx->ev[ctx->ev_used]) {
+  // no timing events inside a captured graph (a replay is timed as a whole)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PJ_CK(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusNone && ctx->ev_used + 2 <= 60 && ctx->ev[ctx->ev_used]) {
     ev = ctx->ev_used;
     ctx->ev_used += 2;
   }
@@ -1034,7 +1043,7 @@ void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
   int th = 256;
   k_setup_pairs<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, b.pr, b.ps, R->mbb, S->mbb, R->anchor, S->anchor,
                                                               0.0, 0, b.origin, b.thr, b.box_lb, b.anc_ub, b.status,
-                                                              b.lod0, b.exact, b.dlo, b.dhi, b.d);
+                                                              b.lod0, b.exact, b.dlo, b.dhi, b.d, nullptr);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }

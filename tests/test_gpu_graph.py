@@ -1,0 +1,89 @@
+"""PJ_USE_GRAPH: after the filter, a within-tau join runs as one captured
+CUDA graph per (sets, query, candidate capacity); the candidate list is
+padded to a power of two with pairs marked REMOVED.  A replayed join must
+return exactly what the direct join returns, for resident sets, every
+precision, a changed query, and streamed chunks (whose slots alternate)."""
+import numpy as np
+import pytest
+
+from synth import configs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_19982_gb300 import pj
+    c = pj.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def sets(ctx):
+    w = configs.blobs20k(n=4000)
+    return w, ctx.load_set(w.R), ctx.load_set(w.S)
+
+
+def key(res):
+    o = np.lexsort((res.s, res.r))
+    return tuple(x[o] for x in (res.r, res.s, res.d_lo, res.d_hi, res.d, res.exact))
+
+
+def same(a, b):
+    for x, y in zip(key(a), key(b)):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec,flags", [(1, 16), (1, 16 | 1), (0, 0), (1, 0)])
+def test_graph_replay_equals_direct(ctx, sets, prec, flags):
+    from paper_2604_19982_gb300 import pj
+    w, gR, gS = sets
+    for tau in (0.0, 1.0):
+        ref = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=prec, flags=flags)
+        modes, launches = [], []
+        for _ in range(3):
+            res = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=prec, flags=flags | pj.USE_GRAPH)
+            st = ctx.stats()
+            modes.append(st["graph"])
+            launches.append(st["launches"])
+            assert st["candidates"] <= st["capacity"]
+            same(ref, res)
+        assert modes[0] == "captured" and modes[1:] == ["replay", "replay"]
+        assert launches[1] == launches[2] == launches[0]   # the graph holds the direct run's kernels
+
+
+def test_graph_with_autotune_and_timeout(ctx, sets):
+    from paper_2604_19982_gb300 import pj
+    w, gR, gS = sets
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+    for _ in range(2):
+        res = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32,
+                       flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.USE_GRAPH | pj.AUTOTUNE)
+        same(ref, res)
+    res = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.USE_GRAPH,
+                   timeout_s=30.0)
+    same(ref, res)
+
+
+def test_graph_streamed_chunks(ctx, sets):
+    from paper_2604_19982_gb300 import pj
+    w, gR, gS = sets
+    side = configs.scaled_side(400.0, 20_000, 4000)
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+    parts = [(a, 500) for a in range(0, 4000, 500)]
+    g = ctx.load_set_streamed(4000, len(parts), lambda c: configs.blob_set(4000, side, 0, 0, start=parts[c][0],
+                                                                           count=parts[c][1]))
+    for _ in range(2):
+        res = ctx.join(g, gS, pj.WITHIN, tau=1.0, prec=pj.FP32,
+                       flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.USE_GRAPH)
+        same(ref, res)
+    g.free()
+
+
+def test_graph_flag_ignored_for_knn(ctx, sets):
+    from paper_2604_19982_gb300 import pj
+    w, gR, gS = sets
+    a = ctx.join(gR, gS, pj.KNN, k=2, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+    b = ctx.join(gR, gS, pj.KNN, k=2, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.USE_GRAPH)
+    same(a, b)
