@@ -42,6 +42,9 @@ TAUS = (0.0, 1.0)
 # kernel at full resolution (FMA = 2): 27 differences, 2 x 3 x 22 for the
 # vertex-to-face cases, 9 x 45 for the edge-to-edge cases.
 FLOPS_PER_TEST = 564
+# the single-precision refinement kernel the tuned path runs (scalar variant
+# with facet-ball culling); the traffic counters in profiles/ name it
+REFINE_KERNEL_ID = "k_refine<float>+ballcull"
 
 
 def parse():
@@ -336,16 +339,20 @@ def ours_arm(args):
     prof = os.path.join(ROOT, "profiles", "refine_fp32_traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
+            tr = json.load(open(prof))
+            # counters of another kernel (or an older build of it) do not apply
+            if tr.get("kernel_id") == REFINE_KERNEL_ID:
+                traffic = tr.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                 "frac": achieved / peak32 if peak32 else None, "traffic": traffic,
-                "kernel": "k_refine2 (single-precision refinement, packed FP32x2)",
+                "kernel": "k_refine<float> (single-precision refinement, facet-ball culling)",
                 "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x 2.070 GHz",
                 "measured_fma_peak": measured32, "frac_of_measured": achieved / measured32 if measured32 else None,
                 "flops_per_test": FLOPS_PER_TEST,
                 "kernel_ms_per_step": kms_fp32 / ksteps, "tests_per_step": tests_fp32 // ksteps,
+                "culled_tests_per_step": sum(s.get("tests_culled", 0) for s, _ in kstats) // ksteps,
                 "kernel_timing": "CUDA events around each refinement launch, 2 direct (non-graph) steps"}
 
     plain = None
@@ -534,7 +541,7 @@ def extra_arm(args):
                       "results_per_step": stats[-1]["results"]},
            "tri_tests_per_s": sum(st["tests_fp32"] + st["tests_fp64"] for st in stats) / (ms / 1000.0),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak(nsm), "unit": "TFLOP/s",
-                        "frac": achieved / alu_peak(nsm), "kernel": "k_refine2 (single-precision refinement)",
+                        "frac": achieved / alu_peak(nsm), "kernel": "k_refine<float> (single-precision refinement)",
                         "kernel_ms_per_step": kms32 / args.steps},
            "last_step_stats": {k: v for k, v in stats[-1].items() if k != "steps"},
            "clocks": clk}

@@ -130,7 +130,7 @@ struct pj_ctx {
   };
   std::vector<GraphEntry> graphs;   // captured joins (PJ_USE_GRAPH), oldest first
   int ctas_per_sm = 0;             // 0 = from occupancy
-  int refine_variant = 2;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
+  int refine_variant = 1;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
   int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
   std::string autotune_cache;
   // per-query workspace

@@ -183,9 +183,14 @@ __global__ void k_decide_within(int64_t n, uint8_t* status, const uint8_t* lod0,
   } else if (l > tau || (full && F64)) {
     status[p] = REMOVED;
     atomicAdd(&cnt[3], 1ULL);
-  } else if (full) {
-    status[p] = REDECIDE;
-    atomicAdd(&cnt[4], 1ULL);
+  } else {
+    // still open: keep the tightest upper bound (it lets the next step skip
+    // facet pairs that cannot attain the minimum)
+    dhi[p] = fmin(dhi[p], u);
+    if (full) {
+      status[p] = REDECIDE;
+      atomicAdd(&cnt[4], 1ULL);
+    }
   }
 }
 
@@ -608,12 +613,12 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
            "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"graph_ms\":%.4f,"
            "\"capacity\":%lld,"
            "\"candidates\":%lld,\"results\":%lld,"
-           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%llu,"
+           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%llu,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
            tau, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, gmode, graph_ms, (long long)nn, (long long)n, (long long)m,
            cnt[0],
-           cnt[1], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
+           cnt[1], cnt[5], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
            ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   JoinSummary& js = ctx->last_sum;

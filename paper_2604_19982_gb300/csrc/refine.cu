@@ -402,6 +402,7 @@ struct RefineArgs {
   void* ub;
   void* mid;
   unsigned long long* ntests;
+  unsigned long long* nculled;   // facet pairs skipped by the ball test (may be null)
   int* err;
   int4* queue;       // straddling facet pairs: (pair, r facet, s facet, eps bits)
   unsigned* qcount;
@@ -409,6 +410,7 @@ struct RefineArgs {
   uint8_t* flag;     // per pair: a unit proved ub <= threshold (early exit)
   int early;         // skip the units of flagged pairs
   int exact_cross;   // decide every straddling pair's meeting test (bounds entry points)
+  const double* ub_prev;   // per pair: a valid upper bound of d known before this step (may be null)
 };
 
 template <class T>
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
   const int64_t NT = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
   uint32_t ph0 = 0, ph1 = 0;
   int b = 0;
-  unsigned long long ntest = 0;
+  unsigned long long ntest = 0, nskip = 0;
 
   int64_t cur = 0;
   if (lane == 0) {
@@ -578,17 +580,42 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     T lbm = INF, ubu = INF, d2m = INF;
     bool anyposs = false;
     const T eh = T(tl.eh);
-    if (act) {
-      ntest += (unsigned long long)sl;
+    // single precision: facet pairs whose balls are farther apart than what
+    // the lane can still improve are skipped (when the whole warp agrees)
+    float dcur = __int_as_float(0x7f800000);
+    if (sizeof(T) == 4 && FULL && a.ub_prev) dcur = __double2float_ru(a.ub_prev[tl.pair]);
+    {
       for (int j = 0; j < sl; ++j) {
+        if constexpr (sizeof(T) == 4) {
+          // the ball (and hd / ph) first; the record only when needed
+          const float* qx = reinterpret_cast<const float*>(&rec[j]);
+          const float qc[3] = {qx[45], qx[46], qx[47]};
+          const float qr = qx[48];
+          bool need = act;
+          if (need) {
+            if (FULL) need = !balls_apart(P.sc, P.sr, qc, qr, dcur);
+            else
+              need = !(balls_apart(P.sc, P.sr, qc, qr, __fadd_ru(lbm, __fadd_ru(P.ph, qx[7]))) &&
+                       balls_apart(P.sc, P.sr, qc, qr, __fsub_ru(ubu, __fadd_rd(P.hd, qx[3]))));
+          }
+          if (!__any_sync(FULLM, need)) {
+            nskip += act;
+            continue;
+          }
+        }
+        if (!act) continue;
         RecT Q;
         load_rec(Q, rec[j]);
+        ++ntest;
         bool maybe;
         T d2 = tri_d2(P, Q, eh, maybe);
         if (maybe && boxes_apart(P, Q)) maybe = false;   // straddling planes, but apart
         if (!maybe) {
           if (FULL) {
-            d2m = min(d2m, d2);
+            if (d2 < d2m) {
+              d2m = d2;
+              if (sizeof(T) == 4) dcur = fminf(dcur, __fsqrt_ru((float)d2m));
+            }
           } else {
             T d = sqrt_test(d2);
             lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
@@ -669,6 +696,8 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
   }
   ntest = warp_sum_u64(ntest);
   if (lane == 0 && ntest) atomicAdd(a.ntests, ntest);
+  nskip = warp_sum_u64(nskip);
+  if (lane == 0 && nskip && a.nculled) atomicAdd(a.nculled, nskip);
 }
 
 // Bounds contribution of the queued straddling facet pairs: the 15-candidate
@@ -711,7 +740,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
   const int64_t NT = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
   uint32_t ph0 = 0, ph1 = 0;
   int b = 0;
-  unsigned long long ntest = 0;
+  unsigned long long ntest = 0, nskip = 0;
 
   int64_t cur = 0;
   if (lane == 0) {
@@ -742,6 +771,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
     const bool act = lane < rl;
     RecL2 P;
     T Pph, Phd;
+    float Psc[3], Psr;
     {
       const float4* f = a.facR + 3LL * (tl.rb + (act ? lane : 0));
       float4 A = f[0], B = f[1], C = f[2];
@@ -754,6 +784,10 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
       dup_rec(P, R);
       Pph = R.ph;
       Phd = R.hd;
+      Psc[0] = R.sc[0];
+      Psc[1] = R.sc[1];
+      Psc[2] = R.sc[2];
+      Psr = R.sr;
     }
     const bool ok = mbar_wait_bounded(b ? bar1 : bar0, b ? ph1 : ph0, MBAR_POLL_LIMIT);
     if (__any_sync(FULLM, !ok)) {
@@ -789,9 +823,33 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
     T lbm = INF, ubu = INF, d2m = INF;
     bool anyposs = false;
     const T eh = T(tl.eh);
-    if (act) {
-      ntest += (unsigned long long)sl;
+    // facet pairs whose balls are farther apart than what the lane can
+    // still improve are skipped (a record pair when the whole warp agrees)
+    float dcur = FULL && a.ub_prev ? __double2float_ru(a.ub_prev[tl.pair]) : INF;
+    {
       for (int jp = 0; jp < (sl2 >> 1); ++jp) {
+        bool need = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!act || 2 * jp + h >= sl) continue;
+          const RecSmem2& S2 = rec[jp];
+          const float qc[3] = {S2.x[2 * F_SC + h], S2.x[2 * (F_SC + 1) + h], S2.x[2 * (F_SC + 2) + h]};
+          const float qr = S2.x[2 * F_SR + h];
+          bool nh;
+          if (FULL) {
+            nh = !balls_apart(Psc, Psr, qc, qr, dcur);
+          } else {
+            const float qph = S2.x[2 * F_PH + h], qhd = S2.x[2 * F_HD + h];
+            nh = !(balls_apart(Psc, Psr, qc, qr, __fadd_ru(lbm, __fadd_ru(Pph, qph))) &&
+                   balls_apart(Psc, Psr, qc, qr, __fsub_ru(ubu, __fadd_rd(Phd, qhd))));
+          }
+          need = need || nh;
+        }
+        if (!__any_sync(FULLM, need)) {
+          if (act) nskip += min(2, sl - 2 * jp);
+          continue;
+        }
+        if (!act) continue;
         RecL2 Q;
         load_pair(Q, rec[jp]);
         bool m0, m1;
@@ -800,13 +858,17 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
         for (int h = 0; h < 2; ++h) {
           const int j = 2 * jp + h;
           if (j >= sl) continue;
+          ++ntest;
           const T d2 = h ? hi2(d2p) : lo2(d2p);
           bool maybe = h ? m1 : m0;
           if (maybe && boxes_apart_half(P, rec[jp], h)) maybe = false;
           const T qph = rec[jp].x[2 * F_PH + h], qhd = rec[jp].x[2 * F_HD + h];
           if (!maybe) {
             if (FULL) {
-              d2m = min(d2m, d2);
+              if (d2 < d2m) {
+                d2m = d2;
+                dcur = fminf(dcur, __fsqrt_ru(d2m));
+              }
             } else {
               T d = sqrt_test(d2);
               lbm = min(lbm, sub_rd(d, add_ru(Pph, qph)));
@@ -882,6 +944,8 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
   }
   ntest = warp_sum_u64(ntest);
   if (lane == 0 && ntest) atomicAdd(a.ntests, ntest);
+  nskip = warp_sum_u64(nskip);
+  if (lane == 0 && nskip && a.nculled) atomicAdd(a.nculled, nskip);
 }
 
 template <class T, bool FULL>
@@ -973,8 +1037,8 @@ static void launch_refine2(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaS
   }
 }
 
-// FP64 steps use k_refine<double>; FP32 steps the packed kernel (variant 2,
-// default) or the scalar one (variant 1), chosen per context.
+// FP64 steps use k_refine<double>; FP32 steps the scalar kernel (variant 1,
+// default) or the packed one (variant 2), chosen per context or autotuned.
 static void dispatch_refine(pj_ctx* ctx, RefineArgs& a, int64_t n_tiles, const StepSpec& sp, cudaStream_t st) {
   if (sp.fp64) {
     if (sp.full) launch_refine<double, true>(ctx, a, n_tiles, st);
@@ -1017,10 +1081,12 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
   a.facS = S->lod[sp.lodS].fac;
   a.origin = (const float4*)ctx->ws[WS_ORIGIN].p;
   a.thr = (const float*)ctx->ws[WS_THR].p;
+  a.ub_prev = (const double*)ctx->ws[WS_DHI].p;
   a.lb = ctx->ws[WS_LB].p;
   a.ub = ctx->ws[WS_UB].p;
   a.mid = ctx->ws[WS_MID].p;
   a.ntests = ctx->d_counters + (sp.fp64 ? 1 : 0);
+  a.nculled = ctx->d_counters + 5;
   a.err = ctx->d_err;
   a.qcap = CROSS_QUEUE_CAP;
   a.queue = (int4*)ws_get(ctx, WS_MISC2, (size_t)a.qcap * sizeof(int4), st);
@@ -1079,10 +1145,12 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount un
   a.facS = S->lod[sp.lodS].fac;
   a.origin = b.origin;
   a.thr = b.thr;
+  a.ub_prev = b.dhi;
   a.lb = b.lb;
   a.ub = b.ub;
   a.mid = b.mid;
   a.ntests = b.counters;
+  a.nculled = nullptr;
   a.err = err;
   a.queue = b.queue;
   a.qcap = b.qcap;

@@ -305,7 +305,18 @@ struct RecL {
   float m[3][3];
   float c, mc[3], ev[3];
   float hd, ph;
+  float sc[3], sr;   // a ball holding the facet: centroid, radius rounded well up
 };
+
+// Lower bound of the distance of two facets from their balls, as a test on
+// squares: true when |c_P - c_Q| - r_P - r_Q > bound for the exact values
+// (relative slack covers the rounding of the centre distance).
+__device__ __forceinline__ bool balls_apart(const float pc[3], float pr, const float qc[3], float qr, float bound) {
+  const float dx = pc[0] - qc[0], dy = pc[1] - qc[1], dz = pc[2] - qc[2];
+  const float dist2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const float lim = bound + pr + qr;
+  return lim >= 0.f && dist2 * 0.99996f > lim * lim * 1.00002f;
+}
 
 __device__ __forceinline__ void make_rec(RecL& R, const float a[3], const float b[3], const float c[3], float hd,
                                          float ph, bool) {
@@ -348,11 +359,26 @@ __device__ __forceinline__ void make_rec(RecL& R, const float a[3], const float 
   R.c = dot3(R.n, R.v[0]) - hoff;
   R.hd = hd;
   R.ph = ph;
+  float rmax = 0.f, amax = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) R.sc[k] = (R.v[0][k] + R.v[1][k] + R.v[2][k]) * (1.f / 3.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float q2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float dv = R.v[i][k] - R.sc[k];
+      q2 = fmaf(dv, dv, q2);
+      amax = fmaxf(amax, fabsf(R.v[i][k]));
+    }
+    rmax = fmaxf(rmax, q2);
+  }
+  R.sr = sqrtf(rmax) * 1.00001f + amax * 1e-6f + 1e-30f;
 }
 
 // Shared-memory image of a RecL: 48 floats, 12 float4 loads.
 struct RecSmemL {
-  float x[48];
+  float x[52];
 };
 
 __device__ __forceinline__ void store_rec(RecSmemL& S, const RecL& R) {
@@ -368,14 +394,15 @@ __device__ __forceinline__ void store_rec(RecSmemL& S, const RecL& R) {
   q[8] = make_float4(R.m[1][0], R.m[1][1], R.m[1][2], R.iee[2]);
   q[9] = make_float4(R.m[2][0], R.m[2][1], R.m[2][2], R.mc[0]);
   q[10] = make_float4(R.ev[0], R.ev[1], R.ev[2], R.mc[1]);
-  q[11] = make_float4(R.mc[2], 0.f, 0.f, 0.f);
+  q[11] = make_float4(R.mc[2], R.sc[0], R.sc[1], R.sc[2]);
+  q[12] = make_float4(R.sr, 0.f, 0.f, 0.f);
 }
 
 __device__ __forceinline__ void load_rec(RecL& R, const RecSmemL& S) {
   const float4* q = reinterpret_cast<const float4*>(S.x);
-  float4 a[12];
+  float4 a[13];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) a[k] = q[k];
+  for (int k = 0; k < 13; ++k) a[k] = q[k];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     R.v[i][0] = a[i].x; R.v[i][1] = a[i].y; R.v[i][2] = a[i].z;
@@ -387,6 +414,7 @@ __device__ __forceinline__ void load_rec(RecL& R, const RecSmemL& S) {
   R.iee[0] = a[6].w; R.iee[1] = a[7].w; R.iee[2] = a[8].w;
   R.mc[0] = a[9].w; R.mc[1] = a[10].w; R.mc[2] = a[11].x;
   R.ev[0] = a[10].x; R.ev[1] = a[10].y; R.ev[2] = a[10].z;
+  R.sc[0] = a[11].y; R.sc[1] = a[11].z; R.sc[2] = a[11].w; R.sr = a[12].x;
 }
 
 // (a . x) - k as one FMA chain

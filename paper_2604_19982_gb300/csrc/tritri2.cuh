@@ -81,9 +81,9 @@ __device__ __forceinline__ void dup_rec(RecL2& D, const RecL& R) {
 }
 
 // Shared-memory image of two s facets: field f of facet h (0 / 1) at float
-// 2 f + h, 48 fields (hd, ph and two pads included), padded to 100 floats
-// so that the 16 records of a block start on different banks.
-constexpr int REC2_FLOATS = 100;
+// 2 f + h, 49 fields, padded to 102 floats so that the 16 records of a block
+// start on different banks.
+constexpr int REC2_FLOATS = 102;
 struct RecSmem2 {
   float x[REC2_FLOATS];
 };
@@ -99,7 +99,9 @@ enum : int {
   F_NEV = 39,   // -ev[i]
   F_NC = 42,
   F_HD = 43,
-  F_PH = 44
+  F_PH = 44,
+  F_SC = 45,    // ball centre [k]
+  F_SR = 48     // ball radius
 };
 
 __device__ __forceinline__ void store_half(RecSmem2& S, int h, const RecL& R) {
@@ -121,6 +123,9 @@ __device__ __forceinline__ void store_half(RecSmem2& S, int h, const RecL& R) {
   x[2 * F_NC] = -R.c;
   x[2 * F_HD] = R.hd;
   x[2 * F_PH] = R.ph;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) x[2 * (F_SC + k)] = R.sc[k];
+  x[2 * F_SR] = R.sr;
 }
 
 __device__ __forceinline__ f2 ld2(const RecSmem2& S, int f) {
