@@ -411,6 +411,7 @@ struct RefineArgs {
   int early;         // skip the units of flagged pairs
   int exact_cross;   // decide every straddling pair's meeting test (bounds entry points)
   const double* ub_prev;   // per pair: a valid upper bound of d known before this step (may be null)
+  int cull;                // units were pruned against thr (values above thr are not needed)
 };
 
 template <class T>
@@ -581,11 +582,32 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     bool anyposs = false;
     const T eh = T(tl.eh);
     // single precision: facet pairs whose balls are farther apart than what
-    // the lane can still improve are skipped (when the whole warp agrees)
+    // the lane can still improve are skipped (when the whole warp agrees).
+    // At full resolution the bound starts at the pair's upper bound and,
+    // with pruning, at its threshold (distances above it are not needed:
+    // a within decision only compares with tau, and k-NN clamps lb to thr)
     float dcur = __int_as_float(0x7f800000);
-    if (sizeof(T) == 4 && FULL && a.ub_prev) dcur = __double2float_ru(a.ub_prev[tl.pair]);
+    uint32_t cand = sl >= 32 ? 0xffffffffu : ((1u << sl) - 1u);
+    if constexpr (sizeof(T) == 4 && FULL) {
+      if (a.ub_prev) dcur = __double2float_ru(a.ub_prev[tl.pair]);
+      if (a.cull) dcur = fminf(dcur, a.thr[tl.pair]);
+      // the s facets some lane may need, from all balls at once
+      uint32_t mine = 0;
+      if (act) {
+        for (int j = 0; j < sl; ++j) {
+          const float* qx = reinterpret_cast<const float*>(&rec[j]);
+          const float qc[3] = {qx[45], qx[46], qx[47]};
+          if (!balls_apart(P.sc, P.sr, qc, qx[48], dcur)) mine |= 1u << j;
+        }
+      }
+      const uint32_t need_any = __reduce_or_sync(FULLM, mine);
+      if (act) nskip += (unsigned long long)__popc(cand & ~need_any);
+      cand = need_any;
+    }
     {
-      for (int j = 0; j < sl; ++j) {
+      while (cand) {
+        const int j = __ffs(cand) - 1;
+        cand &= cand - 1u;
         if constexpr (sizeof(T) == 4) {
           // the ball (and hd / ph) first; the record only when needed
           const float* qx = reinterpret_cast<const float*>(&rec[j]);
@@ -826,6 +848,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
     // facet pairs whose balls are farther apart than what the lane can
     // still improve are skipped (a record pair when the whole warp agrees)
     float dcur = FULL && a.ub_prev ? __double2float_ru(a.ub_prev[tl.pair]) : INF;
+    if (FULL && a.cull) dcur = fminf(dcur, a.thr[tl.pair]);
     {
       for (int jp = 0; jp < (sl2 >> 1); ++jp) {
         bool need = false;
@@ -1095,6 +1118,7 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
   a.flag = (uint8_t*)ctx->ws[WS_FLAG].p;
   a.early = sp.early ? 1 : 0;
   a.exact_cross = sp.exact_cross ? 1 : 0;
+  a.cull = sp.cull ? 1 : 0;
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
   dispatch_refine(ctx, a, n_tiles, sp, st);
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev + 1], st));
@@ -1159,6 +1183,7 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount un
   a.flag = b.flag;
   a.early = 0;
   a.exact_cross = sp.exact_cross ? 1 : 0;
+  a.cull = sp.cull ? 1 : 0;
   dispatch_refine(ctx, a, n_tiles, sp, st);
 }
 
