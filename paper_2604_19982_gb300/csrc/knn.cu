@@ -100,9 +100,12 @@ __global__ void k_theta(int nR, const float* ancR, const float* ancS, KGrid G, c
       if (z < 0 || z >= G.dim[2]) continue;
       for (int y = cy - sh; y <= cy + sh; ++y) {
         if (y < 0 || y >= G.dim[1]) continue;
-        for (int x = cx - sh; x <= cx + sh; ++x) {
+        // the shell's cells of this row: all of it on the two faces, else
+        // its two ends
+        const bool face = abs(z - cz) == sh || abs(y - cy) == sh;
+        const int xstep = face || sh == 0 ? 1 : 2 * sh;
+        for (int x = cx - sh; x <= cx + sh; x += xstep) {
           if (x < 0 || x >= G.dim[0]) continue;
-          if (max(abs(x - cx), max(abs(y - cy), abs(z - cz))) != sh) continue;   // shell only
           const int64_t c = kcell_id(G, x, y, z);
           for (int64_t q0 = off[c]; q0 < off[c + 1]; q0 += 32) {
             const int64_t q = q0 + lane;
@@ -116,9 +119,13 @@ __global__ void k_theta(int nR, const float* ancR, const float* ancS, KGrid G, c
                 dd = __dsqrt_ru(__dadd_ru(__dadd_ru(__dmul_ru(gx, gx), __dmul_ru(gy, gy)), __dmul_ru(gz, gz)));
               }
             }
-            // lane 0 inserts the batch into the sorted top-k list
-            for (int l = 0; l < 32; ++l) {
-              double v = __shfl_sync(0xffffffffu, dd, l);
+            have += __popc(__ballot_sync(0xffffffffu, dd < INFINITY));
+            // only the lanes that beat the current k-th enter the list
+            unsigned m = __ballot_sync(0xffffffffu, dd < top[k - 1]);
+            while (m) {
+              const int l = __ffs(m) - 1;
+              m &= m - 1u;
+              const double v = __shfl_sync(0xffffffffu, dd, l);
               if (lane == 0 && v < top[k - 1]) {
                 int pos = k - 1;
                 while (pos > 0 && top[pos - 1] > v) {
@@ -127,7 +134,7 @@ __global__ void k_theta(int nR, const float* ancR, const float* ancS, KGrid G, c
                 }
                 top[pos] = v;
               }
-              if (v < INFINITY) ++have;
+              __syncwarp();
             }
             __syncwarp();
           }
@@ -229,8 +236,10 @@ static KGrid make_kgrid(const pj_set* R, const pj_set* S) {
   }
   double vol = 1.0;
   for (int k = 0; k < 3; ++k) vol *= std::max(1e-6, (double)hi[k] - lo[k]);
-  // about two objects per cell on average, never below the mean box size
-  double h = std::max(ext, std::cbrt(vol * 2.0 / std::max(1, S->n)));
+  // cells a quarter of the width that would hold two objects on average
+  // (clustered sets are far denser than that average), never below the
+  // mean box size
+  double h = std::max(ext, 0.25 * std::cbrt(vol * 2.0 / std::max(1, S->n)));
   KGrid G;
   for (;;) {
     int64_t tot = 1;
