@@ -581,23 +581,26 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     T lbm = INF, ubu = INF, d2m = INF;
     bool anyposs = false;
     const T eh = T(tl.eh);
-    // single precision: facet pairs whose balls are farther apart than what
-    // the lane can still improve are skipped (when the whole warp agrees).
-    // At full resolution the bound starts at the pair's upper bound and,
-    // with pruning, at its threshold (distances above it are not needed:
-    // a within decision only compares with tau, and k-NN clamps lb to thr)
-    float dcur = __int_as_float(0x7f800000);
+    // facet pairs whose balls are farther apart than what the lane can
+    // still improve are skipped (when the whole warp agrees): always in
+    // single precision, in double precision when units were pruned.  At
+    // full resolution the bound starts at the pair's upper bound and, with
+    // pruning, at its threshold (distances above it are not needed: a
+    // within decision only compares with tau, and k-NN clamps lb to thr)
+    const bool balls = sizeof(T) == 4 || a.cull;
+    T dcur = INF;
     uint32_t cand = sl >= 32 ? 0xffffffffu : ((1u << sl) - 1u);
-    if constexpr (sizeof(T) == 4 && FULL) {
-      if (a.ub_prev) dcur = __double2float_ru(a.ub_prev[tl.pair]);
-      if (a.cull) dcur = fminf(dcur, a.thr[tl.pair]);
+    if (FULL && balls) {
+      if (a.ub_prev) dcur = T(a.ub_prev[tl.pair]);
+      if (sizeof(T) == 4 && a.ub_prev) dcur = T(__double2float_ru(a.ub_prev[tl.pair]));
+      if (a.cull) dcur = min(dcur, T(a.thr[tl.pair]));
       // the s facets some lane may need, from all balls at once
       uint32_t mine = 0;
       if (act) {
         for (int j = 0; j < sl; ++j) {
-          const float* qx = reinterpret_cast<const float*>(&rec[j]);
-          const float qc[3] = {qx[45], qx[46], qx[47]};
-          if (!balls_apart(P.sc, P.sr, qc, qx[48], dcur)) mine |= 1u << j;
+          T qc[3], qr, qhd, qph;
+          rec_ball(rec[j], qc, qr, qhd, qph);
+          if (!balls_apart(P.sc, P.sr, qc, qr, dcur)) mine |= 1u << j;
         }
       }
       const uint32_t need_any = __reduce_or_sync(FULLM, mine);
@@ -608,17 +611,16 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
       while (cand) {
         const int j = __ffs(cand) - 1;
         cand &= cand - 1u;
-        if constexpr (sizeof(T) == 4) {
+        if (balls) {
           // the ball (and hd / ph) first; the record only when needed
-          const float* qx = reinterpret_cast<const float*>(&rec[j]);
-          const float qc[3] = {qx[45], qx[46], qx[47]};
-          const float qr = qx[48];
+          T qc[3], qr, qhd, qph;
+          rec_ball(rec[j], qc, qr, qhd, qph);
           bool need = act;
           if (need) {
             if (FULL) need = !balls_apart(P.sc, P.sr, qc, qr, dcur);
             else
-              need = !(balls_apart(P.sc, P.sr, qc, qr, __fadd_ru(lbm, __fadd_ru(P.ph, qx[7]))) &&
-                       balls_apart(P.sc, P.sr, qc, qr, __fsub_ru(ubu, __fadd_rd(P.hd, qx[3]))));
+              need = !(balls_apart(P.sc, P.sr, qc, qr, add_ru(lbm, add_ru(P.ph, qph))) &&
+                       balls_apart(P.sc, P.sr, qc, qr, sub_ru(ubu, add_rd(P.hd, qhd))));
           }
           if (!__any_sync(FULLM, need)) {
             nskip += act;
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
           if (FULL) {
             if (d2 < d2m) {
               d2m = d2;
-              if (sizeof(T) == 4) dcur = fminf(dcur, __fsqrt_ru((float)d2m));
+              if (balls) dcur = min(dcur, sqrt_ru(d2m));
             }
           } else {
             T d = sqrt_test(d2);

@@ -39,7 +39,17 @@ struct Rec {
   T n[3];
   T m[3][3];
   T hd, ph, hoff;
+  T sc[3], sr;   // a ball holding the facet: centroid, radius rounded well up
 };
+
+// Facet balls apart by more than `bound` (see the float overload below).
+__device__ __forceinline__ bool balls_apart(const double pc[3], double pr, const double qc[3], double qr,
+                                            double bound) {
+  const double dx = pc[0] - qc[0], dy = pc[1] - qc[1], dz = pc[2] - qc[2];
+  const double dist2 = fma(dz, dz, fma(dy, dy, dx * dx));
+  const double lim = bound + pr + qr;
+  return lim >= 0.0 && dist2 * (1.0 - 1e-12) > lim * lim * (1.0 + 1e-12);
+}
 
 // ---------------------------------------------------------------- scalar ops
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
@@ -64,6 +74,12 @@ __device__ __forceinline__ float add_ru(float a, float b) { return __fadd_ru(a, 
 __device__ __forceinline__ double add_ru(double a, double b) { return __dadd_ru(a, b); }
 __device__ __forceinline__ float sub_rd(float a, float b) { return __fsub_rd(a, b); }
 __device__ __forceinline__ double sub_rd(double a, double b) { return __dsub_rd(a, b); }
+__device__ __forceinline__ float sub_ru(float a, float b) { return __fsub_ru(a, b); }
+__device__ __forceinline__ double sub_ru(double a, double b) { return __dsub_ru(a, b); }
+__device__ __forceinline__ float add_rd(float a, float b) { return __fadd_rd(a, b); }
+__device__ __forceinline__ double add_rd(double a, double b) { return __dadd_rd(a, b); }
+__device__ __forceinline__ float sqrt_ru(float x) { return __fsqrt_ru(x); }
+__device__ __forceinline__ double sqrt_ru(double x) { return __dsqrt_ru(x); }
 
 template <class T>
 __device__ __forceinline__ T dot3(const T* a, const T* b) {
@@ -114,6 +130,21 @@ __device__ __forceinline__ void make_rec(Rec<T>& R, const T a[3], const T b[3], 
   }
   R.hd = hd;
   R.ph = ph;
+  T rmax = T(0), amax = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) R.sc[k] = (R.v[0][k] + R.v[1][k] + R.v[2][k]) * (T(1) / T(3));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T q2 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T dv = R.v[i][k] - R.sc[k];
+      q2 = fma_(dv, dv, q2);
+      amax = max(amax, abs(R.v[i][k]));
+    }
+    rmax = max(rmax, q2);
+  }
+  R.sr = sqrt(rmax) * T(1.00001) + amax * T(1e-6) + T(1e-30);
 }
 
 // |e0 x e1| / (|e0| |e1|) of a facet (its sine; small for slivers)
@@ -133,7 +164,7 @@ __device__ __forceinline__ T facet_sin(const T a[3], const T b[3], const T c[3])
 // Shared-memory image of a record: 40 values, vector-loadable.
 template <class T>
 struct RecSmem {
-  T x[40];
+  T x[44];
 };
 
 template <class T>
@@ -160,6 +191,10 @@ __device__ __forceinline__ void store_rec(RecSmem<T>& S, const Rec<T>& R) {
   x[31] = R.iee[1];
   x[35] = R.iee[2];
   x[39] = T(0);
+  x[40] = R.sc[0];
+  x[41] = R.sc[1];
+  x[42] = R.sc[2];
+  x[43] = R.sr;
 }
 
 template <class T>
@@ -185,9 +220,9 @@ __device__ __forceinline__ void load_rec<float>(Rec<float>& R, const RecSmem<flo
 template <>
 __device__ __forceinline__ void load_rec<double>(Rec<double>& R, const RecSmem<double>& S) {
   const double2* q = reinterpret_cast<const double2*>(S.x);
-  double x[40];
+  double x[44];
 #pragma unroll
-  for (int k = 0; k < 20; ++k) {
+  for (int k = 0; k < 22; ++k) {
     double2 t = q[k];
     x[2 * k] = t.x;
     x[2 * k + 1] = t.y;
@@ -204,6 +239,7 @@ __device__ __forceinline__ void load_rec<double>(Rec<double>& R, const RecSmem<d
   R.ee[0] = x[15]; R.ee[1] = x[19]; R.ee[2] = x[23];
   R.n[0] = x[24]; R.n[1] = x[25]; R.n[2] = x[26];
   R.iee[0] = x[27]; R.iee[1] = x[31]; R.iee[2] = x[35];
+  R.sc[0] = x[40]; R.sc[1] = x[41]; R.sc[2] = x[42]; R.sr = x[43];
 }
 
 // ---------------------------------------------------------------- the test
@@ -465,6 +501,24 @@ __device__ __forceinline__ float tri_d2(const RecL& P, const RecL& Q, float eh, 
   const float qmin = min(hQ[0], min(hQ[1], hQ[2])), qmax = max(hQ[0], max(hQ[1], hQ[2]));
   maybe = (pmin <= eh) && (pmax >= -eh) && (qmin <= eh) && (qmax >= -eh);
   return d2;
+}
+
+// Ball, hd and ph of a shared-memory record (read before the record itself).
+__device__ __forceinline__ void rec_ball(const RecSmemL& S, float c[3], float& r, float& hd, float& ph) {
+  c[0] = S.x[45];
+  c[1] = S.x[46];
+  c[2] = S.x[47];
+  r = S.x[48];
+  hd = S.x[3];
+  ph = S.x[7];
+}
+__device__ __forceinline__ void rec_ball(const RecSmem<double>& S, double c[3], double& r, double& hd, double& ph) {
+  c[0] = S.x[40];
+  c[1] = S.x[41];
+  c[2] = S.x[42];
+  r = S.x[43];
+  hd = S.x[3];
+  ph = S.x[7];
 }
 
 // Record types per precision: FP32 kernels use the form above, FP64 the
