@@ -202,15 +202,16 @@ static T* upload(const T* h, size_t count, cudaStream_t st) {
 }
 
 // Lay a described set out on the device (see pj_load_set).
-void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st) {
+void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err) {
   const int n = s->n, L = s->L;
+  if (!err) err = ctx->d_err;
   int th = 256;
   for (int l = 0; l < L; ++l) {
     LodData& ld = s->lod[l];
     if (ld.F == 0) continue;
     k_expand_blocks<<<(unsigned)((ld.B * 32 + th - 1) / th), th, 0, st>>>(
         ld.B, n, raw[l].verts, raw[l].voff, raw[l].faces, ld.foff, ld.boff, raw[l].nfs, raw[l].hd, raw[l].ph, ld.fac,
-        ld.blk, ctx->d_err);
+        ld.blk, err);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
     k_chunks_from_blocks<<<(unsigned)((ld.C + th - 1) / th), th, 0, st>>>(ld.C, n, ld.coff, ld.boff, ld.blk,
@@ -220,7 +221,7 @@ void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t s
   }
   if (n > 0) {
     k_mbb<<<(unsigned)(((int64_t)n * 32 + th - 1) / th), th, 0, st>>>(n, raw[L - 1].verts, raw[L - 1].voff, s->anchor,
-                                                                       s->mbb, ctx->d_err);
+                                                                       s->mbb, err);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
   }
@@ -421,6 +422,7 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
     (void)cudaGetLastError();
   }
   PJ_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  PJ_CK(cudaStreamCreateWithFlags(&ctx->build_stream, cudaStreamNonBlocking));
   PJ_CK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
   PJ_CK(cudaMalloc((void**)&ctx->d_counters, 16 * sizeof(unsigned long long)));
   PJ_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
@@ -471,10 +473,13 @@ void pj_destroy(pj_ctx* ctx) {
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   for (void* hp : ctx->stream_pinned)
     if (hp) cudaFreeHost(hp);
+  for (void* hp : ctx->stream_box_pinned)
+    if (hp) cudaFreeHost(hp);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->build_stream) cudaStreamDestroy(ctx->build_stream);
   delete ctx;
 }
 

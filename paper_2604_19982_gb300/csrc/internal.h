@@ -115,6 +115,7 @@ struct pj_ctx {
   int cc_major = 0, cc_minor = 0;
   cudaStream_t stream = nullptr;   // default work stream
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t build_stream = nullptr;   // set building of streamed chunks
   int* d_err = nullptr;            // device error word
   unsigned long long* d_counters = nullptr;  // [16] device counters
   std::string last_error;
@@ -151,6 +152,8 @@ struct pj_ctx {
   size_t h_stage_cap = 0;
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};
+  void* stream_box_pinned[2] = {};  // pinned copies of a chunk's object boxes and error word
+  size_t stream_box_cap[2] = {};
 };
 
 namespace pj {
@@ -170,6 +173,7 @@ enum Slot {
   WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
   WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5,
   WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3, WS_STREAM4, WS_STREAM5,
+  WS_STREAM6, WS_STREAM7, WS_STREAM8,
   WS_COUNT
 };
 
@@ -317,7 +321,7 @@ struct RawLod {
 // Facet records, chunk and block boxes of every LoD and the object boxes,
 // into the set's allocated buffers (foff / coff / boff already on the
 // device); kernel errors go to ctx->d_err.
-void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st);
+void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err = nullptr);
 
 // ---- triangle distance batch (refine.cu)
 void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool fp64, double* out,

@@ -187,15 +187,17 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   double ms_fill = 0, ms_pack = 0;
   int L_first = 0;
   struct Events {
-    cudaEvent_t e[6] = {};
+    cudaEvent_t e[8] = {};
     ~Events() {
       for (cudaEvent_t x : e)
         if (x) cudaEventDestroy(x);
     }
   } evs;
-  for (int i = 0; i < 6; ++i) PJ_CK(cudaEventCreateWithFlags(&evs.e[i], i < 2 ? cudaEventDisableTiming : 0));
+  for (int i = 0; i < 8; ++i)
+    PJ_CK(cudaEventCreateWithFlags(&evs.e[i], (i < 2 || i >= 6) ? cudaEventDisableTiming : 0));
   slots[0].copied = evs.e[0];
   slots[1].copied = evs.e[1];
+  cudaEvent_t built[2] = {evs.e[6], evs.e[7]};
   cudaEvent_t h2d0[2] = {evs.e[2], evs.e[3]}, h2d1[2] = {evs.e[4], evs.e[5]};
   Plan plans[2];   // the calling thread's copy of the plan of each slot in flight
   const int device = ctx->device;
@@ -326,25 +328,18 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     return true;
   };
 
-  std::vector<int32_t> rr, ss;
-  std::vector<double> dlo, dhi, dd;
-  std::vector<uint8_t> ex;
-  JoinSummary tot;
-  int64_t objects = 0;
-  for (int c = 0; c < N; ++c) {
-    if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
-    if (enqueued <= c) {
-      enqueue(c, true);
-      enqueued = c + 1;
-    }
-    ChunkSlot& sl = slots[c & 1];
-    const Plan P = plans[c & 1];
-    // the copy of the next chunk overlaps this chunk's build and join
-    if (c + 1 < N && enqueued == c + 1 && enqueue(c + 1, false)) enqueued = c + 2;
-    PJ_CK(cudaStreamWaitEvent(st, sl.copied, 0));
-    unsigned char* dev = (unsigned char*)ctx->ws[(c & 1) ? WS_STREAM5 : WS_STREAM4].p;
-    // device view of the chunk
-    pj_set view;
+  // set building of chunk c (its copy issued) on the build stream, into
+  // the derived buffers of its slot; the boxes and the error word come back
+  // to pinned memory, and built[slot] marks the end
+  pj_set views[2];
+  int prepared[2] = {-1, -1};
+  auto prepare = [&](int c) {
+    const int si = c & 1;
+    const Plan& P = plans[si];
+    unsigned char* dev = (unsigned char*)ctx->ws[si ? WS_STREAM5 : WS_STREAM4].p;
+    cudaStream_t bst = ctx->build_stream;
+    pj_set& view = views[si];
+    view = pj_set();
     view.ctx = ctx;
     view.device = ctx->device;
     view.n = P.n;
@@ -354,9 +349,12 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       fac_n += 3 * std::max<int64_t>(1, P.F[l]);
       box_n += 3 * (std::max<int64_t>(1, P.C[l]) + std::max<int64_t>(1, P.B[l]));
     }
-    float4* fac = (float4*)ws_get(ctx, WS_STREAM, fac_n * sizeof(float4), st);
-    float4* box = (float4*)ws_get(ctx, WS_STREAM2, box_n * sizeof(float4), st);
-    view.mbb = (float*)ws_get(ctx, WS_STREAM3, (size_t)std::max(1, P.n) * 6 * sizeof(float), st);
+    float4* fac = (float4*)ws_get(ctx, si ? WS_STREAM6 : WS_STREAM, fac_n * sizeof(float4), bst);
+    float4* box = (float4*)ws_get(ctx, si ? WS_STREAM7 : WS_STREAM2, box_n * sizeof(float4), bst);
+    const size_t box_bytes = (size_t)std::max(1, P.n) * 24;
+    unsigned char* mb = (unsigned char*)ws_get(ctx, si ? WS_STREAM8 : WS_STREAM3, box_bytes + 16, bst);
+    view.mbb = (float*)mb;
+    int* err = (int*)(mb + box_bytes);
     view.anchor = (float*)(dev + P.o_anchor);
     RawLod raw[PJ_MAX_LODS];
     for (int l = 0; l < P.L; ++l) {
@@ -379,16 +377,52 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
                       P.has_hd[l] ? (const float*)(dev + P.o_hd[l]) : nullptr,
                       P.has_ph[l] ? (const float*)(dev + P.o_ph[l]) : nullptr};
     }
+    if (ctx->stream_box_cap[si] < box_bytes + 16) {
+      if (ctx->stream_box_pinned[si]) PJ_CK(cudaFreeHost(ctx->stream_box_pinned[si]));
+      ctx->stream_box_pinned[si] = nullptr;
+      ctx->stream_box_cap[si] = 0;
+      PJ_CK(cudaHostAlloc(&ctx->stream_box_pinned[si], box_bytes + 16, cudaHostAllocDefault));
+      ctx->stream_box_cap[si] = box_bytes + 16;
+    }
+    PJ_CK(cudaStreamWaitEvent(bst, slots[si].copied, 0));
+    PJ_CK(cudaMemsetAsync(err, 0, sizeof(int), bst));
+    build_set_kernels(ctx, &view, raw, bst, err);
+    PJ_CK(cudaMemcpyAsync(ctx->stream_box_pinned[si], mb, box_bytes + sizeof(int), cudaMemcpyDeviceToHost, bst));
+    PJ_CK(cudaEventRecord(built[si], bst));
+    prepared[si] = c;
+  };
+
+  std::vector<int32_t> rr, ss;
+  std::vector<double> dlo, dhi, dd;
+  std::vector<uint8_t> ex;
+  JoinSummary tot;
+  int64_t objects = 0;
+  for (int c = 0; c < N; ++c) {
+    if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
+    if (enqueued <= c) {
+      enqueue(c, true);
+      enqueued = c + 1;
+    }
+    if (prepared[c & 1] != c) prepare(c);
+    const Plan P = plans[c & 1];
+    // the copy and the set building of the next chunk overlap this chunk's join
+    if (c + 1 < N && enqueued == c + 1 && enqueue(c + 1, false)) {
+      enqueued = c + 2;
+      prepare(c + 1);
+    }
     Timer tb;
-    PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
-    build_set_kernels(ctx, &view, raw, st);
-    view.mbb_h.resize((size_t)P.n * 6);
+    PJ_CK(cudaEventSynchronize(built[c & 1]));
+    pj_set& view = views[c & 1];
+    const size_t box_bytes = (size_t)std::max(1, P.n) * 24;
     int herr = 0;
-    if (P.n > 0) PJ_CK(cudaMemcpyAsync(view.mbb_h.data(), view.mbb, (size_t)P.n * 24, cudaMemcpyDeviceToHost, st));
-    PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PJ_CK(cudaStreamSynchronize(st));
-    if (herr & ERR_BOUNDS) throw ApiError{PJ_EBOUNDS, "chunk " + std::to_string(c) + ": a face index lies outside its object's vertices"};
-    if (herr & ERR_NONFINITE) throw ApiError{PJ_ENONFINITE, "chunk " + std::to_string(c) + ": non-finite vertex, anchor, hd or ph"};
+    memcpy(&herr, (const unsigned char*)ctx->stream_box_pinned[c & 1] + box_bytes, sizeof(int));
+    if (herr & ERR_BOUNDS)
+      throw ApiError{PJ_EBOUNDS, "chunk " + std::to_string(c) + ": a face index lies outside its object's vertices"};
+    if (herr & ERR_NONFINITE)
+      throw ApiError{PJ_ENONFINITE, "chunk " + std::to_string(c) + ": non-finite vertex, anchor, hd or ph"};
+    const float* hb = (const float*)ctx->stream_box_pinned[c & 1];
+    view.mbb_h.assign(hb, hb + (size_t)P.n * 6);
+    PJ_CK(cudaStreamWaitEvent(st, built[c & 1], 0));
     ms_build += tb.ms();
     float h2d = 0;
     if (cudaEventElapsedTime(&h2d, h2d0[c & 1], h2d1[c & 1]) == cudaSuccess) ms_h2d += h2d;
