@@ -62,6 +62,8 @@ def parse():
                          "tubes-vs-blobs and streamed workloads for the profiles")
     ap.add_argument("--stream-chunks", type=int, default=8,
                     help="stream workload: chunks of 31,250 blobs streamed against 20,000 tubes (64 = full size)")
+    ap.add_argument("--options", default=None,
+                    help="context options as a JSON object (e.g. '{\"refine_split\": 1}'), default: none")
     return ap.parse_args()
 
 
@@ -278,13 +280,18 @@ def ours_arm(args):
     world, rank, local = dist_init()
     torch.cuda.set_device(local)
     w = configs.blobs20k(seed=rank, n=args.n)        # weak scaling: one independent batch per rank
-    ctx = pj.Context(local)
+    # the scalar single-precision kernel throughout (the autotuner then picks
+    # the LoD schedule only), so that one kernel carries the roofline
+    opts = {"refine_variant": 1}
+    opts.update(json.loads(args.options) if args.options else {})
+    ctx = pj.Context(local, opts)
     gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
     stream = torch.cuda.Stream()
-    # tuned path: single precision with FP64 re-decide, unit pruning, and the
+    # tuned path: single precision with FP64 re-decide, unit pruning, the LoD
+    # schedule autotuned per predicate (during the warm-up steps), and the
     # post-filter sequence replayed from a captured CUDA graph
-    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.USE_GRAPH)
-    direct = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
+    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE | pj.USE_GRAPH)
+    direct = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
 
     def step(mode, collect=None):
         pairs = 0
@@ -405,8 +412,8 @@ def ours_arm(args):
         et = max_over_ranks(et, world)
         e2e = {"value": sum_over_ranks(tot_pairs, world) / et, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": int(tot_n / ke * RESULT_BYTES_PER_PAIR),
-               "how": "pj_load_set of R and S from pinned host memory + two pj_join (TILE_PRUNE, no graph: "
-                      "the sets are new every step) + result copy, host clock"}
+               "how": "pj_load_set of R and S from pinned host memory + two pj_join (TILE_PRUNE | AUTOTUNE, "
+                      "no graph: the sets are new every step) + result copy, host clock"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -426,7 +433,9 @@ def ours_arm(args):
                 "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_per_set": args.n, "precision": "fp32 + fp64 re-decide",
-                           "flags": "TILE_PRUNE | USE_GRAPH", "candidate_pairs_per_step": pairs_per_step,
+                           "flags": "TILE_PRUNE | AUTOTUNE | USE_GRAPH", "candidate_pairs_per_step": pairs_per_step,
+                           "schedule": {str(t): s.get("autotune", {}).get("start") for (s, _), t in
+                                        zip(stats[:len(TAUS)], TAUS)},
                            "results_per_step": results,
                            "l2": "inputs larger than L2: 3.2 GB of facets resident, ~0.2 GB touched per step"},
                 "tri_tests_per_s": tests / (ms / 1000.0),
@@ -454,7 +463,9 @@ def extra_arm(args):
     from paper_2604_19982_gb300 import pj
 
     torch.cuda.set_device(0)
-    ctx = pj.Context(0)
+    opts = {"refine_variant": 1}
+    opts.update(json.loads(args.options) if args.options else {})
+    ctx = pj.Context(0, opts)
     stream = torch.cuda.Stream()
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     extra = {}
@@ -478,7 +489,7 @@ def extra_arm(args):
         w = configs.tubes2k()
         gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
         q = dict(pred=pj.WITHIN, tau=2.0)
-        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
+        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
         untrained = None
         plain = dict(prec=pj.FP64, flags=0)
         gP = ctx.load_set(configs.tube_set(2000, 2320.0, 0, 0, start=0, count=100))
@@ -490,7 +501,7 @@ def extra_arm(args):
         gS = ctx.load_set(S_stream)
         gR = ctx.load_set_streamed(31250 * n_ch, n_ch, lambda c: chunks[c])
         q = dict(pred=pj.WITHIN, tau=1.0)
-        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
+        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
         untrained = None
         plain = None
         gP = None

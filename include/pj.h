@@ -136,11 +136,18 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  options_json may be NULL or a
  * JSON object with optional keys "persistent_ctas_per_sm" (int, 0 = from
- * occupancy), "refine_variant" (1: scalar single-precision refinement, one
- * triangle test per lane and instruction; 2, the default: packed FP32x2
+ * occupancy), "refine_variant" (1, the default: scalar single-precision
+ * refinement, one triangle test per lane and instruction; 2: packed FP32x2
  * refinement, two tests per lane and instruction; anything else gives
- * PJ_EINVAL) and "autotune_cache" (path string).  Fails with PJ_ECUDA when
- * the device is not compute capability 10.3 (GB300). */
+ * PJ_EINVAL; when given, PJ_AUTOTUNE keeps it and tunes the schedule only),
+ * "refine_split" (1 (default), 2, 4 or 8: the last units of a
+ * refinement launch are handed out as that many parts over their s facets,
+ * 1 = never; anything else gives PJ_EINVAL; parts restart the facet-ball
+ * culling bound, so splitting pays only when launches are tail-bound),
+ * "refine_tail" (0..64, default 2: how many units per resident warp are
+ * split) and "autotune_cache" (path
+ * string).  The options change scheduling only, never a result.  Fails with
+ * PJ_ECUDA when the device is not compute capability 10.3 (GB300). */
 pj_status pj_create(pj_ctx** out, int device, const char* options_json);
 void pj_destroy(pj_ctx* ctx);
 

@@ -439,6 +439,25 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
       return PJ_EINVAL;
     }
     ctx->refine_variant = rv;
+    ctx->variant_fixed = true;
+  }
+  v = json_str(options_json, "refine_split");
+  if (!v.empty()) {
+    const int k = atoi(v.c_str());
+    if (k != 1 && k != 2 && k != 4 && k != 8) {
+      pj_destroy(ctx);
+      return PJ_EINVAL;
+    }
+    ctx->refine_split = k;
+  }
+  v = json_str(options_json, "refine_tail");
+  if (!v.empty()) {
+    const int t = atoi(v.c_str());
+    if (t < 0 || t > 64) {
+      pj_destroy(ctx);
+      return PJ_EINVAL;
+    }
+    ctx->refine_tail = t;
   }
   ctx->autotune_cache = json_str(options_json, "autotune_cache");
   *out = ctx;

@@ -15,7 +15,7 @@ enum : int {
 
 constexpr int CHUNK = 256;       // facets per chunk (coarse pruning box)
 constexpr int BLK = 32;          // facets per block (side of a refinement unit)
-constexpr int REFINE_THREADS = 256;
+constexpr int REFINE_THREADS = 384;   // 12 warps: one CTA per SM (shared memory of the stages)
 
 __device__ __forceinline__ void set_err(int* err, int bit) {
   if (err) atomicOr(err, bit);

@@ -79,6 +79,7 @@ struct StepLogData {
   int64_t units[16];
   bool f64[16];
   bool full[16];
+  bool masked[16];   // full-resolution step whose units went through k_unit_masks
 };
 
 // Totals of the last join (also in its JSON stats).
@@ -132,10 +133,13 @@ struct pj_ctx {
   std::vector<GraphEntry> graphs;   // captured joins (PJ_USE_GRAPH), oldest first
   int ctas_per_sm = 0;             // 0 = from occupancy
   int refine_variant = 1;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
+  bool variant_fixed = false;      // refine_variant was given at creation: autotuning keeps it
+  int refine_split = 1;            // the last units of a refinement launch are split this many ways
+  int refine_tail = 2;             // ... that many units per resident warp
   int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
   std::string autotune_cache;
   // per-query workspace
-  pj::DevBuf ws[48];
+  pj::DevBuf ws[56];
   // learned proposal (bf16 MLP), float master weights on the device
   float* mlp_w = nullptr;          // packed: W1 64x16, b1 64, W2 64x64, b2 64, W3 64, b3 1
   bool mlp_ready = false;
@@ -173,11 +177,11 @@ enum Slot {
   WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
   WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5,
   WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3, WS_STREAM4, WS_STREAM5,
-  WS_STREAM6, WS_STREAM7, WS_STREAM8,
+  WS_STREAM6, WS_STREAM7, WS_STREAM8, WS_TILES2,
   WS_COUNT
 };
 
-static_assert(WS_COUNT <= 48, "workspace slots");
+static_assert(WS_COUNT <= 56, "workspace slots");
 void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st);
 
 // ---- set layout (api.cu)

@@ -365,6 +365,9 @@ void StepLog::add(pj_ctx* ctx, const UnitCount& uc, int event, const StepSpec& s
   long long* d = ctx->d_snap + 4 * n;
   if (uc.count < 0) PJ_CK(cudaMemcpyAsync(d, uc.dev, 8, cudaMemcpyDeviceToDevice, st));
   PJ_CK(cudaMemcpyAsync(d + 1, ctx->d_counters, 16, cudaMemcpyDeviceToDevice, st));
+  // units left after the mask pass (counter 13, written by run_refine)
+  masked[n] = uc.count != 0 && sp.full && (!sp.fp64 || sp.cull);
+  if (masked[n]) PJ_CK(cudaMemcpyAsync(d + 3, ctx->d_counters + 13, 8, cudaMemcpyDeviceToDevice, st));
   ev[n] = event;
   units[n] = uc.count;
   f64[n] = sp.fp64;
@@ -386,8 +389,9 @@ std::string StepLog::json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* unit
     *units_total += u;
     char buf[256];
     snprintf(buf, sizeof buf,
-             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tests\":%lld,\"refine_ms\":%.4f}",
-             i ? "," : "", i, f64[i] ? "fp64" : "fp32", full[i] ? 1 : 0, u,
+             "%s{\"step\":%d,\"prec\":\"%s\",\"full\":%d,\"tiles\":%lld,\"tiles_run\":%lld,\"tests\":%lld,"
+             "\"refine_ms\":%.4f}",
+             i ? "," : "", i, f64[i] ? "fp64" : "fp32", full[i] ? 1 : 0, u, masked[i] ? snap[4 * i + 3] : u,
              (snap[4 * i + 1] - prev32) + (snap[4 * i + 2] - prev64), kms);
     prev32 = snap[4 * i + 1];
     prev64 = snap[4 * i + 2];
@@ -439,7 +443,7 @@ static std::string graph_key(pj_ctx* ctx, const pj_set* R, const pj_set* S, cons
   }
   h = fnv(h, &ctx->h_stage, sizeof(void*));
   h = fnv(h, &ctx->h_stage_cap, sizeof(size_t));
-  const int knobs[3] = {ctx->refine_variant, ctx->sched_start, ctx->ctas_per_sm};
+  const int knobs[5] = {ctx->refine_variant, ctx->sched_start, ctx->ctas_per_sm, ctx->refine_split, ctx->refine_tail};
   h = fnv(h, knobs, sizeof knobs);
   char buf[200];
   snprintf(buf, sizeof buf, "%016llx.p%d.t%.17g.x%d.f%u.c%lld", (unsigned long long)h, (int)q->pred, q->tau,

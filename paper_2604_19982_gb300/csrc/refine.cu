@@ -84,7 +84,7 @@ void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, doubl
   auto pr = (int32_t*)ws_get(ctx, WS_PR, n * 4, st);
   auto ps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);
   auto origin = (float4*)ws_get(ctx, WS_ORIGIN, n * 16, st);
-  auto thr = (float*)ws_get(ctx, WS_THR, n * 4, st);
+  auto thr = (float*)ws_get(ctx, WS_THR, ((n + 3) & ~int64_t(3)) * 4, st);   // 16-byte groups (k_refine)
   auto box_lb = (double*)ws_get(ctx, WS_BOXLB, n * 8, st);
   auto anc_ub = (double*)ws_get(ctx, WS_ANCUB, n * 8, st);
   auto status = (uint8_t*)ws_get(ctx, WS_STATUS, n, st);
@@ -342,7 +342,7 @@ UnitCount build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
   auto status = (uint8_t*)ws_get(ctx, WS_STATUS, n, st);
   auto lod0 = (uint8_t*)ws_get(ctx, WS_LOD0, n, st);
   auto origin = (float4*)ws_get(ctx, WS_ORIGIN, n * 16, st);
-  auto thr = (float*)ws_get(ctx, WS_THR, n * 4, st);
+  auto thr = (float*)ws_get(ctx, WS_THR, ((n + 3) & ~int64_t(3)) * 4, st);   // 16-byte groups (k_refine)
   auto cnt1 = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
   auto off1 = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
   auto ucount = (int64_t*)ws_get(ctx, WS_MISC4, 64, st);
@@ -412,7 +412,52 @@ struct RefineArgs {
   int exact_cross;   // decide every straddling pair's meeting test (bounds entry points)
   const double* ub_prev;   // per pair: a valid upper bound of d known before this step (may be null)
   int cull;                // units were pruned against thr (values above thr are not needed)
+  int split_k;             // tail units are handed out as split_k sub-units (1: no splitting)
+  int64_t split_tail;      // how many of the last units are split
+  int masked;              // full resolution: Tile::pad holds the unit's s-facet mask (k_unit_masks)
 };
+
+// Tail splitting.  Units are taken from one counter over a virtual index
+// space: the first NT - T indices are whole units, the rest are the
+// split_k parts of the last T units (part q covers s facets
+// [q 32/K, (q+1) 32/K) of its unit, and the matching bits of its s-facet
+// mask), so that the last units of a launch are short and the warps finish
+// together.  Parts past a ragged unit's s facets are empty (sl = 0).
+struct UnitSpace {
+  int64_t NT, T, NV;
+  int K;
+};
+__host__ __device__ __forceinline__ UnitSpace unit_space(int64_t NT, int K, int64_t tail) {
+  UnitSpace u;
+  u.NT = NT;
+  u.K = K > 1 ? K : 1;
+  u.T = u.K > 1 ? (NT < tail ? NT : tail) : 0;
+  u.NV = NT + u.T * (u.K - 1);
+  return u;
+}
+// the unit array entry of virtual index v, and which part of it (-1: whole)
+__device__ __forceinline__ int64_t unit_index(const UnitSpace& u, int64_t v, int& part) {
+  const int64_t head = u.NT - u.T;
+  if (v < head) {
+    part = -1;
+    return v;
+  }
+  part = (int)((v - head) % u.K);
+  return head + (v - head) / u.K;
+}
+__device__ __forceinline__ Tile unit_part(Tile t, const UnitSpace& u, int part) {
+  if (part < 0) return t;
+  const int w = BLK / u.K, s0 = part * w;
+  t.sb += s0;
+  t.sl = (uint16_t)max(0, min(w, (int)t.sl - s0));
+  t.pad = (int32_t)(((uint32_t)t.pad >> s0) & (w >= 32 ? 0xffffffffu : ((1u << w) - 1u)));   // s-facet mask
+  return t;
+}
+__device__ __forceinline__ Tile unit_at(const Tile* tiles, const UnitSpace& u, int64_t v) {
+  int part;
+  const int64_t i = unit_index(u, v, part);
+  return unit_part(tiles[i], u, part);
+}
 
 template <class T>
 __device__ __forceinline__ void translate(const float4& A, const float4& o, T out[3]) {
@@ -426,9 +471,20 @@ constexpr int REFINE_WARPS = REFINE_THREADS / 32;
 
 constexpr int WARP_LIST = 128;   // straddling facet pairs kept per warp and unit
 
+// k_refine's per-warp shared memory: two stages (header: the unit's tile,
+// its pair's origin and threshold; the unit's r facets; its s facets), the s-facet
+// records, the straddling-pair list, and the slot the next unit's tile is
+// fetched into.
+struct StageHdr {
+  Tile tile;
+  float4 origin;
+  float thr4[4];   // thr[pair & ~3 ..]: the pair's threshold at [pair & 3]
+};
+constexpr size_t STAGE_BYTES = sizeof(StageHdr) + 2 * BLK * 48;
+static_assert(sizeof(StageHdr) == 64 && STAGE_BYTES % 16 == 0, "stage layout");
 template <class T>
 constexpr size_t warp_smem_bytes() {
-  return (size_t)2 * BLK * 48 + (size_t)BLK * sizeof(typename RecOf<T>::S) + (size_t)WARP_LIST * 8;
+  return 2 * STAGE_BYTES + (size_t)BLK * sizeof(typename RecOf<T>::S) + (size_t)WARP_LIST * 8 + sizeof(Tile);
 }
 template <class T>
 constexpr size_t refine_smem_bytes() {
@@ -443,7 +499,8 @@ struct ListOut {
 
 // Contributions of the straddling facet pairs a warp listed during one
 // unit: lane k takes entries k, k+32, ...; the meeting test is decided in
-// double precision (cross_exact64).  Out of line so that its double-precision
+// double precision (cross_decide: single-precision filtered signs, else
+// cross_exact64).  Out of line so that its double-precision
 // registers do not weigh on the unit's inner loop; called only when the
 // warp's list is non-empty.
 template <class T, bool FULL>
@@ -455,7 +512,7 @@ __device__ __noinline__ ListOut<T> process_list(const uint2* list, unsigned nl, 
     const uint2 e = list[k];
     const int li = e.x & 255, lj = e.x >> 8;
     const float4* fr = fr0 + 3 * li;
-    const bool cert = cross_exact64(fr, raw + 3 * lj, o4);
+    const bool cert = cross_decide(fr, raw + 3 * lj, o4);
     const T phs = add_ru(T(fr[1].w), T(raw[3 * lj + 1].w)), hds = add_ru(T(fr[0].w), T(raw[3 * lj].w));
     if (cert) {
       out.lbm = min(out.lbm, -phs);
@@ -475,96 +532,252 @@ __device__ __noinline__ ListOut<T> process_list(const uint2* list, unsigned nl, 
   return out;
 }
 
-// Persistent, warp-granular refinement: every warp takes units from a global
-// counter, prefetches the next unit's 32 s facets with a TMA bulk copy into
-// its second buffer while it computes the current one, expands the s facets
-// into records in its own shared-memory slice, and keeps one r facet per
-// lane in registers.  No barrier couples the warps of a CTA.
+// Full-resolution steps: which s facets of a unit some r facet may still
+// need.  A facet pair whose balls are farther apart than the pair's bound
+// (its upper bound from the previous step and, when units were pruned, its
+// threshold: the same bound k_refine starts from) cannot lower the
+// distance, so it is skipped.  One warp per unit: lane i holds the ball of r
+// facet i and of s facet i; the union of the lanes' needs goes into
+// Tile::pad and the bound into Tile::ew (rounded up to float).  With `out`,
+// units that need nothing are dropped and the rest
+// compacted into `out` (count at *n_out); without it, the masks are written
+// in place.  The skipped facet pairs are added to *nculled (if set).  Light
+// on registers, so it runs at full occupancy and hides the loads that the
+// refinement kernel would otherwise wait on per unit.
+struct MaskArgs {
+  Tile* tiles;
+  int64_t n_tiles;
+  const int64_t* n_tiles_dev;
+  const float4* facR;
+  const float4* facS;
+  const float4* origin;
+  const float* thr;
+  const double* ub_prev;
+  int cull;
+  Tile* out;
+  int64_t* n_out;
+  unsigned long long* nculled;
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) k_unit_masks(MaskArgs m) {
+  const int lane = threadIdx.x & 31;
+  const unsigned FULLM = 0xffffffffu;
+  const int64_t NT = m.n_tiles_dev ? *m.n_tiles_dev : m.n_tiles;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long culled = 0;
+  Tile keep;            // lane k: the k-th kept unit not yet written
+  int nkeep = 0;
+  auto flush = [&]() {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(m.n_out), (unsigned long long)nkeep);
+    base = __shfl_sync(FULLM, base, 0);
+    if (lane < nkeep) m.out[base + lane] = keep;
+    nkeep = 0;
+  };
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < NT; u += nw) {
+    const Tile t = m.tiles[u];
+    const float4 o4 = m.origin[t.pair];
+    const bool ract = lane < t.rl, sact = lane < t.sl;
+    T rc[3], rr, sc[3], sr;
+    {
+      const float4* f = m.facR + 3LL * (t.rb + (ract ? lane : 0));
+      T va[3], vb[3], vc[3];
+      translate(f[0], o4, va);
+      translate(f[1], o4, vb);
+      translate(f[2], o4, vc);
+      facet_ball(va, vb, vc, rc, rr);
+    }
+    {
+      const float4* f = m.facS + 3LL * (t.sb + (sact ? lane : 0));
+      T va[3], vb[3], vc[3];
+      translate(f[0], o4, va);
+      translate(f[1], o4, vb);
+      translate(f[2], o4, vc);
+      facet_ball(va, vb, vc, sc, sr);
+    }
+    T bound = inf_(T(0));
+    if (m.ub_prev) bound = sizeof(T) == 4 ? T(__double2float_ru(m.ub_prev[t.pair])) : T(m.ub_prev[t.pair]);
+    if (m.cull) bound = min(bound, T(m.thr[t.pair]));
+    uint32_t mine = 0;
+    for (int j = 0; j < t.sl; ++j) {
+      const T qc[3] = {__shfl_sync(FULLM, sc[0], j), __shfl_sync(FULLM, sc[1], j), __shfl_sync(FULLM, sc[2], j)};
+      const T qr = __shfl_sync(FULLM, sr, j);
+      if (ract && !balls_apart(rc, rr, qc, qr, bound)) mine |= 1u << j;
+    }
+    const uint32_t need = __reduce_or_sync(FULLM, mine);
+    const uint32_t all = t.sl >= 32 ? 0xffffffffu : ((1u << t.sl) - 1u);
+    if (ract) culled += (unsigned long long)__popc(all & ~need);
+    // the unit's starting bound for k_refine, rounded up to float
+    const float bf = sizeof(T) == 4 ? float(bound) : __double2float_ru(double(bound));
+    if (!m.out) {
+      if (lane == 0) {
+        m.tiles[u].pad = (int32_t)need;
+        m.tiles[u].ew = bf;
+      }
+    } else if (need) {
+      if (lane == nkeep) {
+        keep = t;
+        keep.pad = (int32_t)need;
+        keep.ew = bf;
+      }
+      if (++nkeep == 32) flush();
+    }
+  }
+  if (nkeep) flush();
+  culled = warp_sum_u64(culled);
+  if (lane == 0 && culled && m.nculled) atomicAdd(m.nculled, culled);
+}
+
+// Minimum over the warp: floats through __reduce_min_sync on an
+// order-preserving map of their bits (one instruction instead of a shuffle
+// tree), doubles by shuffles.
+__device__ __forceinline__ float warp_min_fast(float v) {
+  unsigned u = __float_as_uint(v);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  u = __reduce_min_sync(0xffffffffu, u);
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ double warp_min_fast(double v) { return warp_min(v); }
+
+// Persistent, warp-granular refinement.  Every warp takes units (its first
+// two by its index, then from a global counter) and runs a three-deep
+// pipeline of its own: a unit is claimed two iterations before it is
+// computed, its tile is fetched by a bulk copy one iteration before, and
+// then its pair origin and threshold, r facets and s facets are staged by
+// TMA into the warp's second buffer while the current unit computes; so the
+// compute of a unit waits on no global load.  The s facets are expanded into
+// records in the warp's shared-memory slice, one r facet per lane is kept in
+// registers.  No barrier couples the warps of a CTA.
 template <class T, bool FULL>
-__global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_refine(RefineArgs a) {
+__global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine(RefineArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[REFINE_WARPS][2];
+  __shared__ __align__(8) uint64_t bars[REFINE_WARPS][3];
+  __shared__ unsigned list_n[REFINE_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wbase = smem + warp * warp_smem_bytes<T>();
-  float4* raw0 = reinterpret_cast<float4*>(wbase);
-  float4* raw1 = raw0 + 3 * BLK;
   using RecT = typename RecOf<T>::R;
   using RecS = typename RecOf<T>::S;
-  RecS* rec = reinterpret_cast<RecS*>(wbase + 2 * BLK * 48);
-  uint2* list = reinterpret_cast<uint2*>(wbase + 2 * BLK * 48 + BLK * sizeof(RecS));
-  __shared__ unsigned list_n[REFINE_WARPS];
-  uint64_t* bar0 = &bars[warp][0];
-  uint64_t* bar1 = &bars[warp][1];
+  RecS* rec = reinterpret_cast<RecS*>(wbase + 2 * STAGE_BYTES);
+  uint2* list = reinterpret_cast<uint2*>(wbase + 2 * STAGE_BYTES + BLK * sizeof(RecS));
+  Tile* tslot = reinterpret_cast<Tile*>(wbase + 2 * STAGE_BYTES + BLK * sizeof(RecS) + WARP_LIST * 8);
+  uint64_t* bar = bars[warp];   // [0], [1]: stages; [2]: the tile slot
   if (lane == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar1, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     fence_mbar_init();
     list_n[warp] = 0;
   }
   __syncwarp();
   const T INF = inf_(T(0));
   const unsigned FULLM = 0xffffffffu;
-  const int64_t NT = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
-  uint32_t ph0 = 0, ph1 = 0;
-  int b = 0;
+  const UnitSpace us = unit_space(a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles, a.split_k, a.split_tail);
+  uint32_t ph0 = 0, ph1 = 0, ph2 = 0;
   unsigned long long ntest = 0, nskip = 0;
+  bool failed = false;
+  unsigned pend = 0;   // lane 0: barriers with copies in flight (bit k: stage k, bit 2: tile slot)
 
-  int64_t cur = 0;
-  if (lane == 0) {
-    cur = atomicAdd(a.counter, 1);
-    if (cur < NT) {
-      const Tile t0 = a.tiles[cur];
-      mbar_arrive_expect_tx(bar0, (uint32_t)t0.sl * 48u);
-      tma_load_1d(raw0, a.facS + 3LL * t0.sb, (uint32_t)t0.sl * 48u, bar0);
+  // lane 0: stage unit t into buffer k (header by a store, the rest by TMA)
+  auto stage = [&](int k, const Tile& t) {
+    unsigned char* sb = wbase + k * STAGE_BYTES;
+    StageHdr* h = reinterpret_cast<StageHdr*>(sb);
+    h->tile = t;
+    if (t.sl == 0) {   // an empty part: nothing to copy
+      mbar_arrive_expect_tx(&bar[k], 0);
+      return;
     }
+    pend |= 1u << k;
+    fence_proxy_async();
+    const uint32_t rb = (uint32_t)t.rl * 48u, sbytes = (uint32_t)t.sl * 48u;
+    mbar_arrive_expect_tx(&bar[k], 32u + rb + sbytes);
+    tma_load_1d(&h->origin, a.origin + t.pair, 16u, &bar[k]);
+    tma_load_1d(h->thr4, a.thr + (t.pair & ~3), 16u, &bar[k]);
+    tma_load_1d(sb + sizeof(StageHdr), a.facR + 3LL * t.rb, rb, &bar[k]);
+    tma_load_1d(sb + sizeof(StageHdr) + BLK * 48, a.facS + 3LL * t.sb, sbytes, &bar[k]);
+  };
+  // lane 0: fetch the tile of virtual unit v into the slot
+  auto fetch = [&](int v) {
+    int part;
+    const int64_t i = unit_index(us, v, part);
+    pend |= 4u;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bar[2], (uint32_t)sizeof(Tile));
+    tma_load_1d(tslot, a.tiles + i, (uint32_t)sizeof(Tile), &bar[2]);
+  };
+
+  // the first two units of every warp are assigned statically (warp w: w
+  // and w + NW), later ones come from the counter, offset by 2 NW; so a
+  // launch with few units per warp spreads them evenly
+  const int NV = (int)us.NV;
+  const int NW = (int)(gridDim.x * REFINE_WARPS), gw = (int)(blockIdx.x * REFINE_WARPS) + warp;
+  int cur = gw, vnext = 0, vclaim = 0;   // virtual unit indices; vnext, vclaim: lane 0 only
+  if (lane == 0) {
+    if (cur < NV) stage(0, unit_at(a.tiles, us, cur));
+    vnext = gw + NW;
+    if (vnext < NV) fetch(vnext);
+    vclaim = 2 * NW + atomicAdd(a.counter, 1);
   }
   cur = __shfl_sync(FULLM, cur, 0);
-  while (cur < NT) {
-    // prefetch the next unit into the other buffer
-    int64_t nxt = 0;
+  int b = 0;
+  while (cur < NV) {
+    // lane 0: the next unit into the other stage, the tile after it into the
+    // slot, and one more claim
+    int nxt = 0;
     if (lane == 0) {
-      nxt = atomicAdd(a.counter, 1);
-      if (nxt < NT) {
-        const Tile tn = a.tiles[nxt];
-        fence_proxy_async();
-        uint64_t* bn = b ? bar0 : bar1;
-        mbar_arrive_expect_tx(bn, (uint32_t)tn.sl * 48u);
-        tma_load_1d(b ? raw0 : raw1, a.facS + 3LL * tn.sb, (uint32_t)tn.sl * 48u, bn);
+      nxt = vnext;
+      if (vnext < NV) {
+        if (mbar_wait_bounded(&bar[2], ph2, MBAR_POLL_LIMIT)) {
+          ph2 ^= 1u;
+          pend &= ~4u;
+          int part;
+          unit_index(us, vnext, part);
+          stage(b ^ 1, unit_part(*tslot, us, part));
+          vnext = vclaim;
+          if (vnext < NV) fetch(vnext);
+          vclaim = 2 * NW + atomicAdd(a.counter, 1);
+        } else {
+          failed = true;
+          nxt = NV;
+        }
       }
     }
     nxt = __shfl_sync(FULLM, nxt, 0);
-    const Tile tl = a.tiles[cur];
+    // this unit's stage
+    const bool ok = mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? ph1 : ph0, MBAR_POLL_LIMIT);
+    if (__any_sync(FULLM, !ok) || __any_sync(FULLM, failed)) {
+      failed = true;
+      break;
+    }
+    if (b) ph1 ^= 1u;
+    else ph0 ^= 1u;
+    pend &= ~(1u << b);
+    const unsigned char* sbuf = wbase + b * STAGE_BYTES;
+    const StageHdr* hdr = reinterpret_cast<const StageHdr*>(sbuf);
+    const Tile tl = hdr->tile;
     const int rl = tl.rl, sl = tl.sl;
-    const float4 o4 = a.origin[tl.pair];
     const bool act = lane < rl;
+    // the decided flag (written by other warps) and the threshold, loaded
+    // now and used after the records are built
+    const uint8_t decided = (a.early && sl) ? __ldcg(a.flag + tl.pair) : (uint8_t)0;
+    if (sl == 0 || (FULL && a.masked && tl.pad == 0)) {   // an empty part or mask
+      __syncwarp();
+      cur = nxt;
+      b ^= 1;
+      continue;
+    }
+    const float4 o4 = hdr->origin;
+    const float4* rfac = reinterpret_cast<const float4*>(sbuf + sizeof(StageHdr));
+    const float4* raw = reinterpret_cast<const float4*>(sbuf + sizeof(StageHdr) + BLK * 48);
     RecT P;
     {
-      const float4* f = a.facR + 3LL * (tl.rb + (act ? lane : 0));
+      const float4* f = rfac + 3 * (act ? lane : 0);
       float4 A = f[0], B = f[1], C = f[2];
       T va[3], vb[3], vc[3];
       translate(A, o4, va);
       translate(B, o4, vb);
       translate(C, o4, vc);
       make_rec(P, va, vb, vc, T(A.w), T(B.w), true);
-    }
-    // wait for this unit's s facets, then expand them into records
-    const bool ok = mbar_wait_bounded(b ? bar1 : bar0, b ? ph1 : ph0, MBAR_POLL_LIMIT);
-    if (__any_sync(FULLM, !ok)) {
-      if (lane == 0) {
-        set_err(a.err, ERR_MBAR_TIMEOUT);
-        // let a prefetch in flight land (bounded) before the warp leaves
-        if (nxt < NT) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
-      }
-      break;
-    }
-    if (b) ph1 ^= 1u;
-    else ph0 ^= 1u;
-    const float4* raw = b ? raw1 : raw0;
-    if (a.early && __ldcg(a.flag + tl.pair)) {   // the pair is already decided
-      __syncwarp();
-      cur = nxt;
-      b ^= 1;
-      continue;
     }
     if (lane < sl) {
       float4 A = raw[3 * lane], B = raw[3 * lane + 1], C = raw[3 * lane + 2];
@@ -577,6 +790,12 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
       store_rec(rec[lane], Q);
     }
     __syncwarp();
+    if (decided) {   // the pair is already decided
+      __syncwarp();
+      cur = nxt;
+      b ^= 1;
+      continue;
+    }
 
     T lbm = INF, ubu = INF, d2m = INF;
     bool anyposs = false;
@@ -584,92 +803,76 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     // facet pairs whose balls are farther apart than what the lane can
     // still improve are skipped (when the whole warp agrees): always in
     // single precision, in double precision when units were pruned.  At
-    // full resolution the bound starts at the pair's upper bound and, with
-    // pruning, at its threshold (distances above it are not needed: a
-    // within decision only compares with tau, and k-NN clamps lb to thr)
+    // full resolution only the s facets of the unit's mask are visited
+    // (k_unit_masks), and the bound starts at the mask pass's bound.
     const bool balls = sizeof(T) == 4 || a.cull;
     T dcur = INF;
     uint32_t cand = sl >= 32 ? 0xffffffffu : ((1u << sl) - 1u);
-    if (FULL && balls) {
-      if (a.ub_prev) dcur = T(a.ub_prev[tl.pair]);
-      if (sizeof(T) == 4 && a.ub_prev) dcur = T(__double2float_ru(a.ub_prev[tl.pair]));
-      if (a.cull) dcur = min(dcur, T(a.thr[tl.pair]));
-      // the s facets some lane may need, from all balls at once
-      uint32_t mine = 0;
-      if (act) {
-        for (int j = 0; j < sl; ++j) {
-          T qc[3], qr, qhd, qph;
-          rec_ball(rec[j], qc, qr, qhd, qph);
-          if (!balls_apart(P.sc, P.sr, qc, qr, dcur)) mine |= 1u << j;
+    if (FULL && balls && a.masked) {
+      cand &= (uint32_t)tl.pad;
+      dcur = T(tl.ew);
+    }
+    while (cand) {
+      const int j = __ffs(cand) - 1;
+      cand &= cand - 1u;
+      if (balls) {
+        // the ball (and hd / ph) first; the record only when needed
+        T qc[3], qr, qhd, qph;
+        rec_ball(rec[j], qc, qr, qhd, qph);
+        bool need = act;
+        if (need) {
+          if (FULL) need = !balls_apart(P.sc, P.sr, qc, qr, dcur);
+          else
+            need = !(balls_apart(P.sc, P.sr, qc, qr, add_ru(lbm, add_ru(P.ph, qph))) &&
+                     balls_apart(P.sc, P.sr, qc, qr, sub_ru(ubu, add_rd(P.hd, qhd))));
+        }
+        if (!__any_sync(FULLM, need)) {
+          nskip += act;
+          continue;
         }
       }
-      const uint32_t need_any = __reduce_or_sync(FULLM, mine);
-      if (act) nskip += (unsigned long long)__popc(cand & ~need_any);
-      cand = need_any;
-    }
-    {
-      while (cand) {
-        const int j = __ffs(cand) - 1;
-        cand &= cand - 1u;
-        if (balls) {
-          // the ball (and hd / ph) first; the record only when needed
-          T qc[3], qr, qhd, qph;
-          rec_ball(rec[j], qc, qr, qhd, qph);
-          bool need = act;
-          if (need) {
-            if (FULL) need = !balls_apart(P.sc, P.sr, qc, qr, dcur);
-            else
-              need = !(balls_apart(P.sc, P.sr, qc, qr, add_ru(lbm, add_ru(P.ph, qph))) &&
-                       balls_apart(P.sc, P.sr, qc, qr, sub_ru(ubu, add_rd(P.hd, qhd))));
+      if (!act) continue;
+      RecT Q;
+      load_rec(Q, rec[j]);
+      ++ntest;
+      bool maybe;
+      T d2 = tri_d2(P, Q, eh, maybe);
+      if (maybe && boxes_apart(P, Q)) maybe = false;   // straddling planes, but apart
+      if (!maybe) {
+        if (FULL) {
+          if (d2 < d2m) {
+            d2m = d2;
+            if (balls) dcur = min(dcur, sqrt_ru(d2m));
           }
-          if (!__any_sync(FULLM, need)) {
-            nskip += act;
-            continue;
-          }
+        } else {
+          T d = sqrt_test(d2);
+          lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
+          ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
         }
-        if (!act) continue;
-        RecT Q;
-        load_rec(Q, rec[j]);
-        ++ntest;
-        bool maybe;
-        T d2 = tri_d2(P, Q, eh, maybe);
-        if (maybe && boxes_apart(P, Q)) maybe = false;   // straddling planes, but apart
-        if (!maybe) {
-          if (FULL) {
-            if (d2 < d2m) {
-              d2m = d2;
-              if (balls) dcur = min(dcur, sqrt_ru(d2m));
-            }
+      } else if (!FULL && sizeof(T) == 4 && !a.exact_cross) {
+        // coarse LoD: a crossing is taken as possible (lower term -ph-ph,
+        // upper term d+hd+hd); both stay valid and are only ~d looser
+        T d = sqrt_test(d2);
+        lbm = min(lbm, -add_ru(P.ph, Q.ph));
+        ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
+      } else {
+        // rare at full resolution: both triangles straddle each other's
+        // planes; decided after the loop (warp list), or by k_cross_fix
+        // when the list is full
+        unsigned li = atomicAdd(&list_n[warp], 1u);
+        if (li < WARP_LIST) {
+          list[li] = make_uint2((unsigned)(lane | (j << 8)), __float_as_uint((float)d2));
+        } else {
+          unsigned qk = atomicAdd(a.qcount, 1u);
+          if (qk < a.qcap) {
+            a.queue[qk] = make_int4(tl.pair, tl.rb + lane, tl.sb + j, __float_as_int(tl.eps));
+          } else if (FULL) {
+            anyposs = true;   // a crossing is possible: lower bound 0 stays valid
+            d2m = min(d2m, d2);
           } else {
             T d = sqrt_test(d2);
-            lbm = min(lbm, sub_rd(d, add_ru(P.ph, Q.ph)));
+            lbm = min(lbm, -add_ru(P.ph, Q.ph));
             ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
-          }
-        } else if (!FULL && sizeof(T) == 4 && !a.exact_cross) {
-          // coarse LoD: a crossing is taken as possible (lower term -ph-ph,
-          // upper term d+hd+hd); both stay valid and are only ~d looser
-          T d = sqrt_test(d2);
-          lbm = min(lbm, -add_ru(P.ph, Q.ph));
-          ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
-        } else {
-          // rare at full resolution: both triangles straddle each other's
-          // planes; decided after the loop (warp list), or by k_cross_fix
-          // when the list is full
-          unsigned li = atomicAdd(&list_n[warp], 1u);
-          if (li < WARP_LIST) {
-            list[li] = make_uint2((unsigned)(lane | (j << 8)), __float_as_uint((float)d2));
-          } else {
-            unsigned qk = atomicAdd(a.qcount, 1u);
-            if (qk < a.qcap) {
-              a.queue[qk] = make_int4(tl.pair, tl.rb + lane, tl.sb + j, __float_as_int(tl.eps));
-            } else if (FULL) {
-              anyposs = true;   // a crossing is possible: lower bound 0 stays valid
-              d2m = min(d2m, d2);
-            } else {
-              T d = sqrt_test(d2);
-              lbm = min(lbm, -add_ru(P.ph, Q.ph));
-              ubu = min(ubu, add_ru(d, add_ru(P.hd, Q.hd)));
-            }
           }
         }
       }
@@ -679,7 +882,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
     const unsigned nl = min(list_n[warp], (unsigned)WARP_LIST);
     T ubc = INF;
     if (nl) {
-      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, a.facR + 3LL * tl.rb, raw, o4);
+      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, rfac, raw, o4);
       lbm = min(lbm, lo.lbm);
       ubu = min(ubu, lo.ubu);
       ubc = lo.ubc;
@@ -698,10 +901,10 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
       lbv = lbm;
       ubv = ubu;
     }
-    lbv = warp_min(lbv);
-    ubv = warp_min(ubv);
-    ubc = warp_min(ubc);
-    if (FULL) midv = warp_min(midv);
+    lbv = warp_min_fast(lbv);
+    ubv = warp_min_fast(ubv);
+    ubc = warp_min_fast(ubc);
+    if (FULL) midv = warp_min_fast(midv);
     if (lane == 0) {
       const T eps = T(tl.eps);
       T lb = lbv < INF ? sub_rd(lbv, eps) : INF;
@@ -712,11 +915,18 @@ __global__ void __launch_bounds__(REFINE_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_re
       if (lb < INF) atomicMin(&((typename Bt::U*)a.lb)[tl.pair], Bt::enc(lb));
       if (ub < INF) atomicMin(&((typename Bt::U*)a.ub)[tl.pair], Bt::enc(ub));
       if (FULL && midv < INF) atomicMin(&((typename Bt::U*)a.mid)[tl.pair], Bt::enc(midv));
-      if (a.early && ub <= a.thr[tl.pair]) a.flag[tl.pair] = 1;
+      if (a.early && ub <= hdr->thr4[tl.pair & 3]) a.flag[tl.pair] = 1;
     }
     __syncwarp();   // records of this unit are read; the next unit overwrites them
     cur = nxt;
     b ^= 1;
+  }
+  if (failed && lane == 0) {
+    set_err(a.err, ERR_MBAR_TIMEOUT);
+    // let the copies in flight land (bounded) before the warp leaves
+    if (pend & 1u) mbar_wait_bounded(&bar[0], ph0, MBAR_POLL_LIMIT);
+    if (pend & 2u) mbar_wait_bounded(&bar[1], ph1, MBAR_POLL_LIMIT);
+    if (pend & 4u) mbar_wait_bounded(&bar[2], ph2, MBAR_POLL_LIMIT);
   }
   ntest = warp_sum_u64(ntest);
   if (lane == 0 && ntest) atomicAdd(a.ntests, ntest);
@@ -761,7 +971,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
   __syncwarp();
   const T INF = inf_(T(0));
   const unsigned FULLM = 0xffffffffu;
-  const int64_t NT = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
+  const UnitSpace us = unit_space(a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles, a.split_k, a.split_tail);
   uint32_t ph0 = 0, ph1 = 0;
   int b = 0;
   unsigned long long ntest = 0, nskip = 0;
@@ -769,27 +979,27 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
   int64_t cur = 0;
   if (lane == 0) {
     cur = atomicAdd(a.counter, 1);
-    if (cur < NT) {
-      const Tile t0 = a.tiles[cur];
+    if (cur < us.NV) {
+      const Tile t0 = unit_at(a.tiles, us, cur);
       mbar_arrive_expect_tx(bar0, (uint32_t)t0.sl * 48u);
-      tma_load_1d(raw0, a.facS + 3LL * t0.sb, (uint32_t)t0.sl * 48u, bar0);
+      if (t0.sl) tma_load_1d(raw0, a.facS + 3LL * t0.sb, (uint32_t)t0.sl * 48u, bar0);
     }
   }
   cur = __shfl_sync(FULLM, cur, 0);
-  while (cur < NT) {
+  while (cur < us.NV) {
     int64_t nxt = 0;
     if (lane == 0) {
       nxt = atomicAdd(a.counter, 1);
-      if (nxt < NT) {
-        const Tile tn = a.tiles[nxt];
+      if (nxt < us.NV) {
+        const Tile tn = unit_at(a.tiles, us, nxt);
         fence_proxy_async();
         uint64_t* bn = b ? bar0 : bar1;
         mbar_arrive_expect_tx(bn, (uint32_t)tn.sl * 48u);
-        tma_load_1d(b ? raw0 : raw1, a.facS + 3LL * tn.sb, (uint32_t)tn.sl * 48u, bn);
+        if (tn.sl) tma_load_1d(b ? raw0 : raw1, a.facS + 3LL * tn.sb, (uint32_t)tn.sl * 48u, bn);
       }
     }
     nxt = __shfl_sync(FULLM, nxt, 0);
-    const Tile tl = a.tiles[cur];
+    const Tile tl = unit_at(a.tiles, us, cur);
     const int rl = tl.rl, sl = tl.sl;
     const float4 o4 = a.origin[tl.pair];
     const bool act = lane < rl;
@@ -817,14 +1027,14 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
     if (__any_sync(FULLM, !ok)) {
       if (lane == 0) {
         set_err(a.err, ERR_MBAR_TIMEOUT);
-        if (nxt < NT) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
+        if (nxt < us.NV) mbar_wait_bounded(b ? bar0 : bar1, b ? ph0 : ph1, MBAR_POLL_LIMIT);
       }
       break;
     }
     if (b) ph1 ^= 1u;
     else ph0 ^= 1u;
     const float4* raw = b ? raw1 : raw0;
-    if (a.early && __ldcg(a.flag + tl.pair)) {
+    if (sl == 0 || (FULL && a.masked && tl.pad == 0) || (a.early && __ldcg(a.flag + tl.pair))) {
       __syncwarp();
       cur = nxt;
       b ^= 1;
@@ -853,6 +1063,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
     if (FULL && a.cull) dcur = fminf(dcur, a.thr[tl.pair]);
     {
       for (int jp = 0; jp < (sl2 >> 1); ++jp) {
+        if (FULL && a.masked && !((((uint32_t)tl.pad) >> (2 * jp)) & 3u)) continue;   // counted by k_unit_masks
         bool need = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -997,7 +1208,7 @@ __global__ void __launch_bounds__(256) k_cross_fix(RefineArgs a) {
     bool maybe;
     T d2 = tri_d2(P, Q, T(0), maybe);
     float4 rr[3] = {r0, r1, r2}, ss[3] = {s0, s1, s2};
-    const bool cert = cross_exact64(rr, ss, o4);
+    const bool cert = cross_decide(rr, ss, o4);
     const T phs = add_ru(P.ph, Q.ph), hds = add_ru(P.hd, Q.hd);
     T lb, ub, mid;
     if (cert) {
@@ -1018,17 +1229,28 @@ __global__ void __launch_bounds__(256) k_cross_fix(RefineArgs a) {
   }
 }
 
+// The last refine_tail units per resident warp are split refine_split ways.
+static void set_split(const pj_ctx* ctx, RefineArgs& args, int64_t resident_warps) {
+  args.split_k = ctx->refine_split;
+  args.split_tail = ctx->refine_split > 1 ? (int64_t)ctx->refine_tail * resident_warps : 0;
+}
+
 template <class T, bool FULL>
 static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaStream_t st) {
   auto kern = k_refine<T, FULL>;
   const size_t smem = refine_smem_bytes<T>();
   PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the stages of a 12-warp CTA need most of the shared memory
+  PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int occ = 0;
   PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, REFINE_THREADS, smem));
   if (occ < 1) occ = 1;
   if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
   int64_t grid = (int64_t)occ * ctx->sm_count;
-  if (n_tiles >= 0) grid = std::min<int64_t>((n_tiles + REFINE_WARPS - 1) / REFINE_WARPS, grid);
+  set_split(ctx, args, grid * REFINE_WARPS);
+  if (n_tiles >= 0)
+    grid = std::min<int64_t>((unit_space(n_tiles, args.split_k, args.split_tail).NV + REFINE_WARPS - 1) / REFINE_WARPS,
+                             grid);
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
@@ -1050,7 +1272,10 @@ static void launch_refine2(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaS
   if (occ < 1) occ = 1;
   if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
   int64_t grid = (int64_t)occ * ctx->sm_count;
-  if (n_tiles >= 0) grid = std::min<int64_t>((n_tiles + REFINE_WARPS - 1) / REFINE_WARPS, grid);
+  set_split(ctx, args, grid * REFINE_WARPS);
+  if (n_tiles >= 0)
+    grid = std::min<int64_t>((unit_space(n_tiles, args.split_k, args.split_tail).NV + REFINE_WARPS - 1) / REFINE_WARPS,
+                             grid);
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
@@ -1075,6 +1300,15 @@ static void dispatch_refine(pj_ctx* ctx, RefineArgs& a, int64_t n_tiles, const S
     if (sp.full) launch_refine2<true>(ctx, a, n_tiles, st);
     else launch_refine2<false>(ctx, a, n_tiles, st);
   }
+}
+
+static void launch_masks(pj_ctx* ctx, const MaskArgs& m, int64_t n_tiles, bool fp64, cudaStream_t st) {
+  int64_t grid = (int64_t)ctx->sm_count * 8;
+  if (n_tiles >= 0) grid = std::max<int64_t>(1, std::min<int64_t>(grid, (n_tiles + 7) / 8));
+  if (fp64) k_unit_masks<double><<<(unsigned)grid, 256, 0, st>>>(m);
+  else k_unit_masks<float><<<(unsigned)grid, 256, 0, st>>>(m);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 float refine_ms(pj_ctx* ctx, int ev) {
@@ -1121,8 +1355,25 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
   a.early = sp.early ? 1 : 0;
   a.exact_cross = sp.exact_cross ? 1 : 0;
   a.cull = sp.cull ? 1 : 0;
+  a.masked = 0;
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
-  dispatch_refine(ctx, a, n_tiles, sp, st);
+  int64_t n_run = n_tiles;
+  if (sp.full && (!sp.fp64 || sp.cull)) {
+    // full resolution with facet balls: per-unit s masks first, the units
+    // that need nothing dropped (timed with the refinement)
+    Tile* out = (Tile*)ws_get(ctx, WS_TILES2, std::max<size_t>(ctx->ws[WS_TILES].cap, sizeof(Tile)), st);
+    int64_t* n_out = (int64_t*)(ctx->d_counters + 13);
+    PJ_CK(cudaMemsetAsync(n_out, 0, sizeof(int64_t), st));
+    MaskArgs m{(Tile*)ctx->ws[WS_TILES].p, a.n_tiles, a.n_tiles_dev, a.facR, a.facS, a.origin, a.thr, a.ub_prev,
+               a.cull, out, n_out, a.nculled};
+    launch_masks(ctx, m, n_tiles, sp.fp64, st);
+    a.tiles = out;
+    a.n_tiles = -1;
+    a.n_tiles_dev = n_out;
+    a.masked = 1;
+    n_run = -1;
+  }
+  dispatch_refine(ctx, a, n_run, sp, st);
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev + 1], st));
   return ev;
 }
@@ -1186,6 +1437,14 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount un
   a.early = 0;
   a.exact_cross = sp.exact_cross ? 1 : 0;
   a.cull = sp.cull ? 1 : 0;
+  a.masked = 0;
+  if (sp.full && (!sp.fp64 || sp.cull)) {
+    // per-unit s masks in place (no buffer to compact into)
+    MaskArgs m{b.tiles, a.n_tiles, a.n_tiles_dev, a.facR, a.facS, a.origin, a.thr, a.ub_prev, a.cull, nullptr,
+               nullptr, nullptr};
+    launch_masks(ctx, m, n_tiles, sp.fp64, st);
+    a.masked = 1;
+  }
   dispatch_refine(ctx, a, n_tiles, sp, st);
 }
 
@@ -1228,7 +1487,7 @@ __global__ void k_tri_dist(const float* P, const float* Q, int64_t n, double* ou
                   make_float4(a[6], a[7], a[8], 0.f)};
   float4 fq[3] = {make_float4(b[0], b[1], b[2], 0.f), make_float4(b[3], b[4], b[5], 0.f),
                   make_float4(b[6], b[7], b[8], 0.f)};
-  const bool cert = maybe && cross_exact64(fp, fq, make_float4(o[0], o[1], o[2], 0.f));
+  const bool cert = maybe && cross_decide(fp, fq, make_float4(o[0], o[1], o[2], 0.f));
   (void)ew;
   T d = sqrt_rn(d2);
   out[p] = cert ? 0.0 : double(d);

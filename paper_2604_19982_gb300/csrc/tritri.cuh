@@ -87,6 +87,30 @@ __device__ __forceinline__ T dot3(const T* a, const T* b) {
 }
 
 // ---------------------------------------------------------------- records
+// A ball holding the facet (a, b, c): the centroid and the largest vertex
+// distance, rounded well up (relative 1e-5 plus 1e-6 of the largest
+// coordinate), so that it holds the exact facet despite the rounding of the
+// translation and of the centroid.
+template <class T>
+__device__ __forceinline__ void facet_ball(const T a[3], const T b[3], const T c[3], T sc[3], T& sr) {
+  T rmax = T(0), amax = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sc[k] = (a[k] + b[k] + c[k]) * (T(1) / T(3));
+  const T* v[3] = {a, b, c};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T q2 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T dv = v[i][k] - sc[k];
+      q2 = fma_(dv, dv, q2);
+      amax = max(amax, abs(v[i][k]));
+    }
+    rmax = max(rmax, q2);
+  }
+  sr = sqrt(rmax) * T(1.00001) + amax * T(1e-6) + T(1e-30);
+}
+
 // Build a record from three (already translated) vertices.  `neg` flips n
 // and m for the register side.  sin_min (optional) receives the facet's
 // conditioning |e0 x e1| / (|e0| |e1|).
@@ -130,21 +154,7 @@ __device__ __forceinline__ void make_rec(Rec<T>& R, const T a[3], const T b[3], 
   }
   R.hd = hd;
   R.ph = ph;
-  T rmax = T(0), amax = T(0);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) R.sc[k] = (R.v[0][k] + R.v[1][k] + R.v[2][k]) * (T(1) / T(3));
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    T q2 = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const T dv = R.v[i][k] - R.sc[k];
-      q2 = fma_(dv, dv, q2);
-      amax = max(amax, abs(R.v[i][k]));
-    }
-    rmax = max(rmax, q2);
-  }
-  R.sr = sqrt(rmax) * T(1.00001) + amax * T(1e-6) + T(1e-30);
+  facet_ball(a, b, c, R.sc, R.sr);
 }
 
 // |e0 x e1| / (|e0| |e1|) of a facet (its sine; small for slivers)
@@ -395,21 +405,7 @@ __device__ __forceinline__ void make_rec(RecL& R, const float a[3], const float 
   R.c = dot3(R.n, R.v[0]) - hoff;
   R.hd = hd;
   R.ph = ph;
-  float rmax = 0.f, amax = 0.f;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) R.sc[k] = (R.v[0][k] + R.v[1][k] + R.v[2][k]) * (1.f / 3.f);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float q2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float dv = R.v[i][k] - R.sc[k];
-      q2 = fmaf(dv, dv, q2);
-      amax = fmaxf(amax, fabsf(R.v[i][k]));
-    }
-    rmax = fmaxf(rmax, q2);
-  }
-  R.sr = sqrtf(rmax) * 1.00001f + amax * 1e-6f + 1e-30f;
+  facet_ball(a, b, c, R.sc, R.sr);
 }
 
 // Shared-memory image of a RecL: 48 floats, 12 float4 loads.
@@ -575,6 +571,68 @@ static __device__ __forceinline__ bool cross_exact64(const float4* fp, const flo
     }
   }
   return false;
+}
+
+// Sign of the orientation determinant of (a, b, c, d) from single-precision
+// differences of the raw float coordinates, or 0 when the sign is not
+// certain.  Each difference carries a relative rounding error of at most
+// u = 2^-24, and the evaluation of the 3x3 determinant adds a few u of the
+// permanent Pm (the same sum with absolute values), so the computed value is
+// within 12 u Pm of the exact one; a value beyond 2^-19 Pm (32 u Pm) has the
+// exact sign, which the double-precision evaluation of cross_exact64 (exact
+// differences, error ~7 u_64 Pm) also gets.  A semi-static filter in the
+// manner of adaptive-precision geometric predicates.
+__device__ __forceinline__ int orient_sign32(const float4& a, const float4& b, const float4& c, const float4& d) {
+  const float x0 = b.x - a.x, x1 = b.y - a.y, x2 = b.z - a.z;
+  const float y0 = c.x - a.x, y1 = c.y - a.y, y2 = c.z - a.z;
+  const float z0 = d.x - a.x, z1 = d.y - a.y, z2 = d.z - a.z;
+  const float c0 = y1 * z2 - y2 * z1, c1 = y2 * z0 - y0 * z2, c2 = y0 * z1 - y1 * z0;
+  const float det = x0 * c0 + x1 * c1 + x2 * c2;
+  const float p0 = fabsf(y1 * z2) + fabsf(y2 * z1), p1 = fabsf(y2 * z0) + fabsf(y0 * z2),
+              p2 = fabsf(y0 * z1) + fabsf(y1 * z0);
+  const float perm = fabsf(x0) * p0 + fabsf(x1) * p1 + fabsf(x2) * p2;
+  const float bound = perm * 1.9073486e-06f;   // 2^-19
+  // outside [1e-20, 1e30] (tiny facets whose products may be subnormal,
+  // overflow, NaN) the sign is left to double precision
+  if (!(perm > 1e-20f && perm < 1e30f)) return 0;
+  return det > bound ? 1 : (det < -bound ? -1 : 0);
+}
+
+// cross_exact64's decision from single-precision filtered signs: 1 or 0
+// when every sign it needs is certain (then it equals cross_exact64's
+// result), -1 when some sign is not.
+__device__ __forceinline__ int cross_filter32(const float4* fp, const float4* fq) {
+  bool unsure = false;
+  for (int side = 0; side < 2; ++side) {
+    const float4* A = side ? fq : fp;
+    const float4* B = side ? fp : fq;
+    int h[3];
+    for (int i = 0; i < 3; ++i) h[i] = orient_sign32(B[0], B[1], B[2], A[i]);
+    for (int i = 0; i < 3; ++i) {
+      const int k = (i + 1) % 3;
+      if (h[i] == 0 || h[k] == 0) {
+        unsure = true;   // the edge may or may not cross B's plane
+        continue;
+      }
+      if (h[i] == h[k]) continue;   // both ends on one side
+      const int o1 = orient_sign32(A[i], A[k], B[0], B[1]);
+      const int o2 = orient_sign32(A[i], A[k], B[1], B[2]);
+      const int o3 = orient_sign32(A[i], A[k], B[2], B[0]);
+      if (o1 == 0 || o2 == 0 || o3 == 0) {
+        unsure = true;
+        continue;
+      }
+      if (o1 == o2 && o2 == o3) return 1;
+    }
+  }
+  return unsure ? -1 : 0;
+}
+
+// The crossing decision of cross_exact64, in single precision where the
+// filter is certain.
+static __device__ __forceinline__ bool cross_decide(const float4* fp, const float4* fq, float4 o) {
+  const int f = cross_filter32(fp, fq);
+  return f >= 0 ? f == 1 : cross_exact64(fp, fq, o);
 }
 
 // Forward error margins of the single-precision test for coordinates

@@ -3,7 +3,8 @@
 // largest facet count per LoD) -- the first join runs every candidate
 // configuration, keeps the fastest, and later joins with the same key use
 // it.  Candidates: the single-precision refinement variant (scalar, one
-// triangle test per lane and instruction, or packed FP32x2, two), and for
+// triangle test per lane and instruction, or packed FP32x2, two; unless the
+// context fixed it with the "refine_variant" option), and for
 // within-tau / intersection joins the LoD schedule (every pair starts at
 // step 0, 1, ... or at full resolution; with PJ_USE_MLP also the learned
 // per-pair start).  Configurations only change how the work is scheduled,
@@ -115,7 +116,11 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
   }
   std::vector<Choice> cand;
   const int Lmax = std::max(R->L, S->L);
-  const std::vector<int> variants = q->prec == PJ_PREC_FP64 ? std::vector<int>{2} : std::vector<int>{2, 1};
+  // FP64 joins have one refinement kernel; a variant fixed at context
+  // creation is kept, only the schedule is tuned
+  const std::vector<int> variants = (q->prec == PJ_PREC_FP64 || ctx->variant_fixed)
+                                        ? std::vector<int>{ctx->refine_variant}
+                                        : std::vector<int>{2, 1};
   for (int v : variants) {
     if (q->pred == PJ_KNN) {
       cand.push_back(Choice{v, -1});

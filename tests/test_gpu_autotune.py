@@ -57,6 +57,21 @@ def test_autotune_within_and_cache_file(sets, tmp_path):
     ctx2.close()
 
 
+def test_autotune_keeps_fixed_variant(sets):
+    """A refinement variant fixed at context creation is kept: only the
+    LoD schedule is tuned, and the result equals the untuned join."""
+    from paper_2604_19982_gb300 import pj
+    ctx = pj.Context(0, {"refine_variant": 1})
+    gR, gS = ctx.load_set(sets.R), ctx.load_set(sets.S)
+    fl = pj.TILE_PRUNE | pj.EXACT_DIST
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl)
+    a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
+    tried = ctx.stats()["autotune"]["tried"]
+    assert len(tried) == 3 and all(t["variant"] == 1 for t in tried)
+    same(ref, a)
+    ctx.close()
+
+
 def test_autotune_knn_and_fp64(sets):
     from paper_2604_19982_gb300 import pj
     ctx = pj.Context(0)
@@ -89,6 +104,33 @@ def test_refine_variants_agree(sets, variant):
     ctx.close()
     with pytest.raises(pj.PJError):
         pj.Context(0, {"refine_variant": 3})
+
+
+@pytest.mark.parametrize("opts", [{"refine_split": 1}, {"refine_split": 2, "refine_tail": 64},
+                                  {"refine_split": 8, "refine_tail": 64},
+                                  {"refine_split": 4, "refine_tail": 64, "refine_variant": 2}])
+def test_tail_split_agrees(sets, opts):
+    """Splitting the last units (here: all of them) into parts over their s
+    facets only reschedules the refinement: the same pairs, and with
+    PJ_EXACT_DIST the same fields, for within and k-NN joins."""
+    from paper_2604_19982_gb300 import pj
+    base = pj.Context(0, {"refine_split": 1})
+    ctx = pj.Context(0, opts)
+    out = []
+    for c in (base, ctx):
+        gR, gS = c.load_set(sets.R), c.load_set(sets.S)
+        out.append([c.join(gR, gS, pj.WITHIN, tau=t, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
+                    for t in (0.0, 1.0)]
+                   + [c.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE),
+                      c.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP64, flags=pj.TILE_PRUNE | pj.EXACT_DIST),
+                      c.join(gR, gS, pj.KNN, k=3, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)])
+    for i, (a, b) in enumerate(zip(*out)):
+        same(a, b, exact=(i != 2))
+    base.close()
+    ctx.close()
+    for bad in ({"refine_split": 3}, {"refine_tail": -1}):
+        with pytest.raises(pj.PJError):
+            pj.Context(0, bad)
 
 
 def test_autotune_streamed(sets):

@@ -130,3 +130,54 @@ def test_fp64_degenerate(ctx):
     d, _ = run(ctx, P, Q, pj.FP64)
     ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
     assert (np.abs(d - ref) <= 1e-12 * ref + 1e-12).all()
+
+
+def piercing_pairs(rng, n):
+    """Q's edge pierces P at depths 1e-7..1 (relative to the facet size
+    0.1..10), away from P's edges, at offsets up to 1e3 from the origin: the
+    crossing decisions go through the single-precision filter when clear and
+    fall back to double precision when the depth is near the rounding."""
+    P = np.empty((n, 3, 3))
+    Q = np.empty((n, 3, 3))
+    for i in range(n):
+        L = 10 ** rng.uniform(-1, 1)
+        c = rng.normal(size=3) * 10 ** rng.uniform(0, 3)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        w = rng.normal(size=3)
+        w -= (w @ u) * u
+        w /= np.linalg.norm(w)
+        nrm = np.cross(u, w)
+        P[i] = [c, c + L * u, c + L * w]
+        hit = c + L * (rng.uniform(0.2, 0.4) * u + rng.uniform(0.2, 0.4) * w)   # inside P
+        depth = L * 10 ** rng.uniform(-7, 0)
+        side = rng.normal(size=3) * 0.3
+        a = hit + depth * nrm + side * depth
+        b = hit - L * nrm * rng.uniform(0.3, 1.0)
+        Q[i] = [a, b, b + L * (rng.normal(size=3) * 0.5)]
+    return P.astype(np.float32), Q.astype(np.float32)
+
+
+def test_crossing_decisions_filtered(ctx):
+    """A crossing the oracle is sure of (depth beyond its error bound) is
+    found by both kernels (distance 0); a pair the oracle is not sure of
+    gets its distance within the usual tolerance, or 0 when the kernel's
+    double-precision signs see a crossing, which happens only at depths near
+    the rounding of the inputs (then the oracle's distance is tiny against
+    the facet size)."""
+    from paper_2604_19982_gb300 import pj
+    rng = np.random.default_rng(12)
+    P, Q = piercing_pairs(rng, 20000)
+    ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
+    d64, _ = run(ctx, P, Q, pj.FP64)
+    d32, err = run(ctx, P, Q, pj.FP32)
+    L = np.linalg.norm(P[:, 1].astype(np.float64) - P[:, 0], axis=1)
+    sure = ref == 0
+    assert sure.sum() > 15000
+    assert (d64[sure] == 0).mean() > 0.999 and (d32[sure] == 0).mean() > 0.999
+    rest = ~sure
+    z64, z32 = rest & (d64 == 0), rest & (d32 == 0)
+    assert (ref[z64] <= 1e-3 * L[z64]).all() and (ref[z32] <= 1e-3 * L[z32]).all()
+    m64, m32 = rest & (d64 > 0), rest & (d32 > 0)
+    assert (np.abs(d64[m64] - ref[m64]) <= 1e-12 * ref[m64] + 1e-12).all()
+    assert (np.abs(d32[m32] - ref[m32]) <= err[m32]).all()
