@@ -42,9 +42,10 @@ TAUS = (0.0, 1.0)
 # kernel at full resolution (FMA = 2): 27 differences, 2 x 3 x 22 for the
 # vertex-to-face cases, 9 x 45 for the edge-to-edge cases.
 FLOPS_PER_TEST = 564
-# the single-precision refinement kernel the tuned path runs (scalar variant
-# with facet-ball culling); the traffic counters in profiles/ name it
-REFINE_KERNEL_ID = "k_refine<float>+ballcull"
+# the single-precision refinement kernel the tuned path runs (scalar variant:
+# facet-ball culling, TMA-staged unit pipeline, unit masks at full
+# resolution); the traffic counters in profiles/ name it
+REFINE_KERNEL_ID = "k_refine<float>+staged+masks"
 
 
 def parse():
@@ -354,7 +355,8 @@ def ours_arm(args):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                 "frac": achieved / peak32 if peak32 else None, "traffic": traffic,
-                "kernel": "k_refine<float> (single-precision refinement, facet-ball culling)",
+                "kernel": "k_refine<float> (single-precision refinement, facet-ball culling; full-resolution "
+                          "steps include their k_unit_masks pre-pass in the timed window)",
                 "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x 2.070 GHz",
                 "measured_fma_peak": measured32, "frac_of_measured": achieved / measured32 if measured32 else None,
                 "flops_per_test": FLOPS_PER_TEST,
