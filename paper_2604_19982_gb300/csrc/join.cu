@@ -612,17 +612,18 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total);
   float graph_ms = 0.f;
   if (!strcmp(gmode, "replay")) PJ_CK(cudaEventElapsedTime(&graph_ms, ctx->ev[60], ctx->ev[61]));
-  char buf[1000];
+  char buf[1500];
   snprintf(buf, sizeof buf,
            "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"graph_ms\":%.4f,"
            "\"capacity\":%lld,"
            "\"candidates\":%lld,\"results\":%lld,"
-           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"redecide\":%llu,"
+           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"tests_needed\":%llu,\"confirmed\":%llu,"
+           "\"removed\":%llu,\"redecide\":%llu,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
            tau, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, gmode, graph_ms, (long long)nn, (long long)n, (long long)m,
            cnt[0],
-           cnt[1], cnt[5], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
+           cnt[1], cnt[5], cnt[6], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
            ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   JoinSummary& js = ctx->last_sum;

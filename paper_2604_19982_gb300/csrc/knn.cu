@@ -692,13 +692,14 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
   double rms32 = 0, rms64 = 0;
   int64_t units = 0;
   const std::string steps = log.json(ctx, &rms32, &rms64, &units);
-  char buf[700];
+  char buf[1500];
   snprintf(buf, sizeof buf,
            "{\"pred\":\"knn\",\"k\":%d,\"prec\":\"%s\",\"mlp\":%d,\"candidates\":%lld,\"results\":%lld,\"tests_fp32\":%llu,"
-           "\"tests_fp64\":%llu,\"tests_culled\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,\"ms_filter\":%.3f,"
+           "\"tests_fp64\":%llu,\"tests_culled\":%llu,\"tests_needed\":%llu,\"confirmed\":%llu,\"removed\":%llu,"
+           "\"tiles\":%lld,\"ms_filter\":%.3f,"
            "\"ms_gather\":%.3f,\"ms_total\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,"
            "\"launches\":%llu,\"steps\":",
-           k, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, (long long)n, (long long)m, cnt[0], cnt[1], cnt[5], cnt[2], cnt[3],
+           k, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, (long long)n, (long long)m, cnt[0], cnt[1], cnt[5], cnt[6], cnt[2], cnt[3],
            (long long)units,
            ms_filter, tg.ms(), tall.ms(), rms32, rms64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";

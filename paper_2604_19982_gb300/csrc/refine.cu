@@ -403,6 +403,7 @@ struct RefineArgs {
   void* mid;
   unsigned long long* ntests;
   unsigned long long* nculled;   // facet pairs skipped by the ball test (may be null)
+  unsigned long long* nneeded;   // executed tests whose lane's own ball test asked for them (may be null)
   int* err;
   int4* queue;       // straddling facet pairs: (pair, r facet, s facet, eps bits)
   unsigned* qcount;
@@ -468,6 +469,12 @@ __device__ __forceinline__ void translate(const float4& A, const float4& o, T ou
 
 constexpr uint32_t MBAR_POLL_LIMIT = 1u << 20;
 constexpr int REFINE_WARPS = REFINE_THREADS / 32;
+// k_refine's warps per CTA: 12 in single precision (166 registers), 8 in
+// double precision (its records need up to 255 registers)
+template <class T>
+constexpr int kref_warps() {
+  return sizeof(T) == 4 ? REFINE_WARPS : 8;
+}
 
 constexpr int WARP_LIST = 128;   // straddling facet pairs kept per warp and unit
 
@@ -488,7 +495,7 @@ constexpr size_t warp_smem_bytes() {
 }
 template <class T>
 constexpr size_t refine_smem_bytes() {
-  return REFINE_WARPS * warp_smem_bytes<T>();
+  return kref_warps<T>() * warp_smem_bytes<T>();
 }
 
 template <class T>
@@ -650,10 +657,11 @@ __device__ __forceinline__ double warp_min_fast(double v) { return warp_min(v); 
 // records in the warp's shared-memory slice, one r facet per lane is kept in
 // registers.  No barrier couples the warps of a CTA.
 template <class T, bool FULL>
-__global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine(RefineArgs a) {
+__global__ void __launch_bounds__(kref_warps<T>() * 32, 1) k_refine(RefineArgs a) {
+  constexpr int WARPS = kref_warps<T>();
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[REFINE_WARPS][3];
-  __shared__ unsigned list_n[REFINE_WARPS];
+  __shared__ __align__(8) uint64_t bars[WARPS][3];
+  __shared__ unsigned list_n[WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wbase = smem + warp * warp_smem_bytes<T>();
   using RecT = typename RecOf<T>::R;
@@ -674,7 +682,7 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine(RefineArgs a) {
   const unsigned FULLM = 0xffffffffu;
   const UnitSpace us = unit_space(a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles, a.split_k, a.split_tail);
   uint32_t ph0 = 0, ph1 = 0, ph2 = 0;
-  unsigned long long ntest = 0, nskip = 0;
+  unsigned ntest = 0, nskip = 0, nneed = 0;   // per lane (a lane sees far fewer than 2^32)
   bool failed = false;
   unsigned pend = 0;   // lane 0: barriers with copies in flight (bit k: stage k, bit 2: tile slot)
 
@@ -707,10 +715,11 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine(RefineArgs a) {
   };
 
   // the first two units of every warp are assigned statically (warp w: w
-  // and w + NW), later ones come from the counter, offset by 2 NW; so a
-  // launch with few units per warp spreads them evenly
+  // and w + NW, with w counted CTA-minor so that consecutive units land on
+  // different SMs), later ones come from the counter, offset by 2 NW; so a
+  // launch with few units spreads them over the SMs
   const int NV = (int)us.NV;
-  const int NW = (int)(gridDim.x * REFINE_WARPS), gw = (int)(blockIdx.x * REFINE_WARPS) + warp;
+  const int NW = (int)gridDim.x * WARPS, gw = warp * (int)gridDim.x + (int)blockIdx.x;
   int cur = gw, vnext = 0, vclaim = 0;   // virtual unit indices; vnext, vclaim: lane 0 only
   if (lane == 0) {
     if (cur < NV) stage(0, unit_at(a.tiles, us, cur));
@@ -822,14 +831,15 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine(RefineArgs a) {
         bool need = act;
         if (need) {
           if (FULL) need = !balls_apart(P.sc, P.sr, qc, qr, dcur);
-          else
-            need = !(balls_apart(P.sc, P.sr, qc, qr, add_ru(lbm, add_ru(P.ph, qph))) &&
-                     balls_apart(P.sc, P.sr, qc, qr, sub_ru(ubu, add_rd(P.hd, qhd))));
+          else need = !coarse_cull(P.sc, P.sr, P.ph, P.hd, qc, qr, qph, qhd, lbm, ubu);
         }
         if (!__any_sync(FULLM, need)) {
           nskip += act;
           continue;
         }
+        nneed += need;
+      } else {
+        nneed += act;
       }
       if (!act) continue;
       RecT Q;
@@ -928,10 +938,10 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine(RefineArgs a) {
     if (pend & 2u) mbar_wait_bounded(&bar[1], ph1, MBAR_POLL_LIMIT);
     if (pend & 4u) mbar_wait_bounded(&bar[2], ph2, MBAR_POLL_LIMIT);
   }
-  ntest = warp_sum_u64(ntest);
-  if (lane == 0 && ntest) atomicAdd(a.ntests, ntest);
-  nskip = warp_sum_u64(nskip);
-  if (lane == 0 && nskip && a.nculled) atomicAdd(a.nculled, nskip);
+  const unsigned long long nt = warp_sum_u64(ntest), ns = warp_sum_u64(nskip), nn = warp_sum_u64(nneed);
+  if (lane == 0 && nt) atomicAdd(a.ntests, nt);
+  if (lane == 0 && ns && a.nculled) atomicAdd(a.nculled, ns);
+  if (lane == 0 && nn && a.nneeded) atomicAdd(a.nneeded, nn);
 }
 
 // Bounds contribution of the queued straddling facet pairs: the 15-candidate
@@ -1243,16 +1253,17 @@ static void launch_refine(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaSt
   // the stages of a 12-warp CTA need most of the shared memory
   PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int occ = 0;
-  PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, REFINE_THREADS, smem));
+  constexpr int threads = kref_warps<T>() * 32;
+  PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
   if (occ < 1) occ = 1;
   if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
   int64_t grid = (int64_t)occ * ctx->sm_count;
-  set_split(ctx, args, grid * REFINE_WARPS);
-  if (n_tiles >= 0)
-    grid = std::min<int64_t>((unit_space(n_tiles, args.split_k, args.split_tail).NV + REFINE_WARPS - 1) / REFINE_WARPS,
-                             grid);
+  set_split(ctx, args, grid * kref_warps<T>());
+  // few units: one CTA per unit up to the resident limit, so that they
+  // spread over the SMs (units are dealt CTA-minor)
+  if (n_tiles >= 0) grid = std::min<int64_t>(unit_space(n_tiles, args.split_k, args.split_tail).NV, grid);
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
+  kern<<<(unsigned)grid, threads, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   if (args.qcap > 0) {
@@ -1273,9 +1284,7 @@ static void launch_refine2(pj_ctx* ctx, RefineArgs& args, int64_t n_tiles, cudaS
   if (ctx->ctas_per_sm > 0) occ = std::min(occ, ctx->ctas_per_sm);
   int64_t grid = (int64_t)occ * ctx->sm_count;
   set_split(ctx, args, grid * REFINE_WARPS);
-  if (n_tiles >= 0)
-    grid = std::min<int64_t>((unit_space(n_tiles, args.split_k, args.split_tail).NV + REFINE_WARPS - 1) / REFINE_WARPS,
-                             grid);
+  if (n_tiles >= 0) grid = std::min<int64_t>(unit_space(n_tiles, args.split_k, args.split_tail).NV, grid);
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, REFINE_THREADS, smem, st>>>(args);
   PJ_CK(cudaGetLastError());
@@ -1346,6 +1355,7 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
   a.mid = ctx->ws[WS_MID].p;
   a.ntests = ctx->d_counters + (sp.fp64 ? 1 : 0);
   a.nculled = ctx->d_counters + 5;
+  a.nneeded = ctx->d_counters + 6;
   a.err = ctx->d_err;
   a.qcap = CROSS_QUEUE_CAP;
   a.queue = (int4*)ws_get(ctx, WS_MISC2, (size_t)a.qcap * sizeof(int4), st);
@@ -1428,6 +1438,7 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount un
   a.mid = b.mid;
   a.ntests = b.counters;
   a.nculled = nullptr;
+  a.nneeded = nullptr;
   a.err = err;
   a.queue = b.queue;
   a.qcap = b.qcap;

@@ -426,8 +426,8 @@ __device__ __forceinline__ void store_rec(RecSmemL& S, const RecL& R) {
   q[8] = make_float4(R.m[1][0], R.m[1][1], R.m[1][2], R.iee[2]);
   q[9] = make_float4(R.m[2][0], R.m[2][1], R.m[2][2], R.mc[0]);
   q[10] = make_float4(R.ev[0], R.ev[1], R.ev[2], R.mc[1]);
-  q[11] = make_float4(R.mc[2], R.sc[0], R.sc[1], R.sc[2]);
-  q[12] = make_float4(R.sr, 0.f, 0.f, 0.f);
+  q[11] = make_float4(R.sc[0], R.sc[1], R.sc[2], R.sr);   // the ball: one aligned load
+  q[12] = make_float4(R.mc[2], R.hd, R.ph, 0.f);          // hd, ph again beside it for the ball test
 }
 
 __device__ __forceinline__ void load_rec(RecL& R, const RecSmemL& S) {
@@ -444,9 +444,9 @@ __device__ __forceinline__ void load_rec(RecL& R, const RecSmemL& S) {
   R.hd = a[0].w; R.ph = a[1].w; R.c = a[2].w;
   R.n[0] = a[6].x; R.n[1] = a[6].y; R.n[2] = a[6].z;
   R.iee[0] = a[6].w; R.iee[1] = a[7].w; R.iee[2] = a[8].w;
-  R.mc[0] = a[9].w; R.mc[1] = a[10].w; R.mc[2] = a[11].x;
+  R.mc[0] = a[9].w; R.mc[1] = a[10].w; R.mc[2] = a[12].x;
   R.ev[0] = a[10].x; R.ev[1] = a[10].y; R.ev[2] = a[10].z;
-  R.sc[0] = a[11].y; R.sc[1] = a[11].z; R.sc[2] = a[11].w; R.sr = a[12].x;
+  R.sc[0] = a[11].x; R.sc[1] = a[11].y; R.sc[2] = a[11].z; R.sr = a[11].w;
 }
 
 // (a . x) - k as one FMA chain
@@ -499,14 +499,37 @@ __device__ __forceinline__ float tri_d2(const RecL& P, const RecL& Q, float eh, 
   return d2;
 }
 
+// Coarse-LoD culling of a facet pair from its balls: true when the pair can
+// lower neither the running lower bound lbm (its terms are d - ph - ph) nor
+// the running upper bound ubu (d + hd + hd), i.e. when the balls are apart
+// by more than both lbm + ph + ph and ubu - hd - hd (the test of
+// balls_apart for both bounds, sharing the centre distance: both hold iff
+// the smaller limit is >= 0 and the squared distance beats the larger one).
+__device__ __forceinline__ bool coarse_cull(const float pc[3], float pr, float pph, float phd, const float qc[3],
+                                            float qr, float qph, float qhd, float lbm, float ubu) {
+  const float dx = pc[0] - qc[0], dy = pc[1] - qc[1], dz = pc[2] - qc[2];
+  const float dist2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const float rr = pr + qr;
+  const float l1 = __fadd_ru(lbm, __fadd_ru(pph, qph)) + rr;
+  const float l2 = __fsub_ru(ubu, __fadd_rd(phd, qhd)) + rr;
+  const float lo = fminf(l1, l2), hi = fmaxf(l1, l2);
+  return lo >= 0.f && dist2 * 0.99996f > hi * hi * 1.00002f;
+}
+__device__ __forceinline__ bool coarse_cull(const double*, double, double, double, const double*, double, double,
+                                            double, double, double) {
+  return false;   // double precision: coarse steps do not cull
+}
+
 // Ball, hd and ph of a shared-memory record (read before the record itself).
 __device__ __forceinline__ void rec_ball(const RecSmemL& S, float c[3], float& r, float& hd, float& ph) {
-  c[0] = S.x[45];
-  c[1] = S.x[46];
-  c[2] = S.x[47];
-  r = S.x[48];
-  hd = S.x[3];
-  ph = S.x[7];
+  const float4 b = reinterpret_cast<const float4*>(S.x)[11];
+  const float2 h = *reinterpret_cast<const float2*>(S.x + 49);   // hd, ph
+  c[0] = b.x;
+  c[1] = b.y;
+  c[2] = b.z;
+  r = b.w;
+  hd = h.x;
+  ph = h.y;
 }
 __device__ __forceinline__ void rec_ball(const RecSmem<double>& S, double c[3], double& r, double& hd, double& ph) {
   c[0] = S.x[40];
