@@ -511,7 +511,10 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
       PJ_COUNT_LAUNCH;
     }
     ctx->ev_used = 0;
-    for (int step = 0; step < Lmax; ++step) {
+    // with a fixed start step (autotuned schedule, no learned start) the
+    // steps before it select no pair: they are not enqueued at all
+    const int first = (ctx->sched_start > 0 && !use_mlp) ? std::min(ctx->sched_start, Lmax - 1) : 0;
+    for (int step = first; step < Lmax; ++step) {
       if (deadline_hit()) return false;
       StepSpec sp;
       sp.lodR = std::max(0, step - (Lmax - R->L));

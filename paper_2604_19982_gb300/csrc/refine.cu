@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <stdexcept>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "tritri.cuh"
 #include "tritri2.cuh"
@@ -568,7 +570,10 @@ struct MaskArgs {
 
 template <class T>
 __global__ void __launch_bounds__(256) k_unit_masks(MaskArgs m) {
+  using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+  __shared__ T4 sball[8][32];   // per warp: the s facets' balls (centre, radius)
   const int lane = threadIdx.x & 31;
+  T4* sb = sball[threadIdx.x >> 5];
   const unsigned FULLM = 0xffffffffu;
   const int64_t NT = m.n_tiles_dev ? *m.n_tiles_dev : m.n_tiles;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -607,11 +612,19 @@ __global__ void __launch_bounds__(256) k_unit_masks(MaskArgs m) {
     if (m.ub_prev) bound = sizeof(T) == 4 ? T(__double2float_ru(m.ub_prev[t.pair])) : T(m.ub_prev[t.pair]);
     if (m.cull) bound = min(bound, T(m.thr[t.pair]));
     uint32_t mine = 0;
+    T4 mb;
+    mb.x = sc[0];
+    mb.y = sc[1];
+    mb.z = sc[2];
+    mb.w = sr;
+    sb[lane] = mb;
+    __syncwarp();
     for (int j = 0; j < t.sl; ++j) {
-      const T qc[3] = {__shfl_sync(FULLM, sc[0], j), __shfl_sync(FULLM, sc[1], j), __shfl_sync(FULLM, sc[2], j)};
-      const T qr = __shfl_sync(FULLM, sr, j);
-      if (ract && !balls_apart(rc, rr, qc, qr, bound)) mine |= 1u << j;
+      const T4 q = sb[j];   // broadcast read
+      const T qc[3] = {q.x, q.y, q.z};
+      if (ract && !balls_apart(rc, rr, qc, q.w, bound)) mine |= 1u << j;
     }
+    __syncwarp();   // the balls are read before the next unit writes them
     const uint32_t need = __reduce_or_sync(FULLM, mine);
     const uint32_t all = t.sl >= 32 ? 0xffffffffu : ((1u << t.sl) - 1u);
     if (ract) culled += (unsigned long long)__popc(all & ~need);
