@@ -145,9 +145,12 @@ typedef struct {
  * 1 = never; anything else gives PJ_EINVAL; parts restart the facet-ball
  * culling bound, so splitting pays only when launches are tail-bound),
  * "refine_tail" (0..64, default 2: how many units per resident warp are
- * split) and "autotune_cache" (path
- * string).  The options change scheduling only, never a result.  Fails with
- * PJ_ECUDA when the device is not compute capability 10.3 (GB300). */
+ * split), "zero_copy" (0, the default, or 1: pj_load_set reads the arrays
+ * that live in pinned, mapped host memory in place over the host link
+ * instead of staging them, other arrays are copied as usual) and
+ * "autotune_cache" (path string).  The options change scheduling only,
+ * never a result.  Fails with PJ_ECUDA when the device is not compute
+ * capability 10.3 (GB300). */
 pj_status pj_create(pj_ctx** out, int device, const char* options_json);
 void pj_destroy(pj_ctx* ctx);
 

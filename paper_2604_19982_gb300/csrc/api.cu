@@ -201,6 +201,19 @@ static T* upload(const T* h, size_t count, cudaStream_t st) {
   return d;
 }
 
+// With the "zero_copy" context option: the device address of a host array
+// that lives in pinned, mapped host memory (the build kernels then read it
+// over the host link directly, with no staging copy), else nullptr.
+static const void* pinned_view(const pj_ctx* ctx, const void* p) {
+  if (!ctx->zero_copy || !p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Lay a described set out on the device (see pj_load_set).
 void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err) {
   const int n = s->n, L = s->L;
@@ -281,31 +294,40 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
       ld.boff_h[o + 1] = ld.boff_h[o] + (fo + BLK - 1) / BLK;
     }
     ld.B = ld.boff_h[n];
-    // uploads
+    // uploads (or, for pinned arrays with zero_copy, their device views)
     float* dv;
     auto it = vcache.find(D->verts[l]);
     if (it != vcache.end()) {
       dv = it->second;
+    } else if (const void* pv = pinned_view(ctx, D->verts[l])) {
+      dv = (float*)pv;
+      vcache[D->verts[l]] = dv;
     } else {
       dv = upload(D->verts[l], (size_t)nv * 3, st);
       temps.push_back(dv);
       vcache[D->verts[l]] = dv;
     }
-    int64_t* dvo = upload(vo, (size_t)n + 1, st);
-    temps.push_back(dvo);
+    int64_t* dvo = (int64_t*)pinned_view(ctx, vo);
+    if (!dvo) {
+      dvo = upload(vo, (size_t)n + 1, st);
+      temps.push_back(dvo);
+    }
     size_t nrows = shared ? (size_t)nfs : (size_t)ld.F;
-    int32_t* dfa = upload(D->faces[l], nrows * 3, st);
-    temps.push_back(dfa);
+    int32_t* dfa = (int32_t*)pinned_view(ctx, D->faces[l]);
+    if (!dfa) {
+      dfa = upload(D->faces[l], nrows * 3, st);
+      temps.push_back(dfa);
+    }
     ld.foff = upload(ld.foff_h.data(), (size_t)n + 1, st);
     ld.coff = upload(ld.coff_h.data(), (size_t)n + 1, st);
     ld.boff = upload(ld.boff_h.data(), (size_t)n + 1, st);
     float* dhd = nullptr;
     float* dph = nullptr;
-    if (D->hd[l]) {
+    if (D->hd[l] && !(dhd = (float*)pinned_view(ctx, D->hd[l]))) {
       dhd = upload(D->hd[l], (size_t)ld.F, st);
       temps.push_back(dhd);
     }
-    if (D->ph[l]) {
+    if (D->ph[l] && !(dph = (float*)pinned_view(ctx, D->ph[l]))) {
       dph = upload(D->ph[l], (size_t)ld.F, st);
       temps.push_back(dph);
     }
@@ -450,6 +472,8 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
     }
     ctx->refine_split = k;
   }
+  v = json_str(options_json, "zero_copy");
+  if (!v.empty()) ctx->zero_copy = atoi(v.c_str()) != 0;
   v = json_str(options_json, "refine_tail");
   if (!v.empty()) {
     const int t = atoi(v.c_str());

@@ -134,6 +134,7 @@ struct pj_ctx {
   int ctas_per_sm = 0;             // 0 = from occupancy
   int refine_variant = 1;          // FP32 refinement: 1 scalar, 2 packed (two s facets per lane)
   bool variant_fixed = false;      // refine_variant was given at creation: autotuning keeps it
+  bool zero_copy = false;          // pj_load_set reads pinned host arrays in place (no staging copy)
   int refine_split = 1;            // the last units of a refinement launch are split this many ways
   int refine_tail = 2;             // ... that many units per resident warp
   int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
