@@ -44,8 +44,8 @@ TAUS = (0.0, 1.0)
 FLOPS_PER_TEST = 564
 # the single-precision refinement kernel the tuned path runs (scalar variant:
 # facet-ball culling, TMA-staged unit pipeline, unit masks at full
-# resolution); the traffic counters in profiles/ name it
-REFINE_KERNEL_ID = "k_refine<float>+staged+masks"
+# resolution, units dealt across SMs); the traffic counters in profiles/ name it
+REFINE_KERNEL_ID = "k_refine<float>+staged+masks+dealt"
 
 
 def parse():
