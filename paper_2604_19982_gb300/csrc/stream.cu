@@ -198,6 +198,16 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   slots[0].copied = evs.e[0];
   slots[1].copied = evs.e[1];
   cudaEvent_t built[2] = {evs.e[6], evs.e[7]};
+  // on every exit (also a timeout or an error between chunks) the copy and
+  // set-building work still queued for the next chunk finishes before the
+  // buffers it writes can be handed to another call
+  struct Drain {
+    cudaStream_t a, b;
+    ~Drain() {
+      cudaStreamSynchronize(a);
+      cudaStreamSynchronize(b);
+    }
+  } drain{ctx->copy_stream, ctx->build_stream};
   cudaEvent_t h2d0[2] = {evs.e[2], evs.e[3]}, h2d1[2] = {evs.e[4], evs.e[5]};
   Plan plans[2];   // the calling thread's copy of the plan of each slot in flight
   const int device = ctx->device;
