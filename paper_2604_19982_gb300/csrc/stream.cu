@@ -154,8 +154,10 @@ void pack_parallel(const std::vector<Piece>& pieces, unsigned char* dst) {
   for (const Piece& pc : pieces)
     for (size_t a = 0; a < pc.bytes; a += SLICE)
       jobs.push_back(Job{static_cast<const unsigned char*>(pc.src) + a, pc.off + a, std::min(SLICE, pc.bytes - a)});
+  // all host cores but two (the calling thread drives the GPU, the loader
+  // fills the next chunk), at most 16
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const unsigned T = (unsigned)std::min<size_t>(std::min(8u, hw), jobs.size());
+  const unsigned T = (unsigned)std::min<size_t>(std::min(16u, std::max(1u, hw > 2 ? hw - 2 : 1u)), jobs.size());
   if (T <= 1) {
     for (const Job& j : jobs) memcpy(dst + j.off, j.src, j.bytes);
     return;
