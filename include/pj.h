@@ -185,7 +185,13 @@ void pj_result_free(pj_result* res);
 
 /* Counters and timings of the last join as a JSON object (candidates, pairs
  * decided per LoD, tiles, triangle tests scheduled/executed per precision,
- * re-decided pairs, bytes copied, milliseconds per stage). */
+ * re-decided pairs, bytes copied, milliseconds per stage).  Among them:
+ * "tests_fp32" / "tests_fp64" (facet-pair tests executed), "tests_culled"
+ * (facet pairs skipped by the facet-ball tests), "tests_needed" (executed
+ * tests that the testing lane's own ball test asked for; the others ran
+ * because another lane of the warp needed the same s facet), and per step
+ * in "steps": "tiles" (units built) and "tiles_run" (units left after the
+ * full-resolution mask pass).  Fails with PJ_EINVAL when cap is too small. */
 pj_status pj_get_stats(const pj_ctx* ctx, char* json_buf, size_t cap);
 
 /* ------------------------------------------------------------------ *
