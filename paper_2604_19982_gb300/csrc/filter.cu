@@ -77,11 +77,16 @@ __device__ __forceinline__ bool box_within(const float* a, const float* b, doubl
   return s2 <= lim2;
 }
 
+constexpr int PROBE_SLOT = 64;   // candidates of one r kept by the counting probe
+
 // One warp per r: lanes stride over the candidates of each probed cell.
+// The counting pass (EMIT = false) also keeps the first PROBE_SLOT
+// candidates of each r in slot[r][.] (when slot is set) and raises
+// *overflow when an r has more.
 template <bool EMIT>
 __global__ void k_probe(int nR, const float* mbbR, const float* mbbS, float tau, double lim2, Grid G,
                         const int64_t* off, const int32_t* ids, int64_t* rcount, const int64_t* roff,
-                        int32_t* out_r, int32_t* out_s) {
+                        int32_t* out_r, int32_t* out_s, int32_t* slot = nullptr, int* overflow = nullptr) {
   int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= nR) return;
@@ -118,10 +123,47 @@ __global__ void k_probe(int nR, const float* mbbR, const float* mbbS, float tau,
             out_r[pos] = w;
             out_s[pos] = s;
           }
+          if (!EMIT && slot && keep) {
+            const int64_t pos = found + __popc(m & ((1u << lane) - 1u));
+            if (pos < PROBE_SLOT) slot[(int64_t)w * PROBE_SLOT + pos] = s;
+          }
           found += __popc(m);
         }
       }
-  if (!EMIT && lane == 0) rcount[w] = found;
+  if (!EMIT && lane == 0) {
+    rcount[w] = found;
+    if (slot && found > PROBE_SLOT) *overflow = 1;
+  }
+}
+
+// Candidate lists of at most PROBE_SLOT entries per r, from the counting
+// probe's slots: one warp per r ranks its s ids (each appears once; ties would
+// go by position) and writes them in ascending order at roff[r] -- the output of the emitting probe followed by
+// the per-r sort, without probing the grid a second time.
+__global__ void k_slot_emit(int nR, const int32_t* slot, const int64_t* roff, int32_t* out_r, int32_t* out_s) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= nR) return;   // warp-uniform
+  const int64_t base = roff[w];
+  const int n = (int)(roff[w + 1] - base);
+  if (n == 0) return;
+  const int32_t* sl = slot + (int64_t)w * PROBE_SLOT;
+  const int32_t v0 = lane < n ? sl[lane] : 0x7fffffff;
+  const int32_t v1 = lane + 32 < n ? sl[lane + 32] : 0x7fffffff;
+  int r0 = 0, r1 = 0;
+  for (int j = 0; j < n; ++j) {
+    const int32_t u = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+    r0 += u < v0 || (u == v0 && j < lane);   // ties by position: ranks stay distinct
+    r1 += u < v1 || (u == v1 && j < lane + 32);
+  }
+  if (lane < n) {
+    out_r[base + r0] = w;
+    out_s[base + r0] = v0;
+  }
+  if (lane + 32 < n) {
+    out_r[base + r1] = w;
+    out_s[base + r1] = v1;
+  }
 }
 
 // Sort each r's candidate list by s (one CTA per r; bitonic in shared
@@ -282,13 +324,20 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   auto roff = (int64_t*)ws_get(ctx, WS_ROFF, ((int64_t)R->n + 1) * 8, st);
   int64_t warps_threads = (int64_t)R->n * 32;
   unsigned g = (unsigned)((warps_threads + th - 1) / th);
+  // the counting probe also keeps up to PROBE_SLOT candidates per r; if no
+  // r has more, they are ranked into place instead of probing again
+  auto slot = (int32_t*)ws_get(ctx, WS_FSLOT, (int64_t)R->n * PROBE_SLOT * 4, st);
+  int* overflow = (int*)(ctx->d_counters + 12);
+  PJ_CK(cudaMemsetAsync(overflow, 0, sizeof(int), st));
   k_probe<false><<<g, th, 0, st>>>(R->n, R->mbb, S->mbb, ftau, lim2, G, off, ids, rcount, nullptr, nullptr,
-                                   nullptr);
+                                   nullptr, slot, overflow);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   scan_i64(ctx, rcount, roff, R->n, st);
   int64_t total = 0;
+  int over = 0;
   PJ_CK(cudaMemcpyAsync(&total, roff + R->n, 8, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaMemcpyAsync(&over, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaStreamSynchronize(st));
   out.n_pairs = total;
   if (total == 0) return out;
@@ -298,6 +347,12 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   while (cap < total) cap <<= 1;
   auto pr = (int32_t*)ws_get(ctx, WS_PR, cap * 4, st);
   auto ps = (int32_t*)ws_get(ctx, WS_PS, cap * 4, st);
+  if (!over) {
+    k_slot_emit<<<g, th, 0, st>>>(R->n, slot, roff, pr, ps);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+    return out;
+  }
   k_probe<true><<<g, th, 0, st>>>(R->n, R->mbb, S->mbb, ftau, lim2, G, off, ids, nullptr, roff, pr, ps);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;

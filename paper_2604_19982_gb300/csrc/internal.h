@@ -178,7 +178,7 @@ enum Slot {
   WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
   WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5,
   WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3, WS_STREAM4, WS_STREAM5,
-  WS_STREAM6, WS_STREAM7, WS_STREAM8, WS_TILES2,
+  WS_STREAM6, WS_STREAM7, WS_STREAM8, WS_TILES2, WS_FSLOT,
   WS_COUNT
 };
 
