@@ -3,19 +3,25 @@
 //  * unit = one 32-facet block of r x one 32-facet block of s of one
 //    candidate pair at one LoD (replaces the paper's thread block per voxel
 //    pair); units are built on the device (k_items / k_emit_units) and
-//    consumed by a persistent kernel through an atomic counter, one launch
-//    per LoD step;
-//  * every warp works alone: lane 0 prefetches the next unit's s block with
-//    a TMA bulk copy (cp.async.bulk, mbarrier completion, bounded wait) into
-//    the warp's other buffer; the 32 s facets are expanded once into
-//    shared-memory records; each lane holds one r facet in registers and
-//    runs its 32 tests against the broadcast s records;
-//  * per-lane running minima, a warp-shuffle min and one atomicMin per unit
-//    and pair on the order-preserving bits (replaces the block-wide
-//    Hillis-Steele scan and shared-memory aggregation of section 2.2);
-//  * facet pairs whose planes straddle each other are decided by an exact
-//    double-precision meeting test after the loop (warp list, overflow to a
-//    global queue and k_cross_fix);
+//    consumed by a persistent kernel, one launch per LoD step;
+//  * every warp works alone through a pipeline of its own: units are claimed
+//    ahead (the first two by warp index, dealt across the SMs), a unit's tile
+//    is fetched by a bulk copy, and its pair origin / threshold, r block and
+//    s block are staged by TMA (cp.async.bulk, mbarrier completion, bounded
+//    waits) into the warp's other buffer while the current unit computes;
+//    the s facets are expanded once into shared-memory records, each lane
+//    holds one r facet in registers and tests it against the broadcast s
+//    records;
+//  * facet balls skip facet pairs that cannot improve the lane's bounds;
+//    at full resolution k_unit_masks first records which s facets a unit
+//    needs at all and drops the units that need none;
+//  * per-lane running minima, a warp minimum and one atomicMin per unit and
+//    pair on the order-preserving bits (replaces the block-wide Hillis-Steele
+//    scan and shared-memory aggregation of section 2.2);
+//  * facet pairs whose planes straddle each other get the meeting test after
+//    the loop (warp list, overflow to a global queue and k_cross_fix):
+//    single-precision signs where an error bound makes them certain, double
+//    precision otherwise;
 //  * optional pruning (PJ_TILE_PRUNE): block pairs whose box distance minus
 //    the Hausdorff terms exceeds the pair's threshold are never built.
 #include <algorithm>
