@@ -8,10 +8,11 @@
 // offsets computed on the host) into one of two pinned host slots.  The
 // calling thread copies a packed chunk to the matching device slot with one
 // host-to-device copy on the context's copy stream, builds the chunk's
-// facet records and boxes on the compute stream once that copy is done, and
-// joins the chunk against S with the resident-set join.  The copy of chunk
-// c + 1 is issued before the join of chunk c starts, so it overlaps that
-// join; the loader packs chunk c + 2 meanwhile.  Results carry global R ids
+// facet records and boxes on the build stream once that copy is done (into
+// the derived buffers of its slot), and joins the chunk against S with the
+// resident-set join.  The copy and the build of chunk c + 1 are issued
+// before the join of chunk c starts, so they overlap that join; the loader
+// packs chunk c + 2 meanwhile.  Results carry global R ids
 // (the ids of chunk c continue those of chunk c - 1).
 #include <algorithm>
 #include <chrono>

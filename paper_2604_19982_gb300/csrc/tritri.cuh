@@ -17,9 +17,11 @@
 //    underestimates); the distance is taken from the difference vector
 //    r + s d1 - t d2 itself.
 //  * meeting: only when both triangles straddle each other's planes (within
-//    the height error margin) can an edge cross the other triangle; that rare
-//    case is decided in double precision from the float vertices by signed
-//    volumes (cross_exact64), in both precisions of the path.
+//    the height error margin) can an edge cross the other triangle; that case
+//    gets the double-precision decision from the float vertices by signed
+//    volumes (cross_exact64), in both precisions of the path, through
+//    single-precision signs wherever an error bound makes them certain
+//    (cross_decide).
 //
 // The register-side record (P) stores n and m negated so that every dot
 // product reads the same difference vectors D_ij = p_i - q_j.
