@@ -62,7 +62,9 @@ enum {
   PJ_EXACT_DIST = 1,   /* refine every result pair to its exact FP64 distance  */
   PJ_USE_MLP = 2,      /* learned proposal: order k-NN work, pick start LoD    */
   PJ_USE_GRAPH = 4,    /* replay the per-LoD launch sequence from a CUDA graph */
-  PJ_AUTOTUNE = 8,     /* pick launch shape per workload (cached per context)  */
+  PJ_AUTOTUNE = 8,     /* time the FP32 refinement variant and the LoD start step
+                          on the first join of a workload, keep the fastest
+                          (cached per context and in "autotune_cache") */
   PJ_TILE_PRUNE = 16   /* skip facet tiles/blocks that cannot change a decision */
 };
 
@@ -115,8 +117,9 @@ typedef struct {
 } pj_query;
 
 /* Result pairs, library-owned host memory (free with pj_result_free); the
- * device-to-host copy goes through the context's pinned staging buffer.  within/intersection: ordered by (r, s).  k-NN: for each
- * r in order, min(k, |S|) entries ordered by (d, s).
+ * device-to-host copy goes through the context's pinned staging buffer.
+ * within/intersection: ordered by (r, s).  k-NN: for each r in order,
+ * min(k, |S|) entries ordered by (d, s).
  *   d_lo <= d(r, s) <= d_hi always holds; d is the best estimate.
  *   exact[i] = 1: d_lo = d = d_hi is the FP64 full-resolution distance;
  *   exact[i] = 2: d is a single-precision full-resolution distance and

@@ -1,8 +1,9 @@
 // Join orchestration on one GPU: MBB filter -> per-LoD [tile build ->
-// refine -> decide] from the coarsest LoD to the original surfaces (section
-// 3.1 overview: "after each LoD, resolve what is decidable, else go finer"),
-// an FP64 re-decide pass for the single-precision path, optional exact
-// distances, and the compaction of the result pairs.
+// refine -> decide] from the coarsest LoD (or the autotuned start step) to
+// the original surfaces (section 3.1 overview: resolve after each LoD what
+// its bounds decide, refine the rest at the next LoD), an FP64 re-decide
+// pass for the single-precision path, optional exact distances, and the
+// compaction of the result pairs.
 #include <algorithm>
 #include <cstring>
 #include <string>
