@@ -10,7 +10,9 @@ inputs into flat triangle soups and calls it through ctypes.
 
 Functions and the passages they follow (arXiv 2604.19982):
 
-* :func:`tri_dist`      -- triangle-triangle distance (section 2.2)
+* :func:`tri_dist`      -- triangle-triangle distance (section 2.2); 0 exactly
+                           when the closed triangles meet (:func:`tri_meet`,
+                           exact orientation signs)
 * :func:`obj_dist`      -- d(P1, P2) by brute force (section 2.1)
 * :func:`pair_bounds`   -- Eq. 1 / Eq. 2 LoD bounds of object pairs
 * :func:`join_within`   -- within-tau / intersection join (section 3)
@@ -67,6 +69,13 @@ def lib():
                               C.POINTER(i32p), C.POINTER(dp), C.POINTER(i64p)]
         L.or_free.restype = None
         L.or_free.argtypes = [C.c_void_p]
+        L.or_tri_meet.restype = C.c_int
+        L.or_tri_meet.argtypes = [dp, dp]
+        for nm in ("or_orient3d_exact", "or_orient3d"):
+            getattr(L, nm).restype = C.c_int
+            getattr(L, nm).argtypes = [dp, dp, dp, dp]
+        L.or_orient2d_exact.restype = C.c_int
+        L.or_orient2d_exact.argtypes = [dp, dp, dp]
         L.or_pairs.restype = None
         L.or_pairs.argtypes = [fp, i64p, fp, fp, fp, i64p, fp, fp, i32p, i32p, C.c_int64, C.c_int, dp, dp]
         _lib = L
@@ -121,6 +130,28 @@ def tri_dist(P, Q):
     cp = np.empty((n, 6), np.float64)
     lib().or_tri_dist_batch(_p(P, C.c_double), _p(Q, C.c_double), n, _p(d, C.c_double), _p(cp, C.c_double))
     return d, cp.reshape(n, 2, 3)
+
+
+def tri_meet(P, Q) -> bool:
+    """Do the closed triangles ``P``, ``Q`` [3, 3] share a point?  Decided by
+    exact orientation signs (the meeting test of :func:`tri_dist`)."""
+    P = np.ascontiguousarray(P, np.float64).reshape(9)
+    Q = np.ascontiguousarray(Q, np.float64).reshape(9)
+    return bool(lib().or_tri_meet(_p(P, C.c_double), _p(Q, C.c_double)))
+
+
+def orient3d(a, b, c, d, exact_only: bool = False) -> int:
+    """Sign of (b - a) . ((c - a) x (d - a)) for double inputs: filtered
+    (default) or by the integer path alone."""
+    v = [np.ascontiguousarray(x, np.float64).reshape(3) for x in (a, b, c, d)]
+    f = lib().or_orient3d_exact if exact_only else lib().or_orient3d
+    return int(f(*[_p(x, C.c_double) for x in v]))
+
+
+def orient2d_exact(a, b, c) -> int:
+    """Sign of (b - a) x (c - a) for 2-D double inputs, integer path."""
+    v = [np.ascontiguousarray(x, np.float64).reshape(2) for x in (a, b, c)]
+    return int(lib().or_orient2d_exact(*[_p(x, C.c_double) for x in v]))
 
 
 def point_tri_dist(p, T) -> float:

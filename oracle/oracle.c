@@ -111,57 +111,364 @@ static void seg_seg(v3 p0, v3 p1, v3 q0, v3 q1, v3* cp, v3* cq) {
   if (dd < best) { best = dd; *cp = x; *cq = q1; }
 }
 
-/* signed volume of tetrahedron (a, b, c, d), times 6, with a bound on its
- * rounding error: the first-order error of the three differences, the cross
- * product and the dot product is below 8 u times the "permanent" (the same
- * expression with every product taken in absolute value), u = 2^-53; twice
- * that is used.  A sign is trusted only when |value| exceeds the bound. */
-static double orient(v3 a, v3 b, v3 c, v3 d, double* err) {
+/* ------------------------------------------------------ exact signs */
+
+/* Exact integer arithmetic for the orientation signs.  Every finite double
+ * is m * 2^e with an integer m, |m| < 2^53.  With E the smallest such e over
+ * the inputs of one predicate, every input is the integer m * 2^(e - E)
+ * times 2^E, and the determinants below (homogeneous of degree 3 or 2 in
+ * the coordinates) have the sign of the same expressions evaluated on those
+ * integers.  Integers are sign and magnitude, 32-bit limbs, least
+ * significant first; 224 limbs hold the largest case (inputs up to 2^2099
+ * after scaling, products of three differences, sums of six of them). */
+#define BN_LIMBS 224
+typedef struct {
+  int neg;
+  int n; /* limbs in use; 0 is zero */
+  uint32_t d[BN_LIMBS];
+} bn;
+
+static void bn_zero(bn* x) { x->neg = 0; x->n = 0; }
+
+static void bn_trim(bn* x) {
+  while (x->n > 0 && x->d[x->n - 1] == 0) x->n--;
+  if (x->n == 0) x->neg = 0;
+}
+
+/* x = sign * mag * 2^shift, mag < 2^64 */
+static void bn_set(bn* x, int neg, uint64_t mag, int shift) {
+  bn_zero(x);
+  if (mag == 0) return;
+  int w = shift / 32, b = shift % 32;
+  for (int i = 0; i < w; ++i) x->d[i] = 0;
+  /* mag << b spans at most three limbs */
+  uint64_t lo = mag << b;
+  uint64_t hi = b ? mag >> (64 - b) : 0;
+  x->d[w] = (uint32_t)lo;
+  x->d[w + 1] = (uint32_t)(lo >> 32);
+  x->d[w + 2] = (uint32_t)hi;
+  x->n = w + 3;
+  x->neg = neg;
+  bn_trim(x);
+}
+
+static int bn_cmp_mag(const bn* a, const bn* b) {
+  if (a->n != b->n) return a->n < b->n ? -1 : 1;
+  for (int i = a->n - 1; i >= 0; --i)
+    if (a->d[i] != b->d[i]) return a->d[i] < b->d[i] ? -1 : 1;
+  return 0;
+}
+
+/* r = |a| + |b| (r may alias neither) */
+static void bn_add_mag(bn* r, const bn* a, const bn* b) {
+  int n = a->n > b->n ? a->n : b->n;
+  uint64_t carry = 0;
+  for (int i = 0; i < n; ++i) {
+    uint64_t s = carry + (i < a->n ? a->d[i] : 0) + (i < b->n ? b->d[i] : 0);
+    r->d[i] = (uint32_t)s;
+    carry = s >> 32;
+  }
+  r->n = n;
+  if (carry) r->d[r->n++] = (uint32_t)carry;
+}
+
+/* r = |a| - |b| for |a| >= |b| */
+static void bn_sub_mag(bn* r, const bn* a, const bn* b) {
+  int64_t borrow = 0;
+  for (int i = 0; i < a->n; ++i) {
+    int64_t s = (int64_t)a->d[i] - (i < b->n ? b->d[i] : 0) - borrow;
+    borrow = s < 0;
+    r->d[i] = (uint32_t)(s + (borrow ? ((int64_t)1 << 32) : 0));
+  }
+  r->n = a->n;
+}
+
+/* r = a + (flip ? -b : b) */
+static void bn_addsub(bn* r, const bn* a, const bn* b, int flip) {
+  int bneg = b->n ? (b->neg ^ flip) : 0;
+  if (a->neg == bneg) {
+    bn_add_mag(r, a, b);
+    r->neg = a->neg;
+  } else if (bn_cmp_mag(a, b) >= 0) {
+    bn_sub_mag(r, a, b);
+    r->neg = a->neg;
+  } else {
+    bn_sub_mag(r, b, a);
+    r->neg = bneg;
+  }
+  bn_trim(r);
+}
+
+/* r = a * b (schoolbook) */
+static void bn_mul(bn* r, const bn* a, const bn* b) {
+  bn_zero(r);
+  if (a->n == 0 || b->n == 0) return;
+  int n = a->n + b->n;
+  for (int i = 0; i < n; ++i) r->d[i] = 0;
+  for (int i = 0; i < a->n; ++i) {
+    uint64_t carry = 0;
+    for (int j = 0; j < b->n; ++j) {
+      uint64_t t = (uint64_t)a->d[i] * b->d[j] + r->d[i + j] + carry;
+      r->d[i + j] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    r->d[i + b->n] = (uint32_t)carry;
+  }
+  r->n = n;
+  r->neg = a->neg ^ b->neg;
+  bn_trim(r);
+}
+
+static int bn_sign(const bn* x) { return x->n == 0 ? 0 : (x->neg ? -1 : 1); }
+
+/* The inputs v[0..k) as integers over a common power of two. */
+static void to_ints(const double* v, int k, bn* out) {
+  int E = 1 << 30;
+  int ex[12];
+  int64_t m[12];
+  for (int i = 0; i < k; ++i) {
+    int e = 0;
+    double f = frexp(v[i], &e); /* v = f 2^e, 1/2 <= |f| < 1 */
+    m[i] = (int64_t)ldexp(f, 53);
+    ex[i] = e - 53;
+    if (m[i] != 0 && ex[i] < E) E = ex[i];
+  }
+  for (int i = 0; i < k; ++i) {
+    if (m[i] == 0) bn_zero(&out[i]);
+    else bn_set(&out[i], m[i] < 0, (uint64_t)(m[i] < 0 ? -m[i] : m[i]), ex[i] - E);
+  }
+}
+
+/* exact sign of (b - a) . ((c - a) x (d - a)) */
+static int orient3d_exact(v3 a, v3 b, v3 c, v3 d) {
+  double v[12] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, d.x, d.y, d.z};
+  bn I[12], x[3], y[3], z[3], t1, t2, m, acc, acc2;
+  to_ints(v, 12, I);
+  for (int k = 0; k < 3; ++k) {
+    bn_addsub(&x[k], &I[3 + k], &I[k], 1);
+    bn_addsub(&y[k], &I[6 + k], &I[k], 1);
+    bn_addsub(&z[k], &I[9 + k], &I[k], 1);
+  }
+  bn_zero(&acc);
+  for (int k = 0; k < 3; ++k) {
+    int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+    /* component k of y x z: y[k1] z[k2] - y[k2] z[k1] */
+    bn_mul(&t1, &y[k1], &z[k2]);
+    bn_mul(&t2, &y[k2], &z[k1]);
+    bn_addsub(&m, &t1, &t2, 1);
+    bn_mul(&t1, &x[k], &m);
+    bn_addsub(&acc2, &acc, &t1, 0);
+    acc = acc2;
+  }
+  return bn_sign(&acc);
+}
+
+/* exact sign of (b - a) x (c - a) in the plane (2-D points) */
+static int orient2d_exact(const double* a, const double* b, const double* c) {
+  double v[6] = {a[0], a[1], b[0], b[1], c[0], c[1]};
+  bn I[6], bx, by, cx, cy, t1, t2, r;
+  to_ints(v, 6, I);
+  bn_addsub(&bx, &I[2], &I[0], 1);
+  bn_addsub(&by, &I[3], &I[1], 1);
+  bn_addsub(&cx, &I[4], &I[0], 1);
+  bn_addsub(&cy, &I[5], &I[1], 1);
+  bn_mul(&t1, &bx, &cy);
+  bn_mul(&t2, &by, &cx);
+  bn_addsub(&r, &t1, &t2, 1);
+  return bn_sign(&r);
+}
+
+/* Orientation signs: a double-precision evaluation whose sign is taken
+ * when it clears an error bound, else the exact integer evaluation.  The
+ * first-order error of the rounded differences, products and sums is below
+ * 8 u times the permanent (the same expression over absolute values),
+ * u = 2^-53, for orient3d and below 4 u of it for orient2d; twice that is
+ * used.  Outside a safe range of magnitudes (underflow, overflow) the exact
+ * path decides. */
+static int orient3d(v3 a, v3 b, v3 c, v3 d) {
   v3 x = sub(b, a), y = sub(c, a), z = sub(d, a);
   double cx = y.y * z.z - y.z * z.y, cy = y.z * z.x - y.x * z.z, cz = y.x * z.y - y.y * z.x;
   double px = fabs(y.y * z.z) + fabs(y.z * z.y), py = fabs(y.z * z.x) + fabs(y.x * z.z),
          pz = fabs(y.x * z.y) + fabs(y.y * z.x);
   double perm = fabs(x.x) * px + fabs(x.y) * py + fabs(x.z) * pz;
-  *err = 16.0 * ldexp(1.0, -53) * perm;
-  return x.x * cx + x.y * cy + x.z * cz;
+  double det = x.x * cx + x.y * cy + x.z * cz;
+  if (perm > 1e-250 && perm < 1e250) {
+    double err = 16.0 * ldexp(1.0, -53) * perm;
+    if (det > err) return 1;
+    if (det < -err) return -1;
+  }
+  return orient3d_exact(a, b, c, d);
 }
 
-static int sure_pos(double v, double e) { return v > e; }
-static int sure_neg(double v, double e) { return v < -e; }
+static int orient2d(const double* a, const double* b, const double* c) {
+  double bx = b[0] - a[0], by = b[1] - a[1], cx = c[0] - a[0], cy = c[1] - a[1];
+  double det = bx * cy - by * cx;
+  double perm = fabs(bx * cy) + fabs(by * cx);
+  if (perm > 1e-250 && perm < 1e250) {
+    double err = 8.0 * ldexp(1.0, -53) * perm;
+    if (det > err) return 1;
+    if (det < -err) return -1;
+  }
+  return orient2d_exact(a, b, c);
+}
 
-/* Does segment [a, b] cross triangle (t0, t1, t2)?  A crossing is claimed
- * only when every sign involved is certain: the endpoints lie strictly on
- * opposite sides of the plane and the line passes strictly inside all three
- * edges.  Touching, coplanar and near-degenerate configurations are left to
- * the vertex/edge distances, which are exact there up to rounding.  If yes,
- * *x is the crossing point. */
-static int seg_crosses_tri(v3 a, v3 b, v3 t0, v3 t1, v3 t2, v3* x) {
-  double ea, eb, e1, e2, e3;
-  double sa = orient(t0, t1, t2, a, &ea), sb = orient(t0, t1, t2, b, &eb);
-  int opposite = (sure_pos(sa, ea) && sure_neg(sb, eb)) || (sure_neg(sa, ea) && sure_pos(sb, eb));
-  if (!opposite) return 0;
-  double o1 = orient(a, b, t0, t1, &e1), o2 = orient(a, b, t1, t2, &e2), o3 = orient(a, b, t2, t0, &e3);
-  int pos = sure_pos(o1, e1) && sure_pos(o2, e2) && sure_pos(o3, e3);
-  int neg = sure_neg(o1, e1) && sure_neg(o2, e2) && sure_neg(o3, e3);
-  if (!pos && !neg) return 0;
-  double t = sa / (sa - sb);
-  *x = add(a, scl(sub(b, a), t));
+/* ------------------------------------------------ exact meeting test */
+
+/* 2-D projection of p that drops coordinate k */
+static void proj(v3 p, int k, double* o) {
+  double c[3] = {p.x, p.y, p.z};
+  o[0] = c[k == 0 ? 1 : 0];
+  o[1] = c[k == 2 ? 1 : 2];
+}
+
+/* x collinear with segment [p, q] (2-D): is it inside the segment's box? */
+static int within_box2(const double* p, const double* q, const double* x) {
+  for (int i = 0; i < 2; ++i) {
+    double lo = p[i] < q[i] ? p[i] : q[i], hi = p[i] < q[i] ? q[i] : p[i];
+    if (x[i] < lo || x[i] > hi) return 0;
+  }
   return 1;
 }
 
+/* Do the closed 2-D segments [a, b] and [c, d] share a point?  (Either may
+ * be a single point.) */
+static int segs_meet2(const double* a, const double* b, const double* c, const double* d) {
+  int s1 = orient2d(c, d, a), s2 = orient2d(c, d, b);
+  int s3 = orient2d(a, b, c), s4 = orient2d(a, b, d);
+  if (s1 * s2 < 0 && s3 * s4 < 0) return 1;
+  if (s1 == 0 && within_box2(c, d, a)) return 1;
+  if (s2 == 0 && within_box2(c, d, b)) return 1;
+  if (s3 == 0 && within_box2(a, b, c)) return 1;
+  if (s4 == 0 && within_box2(a, b, d)) return 1;
+  return 0;
+}
+
+/* Do the closed 3-D segments [a, b] and [c, d] share a point?  They must be
+ * coplanar; then they meet iff their projections onto all three coordinate
+ * planes meet (one of those projections is one-to-one on a plane holding
+ * them, and a common point of the segments projects to a common point of
+ * every projection). */
+static int segs_meet3(v3 a, v3 b, v3 c, v3 d) {
+  if (orient3d(a, b, c, d) != 0) return 0;
+  for (int k = 0; k < 3; ++k) {
+    double A[2], B[2], Cc[2], D[2];
+    proj(a, k, A);
+    proj(b, k, B);
+    proj(c, k, Cc);
+    proj(d, k, D);
+    if (!segs_meet2(A, B, Cc, D)) return 0;
+  }
+  return 1;
+}
+
+/* p in the closed 2-D triangle (t0, t1, t2) of orientation o != 0 */
+static int in_tri2(const double* p, const double* t0, const double* t1, const double* t2, int o) {
+  return orient2d(t0, t1, p) * o >= 0 && orient2d(t1, t2, p) * o >= 0 && orient2d(t2, t0, p) * o >= 0;
+}
+
+/* Does the closed segment [a, b] share a point with the closed triangle
+ * (t0, t1, t2)?  All decisions are exact signs.  *strict is set when the
+ * segment crosses the triangle's plane at one point strictly between its
+ * endpoints (then *x is that point, up to rounding). */
+static int seg_meets_tri(v3 a, v3 b, v3 t0, v3 t1, v3 t2, int* strict, v3* x) {
+  *strict = 0;
+  int sa = orient3d(t0, t1, t2, a), sb = orient3d(t0, t1, t2, b);
+  if (sa * sb > 0) return 0; /* both ends strictly on one side */
+  if (sa != 0 && sb != 0) {
+    /* the segment crosses the (well-defined) plane at one interior point;
+     * it lies in the closed triangle iff the line passes no edge on the
+     * wrong side */
+    int o1 = orient3d(a, b, t0, t1), o2 = orient3d(a, b, t1, t2), o3 = orient3d(a, b, t2, t0);
+    int pos = o1 > 0 || o2 > 0 || o3 > 0, neg = o1 < 0 || o2 < 0 || o3 < 0;
+    if (pos && neg) return 0;
+    double ha = fabs(dot(sub(a, t0), cross(sub(t1, t0), sub(t2, t0))));
+    double hb = fabs(dot(sub(b, t0), cross(sub(t1, t0), sub(t2, t0))));
+    double t = ha + hb > 0.0 ? ha / (ha + hb) : 0.5;
+    *x = add(a, scl(sub(b, a), t));
+    *strict = 1;
+    return 1;
+  }
+  /* a coordinate plane onto which the triangle projects with non-zero area */
+  int k = -1, o = 0;
+  double T0[2], T1[2], T2[2];
+  for (int kk = 0; kk < 3 && k < 0; ++kk) {
+    proj(t0, kk, T0);
+    proj(t1, kk, T1);
+    proj(t2, kk, T2);
+    o = orient2d(T0, T1, T2);
+    if (o != 0) k = kk;
+  }
+  if (k < 0) /* collinear or coincident vertices: the triangle is its edges */
+    return segs_meet3(a, b, t0, t1) || segs_meet3(a, b, t1, t2) || segs_meet3(a, b, t2, t0);
+  double A[2], B[2];
+  proj(a, k, A);
+  proj(b, k, B);
+  if (sa == 0 && sb == 0) /* the segment lies in the triangle's plane */
+    return in_tri2(A, T0, T1, T2, o) || in_tri2(B, T0, T1, T2, o) || segs_meet2(A, B, T0, T1) ||
+           segs_meet2(A, B, T1, T2) || segs_meet2(A, B, T2, T0);
+  /* exactly one end lies in the plane */
+  return in_tri2(sa == 0 ? A : B, T0, T1, T2, o);
+}
+
+/* Do the closed triangles P and Q share a point?  (*strict: 0, or 1 / 2 when
+ * an edge of P / of Q crosses the other's plane inside the other, at *x.)
+ * Two closed triangles meet
+ * iff an edge of one meets the other: in the non-coplanar case their common
+ * part is a segment of the planes' common line whose ends lie on edges; in
+ * the coplanar case the boundaries cross or one triangle holds the other,
+ * with its vertices. */
+static int tri_meet(const v3* p, const v3* q, int* strict, v3* x) {
+  int any = 0;
+  *strict = 0;
+  for (int side = 0; side < 2; ++side) {
+    const v3* A = side ? q : p;
+    const v3* B = side ? p : q;
+    for (int i = 0; i < 3; ++i) {
+      int s = 0;
+      v3 y;
+      if (seg_meets_tri(A[i], A[(i + 1) % 3], B[0], B[1], B[2], &s, &y)) {
+        any = 1;
+        if (s) {
+          *strict = 1 + side; /* 1: an edge of P crosses Q; 2: of Q crosses P */
+          *x = y;
+          return 1;
+        }
+      }
+    }
+  }
+  return any;
+}
+
+int or_tri_meet(const double* P, const double* Q) {
+  v3 p[3] = {mk(P), mk(P + 3), mk(P + 6)};
+  v3 q[3] = {mk(Q), mk(Q + 3), mk(Q + 6)};
+  int s;
+  v3 x;
+  return tri_meet(p, q, &s, &x);
+}
+
+/* signs for the tests: exact (integers only) and filtered */
+int or_orient3d_exact(const double* a, const double* b, const double* c, const double* d) {
+  return orient3d_exact(mk(a), mk(b), mk(c), mk(d));
+}
+int or_orient3d(const double* a, const double* b, const double* c, const double* d) {
+  return orient3d(mk(a), mk(b), mk(c), mk(d));
+}
+int or_orient2d_exact(const double* a, const double* b, const double* c) { return orient2d_exact(a, b, c); }
+
 /* Triangle-triangle distance.  P and Q are 9 doubles (3 vertices).  If cp is
- * not NULL it receives the closest point on P then on Q. */
+ * not NULL it receives the closest point on P then on Q.  The distance is 0
+ * exactly when the closed triangles meet (decided by exact signs); else it
+ * is the smallest of the fifteen candidates, which is positive for exact
+ * values: where rounding makes it 0, the smallest positive double stands
+ * in, so that 0 always means "meet". */
 double or_tri_dist(const double* P, const double* Q, double* cp) {
   v3 p[3] = {mk(P), mk(P + 3), mk(P + 6)};
   v3 q[3] = {mk(Q), mk(Q + 3), mk(Q + 6)};
-  v3 bp = p[0], bq = q[0], x, y;
-  for (int i = 0; i < 3; ++i) {
-    if (seg_crosses_tri(p[i], p[(i + 1) % 3], q[0], q[1], q[2], &x) ||
-        seg_crosses_tri(q[i], q[(i + 1) % 3], p[0], p[1], p[2], &x)) {
-      if (cp) { cp[0] = cp[3] = x.x; cp[1] = cp[4] = x.y; cp[2] = cp[5] = x.z; }
-      return 0.0;
-    }
-  }
+  v3 bp = p[0], bq = q[0], x, y, cx = p[0];
+  int strict = 0;
+  int meet = tri_meet(p, q, &strict, &cx);
+  if (meet && !cp) return 0.0;
   double best = INFINITY, d;
   for (int i = 0; i < 3; ++i) {
     y = tri_point(q[0], q[1], q[2], p[i]);
@@ -177,8 +484,18 @@ double or_tri_dist(const double* P, const double* Q, double* cp) {
       d = dist(x, y);
       if (d < best) { best = d; bp = x; bq = y; }
     }
+  if (meet && strict) {
+    /* a common point: the crossing point (on the crossing edge), and its
+     * nearest point on the crossed triangle; kept when it beats the
+     * candidates' points (which it does unless the crossing is nearly
+     * tangential, where a candidate is nearly 0) */
+    x = strict == 1 ? cx : tri_point(p[0], p[1], p[2], cx);
+    y = strict == 2 ? cx : tri_point(q[0], q[1], q[2], cx);
+    if (dist(x, y) < best) { bp = x; bq = y; }
+  }
   if (cp) { cp[0] = bp.x; cp[1] = bp.y; cp[2] = bp.z; cp[3] = bq.x; cp[4] = bq.y; cp[5] = bq.z; }
-  return best;
+  if (meet) return 0.0;
+  return best > 0.0 ? best : ldexp(1.0, -1074);
 }
 
 /* point to triangle distance (used by the Hausdorff checks in the tests) */
