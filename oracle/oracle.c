@@ -677,9 +677,11 @@ static void* within_worker(void* arg) {
       for (int64_t s = 0; s < nS; ++s) cand[nc++] = (int32_t)s;
     } else {
       set_mbb(j->R, r, rlo, rhi);
+      /* boxes sorted by lo.x: from the first that can reach r's box to the
+       * last whose lo.x is still within tau of its hi.x (equal lo.x values
+       * all included) */
       int64_t a = lower_x(j->boxes, nS, rlo[0] - j->tau - j->max_ext_x - 1.0);
-      int64_t b = lower_x(j->boxes, nS, rhi[0] + j->tau * (1.0 + slack) + 1e-300);
-      for (int64_t q = a; q < nS && q <= b; ++q) {
+      for (int64_t q = a; q < nS; ++q) {
         const sbox* sb = &j->boxes[q];
         if (sb->lo[0] > rhi[0] + j->tau * (1.0 + slack)) break;
         if (box_mindist(rlo, rhi, sb->lo, sb->hi) <= j->tau * (1.0 + slack)) cand[nc++] = sb->id;

@@ -8,6 +8,8 @@ This module only builds geometry; it decides nothing about meeting.
 """
 import numpy as np
 
+from synth import box_triangles, from_triangles
+
 F = np.float32
 
 
@@ -100,3 +102,81 @@ def contact_pairs(rng, n, offset=0.0):
     # exact only where float32 holds the values (labels come from exact
     # checks of the float32 triangles, not from the construction)
     return P.astype(F), Q.astype(F)
+
+
+# ---------------------------------------------------------------- meshes
+
+
+def _step(x, up):
+    return float(np.nextafter(F(x), F(np.inf) if up else F(-np.inf)))
+
+
+def _tet_tris(V):
+    return np.array([[V[0], V[1], V[2]], [V[0], V[3], V[1]], [V[1], V[3], V[2]], [V[2], V[3], V[0]]])
+
+
+def contact_sets(seed, n=240):
+    """R and S with one designed contact per index i (plus random overlaps
+    between neighbours that the grid spacing keeps rare)."""
+    rng = np.random.default_rng(seed)
+    R, S = [], []
+    for i in range(n):
+        base = np.array([(i % 8) * 12.0, ((i // 8) % 8) * 12.0, (i // 64) * 12.0]) + 1000.0 * (seed % 2)
+        kind = i % 6
+        shift = int(rng.integers(0, 3))   # 0: exact, 1: one step apart, 2: one step into
+        if kind < 4:
+            lo = base + rng.integers(0, 4, 3) * 0.25
+            hi = lo + rng.integers(2, 8, 3) * 0.5
+            slo = hi.copy()
+            if kind == 0:    # face on face: S starts where R ends along x
+                slo[1:] = lo[1:] + rng.integers(-2, 3, 2) * 0.25
+            elif kind == 1:  # edge on edge
+                slo[2] = lo[2] + 0.25
+            elif kind == 3:  # face on face along y, offset inside the face
+                slo = lo.copy()
+                slo[1] = hi[1]
+                slo[0] += 0.25
+            if shift:
+                ax = 1 if kind == 3 else 0
+                slo[ax] = _step(slo[ax], up=shift == 1)
+            shi = slo + rng.integers(2, 8, 3) * 0.5
+            R.append(box_triangles(lo, hi))
+            S.append(box_triangles(slo, shi))
+        else:
+            V = base + rng.integers(0, 9, (4, 3)) * 0.25
+            for _ in range(100):
+                if abs(np.linalg.det(V[1:] - V[0])) >= 0.1:
+                    break
+                V = base + rng.integers(0, 9, (4, 3)) * 0.25
+            j = int(rng.integers(0, 4))       # the face opposite vertex j
+            face = [V[k] for k in range(4) if k != j]
+            nrm = np.cross(face[1] - face[0], face[2] - face[0])
+            nrm /= np.linalg.norm(nrm)
+            if nrm @ (V[j] - face[0]) > 0:
+                nrm = -nrm                     # outward, unit
+            if kind == 4:                      # a vertex of S inside that face
+                X = (face[0] + face[1] + 2 * face[2]) / 4.0
+            else:                              # ... on an edge of it
+                X = (face[0] + face[1]) / 2.0
+            if shift:
+                X = X.copy()
+                ax = int(np.argmax(np.abs(nrm)))
+                X[ax] = _step(X[ax], up=(nrm[ax] > 0) == (shift == 1))
+            # the other three vertices well outside the face's plane (at
+            # least 0.5 above it; a random step is that far with probability
+            # about 1/3, so the bounded loop practically never falls back)
+            W = [X]
+            for _ in range(400):
+                v = X + rng.integers(-6, 7, 3) * 0.25
+                if (v - X) @ nrm > 0.5:
+                    W.append(v)
+                    if len(W) == 4 and abs(np.linalg.det(np.array(W[1:]) - X)) > 0.05:
+                        break
+                    if len(W) == 4:
+                        W.pop()
+            assert len(W) == 4, "construction failed"
+            W = np.array(W)
+            R.append(_tet_tris(V))
+            S.append(_tet_tris(W))
+    to32 = lambda L: [np.asarray(t, F) for t in L]  # noqa: E731
+    return from_triangles(to32(R)), from_triangles(to32(S))

@@ -235,6 +235,24 @@ def test_within_pruned_equals_brute(blobs100):
     assert len(a[0]) > 0
 
 
+def test_within_pruned_equals_brute_on_touching_boxes():
+    """Boxes and tetrahedra touching exactly (face, edge, vertex contacts,
+    one-step gaps and overlaps): many S boxes start exactly where an R box
+    ends, the boundary case of the box sweep; the pruned join must still
+    equal brute force over all pairs, for tau = 0 and one step above."""
+    from meet_cases import contact_sets
+    for seed in (0, 1):
+        R, S = contact_sets(seed)
+        for tau in (0.0, 1e-3):
+            a = oracle.join_within(R, S, tau, prune=True)
+            b = oracle.join_within(R, S, tau, prune=False)
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), (seed, tau)
+            if tau == 0.0:   # the designed contacts: both outcomes in numbers
+                own = {(i, i) for i in range(R.n)}
+                assert 60 < len(own & set(zip(a[0].tolist(), a[1].tolist()))) < R.n - 40
+
+
 def test_within_monotone_in_tau(blobs100):
     R, S = blobs100.R, blobs100.S
     prev = set()
