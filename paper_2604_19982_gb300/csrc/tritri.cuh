@@ -6,7 +6,7 @@
 //  * Each facet is pre-processed once into a record: vertices v_i, edges
 //    e_i = v_{i+1} - v_i, |e_i|^2 and its inverse, unit normal n, in-plane
 //    inward edge normals m_i = n x e_i, its Hausdorff bounds hd / ph, and
-//    hoff (0, or +inf for a zero-area facet, which has no interior case).
+//    hoff (0, or NaN for a zero-area facet, which has no interior case).
 //  * vertex-to-triangle: only the case where the vertex projects inside the
 //    other triangle (all m_j . (p - q_j) >= 0) contributes, as the plane
 //    distance n . (p - q_0); when the projection falls outside, the nearest
@@ -17,11 +17,12 @@
 //    underestimates); the distance is taken from the difference vector
 //    r + s d1 - t d2 itself.
 //  * meeting: only when both triangles straddle each other's planes (within
-//    the height error margin) can an edge cross the other triangle; that case
-//    gets the double-precision decision from the float vertices by signed
-//    volumes (cross_exact64), in both precisions of the path, through
-//    single-precision signs wherever an error bound makes them certain
-//    (cross_decide).
+//    the height error margin) can they meet; that case gets the exact
+//    decision from the float vertices (cross_decide: single-precision signs
+//    wherever an error bound makes them certain, else exact expansion
+//    arithmetic, exact.cuh), in both precisions of the path.  A facet with
+//    zero computed area has a NaN plane offset: it has no interior case, and
+//    its straddle test always passes, so it always gets the exact test.
 //
 // The register-side record (P) stores n and m negated so that every dot
 // product reads the same difference vectors D_ij = p_i - q_j.
@@ -29,6 +30,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "exact.cuh"
 
 namespace pj {
 
@@ -64,6 +66,12 @@ __device__ __forceinline__ float pdiv_(float x, float y) { return __fdividef(x, 
 __device__ __forceinline__ double pdiv_(double x, double y) { return x / y; }
 __device__ __forceinline__ float inf_(float) { return __int_as_float(0x7f800000); }
 __device__ __forceinline__ double inf_(double) { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ float nan_(float) { return __int_as_float(0x7fffffff); }
+__device__ __forceinline__ double nan_(double) { return __longlong_as_double(0x7fffffffffffffffLL); }
+// the smallest positive value: the distance of facets that do not meet
+// where the candidates round to 0 (0 is kept for facets that meet)
+__device__ __forceinline__ float tiny_(float) { return __int_as_float(1); }
+__device__ __forceinline__ double tiny_(double) { return __longlong_as_double(1LL); }
 __device__ __forceinline__ float sqrt_test(float x) {
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -145,7 +153,7 @@ __device__ __forceinline__ void make_rec(Rec<T>& R, const T a[3], const T b[3], 
     R.hoff = T(0);
   } else {
     R.n[0] = R.n[1] = R.n[2] = T(0);
-    R.hoff = inf_(T(0));
+    R.hoff = nan_(T(0));
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -316,7 +324,8 @@ __device__ __forceinline__ T tri_d2(const Rec<T>& P, const Rec<T>& Q, T eh, bool
     }
   T pmin = min(hP[0], min(hP[1], hP[2])), pmax = max(hP[0], max(hP[1], hP[2]));
   T qmin = min(hQ[0], min(hQ[1], hQ[2])), qmax = max(hQ[0], max(hQ[1], hQ[2]));
-  maybe = (pmin <= eh) && (pmax >= -eh) && (qmin <= eh) && (qmax >= -eh);
+  // (NaN heights of a zero-area facet fail every comparison: maybe)
+  maybe = !((pmin > eh) || (pmax < -eh) || (qmin > eh) || (qmax < -eh));
   return d2;
 }
 
@@ -394,7 +403,7 @@ __device__ __forceinline__ void make_rec(RecL& R, const float a[3], const float 
     hoff = 0.f;
   } else {
     R.n[0] = R.n[1] = R.n[2] = 0.f;
-    hoff = inf_(0.f);
+    hoff = nan_(0.f);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -497,7 +506,7 @@ __device__ __forceinline__ float tri_d2(const RecL& P, const RecL& Q, float eh, 
     }
   const float pmin = min(hP[0], min(hP[1], hP[2])), pmax = max(hP[0], max(hP[1], hP[2]));
   const float qmin = min(hQ[0], min(hQ[1], hQ[2])), qmax = max(hQ[0], max(hQ[1], hQ[2]));
-  maybe = (pmin <= eh) && (pmax >= -eh) && (qmin <= eh) && (qmax >= -eh);
+  maybe = !((pmin > eh) || (pmax < -eh) || (qmin > eh) || (qmax < -eh));
   return d2;
 }
 
@@ -555,58 +564,14 @@ struct RecOf<float> {
   using S = RecSmemL;
 };
 
-// Crossing decision in double precision from raw float vertices (the three
-// float4 of each facet, .w ignored) and a float origin: differences of
-// floats are exact in double, so this is the FP64 path's test, used by the
-// single-precision kernel in its rare branch.  Edge (a, b) of one triangle
-// crosses the other, (t0, t1, t2), when a and b lie strictly on opposite
-// sides of its plane and the line through them passes strictly inside all
-// three edges (signed volumes of (a, b, t_j, t_j+1) of one sign).
-__device__ __forceinline__ double orient64(const double a[3], const double b[3], const double c[3],
-                                           const double d[3]) {
-  double x0 = b[0] - a[0], x1 = b[1] - a[1], x2 = b[2] - a[2];
-  double y0 = c[0] - a[0], y1 = c[1] - a[1], y2 = c[2] - a[2];
-  double z0 = d[0] - a[0], z1 = d[1] - a[1], z2 = d[2] - a[2];
-  return x0 * (y1 * z2 - y2 * z1) + x1 * (y2 * z0 - y0 * z2) + x2 * (y0 * z1 - y1 * z0);
-}
-
-static __device__ __forceinline__ bool cross_exact64(const float4* fp, const float4* fq, float4 o) {
-  double P[3][3], Q[3][3];
-#pragma unroll
-  for (int v = 0; v < 3; ++v) {
-    P[v][0] = (double)fp[v].x - (double)o.x;
-    P[v][1] = (double)fp[v].y - (double)o.y;
-    P[v][2] = (double)fp[v].z - (double)o.z;
-    Q[v][0] = (double)fq[v].x - (double)o.x;
-    Q[v][1] = (double)fq[v].y - (double)o.y;
-    Q[v][2] = (double)fq[v].z - (double)o.z;
-  }
-  for (int side = 0; side < 2; ++side) {
-    const double(*A)[3] = side ? Q : P;
-    const double(*B)[3] = side ? P : Q;
-    double h[3];
-    for (int i = 0; i < 3; ++i) h[i] = orient64(B[0], B[1], B[2], A[i]);
-    for (int i = 0; i < 3; ++i) {
-      int k = (i + 1) % 3;
-      if (!((h[i] > 0.0 && h[k] < 0.0) || (h[i] < 0.0 && h[k] > 0.0))) continue;
-      double o1 = orient64(A[i], A[k], B[0], B[1]);
-      double o2 = orient64(A[i], A[k], B[1], B[2]);
-      double o3 = orient64(A[i], A[k], B[2], B[0]);
-      if ((o1 > 0.0 && o2 > 0.0 && o3 > 0.0) || (o1 < 0.0 && o2 < 0.0 && o3 < 0.0)) return true;
-    }
-  }
-  return false;
-}
-
 // Sign of the orientation determinant of (a, b, c, d) from single-precision
 // differences of the raw float coordinates, or 0 when the sign is not
 // certain.  Each difference carries a relative rounding error of at most
 // u = 2^-24, and the evaluation of the 3x3 determinant adds a few u of the
 // permanent Pm (the same sum with absolute values), so the computed value is
 // within 12 u Pm of the exact one; a value beyond 2^-19 Pm (32 u Pm) has the
-// exact sign, which the double-precision evaluation of cross_exact64 (exact
-// differences, error ~7 u_64 Pm) also gets.  A semi-static filter in the
-// manner of adaptive-precision geometric predicates.
+// exact sign.  A semi-static filter in the manner of adaptive-precision
+// geometric predicates; uncertain signs go to exact arithmetic.
 __device__ __forceinline__ int orient_sign32(const float4& a, const float4& b, const float4& c, const float4& d) {
   const float x0 = b.x - a.x, x1 = b.y - a.y, x2 = b.z - a.z;
   const float y0 = c.x - a.x, y1 = c.y - a.y, y2 = c.z - a.z;
@@ -623,9 +588,13 @@ __device__ __forceinline__ int orient_sign32(const float4& a, const float4& b, c
   return det > bound ? 1 : (det < -bound ? -1 : 0);
 }
 
-// cross_exact64's decision from single-precision filtered signs: 1 or 0
-// when every sign it needs is certain (then it equals cross_exact64's
-// result), -1 when some sign is not.
+// The meeting decision from single-precision filtered signs: 1 when an edge
+// of one facet certainly crosses the other strictly inside, 0 when every
+// edge certainly misses (both ends strictly on one side of the plane, or
+// the line passing an edge strictly on the wrong side), -1 when some sign
+// is not certain (tri_meet_exact then decides; touching, coplanar and
+// degenerate configurations always land there, since the filter never
+// certifies a zero sign).
 __device__ __forceinline__ int cross_filter32(const float4* fp, const float4* fq) {
   bool unsure = false;
   for (int side = 0; side < 2; ++side) {
@@ -653,11 +622,11 @@ __device__ __forceinline__ int cross_filter32(const float4* fp, const float4* fq
   return unsure ? -1 : 0;
 }
 
-// The crossing decision of cross_exact64, in single precision where the
-// filter is certain.
-static __device__ __forceinline__ bool cross_decide(const float4* fp, const float4* fq, float4 o) {
+// Do the closed facets (raw float vertices) meet?  Exact: single-precision
+// signs where they are certain, else exact expansion arithmetic.
+static __device__ __forceinline__ bool cross_decide(const float4* fp, const float4* fq) {
   const int f = cross_filter32(fp, fq);
-  return f >= 0 ? f == 1 : cross_exact64(fp, fq, o);
+  return f >= 0 ? f == 1 : tri_meet_exact(fp, fq);
 }
 
 // Forward error margins of the single-precision test for coordinates
@@ -672,15 +641,28 @@ struct Margins {
   float eps, eh, ew;
 };
 
+// Below a sine of 1e-6 (slivers) no margin is claimed: eh = eps = +inf, so
+// every straddle test passes (the exact meeting test decides) and the unit
+// decides nothing in single precision (its pairs go to double precision).
 __host__ __device__ __forceinline__ Margins fp32_margins(float rho, float L, float smin) {
   const float u = 5.9604644775390625e-08f;          // 2^-24
   const float su = 2.44140625e-04f;                 // sqrt(2^-24) = 2^-12
-  float s = smin > 1e-6f ? smin : 1e-6f;
   Margins m;
-  m.eh = 128.0f * u * rho / s;
   m.ew = 0.0f;
-  m.eps = 256.0f * u * rho / s + 8.0f * su * L;
+  if (!(smin >= 1e-6f)) {
+    m.eh = m.eps = INFINITY;
+    return m;
+  }
+  m.eh = 128.0f * u * rho / smin;
+  m.eps = 256.0f * u * rho / smin + 8.0f * su * L;
   return m;
+}
+
+// The double-precision kernels take their distances as exact (eps = 0) but
+// need the straddle margin of their heights for the meeting test: the same
+// derivation with u = 2^-53 (the single-precision margin times 2^-29).
+__host__ __device__ __forceinline__ float fp64_height_margin(const Margins& m32) {
+  return m32.eh * 1.862645149230957e-09f;   // 2^-29 (inf stays inf)
 }
 
 }  // namespace pj

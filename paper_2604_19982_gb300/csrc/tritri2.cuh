@@ -201,14 +201,14 @@ __device__ __forceinline__ f2 tri_d2x2(const RecL2& P, const RecL2& Q, float eh,
     const float p1 = fmaxf(lo2(hP[0]), fmaxf(lo2(hP[1]), lo2(hP[2])));
     const float q0 = fminf(lo2(hQ[0]), fminf(lo2(hQ[1]), lo2(hQ[2])));
     const float q1 = fmaxf(lo2(hQ[0]), fmaxf(lo2(hQ[1]), lo2(hQ[2])));
-    maybe0 = (p0 <= eh) && (p1 >= -eh) && (q0 <= eh) && (q1 >= -eh);
+    maybe0 = !((p0 > eh) || (p1 < -eh) || (q0 > eh) || (q1 < -eh));   // NaN (zero area): maybe
   }
   {
     const float p0 = fminf(hi2(hP[0]), fminf(hi2(hP[1]), hi2(hP[2])));
     const float p1 = fmaxf(hi2(hP[0]), fmaxf(hi2(hP[1]), hi2(hP[2])));
     const float q0 = fminf(hi2(hQ[0]), fminf(hi2(hQ[1]), hi2(hQ[2])));
     const float q1 = fmaxf(hi2(hQ[0]), fmaxf(hi2(hQ[1]), hi2(hQ[2])));
-    maybe1 = (p0 <= eh) && (p1 >= -eh) && (q0 <= eh) && (q1 >= -eh);
+    maybe1 = !((p0 > eh) || (p1 < -eh) || (q0 > eh) || (q1 < -eh));
   }
   return d2;
 }

@@ -1,8 +1,10 @@
 """Triangle-distance kernels (pj_tri_dist) against the oracle.
 
 FP64 kernel: equal to the oracle within 1e-12 relative (absolute floor
-1e-14 for coordinates of order 1), identical zero/non-zero decisions on
-generic inputs.  FP32 kernel: within the forward error bound it reports.
+1e-14 for coordinates of order 1).  FP32 kernel: within the forward error
+bound it reports.  Both: a distance is 0 exactly when the oracle's is
+(the closed triangles meet), on every pair, including exact contacts and
+one-float-step near misses.
 """
 import numpy as np
 import pytest
@@ -75,7 +77,7 @@ def test_fp64_random_matches_oracle(ctx):
     P, Q = random_pairs(rng, 20000)
     d, _ = run(ctx, P, Q, pj.FP64)
     ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
-    assert ((d == 0) == (ref == 0)).all()
+    assert np.array_equal(d == 0, ref == 0)
     assert (ref == 0).sum() > 100
     assert (np.abs(d - ref) <= 1e-12 * ref + 1e-14).all()
 
@@ -129,6 +131,7 @@ def test_fp64_degenerate(ctx):
     Q = Q.astype(np.float32)
     d, _ = run(ctx, P, Q, pj.FP64)
     ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
+    assert np.array_equal(d == 0, ref == 0)
     assert (np.abs(d - ref) <= 1e-12 * ref + 1e-12).all()
 
 
@@ -158,26 +161,51 @@ def piercing_pairs(rng, n):
     return P.astype(np.float32), Q.astype(np.float32)
 
 
-def test_crossing_decisions_filtered(ctx):
-    """A crossing the oracle is sure of (depth beyond its error bound) is
-    found by both kernels (distance 0); a pair the oracle is not sure of
-    gets its distance within the usual tolerance, or 0 when the kernel's
-    double-precision signs see a crossing, which happens only at depths near
-    the rounding of the inputs (then the oracle's distance is tiny against
-    the facet size)."""
+def check_zero_and_values(P, Q, ref, d64, d32, err):
+    """Zero-ness equal to the oracle's on every pair (0 exactly when the
+    closed triangles meet), non-zero distances within the tolerances:
+    FP64 1e-12 relative above an absolute floor of a few u_64 times the
+    coordinate scale (the candidate formulas differ in rounding), FP32
+    within the bound the kernel reports."""
+    zero = ref == 0
+    assert np.array_equal(d64 == 0, zero), np.nonzero((d64 == 0) != zero)[0][:10]
+    assert np.array_equal(d32 == 0, zero), np.nonzero((d32 == 0) != zero)[0][:10]
+    nz = ~zero
+    scale = np.maximum(np.abs(P.astype(np.float64)).reshape(len(P), -1).max(1),
+                       np.abs(Q.astype(np.float64)).reshape(len(Q), -1).max(1))
+    assert (np.abs(d64[nz] - ref[nz]) <= 1e-12 * ref[nz] + 1e-14 * scale[nz]).all()
+    assert (np.abs(d32[nz] - ref[nz]) <= err[nz]).all()
+
+
+def test_crossing_decisions_exact(ctx):
+    """Piercing pairs at depths down to the rounding of the inputs: every
+    pair's zero-ness equals the oracle's (exact meeting test on both sides:
+    single-precision filtered signs, then exact arithmetic)."""
     from paper_2604_19982_gb300 import pj
     rng = np.random.default_rng(12)
     P, Q = piercing_pairs(rng, 20000)
     ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
     d64, _ = run(ctx, P, Q, pj.FP64)
     d32, err = run(ctx, P, Q, pj.FP32)
-    L = np.linalg.norm(P[:, 1].astype(np.float64) - P[:, 0], axis=1)
-    sure = ref == 0
-    assert sure.sum() > 15000
-    assert (d64[sure] == 0).mean() > 0.999 and (d32[sure] == 0).mean() > 0.999
-    rest = ~sure
-    z64, z32 = rest & (d64 == 0), rest & (d32 == 0)
-    assert (ref[z64] <= 1e-3 * L[z64]).all() and (ref[z32] <= 1e-3 * L[z32]).all()
-    m64, m32 = rest & (d64 > 0), rest & (d32 > 0)
-    assert (np.abs(d64[m64] - ref[m64]) <= 1e-12 * ref[m64] + 1e-12).all()
-    assert (np.abs(d32[m32] - ref[m32]) <= err[m32]).all()
+    assert (ref == 0).sum() > 15000 and (ref > 0).sum() > 100
+    check_zero_and_values(P, Q, ref, d64, d32, err)
+
+
+@pytest.mark.parametrize("offset", [0.0, 1000.0])
+def test_contacts_exact(ctx, offset):
+    """Exact contacts of every kind (vertex on face, on edge, shared vertex,
+    edge through edge, coplanar overlap, segment and point triangles) and
+    one-float-step near misses: zero-ness equal to the oracle's on every
+    pair, in both precisions."""
+    from paper_2604_19982_gb300 import pj
+    from meet_cases import contact_pairs
+    rng = np.random.default_rng(41 if offset == 0 else 42)
+    P, Q = contact_pairs(rng, 9000, offset)
+    ref, _ = oracle.tri_dist(P.astype(np.float64), Q.astype(np.float64))
+    d64, _ = run(ctx, P, Q, pj.FP64)
+    d32, err = run(ctx, P, Q, pj.FP32)
+    assert (ref == 0).sum() > 2000 and (ref > 0).sum() > 1000
+    check_zero_and_values(P, Q, ref, d64, d32, err)
+    # swapped roles give the same decisions
+    e64, _ = run(ctx, Q, P, pj.FP64)
+    assert np.array_equal(e64 == 0, ref == 0)
