@@ -165,10 +165,19 @@ pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out);
 
 /* A set streamed in n_chunks pieces during pj_join (R side only).  For each
  * chunk the library calls fill(user, chunk, &desc) from a loader thread; the
- * callback fills desc with that chunk's objects (host memory that must stay
- * valid until the next call of fill or the end of the join).  Object ids of
- * chunk c continue those of chunk c-1.  A fill returning PJ_ECANCELLED stops
- * the join with that status; any other non-zero value gives PJ_ESOURCE. */
+ * callback fills desc with that chunk's objects.  Object ids of chunk c
+ * continue those of chunk c-1.  A fill returning PJ_ECANCELLED stops the
+ * join with that status; any other non-zero value gives PJ_ESOURCE.
+ * Where the arrays may live, and for how long:
+ *   - pageable host memory: packed into the library's pinned staging, so it
+ *     must stay valid until the next call of fill or the end of the join;
+ *   - pinned host memory (cudaHostAlloc / cudaHostRegister): copied to the
+ *     device directly, without packing (the link-bound path), so it must
+ *     stay valid and unchanged until pj_join returns;
+ *   - device memory (verts, faces, hd, ph, anchor only): read in place by
+ *     the set-building kernels, likewise until pj_join returns.
+ * vert_off and face_off are always host memory (read by the host; PJ_EINVAL
+ * otherwise). */
 typedef pj_status (*pj_fill_fn)(void* user, int chunk, pj_mesh_set_desc* out);
 pj_status pj_load_set_streamed(pj_ctx* ctx, int64_t n_objects, int n_chunks, pj_fill_fn fill,
                                void* user, pj_set** out);
@@ -194,7 +203,10 @@ void pj_result_free(pj_result* res);
  * tests that the testing lane's own ball test asked for; the others ran
  * because another lane of the warp needed the same s facet), and per step
  * in "steps": "tiles" (units built) and "tiles_run" (units left after the
- * full-resolution mask pass).  Fails with PJ_EINVAL when cap is too small. */
+ * full-resolution mask pass).  Also, at the time of the call: "allocs", the
+ * number of device and pinned-host allocations the library has made in this
+ * process (all contexts), and "ws_bytes", the context's workspace bytes.
+ * Fails with PJ_EINVAL when cap is too small. */
 pj_status pj_get_stats(const pj_ctx* ctx, char* json_buf, size_t cap);
 
 /* ------------------------------------------------------------------ *
@@ -293,9 +305,9 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
  * held by every GPU that loads the library until the process exits.  Its
  * device address is looked up on the first call on each device (with that
  * device current).  Sizes beyond it are rejected with PJ_EINVAL:
- * n <= PJ_STATIC_MAX_PAIRS, n x (blocks of the largest R object) x (blocks
- * of the largest S object) at `lod` <= PJ_STATIC_MAX_TILES with a block of
- * 32 facets, and n x (256-facet chunks of the largest R object) <= 65536.  All calls share the array; it keeps the previous
+ * n <= PJ_STATIC_MAX_PAIRS, and n x (blocks of the largest R object) x
+ * (blocks of the largest S object) at `lod` <= PJ_STATIC_MAX_TILES with a
+ * block of 32 facets.  All calls share the array; it keeps the previous
  * call's contents (the call clears what must start at zero), and calls that
  * overlap on the GPU -- on two streams or from two host threads -- race on
  * it and must be serialized by the caller. */

@@ -28,6 +28,8 @@ pj_status mlp_train_impl(pj_ctx* ctx, const float* feats, const float* target, i
                          uint64_t seed);
 void mlp_ensure(pj_ctx* ctx);
 
+std::atomic<unsigned long long> g_allocs{0};
+
 void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st) {
   (void)st;
   DevBuf& b = ctx->ws[slot];
@@ -37,6 +39,7 @@ void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st) {
     b.p = nullptr;
     b.cap = 0;
     size_t cap = std::max(bytes, b.cap + b.cap / 2);
+    note_alloc();
     PJ_CK(cudaMalloc(&b.p, cap));
     b.cap = cap;
   }
@@ -196,6 +199,7 @@ void free_set_storage(pj_set* s) {
 template <class T>
 static T* upload(const T* h, size_t count, cudaStream_t st) {
   T* d = nullptr;
+  note_alloc();
   PJ_CK(cudaMallocAsync((void**)&d, std::max<size_t>(1, count) * sizeof(T), st));
   if (count) PJ_CK(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
   return d;
@@ -331,11 +335,15 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
       dph = upload(D->ph[l], (size_t)ld.F, st);
       temps.push_back(dph);
     }
+    note_alloc();
     PJ_CK(cudaMallocAsync((void**)&ld.fac, std::max<int64_t>(1, 3 * ld.F) * sizeof(float4), st));
+    note_alloc();
     PJ_CK(cudaMallocAsync((void**)&ld.chunk, std::max<int64_t>(1, 3 * ld.C) * sizeof(float4), st));
+    note_alloc();
     PJ_CK(cudaMallocAsync((void**)&ld.blk, std::max<int64_t>(1, 3 * ld.B) * sizeof(float4), st));
     raw[l] = RawLod{dv, dvo, dfa, nfs, dhd, dph};
   }
+  note_alloc();
   PJ_CK(cudaMallocAsync((void**)&s->mbb, std::max(1, n) * 6 * sizeof(float), st));
   s->anchor = upload(D->anchor, (size_t)n * 3, st);
   build_set_kernels(ctx, s, raw, st);
@@ -445,11 +453,14 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
   }
   PJ_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   PJ_CK(cudaStreamCreateWithFlags(&ctx->build_stream, cudaStreamNonBlocking));
+  note_alloc();
   PJ_CK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
+  note_alloc();
   PJ_CK(cudaMalloc((void**)&ctx->d_counters, 16 * sizeof(unsigned long long)));
   PJ_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   PJ_CK(cudaMemset(ctx->d_counters, 0, 16 * sizeof(unsigned long long)));
   for (auto& e : ctx->ev) PJ_CK(cudaEventCreate(&e));
+  note_alloc();
   PJ_CK(cudaMalloc((void**)&ctx->d_snap, 64 * 4 * sizeof(long long)));
   std::string v = json_str(options_json, "persistent_ctas_per_sm");
   if (!v.empty()) ctx->ctas_per_sm = std::max(0, atoi(v.c_str()));
@@ -623,7 +634,17 @@ void pj_result_free(pj_result* res) {
 
 pj_status pj_get_stats(const pj_ctx* ctx, char* buf, size_t cap) {
   if (!ctx || !buf || cap == 0) return PJ_EINVAL;
-  const std::string& s = ctx->stats.empty() ? std::string("{}") : ctx->stats;
+  // the last join's record plus the library's allocation count and the
+  // context's workspace bytes at the time of the call
+  std::string s = ctx->stats.empty() ? std::string("{}") : ctx->stats;
+  size_t ws = 0;
+  for (const auto& b : ctx->ws) ws += b.cap;
+  const size_t close = s.rfind('}');
+  if (close != std::string::npos) {
+    const bool empty = s.find_first_not_of(" \n\t{", 0) == close;
+    s.insert(close, std::string(empty ? "" : ", ") + "\"allocs\": " + std::to_string(g_allocs.load()) +
+                        ", \"ws_bytes\": " + std::to_string(ws));
+  }
   if (s.size() + 1 > cap) return PJ_EINVAL;
   memcpy(buf, s.c_str(), s.size() + 1);
   return PJ_OK;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -347,6 +348,12 @@ constexpr float PRED_BAND = 0.15f;
 constexpr float START_MARGIN = 0.5f;
 void pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
                    int64_t n, float* out, cudaStream_t st);
+
+// Device and pinned-host allocations made by the library (all contexts of
+// the process), reported by pj_get_stats as "allocs": lets a caller check
+// that an entry point allocated nothing.
+extern std::atomic<unsigned long long> g_allocs;
+inline void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 // count a kernel launch of the library (for the benchmark's launch tally)
 inline void count_launch(pj_ctx* ctx, int n = 1) { ctx->launches += (unsigned long long)n; }

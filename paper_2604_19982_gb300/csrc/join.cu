@@ -100,7 +100,10 @@ void scan_i64(pj_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStrea
     return;
   }
   bool own = tmp == nullptr;
-  if (own) PJ_CK(cudaMallocAsync((void**)&tmp, (size_t)scan_tmp_words(n) * 8, st));
+  if (own) {
+    note_alloc();
+    PJ_CK(cudaMallocAsync((void**)&tmp, (size_t)scan_tmp_words(n) * 8, st));
+  }
   int64_t* bsum = tmp;
   int64_t* boff = tmp + nb;
   k_block_sums<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum);
@@ -294,6 +297,7 @@ static void* stage(pj_ctx* ctx, size_t bytes) {
     if (ctx->h_stage) PJ_CK(cudaFreeHost(ctx->h_stage));
     ctx->h_stage = nullptr;
     size_t cap = std::max(bytes, ctx->h_stage_cap * 2);
+    note_alloc();
     PJ_CK(cudaMallocHost(&ctx->h_stage, cap));
     ctx->h_stage_cap = cap;
   }

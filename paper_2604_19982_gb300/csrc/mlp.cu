@@ -492,7 +492,10 @@ static void mlp_init_host(std::vector<float>& W, uint64_t seed) {
 }
 
 static void ensure_weights(pj_ctx* ctx) {
-  if (!ctx->mlp_w) PJ_CK(cudaMalloc((void**)&ctx->mlp_w, MLP_NW * sizeof(float)));
+  if (!ctx->mlp_w) {
+    note_alloc();
+    PJ_CK(cudaMalloc((void**)&ctx->mlp_w, MLP_NW * sizeof(float)));
+  }
 }
 
 // Adam over shuffled mini-batches of device-resident features X [n][16] and
