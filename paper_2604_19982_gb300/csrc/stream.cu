@@ -5,9 +5,12 @@
 // A loader thread asks the caller's fill callback for chunk c, checks it,
 // and packs its raw arrays (vertices once per distinct host array, vertex
 // and face offsets, faces, hd / ph, anchors, and the facet / chunk / block
-// offsets computed on the host) into one of two pinned host slots.  The
-// calling thread copies a packed chunk to the matching device slot with one
-// host-to-device copy on the context's copy stream, builds the chunk's
+// offsets computed on the host) into one of two pinned host slots.  Arrays
+// the caller already keeps in pinned host memory are not packed: they are
+// copied to the device slot directly; arrays in device memory are read in
+// place.  The calling thread copies a chunk to the matching device slot
+// (one copy per run of packed arrays and one per pinned array) on the
+// context's copy stream, builds the chunk's
 // facet records and boxes on the build stream once that copy is done (into
 // the derived buffers of its slot), and joins the chunk against S with the
 // resident-set join.  The copy and the build of chunk c + 1 are issued
@@ -40,6 +43,26 @@ namespace {
 constexpr size_t PACK_ALIGN = 256;
 size_t pad(size_t x) { return (x + PACK_ALIGN - 1) & ~(PACK_ALIGN - 1); }
 
+// Where the bytes of one array come from: packed into the pinned slot
+// (pageable caller memory, or offsets computed here), copied directly from
+// the caller's pinned memory, or read in place from device memory.
+enum PieceKind { PACK = 0, PINNED = 1, DEVICE = 2 };
+struct Piece {
+  const void* src;
+  size_t off;
+  size_t bytes;
+  int kind;
+};
+
+int memory_kind(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return PACK;
+  }
+  return a.type == cudaMemoryTypeDevice ? DEVICE : (a.type == cudaMemoryTypeHost ? PINNED : PACK);
+}
+
 // Where each array of one chunk sits inside its packed slot (byte offsets).
 struct Plan {
   int index = -1;
@@ -55,6 +78,14 @@ struct Plan {
   int64_t F[PJ_MAX_LODS], C[PJ_MAX_LODS], B[PJ_MAX_LODS], maxF[PJ_MAX_LODS];
   size_t o_anchor = 0;
   size_t bytes = 0;
+  // caller device arrays read in place (nullptr: at their offset in the slot)
+  const void* d_verts[PJ_MAX_LODS] = {};
+  const void* d_faces[PJ_MAX_LODS] = {};
+  const void* d_hd[PJ_MAX_LODS] = {};
+  const void* d_ph[PJ_MAX_LODS] = {};
+  const void* d_anchor = nullptr;
+  std::vector<Piece> pieces;   // what fills the device slot
+  size_t bytes_h2d = 0;        // bytes the chunk moves from the host
 };
 
 struct ChunkSlot {
@@ -64,14 +95,10 @@ struct ChunkSlot {
   cudaEvent_t copied = nullptr;
 };
 
-struct Piece {
-  const void* src;
-  size_t off;
-  size_t bytes;
-};
-
 // Check one chunk description (the rules of pj_load_set) and lay it out.
 // Host offset arrays are computed into `offs` (kept alive until packed).
+// vert_off and face_off must be host memory (read here); verts, faces,
+// hd, ph and anchor may lie anywhere.
 void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Piece>& pieces,
                 std::vector<std::vector<int64_t>>& offs) {
   const int n = D->n_objects, L = D->n_lods;
@@ -81,9 +108,16 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
   P.n = n;
   P.L = L;
   size_t at = 0;
-  auto put = [&](const void* src, size_t bytes) {
+  // a caller array (kind from its address) or one computed here (packed);
+  // a device array takes no room in the slot and is recorded in *dptr
+  auto put = [&](const void* src, size_t bytes, bool caller = false, const void** dptr = nullptr) {
+    const int kind = (caller && bytes) ? memory_kind(src) : PACK;
+    if (kind == DEVICE && dptr) {
+      *dptr = src;
+      return size_t(0);
+    }
     const size_t off = at;
-    if (bytes) pieces.push_back(Piece{src, off, bytes});
+    if (bytes) pieces.push_back(Piece{src, off, bytes, kind == DEVICE ? PINNED : kind});
     at = pad(at + bytes);
     return off;
   };
@@ -92,6 +126,8 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
     if (!D->verts[l] || !D->vert_off[l] || !D->faces[l])
       throw ApiError{PJ_EINVAL, "chunk: verts / vert_off / faces of a LoD is NULL"};
     if (l == L - 1 && (D->hd[l] || D->ph[l])) throw ApiError{PJ_EINVAL, "chunk: hd / ph of the original LoD must be NULL"};
+    if (memory_kind(D->vert_off[l]) == DEVICE || (D->face_off[l] && memory_kind(D->face_off[l]) == DEVICE))
+      throw ApiError{PJ_EINVAL, "chunk: vert_off / face_off must be host arrays"};
     const int64_t* vo = D->vert_off[l];
     if (n > 0 && vo[0] != 0) throw ApiError{PJ_EINVAL, "chunk: vert_off must start at 0"};
     for (int o = 0; o < n; ++o)
@@ -128,23 +164,31 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
         P.vsrc[l] = m;
         break;
       }
-    P.o_verts[l] = P.vsrc[l] == l ? put(D->verts[l], (size_t)nv * 12) : P.o_verts[P.vsrc[l]];
-    P.o_voff[l] = put(vo, (size_t)(n + 1) * 8);
-    P.o_faces[l] = put(D->faces[l], (size_t)(shared ? nfs : P.F[l]) * 12);
+    if (P.vsrc[l] == l) {
+      P.o_verts[l] = put(D->verts[l], (size_t)nv * 12, true, &P.d_verts[l]);
+    } else {
+      P.o_verts[l] = P.o_verts[P.vsrc[l]];
+      P.d_verts[l] = P.d_verts[P.vsrc[l]];
+    }
+    P.o_voff[l] = put(vo, (size_t)(n + 1) * 8, true);
+    P.o_faces[l] = put(D->faces[l], (size_t)(shared ? nfs : P.F[l]) * 12, true, &P.d_faces[l]);
     P.has_hd[l] = D->hd[l] != nullptr;
     P.has_ph[l] = D->ph[l] != nullptr;
-    P.o_hd[l] = P.has_hd[l] ? put(D->hd[l], (size_t)P.F[l] * 4) : 0;
-    P.o_ph[l] = P.has_ph[l] ? put(D->ph[l], (size_t)P.F[l] * 4) : 0;
+    P.o_hd[l] = P.has_hd[l] ? put(D->hd[l], (size_t)P.F[l] * 4, true, &P.d_hd[l]) : 0;
+    P.o_ph[l] = P.has_ph[l] ? put(D->ph[l], (size_t)P.F[l] * 4, true, &P.d_ph[l]) : 0;
     P.o_foff[l] = put(fo.data(), (size_t)(n + 1) * 8);
     P.o_coff[l] = put(co.data(), (size_t)(n + 1) * 8);
     P.o_boff[l] = put(bo.data(), (size_t)(n + 1) * 8);
   }
-  P.o_anchor = put(D->anchor, (size_t)n * 12);
+  P.o_anchor = put(D->anchor, (size_t)n * 12, true, &P.d_anchor);
   P.bytes = at;
+  P.bytes_h2d = 0;
+  for (const Piece& pc : pieces) P.bytes_h2d += pc.bytes;
 }
 
-// Copy the pieces into the pinned slot with several host threads (the
-// chunk is hundreds of MB; one thread's memcpy would pace the pipeline).
+// Copy the packed pieces into the pinned slot with several host threads
+// (the chunk is hundreds of MB; one thread's memcpy would pace the
+// pipeline).
 void pack_parallel(const std::vector<Piece>& pieces, unsigned char* dst) {
   constexpr size_t SLICE = size_t(4) << 20;
   struct Job {
@@ -153,7 +197,7 @@ void pack_parallel(const std::vector<Piece>& pieces, unsigned char* dst) {
   };
   std::vector<Job> jobs;
   for (const Piece& pc : pieces)
-    for (size_t a = 0; a < pc.bytes; a += SLICE)
+    for (size_t a = 0; pc.kind == PACK && a < pc.bytes; a += SLICE)
       jobs.push_back(Job{static_cast<const unsigned char*>(pc.src) + a, pc.off + a, std::min(SLICE, pc.bytes - a)});
   // all host cores but two (the calling thread drives the GPU, the loader
   // fills the next chunk), at most 16
@@ -254,6 +298,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
         try {
           pieces.clear();
           plan_chunk(&d, L_first, P, pieces, offs);
+          P.pieces = pieces;
           if (c == 0) L_first = P.L;
           P.index = c;
           P.first_id = first;
@@ -266,6 +311,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
             if (hp) cudaFreeHost(hp);
             hp = nullptr;
             hc = 0;
+            note_alloc();
             if (cudaHostAlloc(&hp, P.bytes, cudaHostAllocDefault) != cudaSuccess)
               throw ApiError{PJ_ENOMEM, "pinned staging allocation failed"};
             hc = P.bytes;
@@ -326,12 +372,27 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       }
     }
     const size_t bytes = sl.plan.bytes;
-    void* dev = ws_get(ctx, (c & 1) ? WS_STREAM5 : WS_STREAM4, bytes, ctx->copy_stream);
+    unsigned char* dev = (unsigned char*)ws_get(ctx, (c & 1) ? WS_STREAM5 : WS_STREAM4, bytes, ctx->copy_stream);
+    const unsigned char* pinned = (const unsigned char*)ctx->stream_pinned[c & 1];
     PJ_CK(cudaEventRecord(h2d0[c & 1], ctx->copy_stream));
-    PJ_CK(cudaMemcpyAsync(dev, ctx->stream_pinned[c & 1], bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    // runs of adjacent packed pieces in one copy each, pinned caller arrays
+    // one copy each (pieces are in slot order)
+    const std::vector<Piece>& pcs = sl.plan.pieces;
+    for (size_t i = 0; i < pcs.size();) {
+      if (pcs[i].kind == PINNED) {
+        PJ_CK(cudaMemcpyAsync(dev + pcs[i].off, pcs[i].src, pcs[i].bytes, cudaMemcpyDefault, ctx->copy_stream));
+        ++i;
+        continue;
+      }
+      size_t j = i + 1;
+      while (j < pcs.size() && pcs[j].kind == PACK) ++j;
+      const size_t a = pcs[i].off, b = pcs[j - 1].off + pcs[j - 1].bytes;
+      PJ_CK(cudaMemcpyAsync(dev + a, pinned + a, b - a, cudaMemcpyHostToDevice, ctx->copy_stream));
+      i = j;
+    }
     PJ_CK(cudaEventRecord(h2d1[c & 1], ctx->copy_stream));
     PJ_CK(cudaEventRecord(sl.copied, ctx->copy_stream));
-    bytes_h2d += bytes;
+    bytes_h2d += sl.plan.bytes_h2d;
     {
       std::lock_guard<std::mutex> lk(mu);
       plans[c & 1] = sl.plan;
@@ -368,7 +429,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     unsigned char* mb = (unsigned char*)ws_get(ctx, si ? WS_STREAM8 : WS_STREAM3, box_bytes + 16, bst);
     view.mbb = (float*)mb;
     int* err = (int*)(mb + box_bytes);
-    view.anchor = (float*)(dev + P.o_anchor);
+    view.anchor = P.d_anchor ? (float*)P.d_anchor : (float*)(dev + P.o_anchor);
     RawLod raw[PJ_MAX_LODS];
     for (int l = 0; l < P.L; ++l) {
       LodData& ld = view.lod[l];
@@ -385,15 +446,17 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       ld.foff = (int64_t*)(dev + P.o_foff[l]);
       ld.coff = (int64_t*)(dev + P.o_coff[l]);
       ld.boff = (int64_t*)(dev + P.o_boff[l]);
-      raw[l] = RawLod{(const float*)(dev + P.o_verts[l]), (const int64_t*)(dev + P.o_voff[l]),
-                      (const int32_t*)(dev + P.o_faces[l]), P.nfs[l],
-                      P.has_hd[l] ? (const float*)(dev + P.o_hd[l]) : nullptr,
-                      P.has_ph[l] ? (const float*)(dev + P.o_ph[l]) : nullptr};
+      auto at = [&](const void* d, size_t off) { return d ? d : (const void*)(dev + off); };
+      raw[l] = RawLod{(const float*)at(P.d_verts[l], P.o_verts[l]), (const int64_t*)(dev + P.o_voff[l]),
+                      (const int32_t*)at(P.d_faces[l], P.o_faces[l]), P.nfs[l],
+                      P.has_hd[l] ? (const float*)at(P.d_hd[l], P.o_hd[l]) : nullptr,
+                      P.has_ph[l] ? (const float*)at(P.d_ph[l], P.o_ph[l]) : nullptr};
     }
     if (ctx->stream_box_cap[si] < box_bytes + 16) {
       if (ctx->stream_box_pinned[si]) PJ_CK(cudaFreeHost(ctx->stream_box_pinned[si]));
       ctx->stream_box_pinned[si] = nullptr;
       ctx->stream_box_cap[si] = 0;
+      note_alloc();
       PJ_CK(cudaHostAlloc(&ctx->stream_box_pinned[si], box_bytes + 16, cudaHostAllocDefault));
       ctx->stream_box_cap[si] = box_bytes + 16;
     }

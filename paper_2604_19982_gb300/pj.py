@@ -111,34 +111,44 @@ def _ptr(a, t):
     return a.ctypes.data_as(C.POINTER(t)) if a is not None else None
 
 
+def _is_device(a) -> bool:
+    return getattr(a, "is_cuda", False)
+
+
 def describe(ms, keep: list) -> MeshSetDesc:
     """Fill a ``pj_mesh_set_desc`` from a mesh-set object with the attributes
-    ``n, n_lods, verts, vert_off, faces, face_off, hd, ph, anchor`` (numpy).
-    Arrays made contiguous here are appended to ``keep`` (they must outlive
-    the call)."""
+    ``n, n_lods, verts, vert_off, faces, face_off, hd, ph, anchor``: numpy
+    arrays, or (for a streamed set's chunks) contiguous CUDA tensors of the
+    same dtype for verts, faces, hd, ph and anchor, which the library then
+    reads in place.  Arrays made contiguous here are appended to ``keep``
+    (they must outlive the call)."""
     d = MeshSetDesc()
     d.n_objects = int(ms.n)
     d.n_lods = int(ms.n_lods)
 
-    def c(a, dt):
+    def c(a, dt, ct):
+        if _is_device(a):
+            if not a.is_contiguous() or a.element_size() != np.dtype(dt).itemsize:
+                raise ValueError("device arrays must be contiguous and of the host array's dtype")
+            keep.append(a)
+            return C.cast(C.c_void_p(a.data_ptr()), C.POINTER(ct)), int(a.shape[0])
         a = np.ascontiguousarray(a, dtype=dt)
         keep.append(a)
-        return a
+        return _ptr(a, ct), int(a.shape[0])
 
     for lvl in range(ms.n_lods):
-        d.verts[lvl] = _ptr(c(ms.verts[lvl], np.float32), C.c_float)
-        d.vert_off[lvl] = _ptr(c(ms.vert_off[lvl], np.int64), C.c_int64)
-        f = c(ms.faces[lvl], np.int32)
-        d.faces[lvl] = _ptr(f, C.c_int32)
+        d.verts[lvl] = c(ms.verts[lvl], np.float32, C.c_float)[0]
+        d.vert_off[lvl] = c(ms.vert_off[lvl], np.int64, C.c_int64)[0]
+        d.faces[lvl], nf = c(ms.faces[lvl], np.int32, C.c_int32)
         if ms.face_off[lvl] is None:
             d.face_off[lvl] = None
-            d.n_faces_shared[lvl] = int(f.shape[0])
+            d.n_faces_shared[lvl] = nf
         else:
-            d.face_off[lvl] = _ptr(c(ms.face_off[lvl], np.int64), C.c_int64)
+            d.face_off[lvl] = c(ms.face_off[lvl], np.int64, C.c_int64)[0]
             d.n_faces_shared[lvl] = 0
-        d.hd[lvl] = _ptr(c(ms.hd[lvl], np.float32), C.c_float) if ms.hd[lvl] is not None else None
-        d.ph[lvl] = _ptr(c(ms.ph[lvl], np.float32), C.c_float) if ms.ph[lvl] is not None else None
-    d.anchor = _ptr(c(ms.anchor, np.float32), C.c_float)
+        d.hd[lvl] = c(ms.hd[lvl], np.float32, C.c_float)[0] if ms.hd[lvl] is not None else None
+        d.ph[lvl] = c(ms.ph[lvl], np.float32, C.c_float)[0] if ms.ph[lvl] is not None else None
+    d.anchor = c(ms.anchor, np.float32, C.c_float)[0]
     return d
 
 

@@ -68,11 +68,12 @@ def blob_set(n: int, side: float, seed: int, set_id: int, subs=BLOB_SUBS,
     return make_blobs(c, R, C, subs)
 
 
-def tube_set(n: int, side: float, seed: int, set_id: int, start: int = 0,
-             count: int | None = None, length_range=(50.0, 800.0)) -> MeshSet:
-    """Tubes with centres uniform in the cube and arc lengths uniform in
-    ``length_range`` (the workload's range by default; tests use shorter
-    tubes to keep the oracle fast)."""
+def tube_params(n: int, side: float, seed: int, set_id: int, start: int = 0,
+                count: int | None = None, length_range=(50.0, 800.0)):
+    """Centres and arc lengths of tubes ``start .. start+count`` (cheap: no
+    surface is built).  A tube's centre line has the centre as the middle of
+    its box and at most its arc length as extent per axis, so the tube lies
+    in the box centre +- (length / 2 + radius)."""
     count = n - start if count is None else count
     centres = np.empty((count, 3))
     lengths = np.empty(count)
@@ -80,7 +81,23 @@ def tube_set(n: int, side: float, seed: int, set_id: int, start: int = 0,
         rng = _rng(seed, set_id, start + i, 29)
         centres[i] = rng.uniform(0.0, side, size=3)
         lengths[i] = rng.uniform(*length_range)
+    return centres, lengths
+
+
+def tube_set(n: int, side: float, seed: int, set_id: int, start: int = 0,
+             count: int | None = None, length_range=(50.0, 800.0)) -> MeshSet:
+    """Tubes with centres uniform in the cube and arc lengths uniform in
+    ``length_range`` (the workload's range by default; tests use shorter
+    tubes to keep the oracle fast)."""
+    centres, lengths = tube_params(n, side, seed, set_id, start, count, length_range)
     return make_tubes(lambda i: _rng(seed, set_id, start + i, 31), centres, lengths)
+
+
+def tube_list(n: int, side: float, seed: int, set_id: int, ids, length_range=(50.0, 800.0)) -> MeshSet:
+    """The tubes ``ids`` of a tube set, generated alone (each from its own
+    stream), in that order."""
+    parts = [tube_set(n, side, seed, set_id, start=int(i), count=1, length_range=length_range) for i in ids]
+    return concat(parts) if parts else tube_set(n, side, seed, set_id, start=0, count=0)
 
 
 @dataclasses.dataclass

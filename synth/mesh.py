@@ -162,6 +162,41 @@ def concat(sets) -> MeshSet:
                    hd=hd, ph=ph, anchor=np.concatenate([x.anchor for x in sets]), kind=sets[0].kind)
 
 
+def subset(ms: MeshSet, ids) -> MeshSet:
+    """The objects ``ids`` of ``ms`` (in that order) as a MeshSet of their own."""
+    ids = np.asarray(ids, np.int64)
+    L = ms.n_lods
+    verts, voff, faces, foff, hd, ph = [], [], [], [], [], []
+    for l in range(L):
+        same = next((m for m in range(l) if ms.verts[m] is ms.verts[l] and ms.vert_off[m] is ms.vert_off[l]), None)
+        if same is not None:
+            verts.append(verts[same])
+            voff.append(voff[same])
+        else:
+            vo = np.asarray(ms.vert_off[l], np.int64)
+            cnt = vo[ids + 1] - vo[ids]
+            verts.append(np.concatenate([ms.verts[l][vo[i]:vo[i + 1]] for i in ids]) if len(ids)
+                         else np.zeros((0, 3), np.float32))
+            voff.append(np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64))
+        if ms.face_off[l] is None:
+            nf = ms.faces[l].shape[0]
+            fo = np.arange(ms.n + 1, dtype=np.int64) * nf
+            faces.append(ms.faces[l])
+            foff.append(None)
+        else:
+            fo = np.asarray(ms.face_off[l], np.int64)
+            cnt = fo[ids + 1] - fo[ids]
+            faces.append(np.concatenate([ms.faces[l][fo[i]:fo[i + 1]] for i in ids]) if len(ids)
+                         else np.zeros((0, 3), np.int32))
+            foff.append(np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64))
+        pick = (lambda a: None if a is None else
+                (np.concatenate([a[fo[i]:fo[i + 1]] for i in ids]) if len(ids) else a[:0]))
+        hd.append(pick(ms.hd[l]))
+        ph.append(pick(ms.ph[l]))
+    return MeshSet(n=len(ids), n_lods=L, verts=verts, vert_off=voff, faces=faces, face_off=foff, hd=hd, ph=ph,
+                   anchor=np.ascontiguousarray(ms.anchor[ids]), kind=ms.kind)
+
+
 # --------------------------------------------------------------------------
 # icosphere with a hierarchical face order (children of face f are 4f..4f+3)
 

@@ -147,3 +147,85 @@ def test_streamed_errors(ctx, data):
     # the context stays usable
     res = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE)
     assert res.n > 0
+
+
+def _pinned(ms):
+    """The chunk's arrays in pinned host memory (page-locked by torch)."""
+    import copy
+    import torch
+    out = copy.copy(ms)
+    cache = {}
+
+    def pin(a):
+        if a is None:
+            return None
+        if id(a) not in cache:
+            cache[id(a)] = torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        return cache[id(a)]
+
+    for f in ("verts", "vert_off", "faces", "face_off", "hd", "ph"):
+        setattr(out, f, [pin(a) for a in getattr(ms, f)])
+    out.anchor = pin(ms.anchor)
+    return out
+
+
+def _on_device(ms):
+    """verts, faces, hd, ph, anchor as CUDA tensors; offsets stay on the host."""
+    import copy
+    import torch
+    out = copy.copy(ms)
+    cache = {}
+
+    def dev(a):
+        if a is None:
+            return None
+        if id(a) not in cache:
+            cache[id(a)] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        return cache[id(a)]
+
+    for f in ("verts", "faces", "hd", "ph"):
+        setattr(out, f, [dev(a) for a in getattr(ms, f)])
+    out.anchor = dev(ms.anchor)
+    return out
+
+
+@pytest.mark.parametrize("where", ["pinned", "device"])
+def test_streamed_pinned_and_device_chunks(ctx, data, where):
+    """Chunks whose arrays already lie in pinned host memory are copied
+    without packing, and device arrays are read in place: the same result
+    as the resident join, and only the host-side arrays travel."""
+    from paper_2604_19982_gb300 import pj
+    R, S, gR, gS = data
+    parts = bounds([700, 900, 800])
+    conv = _pinned if where == "pinned" else _on_device
+    chunks = [conv(chunk_of(*p)) for p in parts]
+    plain_chunks = [chunk_of(*p) for p in parts]
+    g = ctx.load_set_streamed(N_R, 3, lambda c: chunks[c])
+    gp = ctx.load_set_streamed(N_R, 3, lambda c: plain_chunks[c])
+    for prec, fl in ((pj.FP32, pj.TILE_PRUNE), (pj.FP64, 0)):
+        a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=prec, flags=fl)
+        ctx.join(gp, gS, pj.WITHIN, tau=1.0, prec=prec, flags=fl)
+        packed_bytes = ctx.stats()["bytes_h2d"]
+        b = ctx.join(g, gS, pj.WITHIN, tau=1.0, prec=prec, flags=fl)
+        st = ctx.stats()
+        same(a, b)
+        if where == "pinned":
+            assert st["bytes_h2d"] == packed_bytes     # the same bytes, without packing them
+        else:
+            assert st["bytes_h2d"] < packed_bytes / 20     # offsets only
+    g.free()
+    gp.free()
+
+
+def test_streamed_device_offsets_rejected(ctx, data):
+    import copy
+    import torch
+    from paper_2604_19982_gb300 import pj
+    R, S, gR, gS = data
+    m = copy.copy(chunk_of(0, N_R))
+    m.vert_off = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in m.vert_off]
+    g = ctx.load_set_streamed(N_R, 1, lambda c: m)
+    with pytest.raises(pj.PJError) as e:
+        ctx.join(g, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE)
+    assert e.value.status == pj.PJ_EINVAL
+    g.free()
