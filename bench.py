@@ -1,31 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark of the polyhedral spatial-join hot path on GB300.
 
-Workload (one "step"): the 20,000 x 20,000 nuclei-like blob join, 3 LoDs
-(icosphere subdivision 1/2/3 with SH radial noise, centres uniform in a cube
-of side 400), evaluated for intersection (tau = 0) and within tau = 1.0 --
-two full joins through the C ABI per step.  Inputs are device resident when
-the timed region starts (pj_load_set is outside it); the e2e number loads
-both sets from pinned host memory inside its own timed region.
+Headline workload (one "step"): the chunked streaming within-tau join of
+2,000,000 nuclei-like blobs (R, icosphere subdivision 1/2/3 with SH radial
+noise, streamed in 64 chunks of 31,250) against 20,000 vessel-like tubes
+(S, 2k-50k facets, 3 LoDs) in a cube of side 5,000, tau = 1.0, with every
+tuned feature on: single precision with the FP64 re-decide, unit pruning,
+the autotuned LoD schedule, the learned start LoD (fitted on a seed-1
+chunk) and per-chunk graph replay.
 
-Metric: object pairs joined per second = candidate object pairs emitted by
-the MBB filter and resolved exactly (over both predicates), divided by the
-device time of the step; triangle-pair tests per second is reported beside
-it.  The tuned path is single precision with the FP64 re-decide and tile
-pruning; the plain path is FP64 everywhere without pruning.
+* ``value``: the chunk arrays resident in device memory when the timed
+  region starts (read in place by the set-building kernels); candidate
+  object pairs resolved exactly per second.
+* ``e2e``: the same join with the chunk arrays in pinned host memory, copied
+  to the device inside the timed region through the C ABI (no packing),
+  results copied back.
+* sub-records under ``configs``: the resident workloads blobs20k,
+  knn50k and tubes2k, each tuned against the plain FP64 path on the same
+  inputs, so the tuned / plain ratios are measured in the same run.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+       [--workload stream2m|blobs20k|knn50k|tubes2k] [--no-sub]
 """
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -35,37 +41,48 @@ sys.path.insert(0, ROOT)
 
 METRIC = "object-pairs joined/sec & tri-pair tests/sec, tuned vs plain GPU path, exact"
 UNIT = "object-pairs/s"
-WORKLOAD = ("blobs20k: R, S = 20,000 SH-noised icosphere blobs each (LoDs sub 1/2/3 = 80/320/1280 facets), "
-            "cube side 400, intersection (tau=0) + within tau=1.0 per step")
-TAUS = (0.0, 1.0)
+WORKLOADS = {
+    "stream2m": ("stream2m: 2,000,000 SH-noised icosphere blobs (LoDs sub 1/2/3 = 80/320/1280 facets) streamed "
+                 "in 64 chunks of 31,250 against 20,000 tubes (16-segment swept circles, arc length 50-800, "
+                 "2k-50k facets, 3 LoDs), cube side 5,000, within tau = 1.0"),
+    "blobs20k": ("blobs20k: R, S = 20,000 SH-noised icosphere blobs each (LoDs sub 1/2/3), cube side 400, "
+                 "intersection (tau=0) + within tau=1.0 per step"),
+    "knn50k": ("knn50k: R, S = 50,000 sub-3 blobs each, 20-cluster Gaussian mixture (sigma 15) in a cube of "
+               "side 1,000, k = 3; proposal fitted on the seed-1 run"),
+    "tubes2k": "tubes2k: 2,000 tubes (2k-50k facets, 3 LoDs) x 200,000 sub-3 blobs, cube side 2,320, within tau = 2",
+}
+WORKLOAD = WORKLOADS["stream2m"]
+STREAM = dict(n=2_000_000, chunks=64, tubes=20_000, side=5000.0, tau=1.0)
 # FP32 floating-point operations of one triangle-pair test of the refine
-# kernel at full resolution (FMA = 2): 27 differences, 2 x 3 x 22 for the
-# vertex-to-face cases, 9 x 45 for the edge-to-edge cases.
+# kernel (FMA = 2): 27 differences, 2 x 3 x 22 for the vertex-to-face cases,
+# 9 x 45 for the edge-to-edge cases.
 FLOPS_PER_TEST = 564
-# the single-precision refinement kernel the tuned path runs (scalar variant:
-# facet-ball culling, TMA-staged unit pipeline, unit masks at full
-# resolution, units dealt across SMs); the traffic counters in profiles/ name it
+# the single-precision refinement kernel the tuned path runs; the traffic
+# counters in profiles/ name it
 REFINE_KERNEL_ID = "k_refine<float>+staged+masks+dealt"
+RESULT_BYTES_PER_PAIR = 4 + 4 + 8 + 8 + 8 + 1
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=20_000, help="objects per set (default: the full workload)")
-    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-path measurement")
+    ap.add_argument("--workload", default="stream2m", choices=list(WORKLOADS),
+                    help="the headline line's workload (default: stream2m, the largest)")
+    ap.add_argument("--stream-chunks", type=int, default=STREAM["chunks"],
+                    help="stream2m: chunks of 31,250 blobs streamed (64 = the full 2,000,000)")
+    ap.add_argument("--n", type=int, default=0, help="blobs20k: objects per set (0 = 20,000)")
+    ap.add_argument("--no-sub", action="store_true", help="skip the per-config sub-records")
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-path measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="blobs20k", choices=["blobs20k", "knn50k", "tubes2k", "stream"],
-                    help="blobs20k (default) is the benchmark line; the others measure the k-NN, "
-                         "tubes-vs-blobs and streamed workloads for the profiles")
-    ap.add_argument("--stream-chunks", type=int, default=8,
-                    help="stream workload: chunks of 31,250 blobs streamed against 20,000 tubes (64 = full size)")
-    ap.add_argument("--options", default=None,
-                    help="context options as a JSON object (e.g. '{\"refine_split\": 1}'), default: none")
-    return ap.parse_args()
+    ap.add_argument("--sample-pairs", type=int, default=8,
+                    help="cpu_baseline: candidate blob-tube pairs of the oracle sample (about 1.5 core-minutes "
+                         "each); the reference arm's steps take half as many")
+    ap.add_argument("--options", default=None, help="context options as a JSON object")
+    return ap.parse_args(argv)
 
 
 def alu_peak(nsm: int, mhz: float = 2070.0) -> float:
@@ -125,38 +142,38 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-# ----------------------------------------------------------------- helpers
+# ----------------------------------------------------------------- arrays
 
-def pinned_copy(ms):
-    """The mesh set's arrays copied into pinned host memory (for e2e)."""
-    import torch
-
-    def pin(a):
-        if a is None:
-            return None
-        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        return t.numpy()
-
-    import copy
+def _map_arrays(ms, fn, fields=("verts", "vert_off", "faces", "face_off", "hd", "ph")):
+    """A shallow copy of a mesh set with fn applied to its arrays (shared
+    arrays stay shared)."""
     out = copy.copy(ms)
     cache = {}
 
-    def pin_cached(a):
+    def f(a):
         if a is None:
             return None
-        k = id(a)
-        if k not in cache:
-            cache[k] = pin(a)
-        return cache[k]
+        if id(a) not in cache:
+            cache[id(a)] = fn(a)
+        return cache[id(a)]
 
-    out.verts = [pin_cached(v) for v in ms.verts]
-    out.vert_off = [pin_cached(v) for v in ms.vert_off]
-    out.faces = [pin_cached(v) for v in ms.faces]
-    out.face_off = [pin_cached(v) for v in ms.face_off]
-    out.hd = [pin_cached(v) for v in ms.hd]
-    out.ph = [pin_cached(v) for v in ms.ph]
-    out.anchor = pin(ms.anchor)
+    for name in fields:
+        setattr(out, name, [f(a) for a in getattr(ms, name)])
+    out.anchor = f(ms.anchor)
     return out
+
+
+def pinned_copy(ms):
+    """The mesh set's arrays copied into pinned host memory."""
+    import torch
+    return _map_arrays(ms, lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy())
+
+
+def device_copy(ms):
+    """verts, faces, hd, ph, anchor as CUDA tensors (offsets stay host arrays)."""
+    import torch
+    return _map_arrays(ms, lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda(),
+                       fields=("verts", "faces", "hd", "ph"))
 
 
 def h2d_bytes(ms) -> int:
@@ -170,8 +187,7 @@ def h2d_bytes(ms) -> int:
     return tot
 
 
-RESULT_BYTES_PER_PAIR = 4 + 4 + 8 + 8 + 8 + 1
-
+# ----------------------------------------------------------------- ranks
 
 def dist_init(backend: str | None = None):
     """Process group of a multi-rank run (one replica of the join per rank,
@@ -213,237 +229,472 @@ def sum_over_ranks(x: float, world: int) -> float:
     return _reduce(x, world, "SUM")
 
 
+# ----------------------------------------------------------------- generation
+# every input is drawn in spawned processes before the first CUDA call
+
+def _gen(task):
+    from synth import configs
+    kind = task[0]
+    if kind == "chunk":
+        _, c, seed, chunks = task
+        return configs.stream2m_R_chunk(c, seed=seed, n=STREAM["n"], chunks=chunks, side=STREAM["side"])
+    if kind == "tubes":
+        _, n, side, seed, set_id, start, count = task
+        return configs.tube_set(n, side, seed, set_id, start=start, count=count)
+    if kind == "blobs":
+        _, n, side, seed, set_id, start, count, gmm = task
+        g = configs.gmm_centres(seed, 20, side) if gmm else None
+        return configs.blob_set(n, side, seed, set_id, start=start, count=count, gmm=g)
+    raise ValueError(kind)
+
+
+def _parts(kind, n, side, seed, set_id, pieces, gmm=False):
+    step = max(1, (n + pieces - 1) // pieces)
+    out = []
+    for a in range(0, n, step):
+        c = min(step, n - a)
+        out.append(("tubes", n, side, seed, set_id, a, c) if kind == "tubes" else
+                   ("blobs", n, side, seed, set_id, a, c, gmm))
+    return out
+
+
+def generate(args, seed: int):
+    """Every input of this run: name -> MeshSet (or list of chunks)."""
+    import multiprocessing as mp
+    from synth.mesh import concat
+    procs = max(1, min(16, os.cpu_count() or 1))
+    plan = {}
+    if args.impl == "ours":
+        w = args.workload
+        if w == "stream2m":
+            plan["stream_S"] = _parts("tubes", STREAM["tubes"], STREAM["side"], seed, 1, 4 * procs)
+            plan["chunks"] = [("chunk", c, seed, STREAM["chunks"]) for c in range(args.stream_chunks)]
+            plan["chunk_seed1"] = [("chunk", 0, seed + 1, STREAM["chunks"])]
+        subs = [] if args.no_sub else [x for x in ("blobs20k", "knn50k", "tubes2k") if x != w]
+        for name in ([w] if w != "stream2m" else []) + subs:
+            if name == "blobs20k":
+                n = args.n or 20_000
+                side = 400.0 * (n / 20_000) ** (1 / 3)
+                plan["b20_R"] = _parts("blobs", n, side, seed, 0, procs)
+                plan["b20_S"] = _parts("blobs", n, side, seed, 1, procs)
+            elif name == "knn50k":
+                for s, tag in ((seed, ""), (seed + 1, "1")):
+                    plan["knn_R" + tag] = _parts("blobs", 50_000, 1000.0, s, 0, procs, gmm=True)
+                    plan["knn_S" + tag] = _parts("blobs", 50_000, 1000.0, s, 1, procs, gmm=True)
+            elif name == "tubes2k":
+                plan["t2_R"] = _parts("tubes", 2000, 2320.0, seed, 0, 2 * procs)
+                plan["t2_S"] = _parts("blobs", 200_000, 2320.0, seed, 1, 2 * procs)
+    tasks = [t for v in plan.values() for t in v]
+    if not tasks:
+        return {}
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_gen, tasks, chunksize=1)
+    out, i = {}, 0
+    for k, v in plan.items():
+        part = res[i:i + len(v)]
+        i += len(v)
+        out[k] = part if k == "chunks" else (part[0] if len(part) == 1 else concat(part))
+    return out
+
+
 # ----------------------------------------------------------------- oracle sample
 
-def oracle_sample(w, target_pairs: int, seed: int = 0):
-    """Objects r of R (chosen from the MBBs alone, independently of the GPU
-    path) whose candidate pairs add up to about ``target_pairs`` per tau."""
-    mR, mS = w.R.mbb().astype(np.float64), w.S.mbb().astype(np.float64)
+def _mindist(lo, hi, blo, bhi):
+    gap = np.maximum(0, np.maximum(blo - hi, lo - bhi))
+    return np.sqrt((gap ** 2).sum(-1))
+
+
+def stream_oracle_sample(target_pairs: int, seed: int = 0):
+    """Blobs of the streamed R (from its first chunk) with every tube of S
+    within tau of their boxes, chosen from the boxes alone (tubes are
+    screened by the box their centre and length bound, then generated
+    alone): (R sample, S sample, candidate pairs, description)."""
+    from synth import configs
+    from synth.mesh import subset
+    tau = STREAM["tau"]
+    per = STREAM["n"] // STREAM["chunks"]
+    c, L = configs.tube_params(STREAM["tubes"], STREAM["side"], seed, 1)
+    tlo, thi = c - (L[:, None] / 2 + 2.01), c + (L[:, None] / 2 + 2.01)
     rng = np.random.default_rng(seed)
-    order = rng.permutation(w.R.n)
-    chosen, cand = [], {t: 0 for t in TAUS}
-    for r in order:
-        gap = np.maximum(0, np.maximum(mS[:, :3] - mR[r, 3:], mR[r, :3] - mS[:, 3:]))
-        md = np.sqrt((gap ** 2).sum(1))
-        c1 = int((md <= TAUS[-1]).sum())
-        if c1 == 0:
+    blobs = configs.blob_set(STREAM["n"], STREAM["side"], seed, 0, start=0, count=min(per, 4096))
+    mb = blobs.mbb().astype(np.float64)
+    chosen, tubes, pairs = [], {}, 0
+    for r in rng.permutation(blobs.n):
+        near = np.nonzero(_mindist(mb[r, :3], mb[r, 3:], tlo, thi) <= tau)[0]
+        if len(near) == 0:
+            continue
+        T = configs.tube_list(STREAM["tubes"], STREAM["side"], seed, 1, near)
+        tm = T.mbb().astype(np.float64)
+        hit = near[_mindist(mb[r, :3], mb[r, 3:], tm[:, :3], tm[:, 3:]) <= tau]
+        if len(hit) == 0:
             continue
         chosen.append(int(r))
-        for t in TAUS:
-            cand[t] += int((md <= t).sum())
-        if cand[TAUS[-1]] >= target_pairs:
+        for t in hit:
+            tubes[int(t)] = True
+        pairs += len(hit)
+        if pairs >= target_pairs:
             break
-    return np.array(sorted(chosen), np.int64), cand
+    ids = sorted(tubes)
+    Rs = subset(blobs, np.array(sorted(chosen)))
+    Ss = configs.tube_list(STREAM["tubes"], STREAM["side"], seed, 1, ids)
+    desc = (f"{len(chosen)} blobs of the first chunk with all {pairs} candidate tubes (within tau = 1, "
+            f"{len(ids)} tubes), full-resolution facet pairs in FP64")
+    return Rs, Ss, pairs, desc
 
 
-def run_oracle_step(w, rl, soups, threads):
+def time_oracle(Rs, Ss, tau, steps, warmup):
     import oracle
-    for t in TAUS:
-        oracle.join_within(w.R, w.S, t, rlist=rl, threads=threads, soups=soups)
+    soups = (oracle.soup(Rs), oracle.soup(Ss))
+    threads = oracle.default_threads()
+    for _ in range(warmup):
+        oracle.join_within(Rs, Ss, tau, threads=threads, soups=soups)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.join_within(Rs, Ss, tau, threads=threads, soups=soups)
+    return (time.perf_counter() - t0) / steps, threads
 
 
-# ----------------------------------------------------------------- arms
+# ----------------------------------------------------------------- reference arm
 
 def reference_arm(args):
-    """The CPU oracle as it stands, on a bounded sample of the workload."""
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """The CPU oracle as it stands, on a bounded sample of the headline
+    workload, on the host cores; only rank 0 works."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-    from synth import configs
-    w = configs.blobs20k(n=args.n)
-    rl, cand = oracle_sample(w, 24)
-    soups = (oracle.soup(w.R), oracle.soup(w.S))
-    threads = oracle.default_threads()
-    pairs = sum(cand.values())
-    for _ in range(args.warmup):
-        run_oracle_step(w, rl, soups, threads)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        run_oracle_step(w, rl, soups, threads)
-    dt = time.perf_counter() - t0
-    v = pairs * args.steps / dt
-    sample = f"{len(rl)} objects r of R with all their MBB candidates ({pairs} pairs over tau=0 and tau=1)"
+    Rs, Ss, pairs, sample = stream_oracle_sample(max(1, args.sample_pairs // 2))
+    dt, threads = time_oracle(Rs, Ss, STREAM["tau"], max(1, args.steps), args.warmup)
+    v = pairs / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def ours_arm(args):
+# ----------------------------------------------------------------- GPU helpers
+
+def _traffic():
+    prof = os.path.join(ROOT, "profiles", "refine_fp32_traffic.json")
+    try:
+        tr = json.load(open(prof))
+        # counters of another kernel (or an older build of it) do not apply
+        return tr.get("bytes_per_launch") if tr.get("kernel_id") == REFINE_KERNEL_ID else None
+    except (OSError, ValueError):
+        return None
+
+
+def roofline(stats_list, nsm, measured32):
+    tests = sum(s["tests_fp32"] for s in stats_list)
+    kms = sum(s["refine_ms_fp32"] for s in stats_list)
+    peak = alu_peak(nsm)
+    ach = tests * FLOPS_PER_TEST / (kms / 1000.0) / 1e12 if kms > 0 else 0.0
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": _traffic(),
+            "kernel": "k_refine<float> (single-precision refinement, facet-ball culling; full-resolution steps "
+                      "include their k_unit_masks pre-pass in the timed window)",
+            "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x 2.070 GHz",
+            "measured_fma_peak": measured32, "frac_of_measured": ach / measured32 if measured32 else None,
+            "flops_per_test": FLOPS_PER_TEST, "kernel_ms": kms, "tests": tests,
+            "kernel_timing": "CUDA events around each refinement launch on its stream, direct (non-graph) steps"}
+
+
+def timed(ctx, stream, fn, steps):
+    """Run fn() steps times between CUDA events on stream (synchronized on
+    both sides); returns (ms, [stats])."""
     import torch
-    from paper_2604_19982_gb300 import pj
-    from synth import configs
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+        out.append(ctx.stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
 
-    world, rank, local = dist_init()
-    torch.cuda.set_device(local)
-    w = configs.blobs20k(seed=rank, n=args.n)        # weak scaling: one independent batch per rank
-    # the scalar single-precision kernel throughout (the autotuner then picks
-    # the LoD schedule only), so that one kernel carries the roofline
-    opts = {"refine_variant": 1}
-    opts.update(json.loads(args.options) if args.options else {})
-    ctx = pj.Context(local, opts)
-    gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
-    stream = torch.cuda.Stream()
-    # tuned path: single precision with FP64 re-decide, unit pruning, the LoD
-    # schedule autotuned per predicate (during the warm-up steps), and the
-    # post-filter sequence replayed from a captured CUDA graph
-    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE | pj.USE_GRAPH)
-    direct = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
 
-    def step(mode, collect=None):
-        pairs = 0
-        for t in TAUS:
-            res = ctx.join(gR, gS, pj.WITHIN, tau=t, stream=stream.cuda_stream, **mode)
-            st = ctx.stats()
-            pairs += st["candidates"]
-            if collect is not None:
-                collect.append((st, res.n))
-        return pairs
+def host_timed(fn, steps):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = [fn() for _ in range(steps)]
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1000.0, out
+
+
+# ----------------------------------------------------------------- headline: stream2m
+
+def stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32):
+    import torch
+    S = data["stream_S"]
+    chunks = data["chunks"]
+    n_total = sum(c.n for c in chunks)
+    gS = ctx.load_set(S)
+    # learned start LoD: fitted on a seed-1 chunk against S
+    g1 = ctx.load_set(data["chunk_seed1"])
+    rmse = ctx.mlp_fit(g1, gS, pj.WITHIN, tau=STREAM["tau"], max_pairs=200_000, epochs=30, seed=1)
+    g1.free()
+    dev_chunks = [device_copy(c) for c in chunks]
+    gR = ctx.load_set_streamed(n_total, len(chunks), lambda c: dev_chunks[c])
+    tau = STREAM["tau"]
+    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE | pj.USE_MLP | pj.USE_GRAPH)
+    direct = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE | pj.USE_MLP)
+
+    def join(R, mode):
+        return ctx.join(R, gS, pj.WITHIN, tau=tau, stream=stream.cuda_stream, **mode)
 
     for _ in range(max(3, args.warmup)):
-        pairs_per_step = step(tuned)
-    clocks = ClockSampler(local)
+        join(gR, tuned)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
     barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(tuned, stats)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, stats = timed(ctx, stream, lambda: join(gR, tuned), args.steps)
     barrier(world)
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     ms = max_over_ranks(ms, world)
-    total_pairs = sum_over_ranks(pairs_per_step * args.steps, world)
-    value = total_pairs / (ms / 1000.0)
-    tests = sum(s["tests_fp32"] + s["tests_fp64"] for s, _ in stats)
-    launches = int(sum(s["launches"] for s, _ in stats))
-    results = sum(n for _, n in stats) // max(1, args.steps)
-    # kernel times: a replayed graph has no per-kernel events, so the same
-    # steps run once more as direct launches (identical work) for the roofline
-    kstats = []
-    for _ in range(2):
-        step(direct, kstats)
-    torch.cuda.synchronize()
-    ksteps = 2
-    tests_fp32 = sum(s["tests_fp32"] for s, _ in kstats)
-    kms_fp32 = sum(s["refine_ms_fp32"] for s, _ in kstats)
-
-    # roofline of the dominant kernel: the single-precision refine kernel
-    # against the ALU peak derived from unit counts and the maximum clock
-    measured32 = ctx.fma_peak(False) / 1000.0      # FMA-chain micro-benchmark, TFLOP/s
-    nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    peak32 = alu_peak(nsm)
-    achieved = tests_fp32 * FLOPS_PER_TEST / (kms_fp32 / 1000.0) / 1e12 if kms_fp32 > 0 else 0.0
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "refine_fp32_traffic.json")
-    if os.path.exists(prof):
-        try:
-            tr = json.load(open(prof))
-            # counters of another kernel (or an older build of it) do not apply
-            if tr.get("kernel_id") == REFINE_KERNEL_ID:
-                traffic = tr.get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                "frac": achieved / peak32 if peak32 else None, "traffic": traffic,
-                "kernel": "k_refine<float> (single-precision refinement, facet-ball culling; full-resolution "
-                          "steps include their k_unit_masks pre-pass in the timed window)",
-                "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x 2.070 GHz",
-                "measured_fma_peak": measured32, "frac_of_measured": achieved / measured32 if measured32 else None,
-                "flops_per_test": FLOPS_PER_TEST,
-                "kernel_ms_per_step": kms_fp32 / ksteps, "tests_per_step": tests_fp32 // ksteps,
-                "culled_tests_per_step": sum(s.get("tests_culled", 0) for s, _ in kstats) // ksteps,
-                "kernel_timing": "CUDA events around each refinement launch, 2 direct (non-graph) steps"}
-
-    plain = None
-    if not args.no_plain:
-        step(dict(prec=pj.FP64, flags=0))
-        torch.cuda.synchronize()
-        p_stats = []
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        pp = step(dict(prec=pj.FP64, flags=0), p_stats)
-        p1.record(stream)
-        torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1)
-        ptests = sum(s["tests_fp64"] for s, _ in p_stats)
-        pkms = sum(s["refine_ms_fp64"] for s, _ in p_stats)
-        peak64 = ctx.fma_peak(True) / 1000.0
-        ach64 = ptests * FLOPS_PER_TEST / (pkms / 1000.0) / 1e12 if pkms > 0 else 0.0
-        plain = {"value": pp / (pms / 1000.0), "ms_per_step": pms, "tri_tests_per_s": ptests / (pms / 1000.0),
-                 "dtype": "f64", "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
-                                              "frac": ach64 / peak64 if peak64 else None}}
+    pairs = sum(s["candidates"] for s in stats)
+    value = sum_over_ranks(pairs, world) / (ms / 1000.0)
+    tests = sum(s["tests_fp32"] + s["tests_fp64"] for s in stats)
+    launches = int(sum(s["launches"] for s in stats))
+    _, kst = timed(ctx, stream, lambda: join(gR, direct), 1)
+    roof = roofline(kst, nsm, measured32)
+    last = stats[-1]
+    config = {"workload": WORKLOAD, "objects_R": n_total, "chunks": len(chunks), "objects_S": S.n,
+              "precision": "fp32 + fp64 re-decide",
+              "flags": "TILE_PRUNE | AUTOTUNE | USE_MLP | USE_GRAPH", "candidate_pairs_per_step": pairs // args.steps,
+              "results_per_step": last["results"], "proposal_rmse_log1p": rmse,
+              "inputs": "chunk arrays resident in device memory (read in place), S resident; "
+                        f"{h2d_bytes(chunks[0]) * len(chunks) / 1e9:.1f} GB of raw chunk arrays, larger than L2",
+              "l2": "inputs larger than L2 (129 MB): every step reads all chunks"}
+    gR.free()
+    gR._cb = gR._keep = None
+    dev_chunks.clear()
+    torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
-        Rp, Sp = pinned_copy(w.R), pinned_copy(w.S)
-        bi = h2d_bytes(Rp) + h2d_bytes(Sp)
+        pin_chunks = [pinned_copy(c) for c in chunks]
+        gRp = ctx.load_set_streamed(n_total, len(pin_chunks), lambda c: pin_chunks[c])
+        join(gRp, tuned)
+        ke = max(1, min(args.steps, 3))
 
         def e2e_step():
-            a, b = ctx.load_set(Rp), ctx.load_set(Sp)
-            n = 0
-            pairs = 0
-            for t in TAUS:
-                res = ctx.join(a, b, pj.WITHIN, tau=t, **direct)   # fresh sets: nothing to replay
-                n += res.n
-                pairs += ctx.stats()["candidates"]
-            a.free()
-            b.free()
-            return pairs, n
+            res = join(gRp, tuned)
+            st = ctx.stats()
+            return st["candidates"], res.n, st["bytes_h2d"], st.get("h2d_gbs", 0.0)
 
-        e2e_step()
-        torch.cuda.synchronize()
-        ke = max(1, min(args.steps, 3))
-        t0 = time.perf_counter()
-        tot_pairs, tot_n = 0, 0
-        for _ in range(ke):
-            p, n = e2e_step()
-            tot_pairs += p
-            tot_n += n
-        torch.cuda.synchronize()
-        et = time.perf_counter() - t0
-        et = max_over_ranks(et, world)
-        e2e = {"value": sum_over_ranks(tot_pairs, world) / et, "unit": UNIT, "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": int(tot_n / ke * RESULT_BYTES_PER_PAIR),
-               "how": "pj_load_set of R and S from pinned host memory + two pj_join (TILE_PRUNE | AUTOTUNE, "
-                      "no graph: the sets are new every step) + result copy, host clock"}
+        ems, outs = host_timed(e2e_step, ke)
+        ems = max_over_ranks(ems, world)
+        e2e = {"value": sum_over_ranks(sum(o[0] for o in outs), world) / (ems / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(o[2] for o in outs) / ke),
+               "d2h_bytes_per_step": int(sum(o[1] for o in outs) / ke * RESULT_BYTES_PER_PAIR),
+               "ms_per_step": ems / ke, "h2d_gbs_during_join": statistics.median(o[3] for o in outs),
+               "how": "pj_join of the streamed R with every chunk array in pinned host memory (copied by the "
+                      "library's copy stream without packing, overlapped with the previous chunk's join) + "
+                      "result copy, host clock"}
+        gRp.free()
+        gRp._cb = gRp._keep = None
+        pin_chunks.clear()
 
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        import oracle
-        rl, cand = oracle_sample(w, 24)
-        soups = (oracle.soup(w.R), oracle.soup(w.S))
-        threads = oracle.default_threads()
-        t0 = time.perf_counter()
-        run_oracle_step(w, rl, soups, threads)
-        dt = time.perf_counter() - t0
-        cpu = {"value": sum(cand.values()) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{len(rl)} objects r with all their MBB candidates ({sum(cand.values())} pairs, "
-                         f"tau=0 and tau=1), {dt:.1f} s"}
+    plain = None
+    if not args.no_plain:
+        from synth.mesh import subset
+        part = subset(chunks[0], np.arange(min(4096, chunks[0].n)))
+        gP = ctx.load_set(part)
+        join(gP, direct)
+        pms, pst = host_timed(lambda: (join(gP, dict(prec=pj.FP64, flags=0)), ctx.stats())[1], 1)
+        tms, tst = host_timed(lambda: (join(gP, direct), ctx.stats())[1], 3)
+        tms /= 3
+        plain = {"inputs": f"the first {part.n} blobs of chunk 0 against all of S",
+                 "value": pst[0]["candidates"] / (pms / 1000.0), "ms": pms, "dtype": "f64",
+                 "tri_tests_per_s": (pst[0]["tests_fp64"] + pst[0]["tests_fp32"]) / (pms / 1000.0),
+                 "tuned_same_inputs": {"value": tst[0]["candidates"] / (tms / 1000.0), "ms": tms},
+                 "speedup": (tst[0]["candidates"] / tms) / (pst[0]["candidates"] / pms)}
+        gP.free()
+    gS.free()
+    return {"value": value, "ms": ms, "tests": tests, "launches": launches, "roofline": roof, "config": config,
+            "e2e": e2e, "plain": plain, "clocks": clk, "last_stats": {k: v for k, v in last.items() if k != "steps"}}
 
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+
+# ----------------------------------------------------------------- resident workloads
+
+def blobs20k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
+    R, S = data["b20_R"], data["b20_S"]
+    gR, gS = ctx.load_set(R), ctx.load_set(S)
+    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE | pj.USE_GRAPH)
+    direct = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
+
+    def cands(sts):
+        return sum(s["candidates"] for s in sts)
+
+    for _ in range(3):
+        _two(ctx, gR, gS, pj, stream, tuned)
+    sts = []
+    ms, _ = timed(ctx, stream, lambda: sts.extend(_two(ctx, gR, gS, pj, stream, tuned)), steps)
+    kst = []
+    timed(ctx, stream, lambda: kst.extend(_two(ctx, gR, gS, pj, stream, direct)), 2)
+    rec = {"workload": WORKLOADS["blobs20k"], "value": cands(sts) / (ms / 1000.0), "ms_per_step": ms / steps,
+           "tri_tests_per_s": sum(s["tests_fp32"] + s["tests_fp64"] for s in sts) / (ms / 1000.0),
+           "flags": "TILE_PRUNE | AUTOTUNE | USE_GRAPH", "roofline": roofline(kst, nsm, measured32)}
+    if not args.no_plain:
+        pst = []
+        pms, _ = timed(ctx, stream, lambda: pst.extend(_two(ctx, gR, gS, pj, stream, dict(prec=pj.FP64, flags=0))),
+                       1)
+        rec["plain"] = {"value": cands(pst) / (pms / 1000.0), "ms_per_step": pms, "dtype": "f64",
+                        "inputs": "the same sets"}
+        rec["speedup_vs_plain"] = rec["value"] / rec["plain"]["value"]
+    gR.free()
+    gS.free()
+    return rec
+
+
+def _two(ctx, gR, gS, pj, stream, mode):
+    out = []
+    for t in (0.0, 1.0):
+        ctx.join(gR, gS, pj.WITHIN, tau=t, stream=stream.cuda_stream, **mode)
+        out.append(ctx.stats())
+    return out
+
+
+def knn50k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
+    from synth.mesh import subset
+    a, b = ctx.load_set(data["knn_R1"]), ctx.load_set(data["knn_S1"])
+    rmse = ctx.mlp_fit(a, b, pj.KNN, k=3, max_pairs=200_000, epochs=30, seed=1)
+    a.free()
+    b.free()
+    R, S = data["knn_R"], data["knn_S"]
+    gR, gS = ctx.load_set(R), ctx.load_set(S)
+    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.USE_MLP)
+
+    def run(Rset, mode):
+        ctx.join(Rset, gS, pj.KNN, k=3, stream=stream.cuda_stream, **mode)
+
+    run(gR, tuned)
+    ms, sts = timed(ctx, stream, lambda: run(gR, tuned), steps)
+    rec = {"workload": WORKLOADS["knn50k"], "value": sum(s["candidates"] for s in sts) / (ms / 1000.0),
+           "ms_per_step": ms / steps,
+           "tri_tests_per_s": sum(s["tests_fp32"] + s["tests_fp64"] for s in sts) / (ms / 1000.0),
+           "flags": "TILE_PRUNE | USE_MLP", "proposal_rmse_log1p": rmse, "roofline": roofline(sts, nsm, measured32)}
+    _, nst = timed(ctx, stream, lambda: run(gR, dict(prec=pj.FP32, flags=pj.TILE_PRUNE)), 1)
+    rec["without_proposal"] = {"tests": nst[0]["tests_fp32"] + nst[0]["tests_fp64"],
+                               "with_proposal_tests": sts[-1]["tests_fp32"] + sts[-1]["tests_fp64"]}
+    if not args.no_plain:
+        gP = ctx.load_set(subset(R, np.arange(2000)))
+        pms, pst = host_timed(lambda: (run(gP, dict(prec=pj.FP64, flags=0)), ctx.stats())[1], 1)
+        run(gP, tuned)
+        tms, tst = host_timed(lambda: (run(gP, tuned), ctx.stats())[1], 3)
+        tms /= 3
+        rec["plain"] = {"inputs": "the first 2,000 objects of R against all of S (the full plain join is minutes "
+                                  "of FP64 work)", "value": pst[0]["candidates"] / (pms / 1000.0), "ms": pms,
+                        "dtype": "f64", "tuned_same_inputs": {"value": tst[0]["candidates"] / (tms / 1000.0),
+                                                              "ms": tms}}
+        rec["speedup_vs_plain"] = (tst[0]["candidates"] / tms) / (pst[0]["candidates"] / pms)
+        gP.free()
+    gR.free()
+    gS.free()
+    return rec
+
+
+def tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
+    from synth.mesh import subset
+    R, S = data["t2_R"], data["t2_S"]
+    gR, gS = ctx.load_set(R), ctx.load_set(S)
+    tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE | pj.USE_GRAPH)
+    direct = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
+
+    def run(Rset, mode):
+        ctx.join(Rset, gS, pj.WITHIN, tau=2.0, stream=stream.cuda_stream, **mode)
+
+    for _ in range(3):
+        run(gR, tuned)
+    ms, sts = timed(ctx, stream, lambda: run(gR, tuned), steps)
+    _, kst = timed(ctx, stream, lambda: run(gR, direct), 1)
+    rec = {"workload": WORKLOADS["tubes2k"], "value": sum(s["candidates"] for s in sts) / (ms / 1000.0),
+           "ms_per_step": ms / steps,
+           "tri_tests_per_s": sum(s["tests_fp32"] + s["tests_fp64"] for s in sts) / (ms / 1000.0),
+           "flags": "TILE_PRUNE | AUTOTUNE | USE_GRAPH", "roofline": roofline(kst, nsm, measured32)}
+    if not args.no_plain:
+        gP = ctx.load_set(subset(R, np.arange(100)))
+        pms, pst = host_timed(lambda: (run(gP, dict(prec=pj.FP64, flags=0)), ctx.stats())[1], 1)
+        run(gP, direct)
+        tms, tst = host_timed(lambda: (run(gP, direct), ctx.stats())[1], 3)
+        tms /= 3
+        rec["plain"] = {"inputs": "the first 100 tubes of R against all of S (the full plain join is many "
+                                  "minutes of FP64 work)", "value": pst[0]["candidates"] / (pms / 1000.0),
+                        "ms": pms, "dtype": "f64",
+                        "tuned_same_inputs": {"value": tst[0]["candidates"] / (tms / 1000.0), "ms": tms}}
+        rec["speedup_vs_plain"] = (tst[0]["candidates"] / tms) / (pst[0]["candidates"] / pms)
+        gP.free()
+    gR.free()
+    gS.free()
+    return rec
+
+
+SUB_RECORDS = {"blobs20k": blobs20k_record, "knn50k": knn50k_record, "tubes2k": tubes2k_record}
+
+
+# ----------------------------------------------------------------- our arm
+
+def ours_arm(args):
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+    data = generate(args, seed=rank)        # weak scaling: one independent batch per rank
+    cpu_sample = None
+    if world == 1 and not args.no_cpu and args.workload == "stream2m":
+        cpu_sample = stream_oracle_sample(max(1, args.sample_pairs))
+    import torch
+    from paper_2604_19982_gb300 import pj
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    opts = {"refine_variant": 1}
+    opts.update(json.loads(args.options) if args.options else {})
+    ctx = pj.Context(local, opts)
+    stream = torch.cuda.Stream()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    measured32 = ctx.fma_peak(False) / 1000.0
+
+    if args.workload == "stream2m":
+        h = stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32)
+        for k in ("stream_S", "chunks", "chunk_seed1"):
+            data.pop(k, None)
+        line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": h["ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_per_set": args.n, "precision": "fp32 + fp64 re-decide",
-                           "flags": "TILE_PRUNE | AUTOTUNE | USE_GRAPH", "candidate_pairs_per_step": pairs_per_step,
-                           "schedule": {str(t): s.get("autotune", {}).get("start") for (s, _), t in
-                                        zip(stats[:len(TAUS)], TAUS)},
-                           "results_per_step": results,
-                           "l2": "inputs larger than L2: 3.2 GB of facets resident, ~0.2 GB touched per step"},
-                "tri_tests_per_s": tests / (ms / 1000.0),
-                "plain": plain, "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk}
+                "config": h["config"], "tri_tests_per_s": h["tests"] / (h["ms"] / 1000.0),
+                "plain": h["plain"], "speedup_vs_plain": h["plain"]["speedup"] if h["plain"] else None,
+                "roofline": h["roofline"], "e2e": h["e2e"], "gpu_launches": h["launches"], "clocks": h["clocks"],
+                "last_step_stats": h["last_stats"]}
+    else:
+        fn = SUB_RECORDS[args.workload]
+        clocks = ClockSampler(local)
+        clocks.start()
+        rec = fn(args, data, ctx, pj, stream, nsm, measured32, args.steps)
+        clk = clocks.stop()
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": rec["workload"], "flags": rec["flags"]},
+                "tri_tests_per_s": rec["tri_tests_per_s"], "plain": rec.get("plain"),
+                "speedup_vs_plain": rec.get("speedup_vs_plain"), "roofline": rec["roofline"], "e2e": None,
+                "gpu_launches": None, "clocks": clk}
+    if not args.no_sub:
+        subs = {}
+        for name, fn in SUB_RECORDS.items():
+            if name == args.workload:
+                continue
+            subs[name] = fn(args, data, ctx, pj, stream, nsm, measured32, max(1, min(args.steps, 5)))
+        line["configs"] = subs
+    if cpu_sample is not None:
+        Rs, Ss, pairs, sample = cpu_sample
+        dt, threads = time_oracle(Rs, Ss, STREAM["tau"], 1, 0)
+        line["cpu_baseline"] = {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": sample + f", {dt:.1f} s"}
+    if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -451,144 +702,10 @@ def ours_arm(args):
         dist.destroy_process_group()
 
 
-def extra_arm(args):
-    """k-NN, tubes-vs-blobs and streamed workloads (one GPU): tuned path, the
-    plain FP64 path on the same inputs (tubes: on a 100-tube subset, the full
-    plain join being hours of FP64 work), refine-kernel roofline."""
-    from synth import configs
-    if args.workload == "stream":
-        # host-side generation in spawned processes, before any CUDA call
-        procs = max(1, min(16, os.cpu_count() or 1))
-        S_stream = configs.tube_set_parallel(20000, 5000.0, 0, 1, procs=procs)
-        chunks = configs.stream_chunks_parallel(range(args.stream_chunks), procs=procs)
-    import torch
-    from paper_2604_19982_gb300 import pj
-
-    torch.cuda.set_device(0)
-    opts = {"refine_variant": 1}
-    opts.update(json.loads(args.options) if args.options else {})
-    ctx = pj.Context(0, opts)
-    stream = torch.cuda.Stream()
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    extra = {}
-    if args.workload == "knn50k":
-        desc = ("knn50k: R, S = 50,000 sub-3 blobs each, 20-cluster Gaussian mixture (sigma 15) in a cube of "
-                "side 1000, k = 3; proposal fitted on the seed-1 run")
-        w1 = configs.knn50k(seed=1)
-        a, b = ctx.load_set(w1.R), ctx.load_set(w1.S)
-        extra["proposal_rmse_log1p"] = ctx.mlp_fit(a, b, pj.KNN, k=3, max_pairs=200000, epochs=30, seed=1)
-        a.free()
-        b.free()
-        w = configs.knn50k()
-        gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
-        q = dict(pred=pj.KNN, k=3)
-        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.USE_MLP)
-        untrained = dict(prec=pj.FP32, flags=pj.TILE_PRUNE)
-        plain = dict(prec=pj.FP64, flags=0)
-        gP = gR
-    elif args.workload == "tubes2k":
-        desc = "tubes2k: 2,000 tubes (2k-50k facets) x 200,000 sub-3 blobs, side 2,320, within tau = 2"
-        w = configs.tubes2k()
-        gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
-        q = dict(pred=pj.WITHIN, tau=2.0)
-        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
-        untrained = None
-        plain = dict(prec=pj.FP64, flags=0)
-        gP = ctx.load_set(configs.tube_set(2000, 2320.0, 0, 0, start=0, count=100))
-        extra["plain_inputs"] = "the first 100 tubes of R against all of S"
-    else:
-        n_ch = args.stream_chunks
-        desc = (f"stream: {n_ch} chunks of 31,250 sub-3 blobs ({n_ch * 31250:,} objects) streamed against "
-                "20,000 tubes, side 5,000, within tau = 1")
-        gS = ctx.load_set(S_stream)
-        gR = ctx.load_set_streamed(31250 * n_ch, n_ch, lambda c: chunks[c])
-        q = dict(pred=pj.WITHIN, tau=1.0)
-        tuned = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.AUTOTUNE)
-        untrained = None
-        plain = None
-        gP = None
-        # pinned host-to-device copy peak: 1 GiB, best of 5
-        h = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
-        d = torch.empty_like(h, device="cuda")
-        best = 0.0
-        for _ in range(5):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            d.copy_(h, non_blocking=True)
-            e1.record()
-            torch.cuda.synchronize()
-            best = max(best, h.numel() * 4 / (e0.elapsed_time(e1) / 1000.0) / 1e9)
-        extra["h2d_peak_gbs"] = best
-        del h, d
-
-    def run(R, mode):
-        ctx.join(R, gS, stream=stream.cuda_stream, **q, **mode)
-        return ctx.stats()
-
-    for _ in range(max(1, args.warmup)):
-        run(gR, tuned)
-    clocks = ClockSampler(0)
-    clocks.start()
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    stats = []
-    t0 = time.perf_counter()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        stats.append(run(gR, tuned))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    wall = (time.perf_counter() - t0) * 1000.0
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) if args.workload != "stream" else wall
-    pairs = sum(st["candidates"] for st in stats)
-    tests32 = sum(st["tests_fp32"] for st in stats)
-    kms32 = sum(st["refine_ms_fp32"] for st in stats)
-    value = pairs / (ms / 1000.0)
-    achieved = tests32 * FLOPS_PER_TEST / (kms32 / 1000.0) / 1e12 if kms32 > 0 else 0.0
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": max(1, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "dtype": "f32", "data": "synthetic",
-           "config": {"workload": desc, "flags": tuned["flags"], "candidate_pairs_per_step": pairs // args.steps,
-                      "results_per_step": stats[-1]["results"]},
-           "tri_tests_per_s": sum(st["tests_fp32"] + st["tests_fp64"] for st in stats) / (ms / 1000.0),
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak(nsm), "unit": "TFLOP/s",
-                        "frac": achieved / alu_peak(nsm), "kernel": "k_refine<float> (single-precision refinement)",
-                        "kernel_ms_per_step": kms32 / args.steps},
-           "last_step_stats": {k: v for k, v in stats[-1].items() if k != "steps"},
-           "clocks": clk}
-    out.update(extra)
-    if untrained is not None:
-        st = run(gR, untrained)
-        t = time.perf_counter()
-        st = run(gR, untrained)
-        out["without_proposal"] = {"ms": (time.perf_counter() - t) * 1000.0, "tests": st["tests_fp32"] + st["tests_fp64"]}
-        out["with_proposal_tests"] = stats[-1]["tests_fp32"] + stats[-1]["tests_fp64"]
-    if plain is not None and not args.no_plain:
-        t = time.perf_counter()
-        st = run(gP, plain)
-        pms = (time.perf_counter() - t) * 1000.0
-        if gP is not gR:
-            t = time.perf_counter()
-            st2 = run(gP, tuned)
-            tms = (time.perf_counter() - t) * 1000.0
-            out["plain"] = {"value": st["candidates"] / (pms / 1000.0), "ms": pms, "dtype": "f64",
-                            "tuned_same_inputs": {"value": st2["candidates"] / (tms / 1000.0), "ms": tms}}
-            out["speedup_vs_plain"] = (st2["candidates"] / tms) / (st["candidates"] / pms)
-        else:
-            out["plain"] = {"value": st["candidates"] / (pms / 1000.0), "ms": pms, "dtype": "f64"}
-            out["speedup_vs_plain"] = value / out["plain"]["value"]
-    print(json.dumps(out), flush=True)
-    ctx.close()
-
-
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
-    elif args.workload != "blobs20k":
-        extra_arm(args)
     else:
         ours_arm(args)
 

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def run(env_extra):
     env = dict(os.environ, **env_extra)
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--n", "3000"], cwd=ROOT, env=env, capture_output=True, text=True,
+                        "--warmup", "0", "--sample-pairs", "2"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     return p
 
