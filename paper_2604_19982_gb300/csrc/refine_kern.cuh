@@ -40,7 +40,19 @@ struct RefineArgs {
   int split_k;             // tail units are handed out as split_k sub-units (1: no splitting)
   int64_t split_tail;      // how many of the last units are split
   int masked;              // full resolution: Tile::pad holds the unit's s-facet mask (k_unit_masks)
+  int64_t tiles_cap;       // units the tile array holds (a device count above it was truncated)
+  unsigned long long* units_max;   // largest device unit count seen (may be null)
 };
+
+// The unit count of a launch: the host's, or the device's clamped to the
+// tile array (a builder that overflowed flags the join, which reruns).
+__device__ __forceinline__ int64_t launch_units(const int64_t* dev, int64_t host, int64_t cap,
+                                                unsigned long long* units_max) {
+  if (!dev) return host;
+  const int64_t n = *dev;
+  if (units_max && blockIdx.x == 0 && threadIdx.x == 0) atomicMax(units_max, (unsigned long long)n);
+  return n < cap ? n : cap;
+}
 
 // Tail splitting.  Units are taken from one counter over a virtual index
 // space: the first NT - T indices are whole units, the rest are the
@@ -97,7 +109,11 @@ constexpr int REFINE_WARPS = REFINE_THREADS / 32;
 // double precision (its records need up to 255 registers)
 template <class T>
 constexpr int kref_warps() {
+#ifdef PJ_REFINE_WARPS_F32
+  return sizeof(T) == 4 ? PJ_REFINE_WARPS_F32 : 8;
+#else
   return sizeof(T) == 4 ? REFINE_WARPS : 8;
+#endif
 }
 
 constexpr int WARP_LIST = 128;   // straddling facet pairs kept per warp and unit
@@ -128,16 +144,29 @@ struct ListOut {
   bool anyposs;
 };
 
+// Where a listed pair goes when filtered signs cannot decide its meeting
+// test: the global queue of k_cross_fix, which decides it exactly.
+struct QueueRef {
+  int4* queue;
+  unsigned* qcount;
+  unsigned qcap;
+  int pair, rb, sb;
+  float eps;
+};
+
 // Contributions of the straddling facet pairs a warp listed during one
-// unit: lane k takes entries k, k+32, ...; the meeting test is exact
-// (cross_decide: single-precision filtered signs, else exact arithmetic).
-// The list holds the single-precision squared distance; in double precision
-// it is recomputed from the facets (the same records, so the same value as
-// in the unit's loop).  Out of line so that its registers do not weigh on
-// the unit's inner loop; called only when the warp's list is non-empty.
+// unit: lane k takes entries k, k+32, ...; the meeting test from filtered
+// signs (cross_filtered: single, then double precision), and the rare pair
+// neither makes certain goes to k_cross_fix's queue (exact arithmetic,
+// where it adds its own contribution; a full queue keeps a meeting
+// possible).  The list holds the single-precision squared distance; in
+// double precision it is recomputed from the facets (the same records, so
+// the same value as in the unit's loop).  Out of line so that its
+// registers do not weigh on the unit's inner loop; called only when the
+// warp's list is non-empty.
 template <class T, bool FULL>
 __device__ __noinline__ ListOut<T> process_list(const uint2* list, unsigned nl, int lane, const float4* fr0,
-                                                const float4* raw, float4 o4) {
+                                                const float4* raw, float4 o4, QueueRef q) {
   const T INF = inf_(T(0));
   ListOut<T> out{INF, INF, INF, INF, false};
   for (unsigned k = lane; k < nl; k += 32) {
@@ -145,35 +174,50 @@ __device__ __noinline__ ListOut<T> process_list(const uint2* list, unsigned nl, 
     const int li = e.x & 255, lj = e.x >> 8;
     const float4* fr = fr0 + 3 * li;
     const float4* fs = raw + 3 * lj;
-    const bool cert = cross_decide(fr, fs);
+    const int f = cross_filtered(fr, fs);
+    if (f < 0) {
+      const unsigned qk = atomicAdd(q.qcount, 1u);
+      if (qk < q.qcap) {
+        q.queue[qk] = make_int4(q.pair, q.rb + li, q.sb + lj, __float_as_int(q.eps));
+        continue;
+      }
+    }
     const T phs = add_ru(T(fr[1].w), T(fs[1].w)), hds = add_ru(T(fr[0].w), T(fs[0].w));
-    if (cert) {
+    if (f == 1) {
       out.lbm = min(out.lbm, -phs);
       out.ubc = min(out.ubc, hds);
       if (FULL) out.anyposs = true;
-    } else {
-      T d2e = T(__uint_as_float(e.y));
-      if (sizeof(T) == 8) {
-        T va[3], vb[3], vc[3], wa[3], wb[3], wc[3];
-        translate(fr[0], o4, va);
-        translate(fr[1], o4, vb);
-        translate(fr[2], o4, vc);
-        translate(fs[0], o4, wa);
-        translate(fs[1], o4, wb);
-        translate(fs[2], o4, wc);
-        typename RecOf<T>::R P, Q;
-        make_rec(P, va, vb, vc, T(fr[0].w), T(fr[1].w), true);
-        make_rec(Q, wa, wb, wc, T(fs[0].w), T(fs[1].w), false);
-        bool mb;
-        d2e = tri_d2(P, Q, T(0), mb);
-      }
+      continue;
+    }
+    T d2e = T(__uint_as_float(e.y));
+    if (sizeof(T) == 8) {
+      T va[3], vb[3], vc[3], wa[3], wb[3], wc[3];
+      translate(fr[0], o4, va);
+      translate(fr[1], o4, vb);
+      translate(fr[2], o4, vc);
+      translate(fs[0], o4, wa);
+      translate(fs[1], o4, wb);
+      translate(fs[2], o4, wc);
+      typename RecOf<T>::R P, Q;
+      make_rec(P, va, vb, vc, T(fr[0].w), T(fr[1].w), true);
+      make_rec(Q, wa, wb, wc, T(fs[0].w), T(fs[1].w), false);
+      bool mb;
+      d2e = tri_d2(P, Q, T(0), mb);
+    }
+    if (f < 0) {   // undecided and the queue is full: a meeting stays possible
       if (FULL) {
+        out.anyposs = true;
         out.d2m = min(out.d2m, d2e);
       } else {
-        T d = sqrt_test(d2e);
-        out.lbm = min(out.lbm, sub_rd(d, phs));
-        out.ubu = min(out.ubu, add_ru(d, hds));
+        out.lbm = min(out.lbm, -phs);
+        out.ubu = min(out.ubu, add_ru(sqrt_test(d2e), hds));
       }
+    } else if (FULL) {
+      out.d2m = min(out.d2m, d2e);
+    } else {
+      T d = sqrt_test(d2e);
+      out.lbm = min(out.lbm, sub_rd(d, phs));
+      out.ubu = min(out.ubu, add_ru(d, hds));
     }
   }
   return out;
@@ -224,7 +268,8 @@ __global__ void __launch_bounds__(kref_warps<T>() * 32, 1) k_refine(RefineArgs a
   __syncwarp();
   const T INF = inf_(T(0));
   const unsigned FULLM = 0xffffffffu;
-  const UnitSpace us = unit_space(a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles, a.split_k, a.split_tail);
+  const UnitSpace us =
+      unit_space(launch_units(a.n_tiles_dev, a.n_tiles, a.tiles_cap, a.units_max), a.split_k, a.split_tail);
   uint32_t ph0 = 0, ph1 = 0, ph2 = 0;
   unsigned ntest = 0, nskip = 0, nneed = 0;   // per lane (a lane sees far fewer than 2^32)
   bool failed = false;
@@ -436,7 +481,8 @@ __global__ void __launch_bounds__(kref_warps<T>() * 32, 1) k_refine(RefineArgs a
     const unsigned nl = min(list_n[warp], (unsigned)WARP_LIST);
     T ubc = INF;
     if (nl) {
-      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, rfac, raw, o4);
+      ListOut<T> lo = process_list<T, FULL>(
+          list, nl, lane, rfac, raw, o4, QueueRef{a.queue, a.qcount, a.qcap, tl.pair, tl.rb, tl.sb, tl.eps});
       lbm = min(lbm, lo.lbm);
       ubu = min(ubu, lo.ubu);
       ubc = lo.ubc;
@@ -525,7 +571,8 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
   __syncwarp();
   const T INF = inf_(T(0));
   const unsigned FULLM = 0xffffffffu;
-  const UnitSpace us = unit_space(a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles, a.split_k, a.split_tail);
+  const UnitSpace us =
+      unit_space(launch_units(a.n_tiles_dev, a.n_tiles, a.tiles_cap, a.units_max), a.split_k, a.split_tail);
   uint32_t ph0 = 0, ph1 = 0;
   int b = 0;
   unsigned long long ntest = 0, nskip = 0;
@@ -693,7 +740,8 @@ __global__ void __launch_bounds__(REFINE_THREADS, 1) k_refine2(RefineArgs a) {
     const unsigned nl = min(list_n[warp], (unsigned)WARP_LIST);
     T ubc = INF;
     if (nl) {
-      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, a.facR + 3LL * tl.rb, raw, o4);
+      ListOut<T> lo = process_list<T, FULL>(list, nl, lane, a.facR + 3LL * tl.rb, raw, o4,
+                                            QueueRef{a.queue, a.qcount, a.qcap, tl.pair, tl.rb, tl.sb, tl.eps});
       lbm = min(lbm, lo.lbm);
       ubu = min(ubu, lo.ubu);
       ubc = lo.ubc;

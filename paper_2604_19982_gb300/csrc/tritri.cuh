@@ -588,20 +588,41 @@ __device__ __forceinline__ int orient_sign32(const float4& a, const float4& b, c
   return det > bound ? 1 : (det < -bound ? -1 : 0);
 }
 
-// The meeting decision from single-precision filtered signs: 1 when an edge
+// The same sign from double-precision differences of the float coordinates
+// (exact for coordinates within 2^29 of each other, else rounded once),
+// trusted beyond 16 u_64 Pm: the first-order error of the rounded
+// differences, products and sums stays below 8 u_64 Pm.  0 when not
+// certain (also outside [1e-200, 1e200]).
+__device__ __forceinline__ int orient_sign64(const float4& a, const float4& b, const float4& c, const float4& d) {
+  const double x0 = (double)b.x - a.x, x1 = (double)b.y - a.y, x2 = (double)b.z - a.z;
+  const double y0 = (double)c.x - a.x, y1 = (double)c.y - a.y, y2 = (double)c.z - a.z;
+  const double z0 = (double)d.x - a.x, z1 = (double)d.y - a.y, z2 = (double)d.z - a.z;
+  const double c0 = y1 * z2 - y2 * z1, c1 = y2 * z0 - y0 * z2, c2 = y0 * z1 - y1 * z0;
+  const double det = x0 * c0 + x1 * c1 + x2 * c2;
+  const double p0 = fabs(y1 * z2) + fabs(y2 * z1), p1 = fabs(y2 * z0) + fabs(y0 * z2),
+               p2 = fabs(y0 * z1) + fabs(y1 * z0);
+  const double perm = fabs(x0) * p0 + fabs(x1) * p1 + fabs(x2) * p2;
+  if (!(perm > 1e-200 && perm < 1e200)) return 0;
+  const double bound = perm * 1.7763568394002505e-15;   // 2^-49 = 16 u_64
+  return det > bound ? 1 : (det < -bound ? -1 : 0);
+}
+
+// The meeting decision from filtered signs (SIGN: orient_sign32 or
+// orient_sign64): 1 when an edge
 // of one facet certainly crosses the other strictly inside, 0 when every
 // edge certainly misses (both ends strictly on one side of the plane, or
 // the line passing an edge strictly on the wrong side), -1 when some sign
 // is not certain (tri_meet_exact then decides; touching, coplanar and
 // degenerate configurations always land there, since the filter never
 // certifies a zero sign).
-__device__ __forceinline__ int cross_filter32(const float4* fp, const float4* fq) {
+template <int (*SIGN)(const float4&, const float4&, const float4&, const float4&)>
+__device__ __forceinline__ int cross_filter(const float4* fp, const float4* fq) {
   bool unsure = false;
   for (int side = 0; side < 2; ++side) {
     const float4* A = side ? fq : fp;
     const float4* B = side ? fp : fq;
     int h[3];
-    for (int i = 0; i < 3; ++i) h[i] = orient_sign32(B[0], B[1], B[2], A[i]);
+    for (int i = 0; i < 3; ++i) h[i] = SIGN(B[0], B[1], B[2], A[i]);
     for (int i = 0; i < 3; ++i) {
       const int k = (i + 1) % 3;
       if (h[i] == 0 || h[k] == 0) {
@@ -609,9 +630,9 @@ __device__ __forceinline__ int cross_filter32(const float4* fp, const float4* fq
         continue;
       }
       if (h[i] == h[k]) continue;   // both ends on one side
-      const int o1 = orient_sign32(A[i], A[k], B[0], B[1]);
-      const int o2 = orient_sign32(A[i], A[k], B[1], B[2]);
-      const int o3 = orient_sign32(A[i], A[k], B[2], B[0]);
+      const int o1 = SIGN(A[i], A[k], B[0], B[1]);
+      const int o2 = SIGN(A[i], A[k], B[1], B[2]);
+      const int o3 = SIGN(A[i], A[k], B[2], B[0]);
       if (o1 == 0 || o2 == 0 || o3 == 0) {
         unsure = true;
         continue;
@@ -622,10 +643,21 @@ __device__ __forceinline__ int cross_filter32(const float4* fp, const float4* fq
   return unsure ? -1 : 0;
 }
 
-// Do the closed facets (raw float vertices) meet?  Exact: single-precision
-// signs where they are certain, else exact expansion arithmetic.
+// The meeting decision where filtered signs make it certain: single
+// precision, then double precision; -1 when neither is certain (touching,
+// coplanar and degenerate configurations, or signs within rounding).
+__device__ __forceinline__ int cross_filtered(const float4* fp, const float4* fq) {
+  const int f = cross_filter<orient_sign32>(fp, fq);
+  return f >= 0 ? f : cross_filter<orient_sign64>(fp, fq);
+}
+
+// Do the closed facets (raw float vertices) meet?  Exact: filtered signs
+// where they are certain, else exact expansion arithmetic.  The refinement
+// kernels use cross_filtered alone and queue the uncertain pairs for a
+// separate kernel, so that the expansion arithmetic (and its local memory)
+// stays out of their code.
 static __device__ __forceinline__ bool cross_decide(const float4* fp, const float4* fq) {
-  const int f = cross_filter32(fp, fq);
+  const int f = cross_filtered(fp, fq);
   return f >= 0 ? f == 1 : tri_meet_exact(fp, fq);
 }
 
