@@ -150,7 +150,11 @@ typedef struct {
  * "refine_tail" (0..64, default 2: how many units per resident warp are
  * split), "zero_copy" (0, the default, or 1: pj_load_set reads the arrays
  * that live in pinned, mapped host memory in place over the host link
- * instead of staging them, other arrays are copied as usual) and
+ * instead of staging them, other arrays are copied as usual),
+ * "unit_budget_mb" (1 .. 2^20, default 512: the refinement-unit buffer is
+ * sized for a step's worst case when that fits this budget; otherwise units
+ * are emitted into the buffer as it is, and a join whose units overflowed
+ * it grows the buffer to the count needed and runs again) and
  * "autotune_cache" (path string).  The options change scheduling only,
  * never a result.  Fails with PJ_ECUDA when the device is not compute
  * capability 10.3 (GB300). */

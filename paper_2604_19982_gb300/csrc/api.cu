@@ -59,17 +59,15 @@ __device__ __forceinline__ int64_t upper_obj(const int64_t* off, int n, int64_t 
   return lo;
 }
 
-// One warp per 32-facet block: each lane expands one facet into its
+// One 32-facet block, one warp: each lane expands one facet into its
 // record (v0, hd), (v1, ph), (v2, 0); the warp reduces the block's box, max
 // hd / ph, max edge length and min facet sine from registers, so the
 // records are written once and never read back.
-__global__ void k_expand_blocks(int64_t B, int n, const float* verts, const int64_t* voff, const int32_t* faces,
-                                const int64_t* foff, const int64_t* boff, int nf_shared, const float* hd,
-                                const float* ph, float4* fac, float4* blk, int* err) {
-  const int64_t bi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void expand_block(int64_t bi, int64_t o, const float* verts, const int64_t* voff,
+                                             const int32_t* faces, const int64_t* foff, const int64_t* boff,
+                                             int nf_shared, const float* hd, const float* ph, float4* fac,
+                                             float4* blk, int* err) {
   const int lane = threadIdx.x & 31;
-  if (bi >= B) return;
-  const int64_t o = upper_obj(boff, n, bi);
   const int64_t f = foff[o] + (bi - boff[o]) * BLK + lane;
   const bool act = f < foff[o + 1];
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -133,12 +131,21 @@ __global__ void k_expand_blocks(int64_t B, int n, const float* verts, const int6
   }
 }
 
-// One thread per 256-facet chunk: the reduction of its (up to 8) blocks.
-__global__ void k_chunks_from_blocks(int64_t C, int n, const int64_t* coff, const int64_t* boff, const float4* blk,
-                                     float4* chunk) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  const int64_t o = upper_obj(coff, n, c);
+// One warp per block of every object (blocks of an object with shared
+// topology are found by division, others by a search of the offsets).
+__global__ void k_expand_blocks(int64_t B, int n, const float* verts, const int64_t* voff, const int32_t* faces,
+                                const int64_t* foff, const int64_t* boff, int nf_shared, const float* hd,
+                                const float* ph, float4* fac, float4* blk, int* err) {
+  const int64_t bi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (bi >= B) return;
+  const int64_t bpo = nf_shared > 0 ? (nf_shared + BLK - 1) / BLK : 0;
+  const int64_t o = bpo ? bi / bpo : upper_obj(boff, n, bi);
+  expand_block(bi, o, verts, voff, faces, foff, boff, nf_shared, hd, ph, fac, blk, err);
+}
+
+// One 256-facet chunk: the reduction of its (up to 8) blocks.
+__device__ __forceinline__ void chunk_from_blocks(int64_t c, int64_t o, const int64_t* coff, const int64_t* boff,
+                                                  const float4* blk, float4* chunk) {
   const int64_t b0 = boff[o] + (c - coff[o]) * (CHUNK / BLK), b1 = min(b0 + CHUNK / BLK, boff[o + 1]);
   float4 lo = blk[3 * b0], hi = blk[3 * b0 + 1], ex = blk[3 * b0 + 2];
   for (int64_t b = b0 + 1; b < b1; ++b) {
@@ -152,19 +159,29 @@ __global__ void k_chunks_from_blocks(int64_t C, int n, const int64_t* coff, cons
   chunk[3 * c + 2] = ex;
 }
 
+__global__ void k_chunks_from_blocks(int64_t C, int n, const int64_t* coff, const int64_t* boff, const float4* blk,
+                                     float4* chunk) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  chunk_from_blocks(c, upper_obj(coff, n, c), coff, boff, blk, chunk);
+}
+
 // one warp per object: box of its original-surface vertices
 __global__ void k_mbb(int n, const float* verts, const int64_t* voff, const float* anchor, float* mbb, int* err) {
   int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (o >= n) return;
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool fin = true;
   for (int64_t v = voff[o] + lane; v < voff[o + 1]; v += 32)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       float x = verts[3 * v + k];
+      fin = fin && isfinite(x);
       lo[k] = fminf(lo[k], x);
       hi[k] = fmaxf(hi[k], x);
     }
+  if (!fin) set_err(err, ERR_NONFINITE);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     lo[k] = warp_min(lo[k]);
@@ -219,11 +236,11 @@ static const void* pinned_view(const pj_ctx* ctx, const void* p) {
 }
 
 // Lay a described set out on the device (see pj_load_set).
-void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err) {
+void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err, int lod_end) {
   const int n = s->n, L = s->L;
   if (!err) err = ctx->d_err;
   int th = 256;
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < (lod_end < 0 ? L : lod_end); ++l) {
     LodData& ld = s->lod[l];
     if (ld.F == 0) continue;
     k_expand_blocks<<<(unsigned)((ld.B * 32 + th - 1) / th), th, 0, st>>>(
@@ -242,6 +259,99 @@ void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t s
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
   }
+}
+
+// Objects of R that the selected pairs of a step need at a lazily built
+// LoD and that are not built yet: state 0 -> 1, appended to the list.
+__global__ void k_lazy_mark(int64_t n, const int32_t* pr, const uint8_t* status, const uint8_t* lod0, uint8_t want,
+                            int step, unsigned* state, int32_t* list, unsigned* count) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n || status[p] != want || lod0[p] > step) return;
+  const int r = pr[p];
+  if (state[r] == 0 && atomicCAS(&state[r], 0u, 1u) == 0u) list[atomicAdd(count, 1u)] = r;
+}
+
+// The listed objects' blocks: warp w takes block (w mod maxb) of listed
+// object (w / maxb) (warps past an object's blocks return).
+__global__ void k_expand_listed(const int32_t* list, const unsigned* count, int64_t maxb, const float* verts,
+                                const int64_t* voff, const int32_t* faces, const int64_t* foff,
+                                const int64_t* boff, int nf_shared, const float* hd, const float* ph, float4* fac,
+                                float4* blk, int* err) {
+  const int64_t total = (int64_t)(*count) * maxb;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    const int o = list[w / maxb];
+    const int64_t bi = boff[o] + w % maxb;
+    if (bi >= boff[o + 1]) continue;   // warp-uniform
+    expand_block(bi, o, verts, voff, faces, foff, boff, nf_shared, hd, ph, fac, blk, err);
+  }
+}
+
+// The listed objects' chunk boxes from their blocks: thread t takes chunk
+// (t mod maxc) of listed object (t / maxc).
+__global__ void k_chunks_listed(const int32_t* list, const unsigned* count, int64_t maxc, const int64_t* coff,
+                                const int64_t* boff, const float4* blk, float4* chunk) {
+  const int64_t total = (int64_t)(*count) * maxc;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += nt) {
+    const int o = list[t / maxc];
+    const int64_t c = coff[o] + t % maxc;
+    if (c < coff[o + 1]) chunk_from_blocks(c, o, coff, boff, blk, chunk);
+  }
+}
+
+void ensure_lod(pj_ctx* ctx, const pj_set* R, int lod, int64_t n_pairs, const int32_t* pr, const uint8_t* status,
+                const uint8_t* lod0, uint8_t want, int step, cudaStream_t st) {
+  if (lod < R->lazy_from || n_pairs == 0 || R->n == 0) return;
+  const LodData& ld = R->lod[lod];
+  const RawLod& raw = R->lazy_raw[lod];
+  unsigned* state = R->lazy_state + (size_t)(lod - R->lazy_from) * R->n;
+  const int th = 256;
+  PJ_CK(cudaMemsetAsync(R->lazy_count, 0, sizeof(unsigned), st));
+  k_lazy_mark<<<(unsigned)((n_pairs + th - 1) / th), th, 0, st>>>(n_pairs, pr, status, lod0, want, step, state,
+                                                                    R->lazy_list, R->lazy_count);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  if (ld.F == 0) return;
+  const int64_t maxb = std::max<int64_t>(1, (ld.maxF + BLK - 1) / BLK);
+  const int64_t maxc = std::max<int64_t>(1, (ld.maxF + CHUNK - 1) / CHUNK);
+  const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>(1, ((int64_t)R->n * maxb * 32 + th - 1) / th),
+                                                    (int64_t)ctx->sm_count * 16);
+  k_expand_listed<<<grid, th, 0, st>>>(R->lazy_list, R->lazy_count, maxb, raw.verts, raw.voff, raw.faces, ld.foff,
+                                       ld.boff, raw.nfs, raw.hd, raw.ph, ld.fac, ld.blk, ctx->d_err);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  const unsigned gc = (unsigned)std::min<int64_t>(std::max<int64_t>(1, ((int64_t)R->n * maxc + th - 1) / th),
+                                                  (int64_t)ctx->sm_count * 8);
+  k_chunks_listed<<<gc, th, 0, st>>>(R->lazy_list, R->lazy_count, maxc, ld.coff, ld.boff, ld.blk, ld.chunk);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+}
+
+// One thread per chunk: the maxima of hd and ph over its facets.
+__global__ void k_chunk_hd_ph(int64_t C, int n, const int64_t* coff, const int64_t* foff, const float* hd,
+                              const float* ph, float4* chunk) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int64_t o = upper_obj(coff, n, c);
+  const int64_t f0 = foff[o] + (c - coff[o]) * CHUNK, f1 = min(f0 + CHUNK, foff[o + 1]);
+  float mh = 0.f, mp = 0.f;
+  for (int64_t f = f0; f < f1; ++f) {
+    if (hd) mh = fmaxf(mh, hd[f]);
+    if (ph) mp = fmaxf(mp, ph[f]);
+  }
+  chunk[3 * c].w = mh;
+  chunk[3 * c + 1].w = mp;
+}
+
+void chunk_hd_ph(pj_ctx* ctx, pj_set* s, int l, const RawLod& raw, cudaStream_t st) {
+  const LodData& ld = s->lod[l];
+  if (ld.C == 0) return;
+  const int th = 256;
+  k_chunk_hd_ph<<<(unsigned)((ld.C + th - 1) / th), th, 0, st>>>(ld.C, s->n, ld.coff, ld.foff, raw.hd, raw.ph,
+                                                                 ld.chunk);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaStream_t st) {
@@ -453,6 +563,11 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
   }
   PJ_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   PJ_CK(cudaStreamCreateWithFlags(&ctx->build_stream, cudaStreamNonBlocking));
+  {
+    int lo = 0, hi = 0;
+    PJ_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    PJ_CK(cudaStreamCreateWithPriority(&ctx->join_stream, cudaStreamNonBlocking, hi));
+  }
   note_alloc();
   PJ_CK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
   note_alloc();
@@ -494,6 +609,15 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
     }
     ctx->refine_tail = t;
   }
+  v = json_str(options_json, "unit_budget_mb");
+  if (!v.empty()) {
+    const long long mb = atoll(v.c_str());
+    if (mb < 1 || mb > (1LL << 20)) {
+      pj_destroy(ctx);
+      return PJ_EINVAL;
+    }
+    ctx->unit_budget = (size_t)mb << 20;
+  }
   ctx->autotune_cache = json_str(options_json, "autotune_cache");
   *out = ctx;
   return PJ_OK;
@@ -534,6 +658,7 @@ void pj_destroy(pj_ctx* ctx) {
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->build_stream) cudaStreamDestroy(ctx->build_stream);
+  if (ctx->join_stream) cudaStreamDestroy(ctx->join_stream);
   delete ctx;
 }
 

@@ -210,6 +210,9 @@ __global__ void k_seg_sort(int nR, const int64_t* roff, int32_t* s) {
   }
 }
 
+// With R == nullptr the grid spans S's boxes alone (for a streamed R, whose
+// chunks then share one grid): an R box outside it probes the clamped edge
+// cells, which hold every S box (grown by tau) that can reach it.
 static Grid make_grid(const pj_set* R, const pj_set* S, double tau) {
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   double extS = 0, extR = 0;
@@ -224,7 +227,7 @@ static Grid make_grid(const pj_set* R, const pj_set* S, double tau) {
     }
     ext /= std::max(1, 3 * X->n);
   };
-  acc(R, extR);
+  if (R) acc(R, extR);
   acc(S, extS);
   for (int k = 0; k < 3; ++k) {
     lo[k] -= (float)tau + 1.f;
@@ -285,41 +288,61 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   if (R->n == 0 || S->n == 0) return out;
   Grid G;
   int64_t nids = 0;
-  const bool cached = grid_cached(ctx, R, S, tau, &G, &nids);
-  if (!cached) G = make_grid(R, S, tau);
   float ftau = (float)tau;
   if ((double)ftau < tau) ftau = nextafterf(ftau, INFINITY);
   double lim = tau * (1.0 + 1e-9);
   double lim2 = lim * lim;
-  auto cnt = (int64_t*)ws_get(ctx, WS_GRID, (G.ncell + 1) * 8, st);
-  auto off = (int64_t*)ws_get(ctx, WS_MISC, (G.ncell + 1) * 8, st);
-  PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
   int th = 256;
-  k_grid_count<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, cnt);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-  scan_i64(ctx, cnt, off, G.ncell, st);
-  // grid entries bounded on the host (one extra cell per axis absorbs
-  // host/device rounding of the cell index), so no synchronization here
-  if (!cached) {
-    for (int o = 0; o < S->n; ++o) {
-      const float* b = &S->mbb_h[6 * o];
-      int64_t c = 1;
-      for (int k = 0; k < 3; ++k) {
-        double a0 = std::floor(((double)b[k] - tau - G.g0[k]) * G.inv_h);
-        double a1 = std::floor(((double)b[3 + k] + tau - G.g0[k]) * G.inv_h);
-        int64_t w = (int64_t)std::min<double>(G.dim[k], std::max(1.0, a1 - a0 + 3.0));
-        c *= w;
+  // a streamed R's chunks (views with uid 0) share one grid over S, kept
+  // in the workspace while no other grid replaces it
+  const bool s_only = R->uid == 0 && S->uid != 0;
+  const bool kept = s_only && ctx->sgrid.valid && ctx->sgrid.sid == S->uid && ctx->sgrid.tau == tau;
+  int64_t* off;
+  int32_t* ids;
+  if (kept) {
+    memcpy(&G, ctx->sgrid.grid, sizeof(Grid));
+    off = (int64_t*)ctx->ws[WS_MISC].p;
+    ids = (int32_t*)ctx->ws[WS_GRIDIDS].p;
+  } else {
+    ctx->sgrid.valid = false;
+    const bool cached = !s_only && grid_cached(ctx, R, S, tau, &G, &nids);
+    if (!cached) G = make_grid(s_only ? nullptr : R, S, tau);
+    auto cnt = (int64_t*)ws_get(ctx, WS_GRID, (G.ncell + 1) * 8, st);
+    off = (int64_t*)ws_get(ctx, WS_MISC, (G.ncell + 1) * 8, st);
+    PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
+    k_grid_count<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, cnt);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+    scan_i64(ctx, cnt, off, G.ncell, st);
+    // grid entries bounded on the host (one extra cell per axis absorbs
+    // host/device rounding of the cell index), so no synchronization here
+    if (!cached) {
+      for (int o = 0; o < S->n; ++o) {
+        const float* b = &S->mbb_h[6 * o];
+        int64_t c = 1;
+        for (int k = 0; k < 3; ++k) {
+          double a0 = std::floor(((double)b[k] - tau - G.g0[k]) * G.inv_h);
+          double a1 = std::floor(((double)b[3 + k] + tau - G.g0[k]) * G.inv_h);
+          int64_t w = (int64_t)std::min<double>(G.dim[k], std::max(1.0, a1 - a0 + 3.0));
+          c *= w;
+        }
+        nids += c;
       }
-      nids += c;
+      if (!s_only) grid_keep(ctx, R, S, tau, G, nids);
     }
-    grid_keep(ctx, R, S, tau, G, nids);
+    ids = (int32_t*)ws_get(ctx, WS_GRIDIDS, std::max<int64_t>(1, nids) * 4, st);
+    PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
+    k_grid_fill<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, off, cnt, ids);
+    PJ_CK(cudaGetLastError());
+    PJ_COUNT_LAUNCH;
+    if (s_only) {
+      ctx->sgrid.valid = true;
+      ctx->sgrid.sid = S->uid;
+      ctx->sgrid.tau = tau;
+      static_assert(sizeof(Grid) <= sizeof(ctx->sgrid.grid), "kept grid");
+      memcpy(ctx->sgrid.grid, &G, sizeof(Grid));
+    }
   }
-  auto ids = (int32_t*)ws_get(ctx, WS_GRIDIDS, std::max<int64_t>(1, nids) * 4, st);
-  PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
-  k_grid_fill<<<(S->n + th - 1) / th, th, 0, st>>>(S->n, S->mbb, ftau, G, off, cnt, ids);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
   auto rcount = (int64_t*)ws_get(ctx, WS_RCOUNT, ((int64_t)R->n + 1) * 8, st);
   auto roff = (int64_t*)ws_get(ctx, WS_ROFF, ((int64_t)R->n + 1) * 8, st);
   int64_t warps_threads = (int64_t)R->n * 32;

@@ -38,6 +38,22 @@ struct ApiError {
   std::string msg;
 };
 
+// Thrown when an autotuning trial exceeds its unit budget (the tuner
+// skips that configuration).
+struct TrialTooLarge {
+  int64_t units;
+};
+
+// Thrown at the end of a join whose unit buffer was too small for some
+// step (its results are discarded): the buffer is grown to `units` and the
+// join runs again.
+struct UnitsOverflow {
+  int64_t units;
+};
+
+// device counter slot of the largest unit count a join's steps asked for
+constexpr int CNT_UNITS_MAX = 11;
+
 // Grow-only device buffer (stream-ordered allocation on the context stream).
 struct DevBuf {
   void* p = nullptr;
@@ -83,6 +99,17 @@ struct StepLogData {
   bool masked[16];   // full-resolution step whose units went through k_unit_masks
 };
 
+// Raw device arrays of one LoD as given by the caller (faces: shared
+// template of nfs rows when nfs > 0, else per-object rows).
+struct RawLod {
+  const float* verts;
+  const int64_t* voff;
+  const int32_t* faces;
+  int nfs;
+  const float* hd;
+  const float* ph;
+};
+
 // Totals of the last join (also in its JSON stats).
 struct JoinSummary {
   int64_t candidates = 0, results = 0, units = 0;
@@ -103,6 +130,16 @@ struct pj_set {
   float* anchor = nullptr;        // device [n][3]
   std::vector<float> mbb_h;       // host copy
   uint64_t uid = 0;               // unique per loaded set (0: a temporary view)
+  // streamed chunk views: the LoDs from lazy_from on (the finer ones,
+  // most of the facets) are laid out only for the objects whose pairs
+  // reach them.  Per lazy LoD l: lazy_state[(l - lazy_from) * n + o] is 0
+  // (not built) or 1 (built); lazy_list / lazy_count hold the objects a
+  // step adds.
+  int lazy_from = PJ_MAX_LODS;
+  pj::RawLod lazy_raw[PJ_MAX_LODS] = {};
+  unsigned* lazy_state = nullptr;
+  int32_t* lazy_list = nullptr;
+  unsigned* lazy_count = nullptr;
   // streamed R: the chunks are loaded inside pj_join
   bool streamed = false;
   int64_t n_total = 0;
@@ -118,6 +155,16 @@ struct pj_ctx {
   cudaStream_t stream = nullptr;   // default work stream
   cudaStream_t copy_stream = nullptr;
   cudaStream_t build_stream = nullptr;   // set building of streamed chunks
+  cudaStream_t join_stream = nullptr;    // streamed chunk joins: the device's greatest priority, so
+                                         // their small launches go ahead of the next chunk's build
+  // the within filter's grid over S alone, kept in its workspace slots
+  // across the chunks of a streamed R (valid until another grid is built)
+  struct {
+    bool valid = false;
+    uint64_t sid = 0;
+    double tau = 0;
+    unsigned char grid[64];
+  } sgrid;
   int* d_err = nullptr;            // device error word
   unsigned long long* d_counters = nullptr;  // [16] device counters
   std::string last_error;
@@ -139,6 +186,8 @@ struct pj_ctx {
   int refine_split = 1;            // the last units of a refinement launch are split this many ways
   int refine_tail = 2;             // ... that many units per resident warp
   int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
+  int64_t trial_unit_cap = 0;      // > 0 while autotuning: a step needing more units abandons the trial
+  size_t unit_budget = size_t(512) << 20;   // unit buffer sized for the worst case up to this many bytes
   std::string autotune_cache;
   // per-query workspace
   pj::DevBuf ws[56];
@@ -225,6 +274,10 @@ struct StepSpec {
   bool cull;        // skip chunk pairs / blocks that cannot reach the threshold
   uint8_t want;     // status of the pairs to refine (UNDECIDED or REDECIDE)
   int step;         // LoD step index (pairs with lod0 > step wait)
+  // the caller checks the unit count after its final synchronization and
+  // reruns on an overflow (check_units): the builder may then emit into the
+  // buffer as it is instead of counting first
+  bool rerun_ok = false;
 };
 
 // Count + emit refinement units for the pairs in state `want`.  count >= 0:
@@ -242,6 +295,11 @@ void init_bounds(pj_ctx* ctx, int64_t n_pairs, const StepSpec& sp, cudaStream_t 
 // index of the CUDA event pair (ctx->ev) bracketing the launch on `st`, or -1.
 int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, const StepSpec& sp,
                cudaStream_t st);
+// After a join's final synchronization (herr: its error word): throws
+// UnitsOverflow when a step's units did not fit the unit buffer.
+void check_units(pj_ctx* ctx, int herr);
+// Grow the unit buffers to hold `units` (and a margin) before a rerun.
+void grow_units(pj_ctx* ctx, int64_t units, cudaStream_t st);
 // Elapsed milliseconds of an event pair returned by run_refine (0 if -1).
 float refine_ms(pj_ctx* ctx, int ev);
 // Per-step record of a join: units, tests and refinement time of every
@@ -287,6 +345,7 @@ struct PairBufs {
   int4* queue;                   // straddling facet pairs (see k_cross_fix)
   unsigned qcap;
   uint8_t* flag;                 // [n] pair proven (early exit), may be null
+  int64_t tiles_cap;             // units the tile array holds
 };
 void setup_pairs_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const PairBufs& b,
                       cudaStream_t st);
@@ -314,20 +373,20 @@ void mark_exact(pj_ctx* ctx, int64_t n, cudaStream_t st);
 void decide_within(pj_ctx* ctx, int64_t n_pairs, double tau, const StepSpec& sp, cudaStream_t st);
 
 // ---- set building (api.cu)
-// Raw device arrays of one LoD as given by the caller (faces: shared
-// template of nfs rows when nfs > 0, else per-object rows).
-struct RawLod {
-  const float* verts;
-  const int64_t* voff;
-  const int32_t* faces;
-  int nfs;
-  const float* hd;
-  const float* ph;
-};
-// Facet records, chunk and block boxes of every LoD and the object boxes,
-// into the set's allocated buffers (foff / coff / boff already on the
-// device); kernel errors go to ctx->d_err.
-void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err = nullptr);
+// Facet records, chunk and block boxes of LoDs [0, lod_end) (default: all)
+// and the object boxes, into the set's allocated buffers (foff / coff / boff
+// already on the device); kernel errors go to ctx->d_err.
+void build_set_kernels(pj_ctx* ctx, pj_set* s, const RawLod* raw, cudaStream_t st, int* err = nullptr,
+                       int lod_end = -1);
+// The per-chunk maxima of hd and ph of LoD l (the .w words of its chunk
+// boxes) from the raw arrays alone, for a LoD whose records are built on
+// demand (the learned start LoD reads them for every pair).
+void chunk_hd_ph(pj_ctx* ctx, pj_set* s, int l, const RawLod& raw, cudaStream_t st);
+// A set whose LoDs from s->lazy_from on are built on demand: the records
+// and boxes of the R objects of the pairs a step selects (status `want`,
+// lod0 <= step) that are not built yet; no-op for other sets and LoDs.
+void ensure_lod(pj_ctx* ctx, const pj_set* R, int lod, int64_t n_pairs, const int32_t* pr, const uint8_t* status,
+                const uint8_t* lod0, uint8_t want, int step, cudaStream_t st);
 
 // ---- triangle distance batch (refine.cu)
 void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool fp64, double* out,

@@ -441,6 +441,11 @@ static std::string graph_key(pj_ctx* ctx, const pj_set* R, const pj_set* S, cons
       h = fnv(h, ptrs, sizeof ptrs);
       h = fnv(h, sz, sizeof sz);
     }
+    // a LoD built on demand reads the chunk's raw arrays inside the sequence
+    h = fnv(h, &X->lazy_from, sizeof X->lazy_from);
+    h = fnv(h, &X->lazy_raw, sizeof X->lazy_raw);
+    h = fnv(h, &X->lazy_state, sizeof X->lazy_state);
+    h = fnv(h, &X->lazy_list, sizeof X->lazy_list);
   }
   for (int i = 0; i < WS_COUNT; ++i) {
     h = fnv(h, &ctx->ws[i].p, sizeof(void*));
@@ -468,8 +473,8 @@ void graphs_clear(pj_ctx* ctx) {
   ctx->graphs.clear();
 }
 
-pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
-                      cudaStream_t st, std::string& stats) {
+static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q,
+                                  pj_result* out, cudaStream_t st, std::string& stats) {
   Timer tall;
   const unsigned long long launches0 = ctx->launches;
   const double tau = q->pred == PJ_INTERSECT ? 0.0 : q->tau;
@@ -496,7 +501,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     for (int l = 0; l < Lmax && graph; ++l) {
       const int lr = std::max(0, l - (Lmax - R->L)), ls = std::max(0, l - (Lmax - S->L));
       const int64_t worst = cap * ((R->lod[lr].maxF + BLK - 1) / BLK) * ((S->lod[ls].maxF + BLK - 1) / BLK);
-      if ((size_t)worst * sizeof(Tile) > (size_t(512) << 20)) graph = false;
+      if ((size_t)worst * sizeof(Tile) > ctx->unit_budget) graph = false;
     }
     if (!graph) cap = n;
   }
@@ -522,6 +527,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     for (int step = first; step < Lmax; ++step) {
       if (deadline_hit()) return false;
       StepSpec sp;
+      sp.rerun_ok = true;
       sp.lodR = std::max(0, step - (Lmax - R->L));
       sp.lodS = std::max(0, step - (Lmax - S->L));
       sp.full = step == Lmax - 1;
@@ -544,6 +550,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
       // the decision only asks d <= tau, so units farther apart than tau may
       // be skipped
       StepSpec sp;
+      sp.rerun_ok = true;
       sp.lodR = R->L - 1;
       sp.lodS = S->L - 1;
       sp.full = true;
@@ -566,6 +573,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
       // every result pair has d <= tau, so its closest facet pair lies in a
       // unit within tau: pruned units cannot hold the minimum
       StepSpec sp;
+      sp.rerun_ok = true;
       sp.lodR = R->L - 1;
       sp.lodS = S->L - 1;
       sp.full = true;
@@ -607,6 +615,13 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     need_capture = graph && !ge;
   } else {
     ms_filter = tf.ms();
+  }
+  {
+    // a step whose units overflowed the buffer voids the join (rerun)
+    int e0 = 0;
+    PJ_CK(cudaMemcpyAsync(&e0, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaStreamSynchronize(st));
+    check_units(ctx, e0);
   }
   Timer tg;
   const int64_t m = gather_host(ctx, nn, out);
@@ -650,6 +665,7 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
+  if (herr & ERR_NONFINITE) return PJ_ENONFINITE;   // data of a LoD built on demand
   if (need_capture) {
     // the direct run sized every buffer: capture the same sequence now
     // (recorded, not executed) under a key taken after it
@@ -689,6 +705,21 @@ pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_qu
     if (g) cudaGraphDestroy(g);
   }
   return PJ_OK;
+}
+
+// A within / intersection join; reruns (at most three times) when a step's
+// refinement units did not fit the unit buffer, which is then grown to the
+// count that step needed.
+pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                      cudaStream_t st, std::string& stats) {
+  for (int attempt = 0;; ++attempt) {
+    try {
+      return join_within_once(ctx, R, S, q, out, st, stats);
+    } catch (const UnitsOverflow& e) {
+      if (attempt >= 3) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer after resizing"};
+      grow_units(ctx, e.units, st);
+    }
+  }
 }
 
 }  // namespace pj

@@ -263,6 +263,7 @@ FilterOut filter_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, int k, cudaS
   FilterOut out;
   if (R->n == 0 || S->n == 0) return out;
   KGrid G = make_kgrid(R, S);
+  ctx->sgrid.valid = false;   // the grid slots are reused here
   auto cnt = (int64_t*)ws_get(ctx, WS_GRID, (G.ncell + 1) * 8, st);
   auto off = (int64_t*)ws_get(ctx, WS_MISC, (G.ncell + 1) * 8, st);
   PJ_CK(cudaMemsetAsync(cnt, 0, (G.ncell + 1) * 8, st));
@@ -574,8 +575,8 @@ static void knn_wave(pj_ctx* ctx, int nR, int k, int step, const float* pred, cu
 
 // ------------------------------------------------------------------ driver
 
-pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
-                   cudaStream_t st, std::string& stats) {
+static pj_status join_knn_once(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                               cudaStream_t st, std::string& stats) {
   Timer tall;
   const unsigned long long launches0 = ctx->launches;
   const int k = q->k;
@@ -617,6 +618,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
   for (int step = 0; step < Lmax && n > 0; ++step) {
     if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
     StepSpec sp;
+    sp.rerun_ok = true;
     sp.lodR = std::max(0, step - (Lmax - R->L));
     sp.lodS = std::max(0, step - (Lmax - S->L));
     sp.full = step == Lmax - 1;
@@ -636,6 +638,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     // resolution, units pruned against the strict threshold, then the last
     // pruning round resolves everything
     StepSpec sp;
+    sp.rerun_ok = true;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
     sp.full = true;
@@ -648,6 +651,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
   if ((q->flags & PJ_EXACT_DIST) && n > 0) {
     mark_exact(ctx, n, st);
     StepSpec sp;
+    sp.rerun_ok = true;
     sp.lodR = R->L - 1;
     sp.lodS = S->L - 1;
     sp.full = true;
@@ -659,6 +663,13 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
     UnitCount uc = build_tiles(ctx, R, S, n, sp, st);
     log.add(ctx, uc, run_refine(ctx, R, S, uc, sp, st), sp, st);
     decide_within(ctx, n, 0.0, sp, st);
+  }
+  {
+    // a step whose units overflowed the buffer voids the join (rerun)
+    int e0 = 0;
+    PJ_CK(cudaMemcpyAsync(&e0, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaStreamSynchronize(st));
+    check_units(ctx, e0);
   }
   Timer tg;
   int64_t m = gather_results(ctx, n, out, st);
@@ -718,7 +729,22 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
   js.launches = ctx->launches - launches0;
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
+  if (herr & ERR_NONFINITE) return PJ_ENONFINITE;   // data of a LoD built on demand
   return PJ_OK;
+}
+
+// A k-NN join; reruns (at most three times) when a step's refinement units
+// did not fit the unit buffer, which is then grown to the count needed.
+pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                   cudaStream_t st, std::string& stats) {
+  for (int attempt = 0;; ++attempt) {
+    try {
+      return join_knn_once(ctx, R, S, q, out, st, stats);
+    } catch (const UnitsOverflow& e) {
+      if (attempt >= 3) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer after resizing"};
+      grow_units(ctx, e.units, st);
+    }
+  }
 }
 
 }  // namespace pj

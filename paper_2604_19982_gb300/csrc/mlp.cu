@@ -759,6 +759,13 @@ pj_status pj_mlp_train(pj_ctx* ctx, const float* feats, const float* target, int
   MLP_CATCH(ctx)
 }
 
+// Each pair's threshold set to its anchor distance (an upper bound of d,
+// rounded up): units and facet pairs farther apart cannot hold the minimum.
+__global__ void k_thr_from_ub(int64_t n, const double* anc_ub, float* thr) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n) thr[p] = __double2float_ru(anc_ub[p]);
+}
+
 pj_status pj_mlp_fit(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, int64_t max_pairs,
                      int epochs, uint64_t seed, double* rmse) {
   if (!ctx || !R || !S || !q || max_pairs < 16 || epochs < 1) return mlp_fail(ctx, PJ_EINVAL, "bad mlp_fit arguments");
@@ -793,14 +800,23 @@ pj_status pj_mlp_fit(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_que
   auto dps = (int32_t*)ws_get(ctx, WS_PS, n * 4, st);
   PJ_CK(cudaMemcpyAsync(dpr, sr.data(), n * 4, cudaMemcpyHostToDevice, st));
   PJ_CK(cudaMemcpyAsync(dps, ss.data(), n * 4, cudaMemcpyHostToDevice, st));
-  // labels: full-resolution distances from the refinement kernel
+  // labels: full-resolution distances from the refinement kernel, with
+  // units pruned against each pair's anchor distance (the minimum lies in
+  // a unit within it)
   setup_pairs(ctx, R, S, n, 0.0, false, st);
+  {
+    const int th = 256;
+    k_thr_from_ub<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, (const double*)ctx->ws[WS_ANCUB].p,
+                                                                 (float*)ctx->ws[WS_THR].p);
+    PJ_CK(cudaGetLastError());
+    count_launch(ctx);
+  }
   StepSpec sp;
   sp.lodR = R->L - 1;
   sp.lodS = S->L - 1;
   sp.full = true;
   sp.fp64 = false;
-  sp.cull = false;
+  sp.cull = true;
   sp.want = UNDECIDED;
   sp.step = STEP_ALL;
   sp.exact_cross = true;

@@ -288,8 +288,6 @@ __global__ void __launch_bounds__(256) k_emit_units(int64_t n, const int32_t* pr
 
 static BoxView box_view(const LodData& L) { return BoxView{L.chunk, L.coff, L.blk, L.boff, L.foff}; }
 
-// Shared by the workspace path and the explicit-buffer path.
-constexpr size_t UNIT_BUDGET_BYTES = size_t(512) << 20;
 
 static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
                              const int32_t* pr, const int32_t* ps, const uint8_t* status, const uint8_t* lod0,
@@ -300,6 +298,8 @@ static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int6
   const LodData& LS = S->lod[sp.lodS];
   BoxView vr = box_view(LR), vs = box_view(LS);
   int th = 256;
+  // a LoD built on demand: lay out the objects this step needs first
+  ensure_lod(ctx, R, sp.lodR, n, pr, status, lod0, sp.want, sp.step, st);
   k_items<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, LR.boff, LS.coff,
                                                         cnt1, ucount);
   PJ_CK(cudaGetLastError());
@@ -313,10 +313,20 @@ static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int6
   const int64_t worst = n * bR * bS;
   UnitCount uc{-1, ucount};
   int64_t cap = tiles_cap;
-  if (worst <= tiles_cap || (grow && (size_t)worst * sizeof(Tile) <= UNIT_BUDGET_BYTES)) {
+  if (worst <= tiles_cap || (grow && (size_t)worst * sizeof(Tile) <= ctx->unit_budget)) {
     if (worst > tiles_cap) {
       *tiles_io = (Tile*)ws_get(ctx, WS_TILES, worst * sizeof(Tile), st);
       cap = worst;
+    }
+  } else if (grow && sp.rerun_ok && ctx->trial_unit_cap == 0) {
+    // the worst case does not fit: emit into the buffer as it is (at least
+    // the budget); an overflow is flagged, the join records the count it
+    // needed, grows the buffer and runs again (so after the first joins of
+    // a workload no step pays for a counting pass and a synchronization)
+    const int64_t floor_units = (int64_t)(ctx->unit_budget / sizeof(Tile));
+    if (tiles_cap < floor_units) {
+      *tiles_io = (Tile*)ws_get(ctx, WS_TILES, floor_units * sizeof(Tile), st);
+      cap = floor_units;
     }
   } else {
     // the worst case does not fit: count first, then size the buffer
@@ -329,6 +339,7 @@ static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int6
     PJ_CK(cudaStreamSynchronize(st));
     uc.count = total;
     if (total == 0) return uc;
+    if (ctx->trial_unit_cap > 0 && total > ctx->trial_unit_cap) throw TrialTooLarge{total};
     if (total > tiles_cap) {
       if (!grow) throw ApiError{PJ_EINVAL, "refinement units above the scratch capacity"};
       *tiles_io = (Tile*)ws_get(ctx, WS_TILES, total * sizeof(Tile), st);
@@ -423,6 +434,8 @@ struct MaskArgs {
   Tile* out;
   int64_t* n_out;
   unsigned long long* nculled;
+  int64_t tiles_cap;               // units the tile array holds
+  unsigned long long* units_max;   // largest device unit count seen (may be null)
 };
 
 template <class T>
@@ -432,7 +445,7 @@ __global__ void __launch_bounds__(256) k_unit_masks(MaskArgs m) {
   const int lane = threadIdx.x & 31;
   T4* sb = sball[threadIdx.x >> 5];
   const unsigned FULLM = 0xffffffffu;
-  const int64_t NT = m.n_tiles_dev ? *m.n_tiles_dev : m.n_tiles;
+  const int64_t NT = launch_units(m.n_tiles_dev, m.n_tiles, m.tiles_cap, m.units_max);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long culled = 0;
   Tile keep;            // lane k: the k-th kept unit not yet written
@@ -569,6 +582,8 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
   a.exact_cross = sp.exact_cross ? 1 : 0;
   a.cull = sp.cull ? 1 : 0;
   a.masked = 0;
+  a.tiles_cap = (int64_t)(ctx->ws[WS_TILES].cap / sizeof(Tile));
+  a.units_max = ctx->d_counters + CNT_UNITS_MAX;
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev], st));
   int64_t n_run = n_tiles;
   if (sp.full && (!sp.fp64 || sp.cull)) {
@@ -578,17 +593,37 @@ int run_refine(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount units, c
     int64_t* n_out = (int64_t*)(ctx->d_counters + 13);
     PJ_CK(cudaMemsetAsync(n_out, 0, sizeof(int64_t), st));
     MaskArgs m{(Tile*)ctx->ws[WS_TILES].p, a.n_tiles, a.n_tiles_dev, a.facR, a.facS, a.origin, a.thr, a.ub_prev,
-               a.cull, out, n_out, a.nculled};
+               a.cull, out, n_out, a.nculled, a.tiles_cap, a.units_max};
     launch_masks(ctx, m, n_tiles, sp.fp64, st);
     a.tiles = out;
     a.n_tiles = -1;
     a.n_tiles_dev = n_out;
     a.masked = 1;
+    a.tiles_cap = (int64_t)(ctx->ws[WS_TILES2].cap / sizeof(Tile));
     n_run = -1;
   }
   dispatch_refine(ctx, a, n_run, sp, st);
   if (ev >= 0) PJ_CK(cudaEventRecord(ctx->ev[ev + 1], st));
   return ev;
+}
+
+// After a join's final synchronization: was a unit buffer too small?  Then
+// the join's results are void; UnitsOverflow asks for a rerun with the
+// buffer grown to the largest count a step needed.
+void check_units(pj_ctx* ctx, int herr) {
+  if (!(herr & ERR_CAPACITY)) return;
+  unsigned long long need = 0;
+  PJ_CK(cudaMemcpy(&need, ctx->d_counters + CNT_UNITS_MAX, sizeof need, cudaMemcpyDeviceToHost));
+  const int64_t have = (int64_t)(ctx->ws[WS_TILES].cap / sizeof(Tile));
+  if ((int64_t)need <= have) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
+  throw UnitsOverflow{(int64_t)need};
+}
+
+void grow_units(pj_ctx* ctx, int64_t units, cudaStream_t st) {
+  const int64_t want = units + units / 4 + 1024;
+  PJ_CK(cudaStreamSynchronize(st));
+  ws_get(ctx, WS_TILES, (size_t)want * sizeof(Tile), st);
+  ws_get(ctx, WS_TILES2, (size_t)want * sizeof(Tile), st);
 }
 
 // ------------------------------------------------------------------ explicit buffers
@@ -652,10 +687,12 @@ void run_refine_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, UnitCount un
   a.exact_cross = sp.exact_cross ? 1 : 0;
   a.cull = sp.cull ? 1 : 0;
   a.masked = 0;
+  a.tiles_cap = b.tiles_cap;
+  a.units_max = nullptr;
   if (sp.full && (!sp.fp64 || sp.cull)) {
     // per-unit s masks in place (no buffer to compact into)
     MaskArgs m{b.tiles, a.n_tiles, a.n_tiles_dev, a.facR, a.facS, a.origin, a.thr, a.ub_prev, a.cull, nullptr,
-               nullptr, nullptr};
+               nullptr, nullptr, b.tiles_cap, nullptr};
     launch_masks(ctx, m, n_tiles, sp.fp64, st);
     a.masked = 1;
   }

@@ -166,6 +166,7 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     b.queue = reinterpret_cast<int4*>(base + OFF_QUEUE);
     b.flag = nullptr;
     b.qcap = (unsigned)MAXQ;
+    b.tiles_cap = MAXT;
     StepSpec sp;
     sp.lodR = lod;
     sp.lodS = lod;

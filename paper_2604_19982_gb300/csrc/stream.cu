@@ -426,9 +426,21 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     float4* fac = (float4*)ws_get(ctx, si ? WS_STREAM6 : WS_STREAM, fac_n * sizeof(float4), bst);
     float4* box = (float4*)ws_get(ctx, si ? WS_STREAM7 : WS_STREAM2, box_n * sizeof(float4), bst);
     const size_t box_bytes = (size_t)std::max(1, P.n) * 24;
-    unsigned char* mb = (unsigned char*)ws_get(ctx, si ? WS_STREAM8 : WS_STREAM3, box_bytes + 16, bst);
+    // the finer LoDs (most of the facets) are laid out on demand, for the
+    // objects whose pairs reach a step that uses them; layout of this
+    // buffer: boxes, error word, per lazy LoD the objects' states, the
+    // list of objects to build and its count
+    const int lazy_from = P.L >= 2 ? 1 : P.L;
+    const size_t nl = (size_t)(P.L - lazy_from), no = (size_t)std::max(1, P.n);
+    const size_t state_bytes = ((nl * no * 4) + 15) & ~size_t(15);
+    unsigned char* mb = (unsigned char*)ws_get(ctx, si ? WS_STREAM8 : WS_STREAM3,
+                                               box_bytes + 16 + state_bytes + no * 4 + 16, bst);
     view.mbb = (float*)mb;
     int* err = (int*)(mb + box_bytes);
+    view.lazy_from = lazy_from;
+    view.lazy_state = nl ? (unsigned*)(mb + box_bytes + 16) : nullptr;
+    view.lazy_list = (int32_t*)(mb + box_bytes + 16 + state_bytes);
+    view.lazy_count = (unsigned*)(mb + box_bytes + 16 + state_bytes + no * 4);
     view.anchor = P.d_anchor ? (float*)P.d_anchor : (float*)(dev + P.o_anchor);
     RawLod raw[PJ_MAX_LODS];
     for (int l = 0; l < P.L; ++l) {
@@ -460,9 +472,13 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       PJ_CK(cudaHostAlloc(&ctx->stream_box_pinned[si], box_bytes + 16, cudaHostAllocDefault));
       ctx->stream_box_cap[si] = box_bytes + 16;
     }
+    for (int l = lazy_from; l < P.L; ++l) view.lazy_raw[l] = raw[l];
     PJ_CK(cudaStreamWaitEvent(bst, slots[si].copied, 0));
     PJ_CK(cudaMemsetAsync(err, 0, sizeof(int), bst));
-    build_set_kernels(ctx, &view, raw, bst, err);
+    if (nl) PJ_CK(cudaMemsetAsync(view.lazy_state, 0, nl * no * 4, bst));
+    build_set_kernels(ctx, &view, raw, bst, err, lazy_from);
+    // the learned start LoD reads every pair's hd / ph maxima per LoD
+    for (int l = lazy_from; l < P.L - 1; ++l) chunk_hd_ph(ctx, &view, l, raw[l], bst);
     PJ_CK(cudaMemcpyAsync(ctx->stream_box_pinned[si], mb, box_bytes + sizeof(int), cudaMemcpyDeviceToHost, bst));
     PJ_CK(cudaEventRecord(built[si], bst));
     prepared[si] = c;
@@ -473,6 +489,24 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   std::vector<uint8_t> ex;
   JoinSummary tot;
   int64_t objects = 0;
+  // the chunk joins run on the context's greatest-priority stream, after
+  // whatever the caller queued on st, so that their many small launches are
+  // scheduled ahead of the next chunk's set building
+  const cudaStream_t caller = st;
+  st = ctx->join_stream;
+  struct Rejoin {
+    cudaStream_t from, to;
+    cudaEvent_t e = nullptr;
+    Rejoin(cudaStream_t a, cudaStream_t b) : from(a), to(b) {
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(e, from) == cudaSuccess)
+        cudaStreamWaitEvent(to, e, 0);
+    }
+    ~Rejoin() {
+      // on every exit the caller's stream waits for the chunk joins
+      if (e && cudaEventRecord(e, to) == cudaSuccess) cudaStreamWaitEvent(from, e, 0);
+      if (e) cudaEventDestroy(e);
+    }
+  } rejoin(caller, st);
   for (int c = 0; c < N; ++c) {
     if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
     if (enqueued <= c) {

@@ -77,21 +77,29 @@ void store(pj_ctx* ctx, const std::string& key, const Choice& c) {
   }
 }
 
+// A trial that needs more refinement units in one step than this is far
+// slower than the alternatives (e.g. starting blobs against long tubes at
+// full resolution): it is abandoned at the unit count, before any refinement.
+constexpr int64_t TRIAL_UNIT_CAP = int64_t(1) << 26;
+
 pj_status run_with(pj_ctx* ctx, const Choice& c, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
-                   cudaStream_t st, std::string& stats) {
+                   cudaStream_t st, std::string& stats, int64_t unit_cap = 0) {
   const int v0 = ctx->refine_variant, s0 = ctx->sched_start;
   ctx->refine_variant = c.variant;
   ctx->sched_start = c.start;
+  ctx->trial_unit_cap = unit_cap;
   pj_status rc;
   try {
     rc = q->pred == PJ_KNN ? join_knn(ctx, R, S, q, out, st, stats) : join_within(ctx, R, S, q, out, st, stats);
   } catch (...) {
     ctx->refine_variant = v0;
     ctx->sched_start = s0;
+    ctx->trial_unit_cap = 0;
     throw;
   }
   ctx->refine_variant = v0;
   ctx->sched_start = s0;
+  ctx->trial_unit_cap = 0;
   return rc;
 }
 
@@ -149,14 +157,24 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
     memset(&res, 0, sizeof res);
     std::string st_i;
     Timer t;
-    pj_status rc = run_with(ctx, cand[i], R, S, q, &res, st, st_i);
+    pj_status rc;
+    char buf[128];
+    try {
+      // the first candidate (the warmed one) always completes
+      rc = run_with(ctx, cand[i], R, S, q, &res, st, st_i, i ? TRIAL_UNIT_CAP : 0);
+    } catch (const TrialTooLarge& e) {
+      PJ_CK(cudaStreamSynchronize(st));
+      snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"skipped_units\":%lld}", i ? "," : "",
+               cand[i].variant, cand[i].start, (long long)e.units);
+      tried += buf;
+      continue;
+    }
     const double ms = t.ms();
     if (rc != PJ_OK) {
       free(res.priv);
       free(keep.priv);
       return rc;
     }
-    char buf[96];
     snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"ms\":%.3f}", i ? "," : "", cand[i].variant,
              cand[i].start, ms);
     tried += buf;

@@ -150,3 +150,29 @@ def test_full_size_tubes2k_sampled(ctx):
     check_pairs(b, w.R, w.S, TAU, 6, 2)
     gR.free()
     gS.free()
+
+
+def test_unit_buffer_overflow_reruns_with_equal_results():
+    """With a unit budget of 1 MB (32,768 units), tube joins overflow the
+    unit buffer; the join grows it to the count needed and runs again: the
+    results equal those of a context with the default budget."""
+    from paper_2604_19982_gb300 import pj
+    R = configs.tube_set(80, 300.0, 3, 0, length_range=(50.0, 200.0))
+    S = configs.blob_set(6000, 300.0, 3, 1)
+    out = []
+    for opts in ({}, {"unit_budget_mb": 1}):
+        c = pj.Context(0, opts)
+        gR, gS = c.load_set(R), c.load_set(S)
+        # no unit pruning: every block pair of a candidate is a unit, so the
+        # coarse step needs far more than the small budget's 32,768 units
+        res = c.join(gR, gS, pj.WITHIN, tau=2.0, prec=pj.FP32, flags=0)
+        again = c.join(gR, gS, pj.WITHIN, tau=2.0, prec=pj.FP32, flags=0)
+        out.append((res, again, c.stats()))
+        c.close()
+    (a, _, _), (b, b2, st) = out
+    assert a.n > 0
+    for x in (b, b2):
+        assert x.pairs() == a.pairs()
+        assert np.array_equal(x.d_lo, a.d_lo) and np.array_equal(x.d_hi, a.d_hi)
+    # the small budget was really exceeded at some step
+    assert max(x["tiles"] for x in st["steps"]) > 32768
