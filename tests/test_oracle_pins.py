@@ -368,6 +368,45 @@ def test_tube_hausdorff_by_sampling():
                 assert oracle.point_mesh_dist(p, fine) <= hd[f] + 1e-9
 
 
+def _ph_gap(p, coarse, ph, near=None):
+    """min over coarse facets f of (distance(p, f) - ph[f]); with `near`,
+    over the `near` facets with the closest centroids only."""
+    fs = range(coarse.shape[0])
+    if near is not None:
+        c = coarse.mean(axis=1)
+        fs = np.argsort(((c - p) ** 2).sum(1))[:near]
+    return min(oracle.point_tri_dist(p, coarse[f]) - ph[f] for f in fs)
+
+
+def test_tube_ph_by_sampling():
+    """ph: every point of the original tube surface lies within ph(f') of
+    some coarse facet f' (the Eq. 2 direction), checked on fine vertices
+    and on points inside fine facets, against the coarse facets nearest to
+    each point (the facet whose patch holds the point is among them)."""
+    T = configs.tube_set(1, 50.0, 4, 0)
+    fine = T.triangles(T.n_lods - 1, 0).astype(np.float64)
+    rng = np.random.default_rng(7)
+    pick = rng.choice(fine.shape[0], 80, replace=False)
+    w = rng.dirichlet((1.0, 1.0, 1.0), size=80)
+    pts = np.vstack([fine.reshape(-1, 3)[::17], np.einsum("ij,ijk->ik", w, fine[pick])])
+    for lod in (0, 1):
+        coarse = T.triangles(lod, 0).astype(np.float64)
+        ph = T.ph_of(lod, 0).astype(np.float64)
+        for p in pts:
+            assert _ph_gap(p, coarse, ph, near=12) <= 1e-9, (lod, p)
+
+
+def test_tube_ph_catches_a_shrunk_bound():
+    """The same check over all coarse facets fails once ph is halved (the
+    pin is not vacuous)."""
+    T = configs.tube_set(1, 50.0, 4, 0)
+    fine = T.triangles(T.n_lods - 1, 0).astype(np.float64).reshape(-1, 3)
+    coarse = T.triangles(0, 0).astype(np.float64)
+    ph = T.ph_of(0, 0).astype(np.float64) * 0.5
+    pts = fine[np.random.default_rng(8).choice(fine.shape[0], 30, replace=False)]
+    assert sum(_ph_gap(p, coarse, ph) > 1e-9 for p in pts) > 0
+
+
 # ---------------------------------------------------------------- Alg 6
 
 
