@@ -500,6 +500,19 @@ def stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32):
         gRp.free()
         gRp._cb = gRp._keep = None
         pin_chunks.clear()
+        # the pinned host-to-device copy rate of this machine: 1 GiB, best of 5
+        h = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+        dd = torch.empty_like(h, device="cuda")
+        best = 0.0
+        for _ in range(5):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            dd.copy_(h, non_blocking=True)
+            a1.record()
+            torch.cuda.synchronize()
+            best = max(best, h.numel() * 4 / (a0.elapsed_time(a1) / 1000.0) / 1e9)
+        e2e["h2d_peak_gbs"] = best
+        del h, dd
 
     plain = None
     if not args.no_plain:
@@ -682,12 +695,17 @@ def ours_arm(args):
                 "tri_tests_per_s": rec["tri_tests_per_s"], "plain": rec.get("plain"),
                 "speedup_vs_plain": rec.get("speedup_vs_plain"), "roofline": rec["roofline"], "e2e": None,
                 "gpu_launches": None, "clocks": clk}
+    ctx.close()
     if not args.no_sub:
+        # each workload in a context of its own (workspace, graphs and tuned
+        # choices of one workload do not weigh on the next)
         subs = {}
         for name, fn in SUB_RECORDS.items():
             if name == args.workload:
                 continue
-            subs[name] = fn(args, data, ctx, pj, stream, nsm, measured32, max(1, min(args.steps, 5)))
+            c = pj.Context(local, opts)
+            subs[name] = fn(args, data, c, pj, stream, nsm, measured32, max(1, min(args.steps, 5)))
+            c.close()
         line["configs"] = subs
     if cpu_sample is not None:
         Rs, Ss, pairs, sample = cpu_sample
@@ -696,7 +714,6 @@ def ours_arm(args):
                                 "sample": sample + f", {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
