@@ -103,17 +103,3 @@ def test_knn_gmm_clusters(ctx):
         check_knn(res, R, S, 3, rlist=np.sort(rl))
     gR.free()
     gS.free()
-
-
-def test_knn_full_size_sampled(ctx):
-    """The k-NN workload at full size: 50,000 x 50,000 sub-3 blobs from a
-    20-cluster mixture, k = 3; all neighbours of sampled objects r."""
-    from paper_2604_19982_gb300 import pj
-    w = configs.knn50k()
-    gR, gS = ctx.load_set(w.R), ctx.load_set(w.S)
-    res = ctx.join(gR, gS, pj.KNN, k=3, prec=pj.FP32, flags=pj.TILE_PRUNE)
-    assert res.n == 3 * w.R.n
-    rl = np.sort(np.random.default_rng(2).choice(w.R.n, 16, replace=False))
-    check_knn(res, w.R, w.S, 3, rlist=rl)
-    gR.free()
-    gS.free()
