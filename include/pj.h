@@ -62,9 +62,12 @@ enum {
   PJ_EXACT_DIST = 1,   /* refine every result pair to its exact FP64 distance  */
   PJ_USE_MLP = 2,      /* learned proposal: order k-NN work, pick start LoD    */
   PJ_USE_GRAPH = 4,    /* replay the per-LoD launch sequence from a CUDA graph */
-  PJ_AUTOTUNE = 8,     /* time the FP32 refinement variant and the LoD start step
-                          on the first join of a workload, keep the fastest
-                          (cached per context and in "autotune_cache") */
+  PJ_AUTOTUNE = 8,     /* time the FP32 refinement variant (tests per lane) and
+                          the LoD start step, then the unit tile (32 r facets
+                          x 32, 16 or 8 s facets), on the first join of a
+                          workload, keep the fastest (cached per context and
+                          in "autotune_cache"; the choices and the timed
+                          trials are in the join's stats under "autotune") */
   PJ_TILE_PRUNE = 16   /* skip facet tiles/blocks that cannot change a decision */
 };
 
@@ -148,7 +151,8 @@ typedef struct {
  * 1 = never; anything else gives PJ_EINVAL; parts restart the facet-ball
  * culling bound, so splitting pays only when launches are tail-bound),
  * "refine_tail" (0..64, default 2: how many units per resident warp are
- * split), "zero_copy" (0, the default, or 1: pj_load_set reads the arrays
+ * split; when either of the two is given, PJ_AUTOTUNE keeps them and does
+ * not tune the tile), "zero_copy" (0, the default, or 1: pj_load_set reads the arrays
  * that live in pinned, mapped host memory in place over the host link
  * instead of staging them, other arrays are copied as usual),
  * "unit_budget_mb" (1 .. 2^20, default 512: the refinement-unit buffer is

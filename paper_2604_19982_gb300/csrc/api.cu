@@ -329,27 +329,40 @@ void ensure_lod(pj_ctx* ctx, const pj_set* R, int lod, int64_t n_pairs, const in
 }
 
 // One thread per chunk: the maxima of hd and ph over its facets.
-__global__ void k_chunk_hd_ph(int64_t C, int n, const int64_t* coff, const int64_t* foff, const float* hd,
-                              const float* ph, float4* chunk) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  const int64_t o = upper_obj(coff, n, c);
-  const int64_t f0 = foff[o] + (c - coff[o]) * CHUNK, f1 = min(f0 + CHUNK, foff[o + 1]);
-  float mh = 0.f, mp = 0.f;
-  for (int64_t f = f0; f < f1; ++f) {
-    if (hd) mh = fmaxf(mh, hd[f]);
-    if (ph) mp = fmaxf(mp, ph[f]);
+// Max hd / ph of each 256-facet chunk: one warp per object walks its
+// chunks (no search for the owning object), the lanes read a chunk's
+// facets in consecutive runs and reduce by shuffles.
+__global__ void k_chunk_hd_ph(int n, const int64_t* coff, const int64_t* foff, const float* hd, const float* ph,
+                              float4* chunk) {
+  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= n) return;   // warp-uniform
+  const int64_t fo = foff[o], fe = foff[o + 1];
+  for (int64_t c = coff[o]; c < coff[o + 1]; ++c) {
+    const int64_t f0 = fo + (c - coff[o]) * CHUNK, f1 = min(f0 + CHUNK, fe);
+    float mh = 0.f, mp = 0.f;
+    for (int64_t f = f0 + lane; f < f1; f += 32) {
+      if (hd) mh = fmaxf(mh, hd[f]);
+      if (ph) mp = fmaxf(mp, ph[f]);
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) {
+      mh = fmaxf(mh, __shfl_xor_sync(0xffffffffu, mh, k));
+      mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, k));
+    }
+    if (lane == 0) {
+      chunk[3 * c].w = mh;
+      chunk[3 * c + 1].w = mp;
+    }
   }
-  chunk[3 * c].w = mh;
-  chunk[3 * c + 1].w = mp;
 }
 
 void chunk_hd_ph(pj_ctx* ctx, pj_set* s, int l, const RawLod& raw, cudaStream_t st) {
   const LodData& ld = s->lod[l];
-  if (ld.C == 0) return;
+  if (ld.C == 0 || s->n == 0) return;
   const int th = 256;
-  k_chunk_hd_ph<<<(unsigned)((ld.C + th - 1) / th), th, 0, st>>>(ld.C, s->n, ld.coff, ld.foff, raw.hd, raw.ph,
-                                                                 ld.chunk);
+  k_chunk_hd_ph<<<(unsigned)(((int64_t)s->n * 32 + th - 1) / th), th, 0, st>>>(s->n, ld.coff, ld.foff, raw.hd,
+                                                                                raw.ph, ld.chunk);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
@@ -597,6 +610,7 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
       return PJ_EINVAL;
     }
     ctx->refine_split = k;
+    ctx->split_fixed = true;
   }
   v = json_str(options_json, "zero_copy");
   if (!v.empty()) ctx->zero_copy = atoi(v.c_str()) != 0;
@@ -608,6 +622,7 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
       return PJ_EINVAL;
     }
     ctx->refine_tail = t;
+    ctx->split_fixed = true;
   }
   v = json_str(options_json, "unit_budget_mb");
   if (!v.empty()) {
@@ -643,6 +658,7 @@ void pj_destroy(pj_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   graphs_clear(ctx);
+  destroy_pack_pool(ctx->pack_pool);
   for (auto& b : ctx->ws) cudaFree(b.p);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_counters);

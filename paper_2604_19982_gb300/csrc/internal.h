@@ -148,6 +148,11 @@ struct pj_set {
   void* user = nullptr;
 };
 
+namespace pj {
+class PackPool;   // host threads that pack streamed chunks (stream.cu)
+void destroy_pack_pool(pj::PackPool* p);
+}  // namespace pj
+
 struct pj_ctx {
   int device = 0;
   int sm_count = 0;
@@ -185,6 +190,7 @@ struct pj_ctx {
   bool zero_copy = false;          // pj_load_set reads pinned host arrays in place (no staging copy)
   int refine_split = 1;            // the last units of a refinement launch are split this many ways
   int refine_tail = 2;             // ... that many units per resident warp
+  bool split_fixed = false;        // refine_split / refine_tail given at creation: autotuning keeps them
   int sched_start = -1;            // within joins: every pair starts at this LoD step (-1: query's own)
   int64_t trial_unit_cap = 0;      // > 0 while autotuning: a step needing more units abandons the trial
   size_t unit_budget = size_t(512) << 20;   // unit buffer sized for the worst case up to this many bytes
@@ -205,6 +211,7 @@ struct pj_ctx {
   // pinned staging of result copies (grow-only)
   void* h_stage = nullptr;
   size_t h_stage_cap = 0;
+  pj::PackPool* pack_pool = nullptr;   // created by the first streamed join, kept until pj_destroy
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};
   void* stream_box_pinned[2] = {};  // pinned copies of a chunk's object boxes and error word
@@ -309,7 +316,10 @@ struct StepLog : StepLogData {
   // Record one refinement step (after run_refine on `st`).
   void add(pj_ctx* ctx, const UnitCount& uc, int event, const StepSpec& sp, cudaStream_t st);
   // JSON array of the steps; also sums refinement ms per precision and units.
-  std::string json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total) const;
+  // host_snap: the step snapshots already copied to the host (else read
+  // from the device here)
+  std::string json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total,
+                   const long long* host_snap = nullptr) const;
 };
 // Pair-setup: origin (pair-local frame), box MINDIST, anchor distance.
 // n_live (device, may be null): pairs at or past *n_live are padding of a
@@ -335,10 +345,7 @@ struct PairBufs {
   void* lb;
   void* ub;
   void* mid;
-  int64_t* tcount;   // [n+1] builder work items per pair
-  int64_t* toff;     // [n+1]
   int64_t* ucount;   // [1] unit counter of the builder
-  int64_t* scan_tmp; // scan temporaries (nullptr: allocate)
   int* err;          // device error word
   Tile* tiles;
   unsigned long long* counters;  // [3]: tests, tile counter, straddle-queue count
@@ -397,7 +404,10 @@ void tri_dist_batch(pj_ctx* ctx, const float* P, const float* Q, int64_t n, bool
 // ---- MLP (mlp.cu)
 void mlp_forward(pj_ctx* ctx, const float* feats, int64_t n, float* out, cudaStream_t st);
 // Predicted log1p(d) of the candidate pairs in WS_PR / WS_PS (into WS_PRED).
-const float* propose(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, cudaStream_t st);
+// n_live: the live pair count of a fixed-capacity (graph) join, rows at or
+// beyond it are padding (nullptr: all n rows are pairs)
+const float* propose(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, cudaStream_t st,
+                     const int64_t* n_live = nullptr);
 // lod0 of the undecided pairs from the predictions (within-tau start LoD).
 void start_lod(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const float* pred, double tau,
                cudaStream_t st);
@@ -406,7 +416,7 @@ void start_lod(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const f
 constexpr float PRED_BAND = 0.15f;
 constexpr float START_MARGIN = 0.5f;
 void pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
-                   int64_t n, float* out, cudaStream_t st);
+                   int64_t n, float* out, cudaStream_t st, const int64_t* n_live = nullptr);
 
 // Device and pinned-host allocations made by the library (all contexts of
 // the process), reported by pj_get_stats as "allocs": lets a caller check

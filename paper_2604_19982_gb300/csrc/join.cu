@@ -304,6 +304,14 @@ static void* stage(pj_ctx* ctx, size_t bytes) {
   return ctx->h_stage;
 }
 
+// Status block behind the results in the pinned stage: the error word, the
+// join counters and the per-step snapshots, copied in stream order after
+// the last kernel so that one synchronization makes all of it readable.
+constexpr size_t RES_PER = 4 + 4 + 8 + 8 + 8 + 1;
+constexpr size_t STATUS_ERR = 0, STATUS_CNT = 64, STATUS_SNAP = 256;
+constexpr size_t STATUS_BYTES = STATUS_SNAP + sizeof(long long) * 4 * StepLog::MAX;
+static size_t status_at(int64_t n) { return ((size_t)n * RES_PER + 8 + 255) & ~size_t(255); }
+
 void gather_device(pj_ctx* ctx, int64_t n, cudaStream_t st) {
   if (n == 0) return;
   int th = 256;
@@ -330,10 +338,21 @@ void gather_device(pj_ctx* ctx, int64_t n, cudaStream_t st) {
                               (const double*)ctx->ws[WS_D].p, (const uint8_t*)ctx->ws[WS_EXACT].p, pk);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  char* h = (char*)stage(ctx, (size_t)n * per + 64);
+  char* h = (char*)stage(ctx, status_at(n) + STATUS_BYTES);
   PJ_CK(cudaMemcpyAsync(h, dev, (size_t)n * per, cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaMemcpyAsync(h + (size_t)n * per, off + n, 8, cudaMemcpyDeviceToHost, st));
 }
+
+void stage_status(pj_ctx* ctx, int64_t n, int steps, cudaStream_t st) {
+  char* h = (char*)stage(ctx, status_at(n) + STATUS_BYTES) + status_at(n);
+  PJ_CK(cudaMemcpyAsync(h + STATUS_ERR, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaMemcpyAsync(h + STATUS_CNT, ctx->d_counters, 15 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        st));
+  if (steps > 0)
+    PJ_CK(cudaMemcpyAsync(h + STATUS_SNAP, ctx->d_snap, sizeof(long long) * 4 * steps, cudaMemcpyDeviceToHost, st));
+}
+
+const char* staged_status(pj_ctx* ctx, int64_t n) { return (const char*)ctx->h_stage + status_at(n); }
 
 int64_t gather_host(pj_ctx* ctx, int64_t n, pj_result* res) {
   if (n == 0) {
@@ -380,9 +399,11 @@ void StepLog::add(pj_ctx* ctx, const UnitCount& uc, int event, const StepSpec& s
   ++n;
 }
 
-std::string StepLog::json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total) const {
+std::string StepLog::json(pj_ctx* ctx, double* ms32, double* ms64, int64_t* units_total,
+                          const long long* host_snap) const {
   long long snap[MAX * 4];
-  if (n) PJ_CK(cudaMemcpy(snap, ctx->d_snap, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost));
+  if (n && host_snap) memcpy(snap, host_snap, sizeof(long long) * 4 * n);
+  else if (n) PJ_CK(cudaMemcpy(snap, ctx->d_snap, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost));
   std::string out = "[";
   long long prev32 = 0, prev64 = 0;
   *ms32 = *ms64 = 0;
@@ -452,6 +473,7 @@ static std::string graph_key(pj_ctx* ctx, const pj_set* R, const pj_set* S, cons
     h = fnv(h, &ctx->ws[i].cap, sizeof(size_t));
   }
   h = fnv(h, &ctx->h_stage, sizeof(void*));
+  h = fnv(h, &ctx->mlp_w, sizeof(void*));   // the proposal's weights are read in place
   h = fnv(h, &ctx->h_stage_cap, sizeof(size_t));
   const int knobs[5] = {ctx->refine_variant, ctx->sched_start, ctx->ctas_per_sm, ctx->refine_split, ctx->refine_tail};
   h = fnv(h, knobs, sizeof knobs);
@@ -482,6 +504,8 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   const bool cull = (q->flags & PJ_TILE_PRUNE) != 0;
   const bool use_mlp = (q->flags & PJ_USE_MLP) != 0;
   if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
+  // the learned per-pair start, unless the autotuner fixed the schedule
+  const bool learned = use_mlp && ctx->sched_start < 0;
   PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
   PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   Timer tf;
@@ -490,20 +514,15 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   const int Lmax = std::max(R->L, S->L);
   auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
 
-  // fixed-capacity graph mode: not with the learned start (its features
-  // read every pair id), nor when a step would have to size its unit buffer
-  // on the host, nor on the legacy default stream
-  bool graph = (q->flags & PJ_USE_GRAPH) && !use_mlp && n > 0 && st != nullptr;
+  // fixed-capacity graph mode: not on the legacy default stream, nor in an
+  // autotuning trial (whose steps count their units on the host first).  A
+  // replay whose units overflow the buffer of the capture flags the join,
+  // which runs again directly with a grown buffer (and a new graph).
+  const bool graph = (q->flags & PJ_USE_GRAPH) && n > 0 && st != nullptr && ctx->trial_unit_cap == 0;
   int64_t cap = n;
   if (graph) {
     cap = 256;
     while (cap < n) cap <<= 1;
-    for (int l = 0; l < Lmax && graph; ++l) {
-      const int lr = std::max(0, l - (Lmax - R->L)), ls = std::max(0, l - (Lmax - S->L));
-      const int64_t worst = cap * ((R->lod[lr].maxF + BLK - 1) / BLK) * ((S->lod[ls].maxF + BLK - 1) / BLK);
-      if ((size_t)worst * sizeof(Tile) > ctx->unit_budget) graph = false;
-    }
-    if (!graph) cap = n;
   }
   const int64_t nn = cap;
   const int64_t* n_live = graph ? (const int64_t*)ctx->ws[WS_ROFF].p + R->n : nullptr;
@@ -511,7 +530,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   // the whole device sequence after the filter; false on an expired deadline
   auto enqueue = [&](StepLog& log) -> bool {
     setup_pairs(ctx, R, S, nn, tau, true, st, n_live);
-    if (use_mlp) start_lod(ctx, R, S, nn, propose(ctx, R, S, nn, st), tau, st);
+    if (learned) start_lod(ctx, R, S, nn, propose(ctx, R, S, nn, st, n_live), tau, st);
     if (ctx->sched_start > 0) {
       // autotuned schedule: no pair is refined before this step
       int th = 256;
@@ -523,7 +542,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
     ctx->ev_used = 0;
     // with a fixed start step (autotuned schedule, no learned start) the
     // steps before it select no pair: they are not enqueued at all
-    const int first = (ctx->sched_start > 0 && !use_mlp) ? std::min(ctx->sched_start, Lmax - 1) : 0;
+    const int first = ctx->sched_start > 0 ? std::min(ctx->sched_start, Lmax - 1) : 0;
     for (int step = first; step < Lmax; ++step) {
       if (deadline_hit()) return false;
       StepSpec sp;
@@ -588,6 +607,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
       log.add(ctx, uc, ev, sp, st);
     }
     gather_device(ctx, nn, st);
+    stage_status(ctx, nn, log.n, st);
     return true;
   };
 
@@ -616,23 +636,28 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   } else {
     ms_filter = tf.ms();
   }
-  {
-    // a step whose units overflowed the buffer voids the join (rerun)
-    int e0 = 0;
-    PJ_CK(cudaMemcpyAsync(&e0, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // after the synchronization the error word, the counters and the step
+  // snapshots are in the pinned stage (with candidates; else read here)
+  int herr = 0;
+  unsigned long long cnt[8];
+  const long long* snap = nullptr;
+  if (nn > 0) {
+    const char* h = staged_status(ctx, nn);
+    memcpy(&herr, h + STATUS_ERR, sizeof(int));
+    memcpy(cnt, h + STATUS_CNT, sizeof cnt);
+    snap = (const long long*)(h + STATUS_SNAP);
+  } else {
+    PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
     PJ_CK(cudaStreamSynchronize(st));
-    check_units(ctx, e0);
   }
+  // a step whose units overflowed the buffer voids the join (rerun)
+  check_units(ctx, herr);
   Timer tg;
   const int64_t m = gather_host(ctx, nn, out);
-  // after the synchronization everything is readable
-  int herr = 0;
-  PJ_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  unsigned long long cnt[8];
-  PJ_CK(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
   double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
   int64_t tiles_total = 0;
-  const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total);
+  const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total, snap);
   float graph_ms = 0.f;
   if (!strcmp(gmode, "replay")) PJ_CK(cudaEventElapsedTime(&graph_ms, ctx->ev[60], ctx->ev[61]));
   char buf[1500];
@@ -644,7 +669,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
            "\"removed\":%llu,\"redecide\":%llu,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
-           tau, fp64 ? "fp64" : "fp32", use_mlp ? 1 : 0, gmode, graph_ms, (long long)nn, (long long)n, (long long)m,
+           tau, fp64 ? "fp64" : "fp32", learned ? 1 : 0, gmode, graph_ms, (long long)nn, (long long)n, (long long)m,
            cnt[0],
            cnt[1], cnt[5], cnt[6], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
            ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);

@@ -387,9 +387,13 @@ __global__ void k_adam(float* w, float* m, float* v, const float* g, float lr, f
 __global__ void k_pair_features(int64_t n, const int32_t* pr, const int32_t* ps, const float* mbbR, const float* mbbS,
                                 const float* ancR, const float* ancS, const float4* chR, const int64_t* coffR,
                                 const float4* chS, const int64_t* coffS, const int64_t* foffR, const int64_t* foffS,
-                                float* out) {
+                                float* out, const int64_t* n_live) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  if (n_live && p >= *n_live) {   // padding of a fixed-capacity (graph) join: no pair ids there
+    for (int k = 0; k < 16; ++k) out[16 * p + k] = 0.f;
+    return;
+  }
   const int r = pr[p], s = ps[p];
   const float* a = mbbR + 6LL * r;
   const float* b = mbbS + 6LL * s;
@@ -446,14 +450,14 @@ __global__ void k_pair_features(int64_t n, const int32_t* pr, const int32_t* ps,
 }
 
 void pair_features(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps, int64_t n,
-                   float* out, cudaStream_t st) {
+                   float* out, cudaStream_t st, const int64_t* n_live) {
   if (n == 0) return;
   const LodData& a = R->lod[0];
   const LodData& b = S->lod[0];
   int th = 128;
   k_pair_features<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, ps, R->mbb, S->mbb, R->anchor, S->anchor,
                                                                 a.chunk, a.coff, b.chunk, b.coff, R->lod[R->L - 1].foff,
-                                                                S->lod[S->L - 1].foff, out);
+                                                                S->lod[S->L - 1].foff, out, n_live);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
 }
@@ -543,10 +547,11 @@ static void mlp_train_dev(pj_ctx* ctx, const float* X, const float* T, int64_t n
 // ------------------------------------------------------------------ proposal
 // The network predicts y = log1p(d) of a candidate pair from its features.
 
-const float* propose(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, cudaStream_t st) {
+const float* propose(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, cudaStream_t st,
+                     const int64_t* n_live) {
   float* X = (float*)ws_get(ctx, WS_FEAT, (size_t)n * 64, st);
   float* y = (float*)ws_get(ctx, WS_PRED, (size_t)n * 4, st);
-  pair_features(ctx, R, S, (const int32_t*)ctx->ws[WS_PR].p, (const int32_t*)ctx->ws[WS_PS].p, n, X, st);
+  pair_features(ctx, R, S, (const int32_t*)ctx->ws[WS_PR].p, (const int32_t*)ctx->ws[WS_PS].p, n, X, st, n_live);
   mlp_forward(ctx, X, n, y, st);
   return y;
 }

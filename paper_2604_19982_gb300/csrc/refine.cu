@@ -2,7 +2,7 @@
 // re-designed for sm_103a:
 //  * unit = one 32-facet block of r x one 32-facet block of s of one
 //    candidate pair at one LoD (replaces the paper's thread block per voxel
-//    pair); units are built on the device (k_items / k_emit_units) and
+//    pair); units are built on the device (k_emit_units, a warp per pair) and
 //    consumed by a persistent kernel, one launch per LoD step;
 //  * every warp works alone through a pipeline of its own: units are claimed
 //    ahead (the first two by warp index, dealt across the SMs), a unit's tile
@@ -109,12 +109,16 @@ void setup_pairs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, doubl
 
 // ------------------------------------------------------------------ units
 // A refinement unit is one 32-facet block of r x one 32-facet block of s of
-// one candidate pair at one LoD.  A work item of the builder is one (pair,
-// r block, 256-facet s chunk): the r block's box is tested against the s
-// chunk's box, then against each of the chunk's (up to 8) s blocks; a box
-// pair whose distance minus the Hausdorff terms exceeds the pair's
-// threshold is skipped (PJ_TILE_PRUNE; without it every block pair is a
-// unit).  The live units of a warp are appended with one atomic add.
+// one candidate pair at one LoD.  The builder takes one warp per selected
+// pair and walks the box hierarchy: the lanes test the pair's (256-facet r
+// chunk, 256-facet s chunk) box pairs, and for each live chunk pair the
+// warp tests its (up to 8 x 8) block pairs; a box pair whose distance minus
+// the Hausdorff terms exceeds the pair's threshold is skipped
+// (PJ_TILE_PRUNE; without it every block pair is a unit).  A block box lies
+// inside its chunk's box and the chunk's Hausdorff and shape terms bound the
+// block's, so the chunk test only ever skips block pairs the block test
+// would skip: the units are exactly the live block pairs.  The live units of
+// 32 block-pair tests are appended with one atomic add.
 
 struct BoxView {
   const float4* chunk;   // [3C] chunk boxes
@@ -156,129 +160,98 @@ __device__ __forceinline__ bool box_pair_live(const float4* cr, const float4* cs
   return !(lb > thr);
 }
 
-__device__ __forceinline__ int64_t find_pair(const int64_t* off, int64_t n, int64_t w) {
-  // largest p with off[p] <= w
-  int64_t lo = 0, hi = n;
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (off[mid] <= w) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
 
-// Work items of every selected pair: r blocks x s chunks.  Also clears the
-// unit counter that k_emit_units appends to.
-__global__ void k_items(int64_t n, const int32_t* pr, const int32_t* ps, const uint8_t* status,
-                        const uint8_t* lod0, uint8_t want, int step, const int64_t* boffR, const int64_t* coffS,
-                        int64_t* cnt, int64_t* ucount) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p == 0) *ucount = 0;
-  if (p >= n) return;
-  const bool sel = status[p] == want && lod0[p] <= step;
-  cnt[p] = sel ? (boffR[pr[p] + 1] - boffR[pr[p]]) * (coffS[ps[p] + 1] - coffS[ps[p]]) : 0;
-}
-
-// EMIT = false: only count the live units into *ucount; EMIT = true: also
-// write them (at most cap; more sets ERR_CAPACITY and drops the excess).
-// Work items w < off1[n] (read on the device), walked in warp-uniform
-// strides so the warp-wide append is safe.
+// EMIT = false: only count the live units into *ucount (zeroed by the
+// caller); EMIT = true: also write them (at most cap; more sets
+// ERR_CAPACITY and drops the excess).  The pair loop, the chunk loop and
+// the block loop are warp-uniform, so the ballots are over full warps.
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_emit_units(int64_t n, const int32_t* pr, const int32_t* ps,
-                                                    const int64_t* off1, BoxView R, BoxView S,
-                                                    const float4* origin, const float* thr, int cull, int fp64,
-                                                    Tile* tiles, int64_t cap, int64_t* ucount, int* err) {
-  constexpr int SB = CHUNK / BLK;
-  const int64_t W = off1[n];
+__global__ void __launch_bounds__(256, 4) k_emit_units(int64_t n, const int32_t* pr, const int32_t* ps,
+                                                    const uint8_t* status, const uint8_t* lod0, uint8_t want,
+                                                    int step, BoxView R, BoxView S, const float4* origin,
+                                                    const float* thr, int cull, int fp64, Tile* tiles, int64_t cap,
+                                                    int64_t* ucount, int* err) {
+  constexpr int SB = CHUNK / BLK;   // blocks per chunk
+  constexpr unsigned FULLW = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); w0 < W; w0 += stride) {
-    const int64_t w = w0 + lane;
-    unsigned mask = 0;
-    float eps[SB], eh[SB];
-    int sl[SB];
-    int32_t pair = 0, fr = 0, fs0 = 0;
-    int rl = 0;
-#pragma unroll
-    for (int j = 0; j < SB; ++j) {
-      eps[j] = eh[j] = 0.f;
-      sl[j] = 0;
-    }
-    if (w < W) {
-      const int64_t p = find_pair(off1, n, w);
-      const int r = pr[p], s = ps[p];
-      const int64_t loc = w - off1[p];
-      const int64_t nsc = S.coff[s + 1] - S.coff[s];
-      const int64_t rb = R.boff[r] + loc / nsc;
-      const int64_t sc = S.coff[s] + loc % nsc;
-      const int64_t sb0 = S.boff[s] + (sc - S.coff[s]) * SB;
-      const int nsb = (int)min((int64_t)SB, S.boff[s + 1] - sb0);
-      const float4 o = origin[p];
-      const float t = thr[p];
-      const float4* ba = R.blk + 3 * rb;
-      const int64_t fr64 = R.foff[r] + (rb - R.boff[r]) * BLK;
-      const int64_t fs64 = S.foff[s] + (sb0 - S.boff[s]) * BLK;
-      pair = (int32_t)p;
-      fr = (int32_t)fr64;
-      fs0 = (int32_t)fs64;
-      rl = (int)min((int64_t)BLK, R.foff[r + 1] - fr64);
-      const int64_t send = S.foff[s + 1];
-      bool live = true;
-      if (cull) {
-        const float4* cb = S.chunk + 3 * sc;
-        live = box_pair_live(ba, cb, t, fp64 ? 0.f : box_margins(ba, cb, o).eps);
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
+    if (!(status[p] == want && lod0[p] <= step)) continue;
+    const int r = pr[p], s = ps[p];
+    const float4 o = origin[p];
+    const float t = thr[p];
+    // facet, block and chunk indices are below 2^31 (a LoD holds fewer facets)
+    const int rc0 = (int)R.coff[r], nrc = (int)R.coff[r + 1] - rc0;
+    const int sc0 = (int)S.coff[s], nsc = (int)S.coff[s + 1] - sc0;
+    const int rb0 = (int)R.boff[r], nrbo = (int)R.boff[r + 1] - rb0;
+    const int sbase = (int)S.boff[s], nsbo = (int)S.boff[s + 1] - sbase;
+    const int64_t items = (int64_t)nrc * nsc;   // chunk pairs
+    for (int64_t i0 = 0; i0 < items; i0 += 32) {
+      const int64_t i = i0 + lane;
+      int rc = 0, sc = 0;   // chunk indices within the objects
+      bool live = false;
+      if (i < items) {
+        rc = (int)(i / nsc);
+        sc = (int)(i - (int64_t)rc * nsc);
+        live = true;
+        if (cull) {
+          const float4* ca = R.chunk + 3 * (int64_t)(rc0 + rc);
+          const float4* cb = S.chunk + 3 * (int64_t)(sc0 + sc);
+          live = box_pair_live(ca, cb, t, fp64 ? 0.f : box_margins(ca, cb, o).eps);
+        }
       }
-      if (live) {
-#pragma unroll
-        for (int j = 0; j < SB; ++j) {
-          if (j < nsb) {
-            const float4* bb = S.blk + 3 * (sb0 + j);
+      unsigned lm = __ballot_sync(FULLW, live);
+      while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int crc = __shfl_sync(FULLW, rc, src), csc = __shfl_sync(FULLW, sc, src);
+        const int nrb = min(SB, nrbo - crc * SB), nsb = min(SB, nsbo - csc * SB);
+        const int nbp = nrb * nsb;   // <= 64 block pairs
+        for (int j0 = 0; j0 < nbp; j0 += 32) {
+          const int j = j0 + lane;
+          bool ul = false;
+          float eps = 0.f, eh = 0.f;
+          int jr = 0, js = 0;
+          if (j < nbp) {
+            jr = crc * SB + j / nsb;   // block indices within the objects
+            js = csc * SB + j % nsb;
+            const float4* ba = R.blk + 3 * (int64_t)(rb0 + jr);
+            const float4* bb = S.blk + 3 * (int64_t)(sbase + js);
             Margins m = box_margins(ba, bb, o);
             if (fp64) {   // exact distances, but the straddle margin of the heights
               m.eh = fp64_height_margin(m);
               m.eps = 0.f;
             }
-            if (!cull || box_pair_live(ba, bb, t, m.eps)) {
-              mask |= 1u << j;
-              eps[j] = m.eps;
-              eh[j] = m.eh;
-              sl[j] = (int)min((int64_t)BLK, send - (fs64 + (int64_t)j * BLK));
-            }
+            ul = !cull || box_pair_live(ba, bb, t, m.eps);
+            eps = m.eps;
+            eh = m.eh;
           }
-        }
-      }
-    }
-    const int c = __popc(mask);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && total)
-      base = atomicAdd(reinterpret_cast<unsigned long long*>(ucount), (unsigned long long)total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    if (EMIT && mask) {
-      int64_t pos = (int64_t)base + incl - c;
-      if (pos + c > cap) {
-        set_err(err, ERR_CAPACITY);
-      } else {
-#pragma unroll
-        for (int j = 0; j < SB; ++j) {
-          if (mask & (1u << j)) {
-            Tile tl;
-            tl.pair = pair;
-            tl.rb = fr;
-            tl.sb = fs0 + j * BLK;
-            tl.rl = (uint16_t)rl;
-            tl.sl = (uint16_t)sl[j];
-            tl.eps = eps[j];
-            tl.eh = eh[j];
-            tl.ew = 0.f;
-            tl.pad = 0;
-            tiles[pos++] = tl;
+          const unsigned um = __ballot_sync(FULLW, ul);
+          if (um == 0u) continue;
+          unsigned long long base = 0;
+          if (lane == 0)
+            base = atomicAdd(reinterpret_cast<unsigned long long*>(ucount), (unsigned long long)__popc(um));
+          base = __shfl_sync(FULLW, base, 0);
+          if (EMIT && ul) {
+            const int64_t pos = (int64_t)base + __popc(um & below);
+            if (pos < cap) {
+              const int fr0 = (int)R.foff[r], fs0 = (int)S.foff[s];
+              const int fr = fr0 + jr * BLK, fs = fs0 + js * BLK;
+              Tile tl;
+              tl.pair = (int32_t)p;
+              tl.rb = fr;
+              tl.sb = fs;
+              tl.rl = (uint16_t)min(BLK, (int)R.foff[r + 1] - fr);
+              tl.sl = (uint16_t)min(BLK, (int)S.foff[s + 1] - fs);
+              tl.eps = eps;
+              tl.eh = eh;
+              tl.ew = 0.f;
+              tl.pad = 0;
+              tiles[pos] = tl;
+            } else {
+              set_err(err, ERR_CAPACITY);
+            }
           }
         }
       }
@@ -291,25 +264,20 @@ static BoxView box_view(const LodData& L) { return BoxView{L.chunk, L.coff, L.bl
 
 static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, const StepSpec& sp,
                              const int32_t* pr, const int32_t* ps, const uint8_t* status, const uint8_t* lod0,
-                             const float4* origin, const float* thr, int64_t* cnt1, int64_t* off1, int64_t* ucount,
-                             Tile** tiles_io, int64_t tiles_cap, bool grow, int64_t* scan_tmp, int* err,
-                             cudaStream_t st) {
+                             const float4* origin, const float* thr, int64_t* ucount, Tile** tiles_io,
+                             int64_t tiles_cap, bool grow, int* err, cudaStream_t st) {
   const LodData& LR = R->lod[sp.lodR];
   const LodData& LS = S->lod[sp.lodS];
   BoxView vr = box_view(LR), vs = box_view(LS);
-  int th = 256;
+  const int th = 256;
   // a LoD built on demand: lay out the objects this step needs first
   ensure_lod(ctx, R, sp.lodR, n, pr, status, lod0, sp.want, sp.step, st);
-  k_items<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, LR.boff, LS.coff,
-                                                        cnt1, ucount);
-  PJ_CK(cudaGetLastError());
-  PJ_COUNT_LAUNCH;
-  scan_i64(ctx, cnt1, off1, n, st, scan_tmp);   // off1[n] = work items
+  PJ_CK(cudaMemsetAsync(ucount, 0, 8, st));
+  // one warp per pair; one wave of 4 blocks of 8 warps per SM (the
+  // kernel's register bound) walks the pairs
+  const unsigned g = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n + th / 32 - 1) / (th / 32), (int64_t)ctx->sm_count * 4));
   const int64_t bR = (LR.maxF + BLK - 1) / BLK, bS = (LS.maxF + BLK - 1) / BLK;
-  const int64_t cS = std::max<int64_t>(1, (LS.maxF + CHUNK - 1) / CHUNK);
-  const int64_t items_max = n * bR * cS;
-  const unsigned g =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>((items_max + th - 1) / th, (int64_t)ctx->sm_count * 16));
   const int64_t worst = n * bR * bS;
   UnitCount uc{-1, ucount};
   int64_t cap = tiles_cap;
@@ -330,8 +298,8 @@ static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int6
     }
   } else {
     // the worst case does not fit: count first, then size the buffer
-    k_emit_units<false><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, nullptr, 0,
-                                          ucount, err);
+    k_emit_units<false><<<g, th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, vr, vs, origin, thr, sp.cull,
+                                          sp.fp64, nullptr, 0, ucount, err);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
     int64_t total = 0;
@@ -347,8 +315,8 @@ static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int6
     }
     PJ_CK(cudaMemsetAsync(ucount, 0, 8, st));
   }
-  k_emit_units<true><<<g, th, 0, st>>>(n, pr, ps, off1, vr, vs, origin, thr, sp.cull, sp.fp64, *tiles_io, cap,
-                                       ucount, err);
+  k_emit_units<true><<<g, th, 0, st>>>(n, pr, ps, status, lod0, sp.want, sp.step, vr, vs, origin, thr, sp.cull,
+                                       sp.fp64, *tiles_io, cap, ucount, err);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   return uc;
@@ -363,14 +331,11 @@ UnitCount build_tiles(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_t n, 
   auto lod0 = (uint8_t*)ws_get(ctx, WS_LOD0, n, st);
   auto origin = (float4*)ws_get(ctx, WS_ORIGIN, n * 16, st);
   auto thr = (float*)ws_get(ctx, WS_THR, ((n + 3) & ~int64_t(3)) * 4, st);   // 16-byte groups (k_refine)
-  auto cnt1 = (int64_t*)ws_get(ctx, WS_TCOUNT, (n + 1) * 8, st);
-  auto off1 = (int64_t*)ws_get(ctx, WS_SCAN, (n + 1) * 8, st);
   auto ucount = (int64_t*)ws_get(ctx, WS_MISC4, 64, st);
-  auto tmp = (int64_t*)ws_get(ctx, WS_MISC5, (scan_tmp_words(n) + 8) * 8, st);
   Tile* tiles = (Tile*)ctx->ws[WS_TILES].p;
   const int64_t cap = (int64_t)(ctx->ws[WS_TILES].cap / sizeof(Tile));
-  return build_units(ctx, R, S, n, sp, pr, ps, status, lod0, origin, thr, cnt1, off1, ucount, &tiles, cap, true,
-                     tmp, ctx->d_err, st);
+  return build_units(ctx, R, S, n, sp, pr, ps, status, lod0, origin, thr, ucount, &tiles, cap, true, ctx->d_err,
+                     st);
 }
 
 __global__ void k_init_bounds(int64_t n, const uint8_t* status, const uint8_t* lod0, uint8_t want, int step,
@@ -643,8 +608,8 @@ UnitCount build_tiles_bufs(pj_ctx* ctx, const pj_set* R, const pj_set* S, int64_
                            const PairBufs& b, int64_t tiles_cap, cudaStream_t st) {
   if (n == 0) return UnitCount{0, nullptr};
   Tile* tiles = b.tiles;
-  return build_units(ctx, R, S, n, sp, b.pr, b.ps, b.status, b.lod0, b.origin, b.thr, b.tcount, b.toff, b.ucount,
-                     &tiles, tiles_cap, false, b.scan_tmp, b.err, st);
+  return build_units(ctx, R, S, n, sp, b.pr, b.ps, b.status, b.lod0, b.origin, b.thr, b.ucount, &tiles, tiles_cap,
+                     false, b.err, st);
 }
 
 void init_bounds_bufs(pj_ctx* ctx, int64_t n, const StepSpec& sp, const PairBufs& b, cudaStream_t st) {

@@ -24,7 +24,6 @@ namespace {
 constexpr int64_t MAXP = PJ_STATIC_MAX_PAIRS;
 constexpr int64_t MAXT = PJ_STATIC_MAX_TILES;
 constexpr int64_t MAXQ = 65536;   // queued straddling facet pairs
-constexpr int64_t SCANW = 64;     // scan temporaries (words), enough for MAXP + 1
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -42,12 +41,9 @@ constexpr size_t OFF_EXACT = OFF_LOD0 + align256(MAXP);
 constexpr size_t OFF_LB = OFF_EXACT + align256(MAXP);
 constexpr size_t OFF_UB = OFF_LB + align256(MAXP * 8);
 constexpr size_t OFF_MID = OFF_UB + align256(MAXP * 8);
-constexpr size_t OFF_TCOUNT = OFF_MID + align256(MAXP * 8);
-constexpr size_t OFF_TOFF = OFF_TCOUNT + align256((MAXP + 1) * 8);
-constexpr size_t OFF_TILES = OFF_TOFF + align256((MAXP + 1) * 8);
+constexpr size_t OFF_TILES = OFF_MID + align256(MAXP * 8);
 constexpr size_t OFF_UCOUNT = OFF_TILES + align256(MAXT * sizeof(Tile));
-constexpr size_t OFF_SCANTMP = OFF_UCOUNT + 256;
-constexpr size_t OFF_QUEUE = OFF_SCANTMP + align256(SCANW * 8);
+constexpr size_t OFF_QUEUE = OFF_UCOUNT + 256;
 constexpr size_t OFF_COUNTERS = OFF_QUEUE + align256(MAXQ * sizeof(int4));
 constexpr size_t OFF_ERR = OFF_COUNTERS + 256;
 constexpr size_t SCRATCH_BYTES = OFF_ERR + 256;
@@ -159,8 +155,6 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     b.lb = base + OFF_LB;
     b.ub = base + OFF_UB;
     b.mid = base + OFF_MID;
-    b.tcount = reinterpret_cast<int64_t*>(base + OFF_TCOUNT);
-    b.toff = reinterpret_cast<int64_t*>(base + OFF_TOFF);
     b.tiles = reinterpret_cast<Tile*>(base + OFF_TILES);
     b.counters = reinterpret_cast<unsigned long long*>(base + OFF_COUNTERS);
     b.queue = reinterpret_cast<int4*>(base + OFF_QUEUE);
@@ -178,7 +172,6 @@ extern "C" pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const p
     sp.exact_cross = true;
     b.ucount = reinterpret_cast<int64_t*>(base + OFF_UCOUNT);
     b.err = err;
-    b.scan_tmp = reinterpret_cast<int64_t*>(base + OFF_SCANTMP);
     setup_pairs_bufs(ctx, R, S, n, b, st);
     init_bounds_bufs(ctx, n, sp, b, st);
     const UnitCount total = build_tiles_bufs(ctx, R, S, n, sp, b, MAXT, st);

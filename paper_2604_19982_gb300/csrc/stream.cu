@@ -18,6 +18,7 @@
 // packs chunk c + 2 meanwhile.  Results carry global R ids
 // (the ids of chunk c continue those of chunk c - 1).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -186,33 +187,106 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
   for (const Piece& pc : pieces) P.bytes_h2d += pc.bytes;
 }
 
-// Copy the packed pieces into the pinned slot with several host threads
-// (the chunk is hundreds of MB; one thread's memcpy would pace the
-// pipeline).
-void pack_parallel(const std::vector<Piece>& pieces, unsigned char* dst) {
-  constexpr size_t SLICE = size_t(4) << 20;
-  struct Job {
-    const unsigned char* src;
-    size_t off, bytes;
-  };
-  std::vector<Job> jobs;
+struct PackJob {
+  const unsigned char* src;
+  size_t off, bytes;
+};
+
+}  // namespace
+
+// Host threads that copy the packed pieces of a chunk into its pinned slot
+// (a pageable chunk is hundreds of MB; one thread's memcpy would pace the
+// pipeline).  The threads live as long as the context: starting them per
+// chunk cost more than packing the few MB of offsets of a chunk whose
+// arrays are already pinned or on the device.  One run at a time; the
+// calling thread copies too.
+class PackPool {
+ public:
+  explicit PackPool(unsigned n) {
+    for (unsigned i = 0; i < n; ++i) th_.emplace_back([this] { work(); });
+  }
+  ~PackPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  size_t threads() const { return th_.size(); }
+  void run(const std::vector<PackJob>& jobs, unsigned char* dst) {
+    std::lock_guard<std::mutex> one(run_mu_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      jobs_ = &jobs;
+      dst_ = dst;
+      next_.store(0);
+      busy_ = th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    drain();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return busy_ == 0; });
+    jobs_ = nullptr;
+  }
+
+ private:
+  void drain() {
+    for (;;) {
+      const size_t k = next_.fetch_add(1);
+      if (k >= jobs_->size()) return;
+      const PackJob& j = (*jobs_)[k];
+      memcpy(dst_ + j.off, j.src, j.bytes);
+    }
+  }
+  void work() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      lk.unlock();
+      drain();
+      lk.lock();
+      if (--busy_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_, run_mu_;
+  std::condition_variable cv_, done_;
+  const std::vector<PackJob>* jobs_ = nullptr;
+  unsigned char* dst_ = nullptr;
+  std::atomic<size_t> next_{0};
+  size_t busy_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+void destroy_pack_pool(PackPool* p) { delete p; }
+
+namespace {
+
+// Copy the packed pieces into the pinned slot: 1 MB slices over the pool's
+// threads (all host cores but two: the calling thread drives the GPU, the
+// loader fills the next chunk; at most 15), inline when there is a single
+// slice.
+void pack_parallel(pj_ctx* ctx, const std::vector<Piece>& pieces, unsigned char* dst, std::vector<PackJob>& jobs) {
+  constexpr size_t SLICE = size_t(1) << 20;
+  jobs.clear();
   for (const Piece& pc : pieces)
     for (size_t a = 0; pc.kind == PACK && a < pc.bytes; a += SLICE)
-      jobs.push_back(Job{static_cast<const unsigned char*>(pc.src) + a, pc.off + a, std::min(SLICE, pc.bytes - a)});
-  // all host cores but two (the calling thread drives the GPU, the loader
-  // fills the next chunk), at most 16
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const unsigned T = (unsigned)std::min<size_t>(std::min(16u, std::max(1u, hw > 2 ? hw - 2 : 1u)), jobs.size());
-  if (T <= 1) {
-    for (const Job& j : jobs) memcpy(dst + j.off, j.src, j.bytes);
+      jobs.push_back(PackJob{static_cast<const unsigned char*>(pc.src) + a, pc.off + a, std::min(SLICE, pc.bytes - a)});
+  if (jobs.size() <= 1) {
+    for (const PackJob& j : jobs) memcpy(dst + j.off, j.src, j.bytes);
     return;
   }
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < T; ++t)
-    th.emplace_back([&, t]() {
-      for (size_t k = t; k < jobs.size(); k += T) memcpy(dst + jobs[k].off, jobs[k].src, jobs[k].bytes);
-    });
-  for (auto& x : th) x.join();
+  if (!ctx->pack_pool) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    ctx->pack_pool = new PackPool(std::min(15u, hw > 3 ? hw - 3 : 1u));
+  }
+  ctx->pack_pool->run(jobs, dst);
 }
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
@@ -264,6 +338,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     cudaSetDevice(device);
     int64_t first = 0;
     std::vector<Piece> pieces;
+    std::vector<PackJob> jobs;
     std::vector<std::vector<int64_t>> offs;
     for (int c = 0; c < N; ++c) {
       ChunkSlot& sl = slots[c & 1];
@@ -316,7 +391,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
               throw ApiError{PJ_ENOMEM, "pinned staging allocation failed"};
             hc = P.bytes;
           }
-          pack_parallel(pieces, static_cast<unsigned char*>(hp));
+          pack_parallel(ctx, pieces, static_cast<unsigned char*>(hp), jobs);
           ms_pack += ms_since(t0);
         } catch (const ApiError& e) {
           err = e.st;

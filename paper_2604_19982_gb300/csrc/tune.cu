@@ -1,15 +1,22 @@
 // Autotuning of the join (PJ_AUTOTUNE): per workload key -- predicate,
 // precision, flags, tau or k, and the shapes of R and S (objects, LoDs,
-// largest facet count per LoD) -- the first join runs every candidate
-// configuration, keeps the fastest, and later joins with the same key use
-// it.  Candidates: the single-precision refinement variant (scalar, one
-// triangle test per lane and instruction, or packed FP32x2, two; unless the
-// context fixed it with the "refine_variant" option), and for
-// within-tau / intersection joins the LoD schedule (every pair starts at
-// step 0, 1, ... or at full resolution; with PJ_USE_MLP also the learned
-// per-pair start).  Configurations only change how the work is scheduled,
-// never a result.  Choices persist across contexts in the "autotune_cache"
-// file of pj_create, one "key choice" line each.
+// largest facet count per LoD) -- the first join runs candidate
+// configurations, keeps the fastest, and later joins with the same key use
+// it.  Three dimensions:
+//   * tests per lane: the single-precision refinement variant, one triangle
+//     test per lane and instruction (scalar) or two (packed FP32x2), unless
+//     the context fixed it with the "refine_variant" option;
+//   * the LoD schedule of within-tau / intersection joins: every pair starts
+//     at step 0, 1, ... or at full resolution (a fixed schedule: the
+//     proposal network is not run), or, with PJ_USE_MLP, at its learned
+//     per-pair start;
+//   * the unit tile: 32 r facets x 32, 16 or 8 s facets (every unit of a
+//     launch handed out as 1, 2 or 4 parts; small launches fill more warps
+//     with shorter parts), unless the context fixed "refine_split".
+// The first two are searched jointly, then the tile with the best of them
+// (coordinate search).  Configurations only change how the work is
+// scheduled, never a result.  Choices persist across contexts in the
+// "autotune_cache" file of pj_create, one "key choice" line each.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "internal.h"
 
 namespace pj {
@@ -32,8 +40,10 @@ namespace {
 struct Choice {
   int variant;   // 1 scalar, 2 packed
   int start;     // -1: the query's own schedule; >= 0: every pair starts at that step
-  int encode() const { return variant * 64 + (start + 1); }
-  static Choice decode(int c) { return Choice{c / 64, c % 64 - 1}; }
+  int split;     // 0: the context's tail splitting; 1, 2, 4: every unit in that many parts
+  int encode() const { return split * 4096 + variant * 64 + (start + 1); }
+  static Choice decode(int c) { return Choice{(c % 4096) / 64, c % 64 - 1, c / 4096}; }
+  int tile_s() const { return split > 0 ? BLK / split : BLK; }
 };
 
 std::string key_of(const pj_set* R, const pj_set* S, const pj_query* q) {
@@ -81,25 +91,36 @@ void store(pj_ctx* ctx, const std::string& key, const Choice& c) {
 // slower than the alternatives (e.g. starting blobs against long tubes at
 // full resolution): it is abandoned at the unit count, before any refinement.
 constexpr int64_t TRIAL_UNIT_CAP = int64_t(1) << 26;
+// refine_tail value whose tail holds every unit of a launch (units per
+// resident warp; launches of more units than this are not split whole)
+constexpr int ALL_UNITS_TAIL = 1 << 16;
 
 pj_status run_with(pj_ctx* ctx, const Choice& c, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                    cudaStream_t st, std::string& stats, int64_t unit_cap = 0) {
-  const int v0 = ctx->refine_variant, s0 = ctx->sched_start;
+  const int v0 = ctx->refine_variant, s0 = ctx->sched_start, k0 = ctx->refine_split, t0 = ctx->refine_tail;
+  auto restore = [&]() {
+    ctx->refine_variant = v0;
+    ctx->sched_start = s0;
+    ctx->refine_split = k0;
+    ctx->refine_tail = t0;
+    ctx->trial_unit_cap = 0;
+  };
   ctx->refine_variant = c.variant;
   ctx->sched_start = c.start;
+  if (c.split > 0) {
+    // every unit of a launch split (the tail covers all of them)
+    ctx->refine_split = c.split;
+    ctx->refine_tail = ALL_UNITS_TAIL;
+  }
   ctx->trial_unit_cap = unit_cap;
   pj_status rc;
   try {
     rc = q->pred == PJ_KNN ? join_knn(ctx, R, S, q, out, st, stats) : join_within(ctx, R, S, q, out, st, stats);
   } catch (...) {
-    ctx->refine_variant = v0;
-    ctx->sched_start = s0;
-    ctx->trial_unit_cap = 0;
+    restore();
     throw;
   }
-  ctx->refine_variant = v0;
-  ctx->sched_start = s0;
-  ctx->trial_unit_cap = 0;
+  restore();
   return rc;
 }
 
@@ -114,11 +135,12 @@ std::string with_tuning(const std::string& stats, const std::string& extra) {
 pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                          cudaStream_t st, std::string& stats) {
   const std::string key = key_of(R, S, q);
-  Choice best;
+  Choice best{ctx->refine_variant, -1, 0};
+  char buf[192];
   if (lookup(ctx, key, &best)) {
     pj_status rc = run_with(ctx, best, R, S, q, out, st, stats);
-    char buf[128];
-    snprintf(buf, sizeof buf, "{\"cached\":1,\"variant\":%d,\"start\":%d}", best.variant, best.start);
+    snprintf(buf, sizeof buf, "{\"cached\":1,\"variant\":%d,\"start\":%d,\"tile_s\":%d}", best.variant, best.start,
+             best.tile_s());
     stats = with_tuning(stats, buf);
     return rc;
   }
@@ -131,10 +153,10 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
                                         : std::vector<int>{2, 1};
   for (int v : variants) {
     if (q->pred == PJ_KNN) {
-      cand.push_back(Choice{v, -1});
+      cand.push_back(Choice{v, -1, 0});
     } else {
-      for (int s = 0; s < Lmax; ++s) cand.push_back(Choice{v, s});
-      if (q->flags & PJ_USE_MLP) cand.push_back(Choice{v, -1});
+      for (int s = 0; s < Lmax; ++s) cand.push_back(Choice{v, s, 0});
+      if (q->flags & PJ_USE_MLP) cand.push_back(Choice{v, -1, 0});
     }
   }
   std::string tried = "[";
@@ -152,40 +174,40 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
     free(warm.priv);
     if (rc != PJ_OK) return rc;
   }
-  for (size_t i = 0; i < cand.size(); ++i) {
+  int n_tried = 0;
+  // one timed trial; false on an error status (returned through rc)
+  auto trial = [&](const Choice& c, pj_status& rc) -> bool {
     pj_result res;
     memset(&res, 0, sizeof res);
     std::string st_i;
     Timer t;
-    pj_status rc;
-    char buf[128];
+    const char* sep = n_tried++ ? "," : "";
     try {
       // the first candidate (the warmed one) always completes
-      rc = run_with(ctx, cand[i], R, S, q, &res, st, st_i, i ? TRIAL_UNIT_CAP : 0);
+      rc = run_with(ctx, c, R, S, q, &res, st, st_i, n_tried > 1 ? TRIAL_UNIT_CAP : 0);
     } catch (const TrialTooLarge& e) {
       PJ_CK(cudaStreamSynchronize(st));
-      snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"skipped_units\":%lld}", i ? "," : "",
-               cand[i].variant, cand[i].start, (long long)e.units);
+      snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"tile_s\":%d,\"skipped_units\":%lld}", sep,
+               c.variant, c.start, c.tile_s(), (long long)e.units);
       tried += buf;
-      continue;
+      rc = PJ_OK;
+      return true;
     }
     const double ms = t.ms();
     if (rc != PJ_OK) {
       free(res.priv);
-      free(keep.priv);
-      return rc;
+      return false;
     }
-    snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"ms\":%.3f}", i ? "," : "", cand[i].variant,
-             cand[i].start, ms);
+    snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"tile_s\":%d,\"ms\":%.3f}", sep, c.variant,
+             c.start, c.tile_s(), ms);
     tried += buf;
     if (keep.priv && res.n != keep.n) {
       free(res.priv);
-      free(keep.priv);
       throw ApiError{PJ_ECUDA, "autotuning: configurations disagree on the number of results"};
     }
     if (ms < best_ms) {
       best_ms = ms;
-      best = cand[i];
+      best = c;
       free(keep.priv);
       keep = res;
       keep_stats = st_i;
@@ -193,13 +215,39 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
     } else {
       free(res.priv);
     }
+    return true;
+  };
+  try {
+    pj_status rc = PJ_OK;
+    // tests per lane x schedule, with the context's tile
+    for (const Choice& c : cand)
+      if (!trial(c, rc)) {
+        free(keep.priv);
+        return rc;
+      }
+    // then the tile, with the best of those
+    if (!ctx->split_fixed) {
+      for (int k : {2, 4}) {
+        Choice c = best;
+        c.split = k;
+        if (!trial(c, rc)) {
+          free(keep.priv);
+          return rc;
+        }
+      }
+      // the whole-unit tile (32 s facets) wins ties: it is the default
+      if (best.split == 0) best.split = 1;
+    }
+  } catch (...) {
+    free(keep.priv);
+    throw;
   }
   tried += "]";
   store(ctx, key, best);
   *out = keep;
   ctx->last_sum = keep_sum;
-  char buf[96];
-  snprintf(buf, sizeof buf, "{\"cached\":0,\"variant\":%d,\"start\":%d,\"tried\":", best.variant, best.start);
+  snprintf(buf, sizeof buf, "{\"cached\":0,\"variant\":%d,\"start\":%d,\"tile_s\":%d,\"tried\":", best.variant,
+           best.start, best.tile_s());
   stats = with_tuning(keep_stats, std::string(buf) + tried + "}");
   return PJ_OK;
 }

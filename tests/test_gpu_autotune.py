@@ -1,5 +1,6 @@
 """PJ_AUTOTUNE: the first join of a workload key tries every candidate
-configuration (refinement variant x LoD schedule) and keeps the fastest;
+configuration (refinement variant x LoD schedule, then the unit tile of 16
+and 8 s facets with the best of those) and keeps the fastest;
 later joins reuse it, also from another context through the cache file.
 Configurations only reschedule work, so the pairs must equal those of the
 untuned join, and with PJ_EXACT_DIST every field (a pair confirmed at
@@ -41,7 +42,13 @@ def test_autotune_within_and_cache_file(sets, tmp_path):
         ref = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=pj.FP32, flags=fl)
         a = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
         st = ctx.stats()["autotune"]
-        assert st["cached"] == 0 and len(st["tried"]) == 6   # 2 variants x 3 start steps
+        # 2 variants x 3 start steps, then tiles of 16 and 8 s facets
+        assert st["cached"] == 0 and len(st["tried"]) == 8
+        assert [t["tile_s"] for t in st["tried"]] == [32] * 6 + [16, 8]
+        assert st["tile_s"] in (32, 16, 8)
+        best = [t for t in st["tried"] if t["tile_s"] == st["tile_s"] and t["variant"] == st["variant"]
+                and t["start"] == st["start"]]
+        assert best and best[0]["ms"] == min(t["ms"] for t in st["tried"] if "ms" in t)
         same(ref, a, fl & pj.EXACT_DIST)
         b = ctx.join(gR, gS, pj.WITHIN, tau=tau, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
         assert ctx.stats()["autotune"]["cached"] == 1
@@ -67,7 +74,21 @@ def test_autotune_keeps_fixed_variant(sets):
     ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl)
     a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
     tried = ctx.stats()["autotune"]["tried"]
-    assert len(tried) == 3 and all(t["variant"] == 1 for t in tried)
+    assert len(tried) == 5 and all(t["variant"] == 1 for t in tried)
+    same(ref, a)
+    ctx.close()
+
+
+def test_autotune_keeps_fixed_split(sets):
+    """A unit split fixed at context creation is kept: no tile trials."""
+    from paper_2604_19982_gb300 import pj
+    ctx = pj.Context(0, {"refine_split": 2, "refine_tail": 64})
+    gR, gS = ctx.load_set(sets.R), ctx.load_set(sets.S)
+    fl = pj.TILE_PRUNE | pj.EXACT_DIST
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl)
+    a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl | pj.AUTOTUNE)
+    tried = ctx.stats()["autotune"]["tried"]
+    assert len(tried) == 6 and all(t["tile_s"] == 32 for t in tried)
     same(ref, a)
     ctx.close()
 
@@ -78,11 +99,11 @@ def test_autotune_knn_and_fp64(sets):
     gR, gS = ctx.load_set(sets.R), ctx.load_set(sets.S)
     ref = ctx.join(gR, gS, pj.KNN, k=3, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
     a = ctx.join(gR, gS, pj.KNN, k=3, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.AUTOTUNE)
-    assert len(ctx.stats()["autotune"]["tried"]) == 2
+    assert len(ctx.stats()["autotune"]["tried"]) == 4   # 2 variants, then 2 tiles
     same(ref, a)
     ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP64)
     a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP64, flags=pj.AUTOTUNE)
-    assert len(ctx.stats()["autotune"]["tried"]) == 3   # FP64: schedules only
+    assert len(ctx.stats()["autotune"]["tried"]) == 5   # FP64: schedules, then tiles
     same(ref, a, exact=False)
     ctx.close()
 

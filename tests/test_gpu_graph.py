@@ -87,3 +87,22 @@ def test_graph_flag_ignored_for_knn(ctx, sets):
     a = ctx.join(gR, gS, pj.KNN, k=2, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
     b = ctx.join(gR, gS, pj.KNN, k=2, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST | pj.USE_GRAPH)
     same(a, b)
+
+
+def test_graph_with_learned_start(ctx, sets):
+    """The learned start inside the captured sequence: the feature kernel
+    skips the padding rows (no pair ids there), replay equals direct."""
+    from paper_2604_19982_gb300 import pj
+    w, gR, gS = sets
+    ctx.mlp_fit(gR, gS, pj.WITHIN, tau=1.0, max_pairs=20_000, epochs=5, seed=1)
+    fl = pj.TILE_PRUNE | pj.USE_MLP
+    ref = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl)
+    plain = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE)
+    assert ref.pairs() == plain.pairs()   # the start step changes no result
+    modes = []
+    for _ in range(3):
+        res = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl | pj.USE_GRAPH)
+        modes.append(ctx.stats()["graph"])
+        assert ctx.stats()["candidates"] < ctx.stats()["capacity"]
+        same(ref, res)
+    assert modes == ["captured", "replay", "replay"]
