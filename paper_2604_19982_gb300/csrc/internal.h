@@ -116,6 +116,7 @@ struct JoinSummary {
   unsigned long long tests32 = 0, tests64 = 0, confirmed = 0, removed = 0;
   double ms_filter = 0, ms_total = 0, refine_ms32 = 0, refine_ms64 = 0;
   unsigned long long launches = 0;
+  int graph = 0;   // within joins: 1 captured, 2 replayed from a graph
 };
 
 }  // namespace pj
@@ -211,6 +212,7 @@ struct pj_ctx {
   // pinned staging of result copies (grow-only)
   void* h_stage = nullptr;
   size_t h_stage_cap = 0;
+  std::string last_tune;            // the autotuner's choice for the last join (JSON), if it ran
   pj::PackPool* pack_pool = nullptr;   // created by the first streamed join, kept until pj_destroy
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};

@@ -483,6 +483,12 @@ static std::string graph_key(pj_ctx* ctx, const pj_set* R, const pj_set* S, cons
   return buf;
 }
 
+// Graphs kept per context (the oldest is dropped beyond): a streamed R whose
+// chunk arrays the caller keeps in device memory gives every chunk its own
+// key (the kernels read those arrays in place), so the cache holds a whole
+// pass of chunks and replays them on the next join.
+constexpr size_t MAX_GRAPHS = 160;
+
 static pj_ctx::GraphEntry* graph_find(pj_ctx* ctx, const std::string& key) {
   for (auto& g : ctx->graphs)
     if (g.key == key) return &g;
@@ -687,6 +693,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   js.refine_ms32 = refine_ms_fp32;
   js.refine_ms64 = refine_ms_fp64;
   js.launches = ctx->launches - launches0;
+  js.graph = !strcmp(gmode, "replay") ? 2 : (!strcmp(gmode, "captured") ? 1 : 0);
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
@@ -713,7 +720,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
     if (ok && g) {
       cudaGraphExec_t ex = nullptr;
       if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
-        if (ctx->graphs.size() >= 16) {
+        if (ctx->graphs.size() >= MAX_GRAPHS) {
           cudaGraphExecDestroy(ctx->graphs.front().exec);
           ctx->graphs.erase(ctx->graphs.begin());
         }

@@ -14,7 +14,8 @@
 //     launch handed out as 1, 2 or 4 parts; small launches fill more warps
 //     with shorter parts), unless the context fixed "refine_split".
 // The first two are searched jointly, then the tile with the best of them
-// (coordinate search).  Configurations only change how the work is
+// (coordinate search); every candidate is timed twice, the faster run
+// counts.  Configurations only change how the work is
 // scheduled, never a result.  Choices persist across contexts in the
 // "autotune_cache" file of pj_create, one "key choice" line each.
 #include <algorithm>
@@ -142,6 +143,7 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
     snprintf(buf, sizeof buf, "{\"cached\":1,\"variant\":%d,\"start\":%d,\"tile_s\":%d}", best.variant, best.start,
              best.tile_s());
     stats = with_tuning(stats, buf);
+    ctx->last_tune = buf;
     return rc;
   }
   std::vector<Choice> cand;
@@ -193,10 +195,25 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
       rc = PJ_OK;
       return true;
     }
-    const double ms = t.ms();
+    double ms = t.ms();
     if (rc != PJ_OK) {
       free(res.priv);
       return false;
+    }
+    {
+      // a second timed run: the faster of the two (one run alone is at the
+      // mercy of a late first-use cost)
+      pj_result again;
+      memset(&again, 0, sizeof again);
+      std::string st_a;
+      Timer t2;
+      rc = run_with(ctx, c, R, S, q, &again, st, st_a);
+      ms = std::min(ms, t2.ms());
+      free(again.priv);
+      if (rc != PJ_OK) {
+        free(res.priv);
+        return false;
+      }
     }
     snprintf(buf, sizeof buf, "%s{\"variant\":%d,\"start\":%d,\"tile_s\":%d,\"ms\":%.3f}", sep, c.variant,
              c.start, c.tile_s(), ms);
@@ -248,6 +265,7 @@ pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj
   ctx->last_sum = keep_sum;
   snprintf(buf, sizeof buf, "{\"cached\":0,\"variant\":%d,\"start\":%d,\"tile_s\":%d,\"tried\":", best.variant,
            best.start, best.tile_s());
+  ctx->last_tune = std::string(buf) + tried + "}";
   stats = with_tuning(keep_stats, std::string(buf) + tried + "}");
   return PJ_OK;
 }
