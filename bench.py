@@ -59,7 +59,7 @@ STREAM = dict(n=2_000_000, chunks=64, tubes=20_000, side=5000.0, tau=1.0)
 FLOPS_PER_TEST = 564
 # the single-precision refinement kernel the tuned path runs; the traffic
 # counters in profiles/ name it
-REFINE_KERNEL_ID = "k_refine<float>+staged+masks+dealt"
+REFINE_KERNEL_ID = "k_refine<float>+staged+masks+dealt+crossq"
 RESULT_BYTES_PER_PAIR = 4 + 4 + 8 + 8 + 8 + 1
 
 
