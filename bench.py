@@ -490,8 +490,12 @@ def stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32):
         ke = max(1, min(args.steps, 3))
         e2e_stats = []
 
+        e2e_ms = []
+
         def e2e_step():
+            t0 = time.perf_counter()
             res = join(gRp, tuned)
+            e2e_ms.append((time.perf_counter() - t0) * 1000.0)
             st = ctx.stats()
             e2e_stats.append(st)
             return st["candidates"], res.n, st["bytes_h2d"], st.get("h2d_gbs", 0.0)
@@ -502,11 +506,15 @@ def stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32):
                "h2d_bytes_per_step": int(sum(o[2] for o in outs) / ke),
                "d2h_bytes_per_step": int(sum(o[1] for o in outs) / ke * RESULT_BYTES_PER_PAIR),
                "ms_per_step": ems / ke, "h2d_gbs_during_join": statistics.median(o[3] for o in outs),
+               "host_read_bytes_max_per_step": e2e_stats[-1].get("bytes_host_read_max"),
+               "join_call_ms": e2e_ms, "join_ms_total": [x.get("ms_total") for x in e2e_stats],
                "how": "pj_join of the streamed R with every chunk array in pinned host memory (copied by the "
-                      "library's copy stream without packing, overlapped with the previous chunk's join) + "
+                      "library's copy stream without packing, overlapped with the previous chunk's join; the "
+                      "hd / ph of the middle LoD read in place by the kernels for the objects that reach it) + "
                       "result copy, host clock; 3 untimed warm passes",
                "last_step_stats": {k: e2e_stats[-1].get(k) for k in (
-                   "bytes_h2d", "ms_h2d", "h2d_gbs", "ms_fill", "ms_pack", "ms_wait_loader", "ms_build", "ms_join",
+                   "bytes_h2d", "bytes_host_read_max", "ms_h2d", "h2d_gbs", "ms_fill", "ms_pack", "ms_wait_loader",
+                   "ms_build", "ms_join",
                    "ms_filter", "ms_total", "graph_replays", "graph_captures")}}
         gRp.free()
         gRp._cb = gRp._keep = None

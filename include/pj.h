@@ -180,8 +180,11 @@ pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out);
  *   - pageable host memory: packed into the library's pinned staging, so it
  *     must stay valid until the next call of fill or the end of the join;
  *   - pinned host memory (cudaHostAlloc / cudaHostRegister): copied to the
- *     device directly, without packing (the link-bound path), so it must
- *     stay valid and unchanged until pj_join returns;
+ *     device directly, without packing (the link-bound path); the hd, ph,
+ *     per-object faces and own vertex arrays of the LoDs between the first
+ *     and the last are not copied but read in place over the host link, for
+ *     the objects whose pairs reach those LoDs; so it must stay valid and
+ *     unchanged until pj_join returns;
  *   - device memory (verts, faces, hd, ph, anchor only): read in place by
  *     the set-building kernels, likewise until pj_join returns.
  * vert_off and face_off are always host memory (read by the host; PJ_EINVAL
@@ -211,7 +214,13 @@ void pj_result_free(pj_result* res);
  * tests that the testing lane's own ball test asked for; the others ran
  * because another lane of the warp needed the same s facet), and per step
  * in "steps": "tiles" (units built) and "tiles_run" (units left after the
- * full-resolution mask pass).  Also, at the time of the call: "allocs", the
+ * full-resolution mask pass).  A join with a streamed R adds per-stage
+ * times summed over its chunks ("ms_fill", "ms_pack", "ms_wait_loader",
+ * "ms_build", "ms_join", "ms_filter", "ms_h2d"), "bytes_h2d" (copied to
+ * the device), "bytes_host_read_max" (pinned caller arrays read in place;
+ * at most this many bytes cross the link), "graph_replays" /
+ * "graph_captures" and, with PJ_AUTOTUNE, the tuned choice under
+ * "autotune".  Also, at the time of the call: "allocs", the
  * number of device and pinned-host allocations the library has made in this
  * process (all contexts), and "ws_bytes", the context's workspace bytes.
  * Fails with PJ_EINVAL when cap is too small. */

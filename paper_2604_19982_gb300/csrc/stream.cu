@@ -38,6 +38,7 @@ pj_status join_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query
                    cudaStream_t st, std::string& stats);
 pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                          cudaStream_t st, std::string& stats);
+bool tuned_schedule_fixed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q);
 
 namespace {
 
@@ -54,6 +55,17 @@ struct Piece {
   size_t bytes;
   int kind;
 };
+
+// The device address of pinned host memory (mapped under unified
+// addressing), or nullptr.
+const void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 
 int memory_kind(const void* p) {
   cudaPointerAttributes a;
@@ -87,6 +99,7 @@ struct Plan {
   const void* d_anchor = nullptr;
   std::vector<Piece> pieces;   // what fills the device slot
   size_t bytes_h2d = 0;        // bytes the chunk moves from the host
+  size_t bytes_host_read = 0;  // pinned caller arrays read in place (at most this many bytes cross)
 };
 
 struct ChunkSlot {
@@ -109,13 +122,31 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
   P.n = n;
   P.L = L;
   size_t at = 0;
+  P.bytes_host_read = 0;
+  // The LoDs between the first (laid out for every object) and the original
+  // surfaces (whose vertices give every object's box) are laid out on
+  // demand for few objects: their arrays in pinned caller memory are not
+  // copied but read in place over the host link by the kernels that lay
+  // those objects out.
+  const int lazy_from = L >= 2 ? 1 : L;
+  auto host_read_lod = [&](int l) { return l >= lazy_from && l < L - 1; };
   // a caller array (kind from its address) or one computed here (packed);
-  // a device array takes no room in the slot and is recorded in *dptr
-  auto put = [&](const void* src, size_t bytes, bool caller = false, const void** dptr = nullptr) {
+  // a device array takes no room in the slot and is recorded in *dptr, and
+  // so does a pinned one when host_read is set (its device address)
+  auto put = [&](const void* src, size_t bytes, bool caller = false, const void** dptr = nullptr,
+                 bool host_read = false) {
     const int kind = (caller && bytes) ? memory_kind(src) : PACK;
     if (kind == DEVICE && dptr) {
       *dptr = src;
       return size_t(0);
+    }
+    if (kind == PINNED && dptr && host_read) {
+      const void* dv = device_view(src);
+      if (dv) {
+        *dptr = dv;
+        P.bytes_host_read += bytes;
+        return size_t(0);
+      }
     }
     const size_t off = at;
     if (bytes) pieces.push_back(Piece{src, off, bytes, kind == DEVICE ? PINNED : kind});
@@ -166,17 +197,20 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
         break;
       }
     if (P.vsrc[l] == l) {
-      P.o_verts[l] = put(D->verts[l], (size_t)nv * 12, true, &P.d_verts[l]);
+      // vertices the first LoD or the original surfaces also use are copied
+      const bool own = D->verts[l] != D->verts[0] && D->verts[l] != D->verts[L - 1];
+      P.o_verts[l] = put(D->verts[l], (size_t)nv * 12, true, &P.d_verts[l], own && host_read_lod(l));
     } else {
       P.o_verts[l] = P.o_verts[P.vsrc[l]];
       P.d_verts[l] = P.d_verts[P.vsrc[l]];
     }
     P.o_voff[l] = put(vo, (size_t)(n + 1) * 8, true);
-    P.o_faces[l] = put(D->faces[l], (size_t)(shared ? nfs : P.F[l]) * 12, true, &P.d_faces[l]);
+    P.o_faces[l] = put(D->faces[l], (size_t)(shared ? nfs : P.F[l]) * 12, true, &P.d_faces[l],
+                       !shared && host_read_lod(l));
     P.has_hd[l] = D->hd[l] != nullptr;
     P.has_ph[l] = D->ph[l] != nullptr;
-    P.o_hd[l] = P.has_hd[l] ? put(D->hd[l], (size_t)P.F[l] * 4, true, &P.d_hd[l]) : 0;
-    P.o_ph[l] = P.has_ph[l] ? put(D->ph[l], (size_t)P.F[l] * 4, true, &P.d_ph[l]) : 0;
+    P.o_hd[l] = P.has_hd[l] ? put(D->hd[l], (size_t)P.F[l] * 4, true, &P.d_hd[l], host_read_lod(l)) : 0;
+    P.o_ph[l] = P.has_ph[l] ? put(D->ph[l], (size_t)P.F[l] * 4, true, &P.d_ph[l], host_read_lod(l)) : 0;
     P.o_foff[l] = put(fo.data(), (size_t)(n + 1) * 8);
     P.o_coff[l] = put(co.data(), (size_t)(n + 1) * 8);
     P.o_boff[l] = put(bo.data(), (size_t)(n + 1) * 8);
@@ -429,7 +463,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   // ---- calling thread: copy, build, join
   int enqueued = 0;   // chunks whose copy has been issued
   double ms_h2d = 0, ms_wait = 0, ms_build = 0, ms_join = 0;
-  size_t bytes_h2d = 0;
+  size_t bytes_h2d = 0, bytes_host_read = 0;
   // issue the copy of chunk c if it is packed (or wait for it when `block`)
   auto enqueue = [&](int c, bool block) -> bool {
     ChunkSlot& sl = slots[c & 1];
@@ -468,6 +502,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     PJ_CK(cudaEventRecord(h2d1[c & 1], ctx->copy_stream));
     PJ_CK(cudaEventRecord(sl.copied, ctx->copy_stream));
     bytes_h2d += sl.plan.bytes_h2d;
+    bytes_host_read += sl.plan.bytes_host_read;
     {
       std::lock_guard<std::mutex> lk(mu);
       plans[c & 1] = sl.plan;
@@ -552,8 +587,13 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     PJ_CK(cudaMemsetAsync(err, 0, sizeof(int), bst));
     if (nl) PJ_CK(cudaMemsetAsync(view.lazy_state, 0, nl * no * 4, bst));
     build_set_kernels(ctx, &view, raw, bst, err, lazy_from);
-    // the learned start LoD reads every pair's hd / ph maxima per LoD
-    for (int l = lazy_from; l < P.L - 1; ++l) chunk_hd_ph(ctx, &view, l, raw[l], bst);
+    // the learned start LoD reads every pair's hd / ph maxima per LoD (at
+    // the LoDs laid out on demand, from all objects' hd / ph); not needed
+    // when the query has no learned start or the tuned schedule is fixed
+    const bool learned = (q->flags & PJ_USE_MLP) && q->pred != PJ_KNN &&
+                         !((q->flags & PJ_AUTOTUNE) && tuned_schedule_fixed(ctx, &view, S, q));
+    if (learned || q->pred == PJ_KNN)
+      for (int l = lazy_from; l < P.L - 1; ++l) chunk_hd_ph(ctx, &view, l, raw[l], bst);
     PJ_CK(cudaMemcpyAsync(ctx->stream_box_pinned[si], mb, box_bytes + sizeof(int), cudaMemcpyDeviceToHost, bst));
     PJ_CK(cudaEventRecord(built[si], bst));
     prepared[si] = c;
@@ -671,12 +711,12 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   snprintf(buf, sizeof buf,
            "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,"
-           "\"bytes_h2d\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
+           "\"bytes_h2d\":%zu,\"bytes_host_read_max\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
            "\"ms_wait_loader\":%.3f,\"ms_build\":%.3f,\"ms_join\":%.3f,\"ms_filter\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"ms_total\":%.3f,\"launches\":%llu,"
            "\"graph_replays\":%d,\"graph_captures\":%d",
            q->pred == PJ_KNN ? "knn" : "within", N, (long long)objects, (long long)tot.candidates, (long long)m,
-           tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, ms_h2d,
+           tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, bytes_host_read, ms_h2d,
            ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, ms_build, ms_join, tot.ms_filter,
            tot.refine_ms32,
            tot.refine_ms64, ms_total, tot.launches, graph_replays, graph_captures);

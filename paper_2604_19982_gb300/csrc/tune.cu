@@ -132,6 +132,13 @@ std::string with_tuning(const std::string& stats, const std::string& extra) {
 
 }  // namespace
 
+// Whether the stored choice for this workload fixes the LoD schedule (every
+// pair from one step, no learned start); false when nothing is stored yet.
+bool tuned_schedule_fixed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q) {
+  Choice c{0, -1, 0};
+  return lookup(ctx, key_of(R, S, q), &c) && c.start >= 0;
+}
+
 // A join of a resident R (or one streamed chunk) with PJ_AUTOTUNE.
 pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                          cudaStream_t st, std::string& stats) {

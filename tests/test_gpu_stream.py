@@ -192,8 +192,10 @@ def _on_device(ms):
 @pytest.mark.parametrize("where", ["pinned", "device"])
 def test_streamed_pinned_and_device_chunks(ctx, data, where):
     """Chunks whose arrays already lie in pinned host memory are copied
-    without packing, and device arrays are read in place: the same result
-    as the resident join, and only the host-side arrays travel."""
+    without packing (the arrays of the LoDs laid out on demand are read in
+    place over the host link instead), and device arrays are read in place:
+    the same result as the resident join, and only the host-side arrays
+    travel."""
     from paper_2604_19982_gb300 import pj
     R, S, gR, gS = data
     parts = bounds([700, 900, 800])
@@ -210,9 +212,16 @@ def test_streamed_pinned_and_device_chunks(ctx, data, where):
         st = ctx.stats()
         same(a, b)
         if where == "pinned":
-            assert st["bytes_h2d"] == packed_bytes     # the same bytes, without packing them
+            # the same bytes without packing them, less those read in place
+            assert st["bytes_host_read_max"] > 0
+            assert st["bytes_h2d"] + st["bytes_host_read_max"] == packed_bytes
         else:
             assert st["bytes_h2d"] < packed_bytes / 20     # offsets only
+    # the learned start reads every object's hd / ph maxima of those LoDs
+    ctx.mlp_fit(gR, gS, pj.WITHIN, tau=1.0, max_pairs=20_000, epochs=3, seed=1)
+    a = ctx.join(gR, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.USE_MLP)
+    b = ctx.join(g, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=pj.TILE_PRUNE | pj.USE_MLP)
+    assert a.pairs() == b.pairs()
     g.free()
     gp.free()
 
