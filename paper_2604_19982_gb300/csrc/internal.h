@@ -117,6 +117,8 @@ struct JoinSummary {
   double ms_filter = 0, ms_total = 0, refine_ms32 = 0, refine_ms64 = 0;
   unsigned long long launches = 0;
   int graph = 0;   // within joins: 1 captured, 2 replayed from a graph
+  double ms_seq = 0;   // within joins: the post-filter sequence from issue to completion (host clock)
+  double graph_ms = 0;  // within joins: device time of a replayed graph (events around its launch)
 };
 
 }  // namespace pj

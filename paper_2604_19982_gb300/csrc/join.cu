@@ -621,6 +621,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   const char* gmode = "off";
   double ms_filter = 0;
   bool need_capture = false;
+  Timer tseq;
   if (nn > 0) {
     pj_ctx::GraphEntry* ge = graph ? graph_find(ctx, graph_key(ctx, R, S, q, cap)) : nullptr;
     ms_filter = tf.ms();
@@ -642,6 +643,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   } else {
     ms_filter = tf.ms();
   }
+  const double ms_seq = tseq.ms();   // the post-filter sequence, issue to completion
   // after the synchronization the error word, the counters and the step
   // snapshots are in the pinned stage (with candidates; else read here)
   int herr = 0;
@@ -694,6 +696,8 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   js.refine_ms64 = refine_ms_fp64;
   js.launches = ctx->launches - launches0;
   js.graph = !strcmp(gmode, "replay") ? 2 : (!strcmp(gmode, "captured") ? 1 : 0);
+  js.ms_seq = ms_seq;
+  js.graph_ms = graph_ms;
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;

@@ -462,7 +462,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
 
   // ---- calling thread: copy, build, join
   int enqueued = 0;   // chunks whose copy has been issued
-  double ms_h2d = 0, ms_wait = 0, ms_build = 0, ms_join = 0;
+  double ms_h2d = 0, ms_wait = 0, ms_build = 0, ms_join = 0, ms_issue = 0;
   size_t bytes_h2d = 0, bytes_host_read = 0;
   // issue the copy of chunk c if it is packed (or wait for it when `block`)
   auto enqueue = [&](int c, bool block) -> bool {
@@ -594,7 +594,13 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
                          !((q->flags & PJ_AUTOTUNE) && tuned_schedule_fixed(ctx, &view, S, q));
     if (learned || q->pred == PJ_KNN)
       for (int l = lazy_from; l < P.L - 1; ++l) chunk_hd_ph(ctx, &view, l, raw[l], bst);
-    PJ_CK(cudaMemcpyAsync(ctx->stream_box_pinned[si], mb, box_bytes + sizeof(int), cudaMemcpyDeviceToHost, bst));
+    // the error word back to pinned memory, and the boxes when the host
+    // needs them (the k-NN grid spans R's boxes; the within grid is over S)
+    if (q->pred == PJ_KNN)
+      PJ_CK(cudaMemcpyAsync(ctx->stream_box_pinned[si], mb, box_bytes + sizeof(int), cudaMemcpyDeviceToHost, bst));
+    else
+      PJ_CK(cudaMemcpyAsync((unsigned char*)ctx->stream_box_pinned[si] + box_bytes, mb + box_bytes, sizeof(int),
+                            cudaMemcpyDeviceToHost, bst));
     PJ_CK(cudaEventRecord(built[si], bst));
     prepared[si] = c;
   };
@@ -626,6 +632,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   } rejoin(caller, st);
   for (int c = 0; c < N; ++c) {
     if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
+    Timer ti;
     if (enqueued <= c) {
       enqueue(c, true);
       enqueued = c + 1;
@@ -637,6 +644,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       enqueued = c + 2;
       prepare(c + 1);
     }
+    ms_issue += ti.ms();
     Timer tb;
     PJ_CK(cudaEventSynchronize(built[c & 1]));
     pj_set& view = views[c & 1];
@@ -647,8 +655,10 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       throw ApiError{PJ_EBOUNDS, "chunk " + std::to_string(c) + ": a face index lies outside its object's vertices"};
     if (herr & ERR_NONFINITE)
       throw ApiError{PJ_ENONFINITE, "chunk " + std::to_string(c) + ": non-finite vertex, anchor, hd or ph"};
-    const float* hb = (const float*)ctx->stream_box_pinned[c & 1];
-    view.mbb_h.assign(hb, hb + (size_t)P.n * 6);
+    if (q->pred == PJ_KNN) {
+      const float* hb = (const float*)ctx->stream_box_pinned[c & 1];
+      view.mbb_h.assign(hb, hb + (size_t)P.n * 6);
+    }
     PJ_CK(cudaStreamWaitEvent(st, built[c & 1], 0));
     ms_build += tb.ms();
     float h2d = 0;
@@ -677,6 +687,8 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     tot.confirmed += js.confirmed;
     tot.removed += js.removed;
     tot.ms_filter += js.ms_filter;
+    tot.ms_seq += js.ms_seq;
+    tot.graph_ms += js.graph_ms;
     tot.refine_ms32 += js.refine_ms32;
     tot.refine_ms64 += js.refine_ms64;
     tot.launches += js.launches;
@@ -712,12 +724,12 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
            "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,"
            "\"bytes_h2d\":%zu,\"bytes_host_read_max\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
-           "\"ms_wait_loader\":%.3f,\"ms_build\":%.3f,\"ms_join\":%.3f,\"ms_filter\":%.3f,"
-           "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"ms_total\":%.3f,\"launches\":%llu,"
+           "\"ms_wait_loader\":%.3f,\"ms_issue\":%.3f,\"ms_build\":%.3f,\"ms_join\":%.3f,\"ms_filter\":%.3f,"
+           "\"ms_seq\":%.3f,\"graph_ms\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"ms_total\":%.3f,\"launches\":%llu,"
            "\"graph_replays\":%d,\"graph_captures\":%d",
            q->pred == PJ_KNN ? "knn" : "within", N, (long long)objects, (long long)tot.candidates, (long long)m,
            tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, bytes_host_read, ms_h2d,
-           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, ms_build, ms_join, tot.ms_filter,
+           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, ms_issue, ms_build, ms_join, tot.ms_filter, tot.ms_seq, tot.graph_ms,
            tot.refine_ms32,
            tot.refine_ms64, ms_total, tot.launches, graph_replays, graph_captures);
   // the autotuner's choice for the chunks (tuned on the first, reused after)
