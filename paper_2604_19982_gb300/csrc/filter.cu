@@ -140,13 +140,21 @@ __global__ void k_probe(int nR, const float* mbbR, const float* mbbS, float tau,
 // probe's slots: one warp per r ranks its s ids (each appears once; ties would
 // go by position) and writes them in ascending order at roff[r] -- the output of the emitting probe followed by
 // the per-r sort, without probing the grid a second time.
-__global__ void k_slot_emit(int nR, const int32_t* slot, const int64_t* roff, int32_t* out_r, int32_t* out_s) {
+// With cap >= 0 (a speculative capacity), an r whose list would end past
+// cap writes nothing and sets bit 1 of *over (the join then runs again with
+// the capacity the count asks for).
+__global__ void k_slot_emit(int nR, const int32_t* slot, const int64_t* roff, int32_t* out_r, int32_t* out_s,
+                            int64_t cap, int* over) {
   const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= nR) return;   // warp-uniform
   const int64_t base = roff[w];
   const int n = (int)(roff[w + 1] - base);
   if (n == 0) return;
+  if (cap >= 0 && roff[w + 1] > cap) {
+    if (lane == 0) atomicOr(over, 2);
+    return;
+  }
   const int32_t* sl = slot + (int64_t)w * PROBE_SLOT;
   const int32_t v0 = lane < n ? sl[lane] : 0x7fffffff;
   const int32_t v1 = lane + 32 < n ? sl[lane + 32] : 0x7fffffff;
@@ -356,7 +364,7 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
                                    nullptr, slot, overflow);
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
-  scan_i64(ctx, rcount, roff, R->n, st);
+  scan_i64(ctx, rcount, roff, R->n, st, (int64_t*)ws_get(ctx, WS_FSCAN, (scan_tmp_words(R->n) + 8) * 8, st));
   int64_t total = 0;
   int over = 0;
   PJ_CK(cudaMemcpyAsync(&total, roff + R->n, 8, cudaMemcpyDeviceToHost, st));
@@ -371,7 +379,7 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   auto pr = (int32_t*)ws_get(ctx, WS_PR, cap * 4, st);
   auto ps = (int32_t*)ws_get(ctx, WS_PS, cap * 4, st);
   if (!over) {
-    k_slot_emit<<<g, th, 0, st>>>(R->n, slot, roff, pr, ps);
+    k_slot_emit<<<g, th, 0, st>>>(R->n, slot, roff, pr, ps, -1, nullptr);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
     return out;
@@ -383,6 +391,44 @@ FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double ta
   PJ_CK(cudaGetLastError());
   PJ_COUNT_LAUNCH;
   return out;
+}
+
+// Whether the grid over S alone is kept for this (R, S, tau): a streamed
+// chunk's filter then needs no host work before its launches.
+bool filter_grid_kept(const pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau) {
+  return R->uid == 0 && S->uid != 0 && ctx->sgrid.valid && ctx->sgrid.sid == S->uid && ctx->sgrid.tau == tau;
+}
+
+// The filter with the kept grid and a capacity fixed in advance (no host
+// synchronization): count probe keeping up to PROBE_SLOT candidates per r,
+// scan (the count lands in WS_ROFF[R->n]), ranked emit into pair arrays of
+// `cap` entries.  *over (a device word the caller clears) gets bit 0 when
+// some r has more than PROBE_SLOT candidates and bit 1 when the pairs
+// exceed cap; either voids the join, which then runs the synchronous filter.
+void filter_within_enqueue(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, int64_t cap, int* over,
+                           cudaStream_t st) {
+  Grid G;
+  memcpy(&G, ctx->sgrid.grid, sizeof(Grid));
+  const int64_t* off = (const int64_t*)ctx->ws[WS_MISC].p;
+  const int32_t* ids = (const int32_t*)ctx->ws[WS_GRIDIDS].p;
+  float ftau = (float)tau;
+  if ((double)ftau < tau) ftau = nextafterf(ftau, INFINITY);
+  const double lim = tau * (1.0 + 1e-9);
+  const int th = 256;
+  auto rcount = (int64_t*)ws_get(ctx, WS_RCOUNT, ((int64_t)R->n + 1) * 8, st);
+  auto roff = (int64_t*)ws_get(ctx, WS_ROFF, ((int64_t)R->n + 1) * 8, st);
+  auto slot = (int32_t*)ws_get(ctx, WS_FSLOT, (int64_t)R->n * PROBE_SLOT * 4, st);
+  auto pr = (int32_t*)ws_get(ctx, WS_PR, cap * 4, st);
+  auto ps = (int32_t*)ws_get(ctx, WS_PS, cap * 4, st);
+  const unsigned g = (unsigned)(((int64_t)R->n * 32 + th - 1) / th);
+  k_probe<false><<<g, th, 0, st>>>(R->n, R->mbb, S->mbb, ftau, lim * lim, G, off, ids, rcount, nullptr, nullptr,
+                                   nullptr, slot, over);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
+  scan_i64(ctx, rcount, roff, R->n, st, (int64_t*)ws_get(ctx, WS_FSCAN, (scan_tmp_words(R->n) + 8) * 8, st));
+  k_slot_emit<<<g, th, 0, st>>>(R->n, slot, roff, pr, ps, cap, over);
+  PJ_CK(cudaGetLastError());
+  PJ_COUNT_LAUNCH;
 }
 
 }  // namespace pj

@@ -119,6 +119,7 @@ struct JoinSummary {
   int graph = 0;   // within joins: 1 captured, 2 replayed from a graph
   double ms_seq = 0;   // within joins: the post-filter sequence from issue to completion (host clock)
   double graph_ms = 0;  // within joins: device time of a replayed graph (events around its launch)
+  int spec = 0;         // within joins: the filter ran inside the speculative sequence
 };
 
 }  // namespace pj
@@ -215,6 +216,17 @@ struct pj_ctx {
   void* h_stage = nullptr;
   size_t h_stage_cap = 0;
   std::string last_tune;            // the autotuner's choice for the last join (JSON), if it ran
+  // candidate capacity of the last join per (R objects, R LoDs, S, tau), for
+  // the speculative graph mode of streamed chunks
+  struct SpecCap {
+    int64_t nR;
+    int LR;
+    uint64_t sid;
+    double tau;
+    int64_t cap;
+  };
+  std::vector<SpecCap> spec_caps;
+  unsigned long long spec_misses = 0;   // speculative joins that ran again unspeculated
   pj::PackPool* pack_pool = nullptr;   // created by the first streamed join, kept until pj_destroy
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};
@@ -239,7 +251,7 @@ enum Slot {
   WS_DLO, WS_DHI, WS_D, WS_EXACT, WS_TCOUNT, WS_TILES, WS_SCAN, WS_GRID, WS_GRIDIDS, WS_RCOUNT,
   WS_ROFF, WS_TMP, WS_RES, WS_KNN, WS_FEAT, WS_PRED, WS_MISC, WS_MISC2, WS_MISC3, WS_MISC4, WS_MISC5,
   WS_FLAG, WS_KNN2, WS_KNN3, WS_KNN4, WS_KNN5, WS_MLP, WS_MLP2, WS_MLP3, WS_STREAM, WS_STREAM2, WS_STREAM3, WS_STREAM4, WS_STREAM5,
-  WS_STREAM6, WS_STREAM7, WS_STREAM8, WS_TILES2, WS_FSLOT,
+  WS_STREAM6, WS_STREAM7, WS_STREAM8, WS_TILES2, WS_FSLOT, WS_FSCAN,
   WS_COUNT
 };
 
@@ -263,6 +275,15 @@ struct FilterOut {
 // Candidate pairs (r, s) with box MINDIST <= tau, grouped by r and sorted by
 // s; results land in WS_PR / WS_PS.
 FilterOut filter_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, cudaStream_t st);
+// The within filter's grid over S alone is kept for (R, S, tau) (a streamed
+// chunk R against a resident S after the first chunk).
+bool filter_grid_kept(const pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau);
+// With the kept grid: the filter's launches with a capacity fixed in
+// advance and no host synchronization (count in WS_ROFF[R->n]; *over bit 0:
+// an r with too many candidates for the ranked emit, bit 1: more than cap
+// pairs; either voids the pairs).
+void filter_within_enqueue(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, int64_t cap, int* over,
+                           cudaStream_t st);
 // k-NN candidates: per r all s with MINDIST <= theta_r (theta_r = k-th
 // smallest anchor distance); roff (WS_ROFF, n_R+1) is the CSR of the result.
 FilterOut filter_knn(pj_ctx* ctx, const pj_set* R, const pj_set* S, int k, cudaStream_t st);

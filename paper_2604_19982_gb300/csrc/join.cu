@@ -308,7 +308,7 @@ static void* stage(pj_ctx* ctx, size_t bytes) {
 // join counters and the per-step snapshots, copied in stream order after
 // the last kernel so that one synchronization makes all of it readable.
 constexpr size_t RES_PER = 4 + 4 + 8 + 8 + 8 + 1;
-constexpr size_t STATUS_ERR = 0, STATUS_CNT = 64, STATUS_SNAP = 256;
+constexpr size_t STATUS_ERR = 0, STATUS_TOTAL = 8, STATUS_CNT = 64, STATUS_SNAP = 256;
 constexpr size_t STATUS_BYTES = STATUS_SNAP + sizeof(long long) * 4 * StepLog::MAX;
 static size_t status_at(int64_t n) { return ((size_t)n * RES_PER + 8 + 255) & ~size_t(255); }
 
@@ -343,9 +343,12 @@ void gather_device(pj_ctx* ctx, int64_t n, cudaStream_t st) {
   PJ_CK(cudaMemcpyAsync(h + (size_t)n * per, off + n, 8, cudaMemcpyDeviceToHost, st));
 }
 
-void stage_status(pj_ctx* ctx, int64_t n, int steps, cudaStream_t st) {
+// total (device, may be null): the filter's pair count, when the filter ran
+// inside the sequence
+void stage_status(pj_ctx* ctx, int64_t n, int steps, cudaStream_t st, const int64_t* total = nullptr) {
   char* h = (char*)stage(ctx, status_at(n) + STATUS_BYTES) + status_at(n);
   PJ_CK(cudaMemcpyAsync(h + STATUS_ERR, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (total) PJ_CK(cudaMemcpyAsync(h + STATUS_TOTAL, total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   PJ_CK(cudaMemcpyAsync(h + STATUS_CNT, ctx->d_counters, 15 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         st));
   if (steps > 0)
@@ -501,6 +504,22 @@ void graphs_clear(pj_ctx* ctx) {
   ctx->graphs.clear();
 }
 
+static int64_t spec_cap_get(const pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau) {
+  for (const auto& e : ctx->spec_caps)
+    if (e.nR == R->n && e.LR == R->L && e.sid == S->uid && e.tau == tau) return e.cap;
+  return 0;
+}
+
+static void spec_cap_set(pj_ctx* ctx, const pj_set* R, const pj_set* S, double tau, int64_t cap) {
+  for (auto& e : ctx->spec_caps)
+    if (e.nR == R->n && e.LR == R->L && e.sid == S->uid && e.tau == tau) {
+      e.cap = cap;
+      return;
+    }
+  if (ctx->spec_caps.size() >= 16) ctx->spec_caps.erase(ctx->spec_caps.begin());
+  ctx->spec_caps.push_back(pj_ctx::SpecCap{R->n, R->L, S->uid, tau, cap});
+}
+
 static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q,
                                   pj_result* out, cudaStream_t st, std::string& stats) {
   Timer tall;
@@ -512,29 +531,49 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   if (use_mlp && !ctx->mlp_ready) throw ApiError{PJ_EINVAL, "PJ_USE_MLP needs trained or loaded proposal weights"};
   // the learned per-pair start, unless the autotuner fixed the schedule
   const bool learned = use_mlp && ctx->sched_start < 0;
-  PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
-  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
-  Timer tf;
-  FilterOut fo = filter_within(ctx, R, S, tau, st);
-  const int64_t n = fo.n_pairs;
-  const int Lmax = std::max(R->L, S->L);
-  auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
-
   // fixed-capacity graph mode: not on the legacy default stream, nor in an
   // autotuning trial (whose steps count their units on the host first).  A
   // replay whose units overflow the buffer of the capture flags the join,
   // which runs again directly with a grown buffer (and a new graph).
-  const bool graph = (q->flags & PJ_USE_GRAPH) && n > 0 && st != nullptr && ctx->trial_unit_cap == 0;
+  const bool graph_ok = (q->flags & PJ_USE_GRAPH) && st != nullptr && ctx->trial_unit_cap == 0;
+  // Speculative mode (graph mode, the filter's grid kept: the chunks of a
+  // streamed R after the first): the filter joins the captured sequence,
+  // with the capacity of the last join of this shape, so a chunk's join is
+  // one graph launch and one synchronization.  A chunk whose pairs exceed
+  // that capacity (or need the filter's slow path) runs again unspeculated.
+  const int64_t spec_cap = graph_ok && filter_grid_kept(ctx, R, S, tau) ? spec_cap_get(ctx, R, S, tau) : 0;
+  const bool spec = spec_cap > 0;
+  int* over = (int*)(ctx->d_counters + 12);   // the filter's slow-path / capacity word (zeroed with the counters)
+  Timer tf;
+  int64_t n = 0;
+  if (!spec) {
+    PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
+    PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+    n = filter_within(ctx, R, S, tau, st).n_pairs;
+  }
+  const int Lmax = std::max(R->L, S->L);
+  auto deadline_hit = [&]() { return q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0; };
+  const bool graph = graph_ok && (spec || n > 0);
   int64_t cap = n;
-  if (graph) {
+  if (spec) {
+    cap = spec_cap;
+  } else if (graph) {
     cap = 256;
     while (cap < n) cap <<= 1;
   }
   const int64_t nn = cap;
-  const int64_t* n_live = graph ? (const int64_t*)ctx->ws[WS_ROFF].p + R->n : nullptr;
+  const int64_t* n_live_0 = graph ? (const int64_t*)ctx->ws[WS_ROFF].p + R->n : nullptr;   // (reset after a speculative filter)
 
-  // the whole device sequence after the filter; false on an expired deadline
+  // the whole device sequence after the filter (with it, speculatively);
+  // false on an expired deadline
+  const int64_t* n_live = n_live_0;
   auto enqueue = [&](StepLog& log) -> bool {
+    if (spec) {
+      PJ_CK(cudaMemsetAsync(ctx->d_counters, 0, 15 * sizeof(unsigned long long), st));
+      PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+      filter_within_enqueue(ctx, R, S, tau, cap, over, st);
+      n_live = (const int64_t*)ctx->ws[WS_ROFF].p + R->n;   // the filter may have grown its arrays
+    }
     setup_pairs(ctx, R, S, nn, tau, true, st, n_live);
     if (learned) start_lod(ctx, R, S, nn, propose(ctx, R, S, nn, st, n_live), tau, st);
     if (ctx->sched_start > 0) {
@@ -613,7 +652,7 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
       log.add(ctx, uc, ev, sp, st);
     }
     gather_device(ctx, nn, st);
-    stage_status(ctx, nn, log.n, st);
+    stage_status(ctx, nn, log.n, st, spec ? n_live : nullptr);
     return true;
   };
 
@@ -622,9 +661,20 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   double ms_filter = 0;
   bool need_capture = false;
   Timer tseq;
+  // a speculative sequence also reads the kept grid: its parameters join the key
+  auto key_now = [&]() {
+    std::string k = graph_key(ctx, R, S, q, cap);
+    if (spec) {
+      char b[48];
+      snprintf(b, sizeof b, ".spec%016llx", (unsigned long long)fnv(1469598103934665603ULL, ctx->sgrid.grid,
+                                                                    sizeof ctx->sgrid.grid));
+      k += b;
+    }
+    return k;
+  };
   if (nn > 0) {
-    pj_ctx::GraphEntry* ge = graph ? graph_find(ctx, graph_key(ctx, R, S, q, cap)) : nullptr;
-    ms_filter = tf.ms();
+    pj_ctx::GraphEntry* ge = graph ? graph_find(ctx, key_now()) : nullptr;
+    ms_filter = spec ? 0.0 : tf.ms();
     if (ge) {
       // replay: one launch for the whole sequence
       if (deadline_hit()) return PJ_ETIMEOUT;
@@ -654,6 +704,19 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
     memcpy(&herr, h + STATUS_ERR, sizeof(int));
     memcpy(cnt, h + STATUS_CNT, sizeof cnt);
     snap = (const long long*)(h + STATUS_SNAP);
+    if (spec) {
+      // the speculated capacity held, and the ranked emit sufficed?
+      int64_t total = 0;
+      unsigned long long ov = 0;
+      memcpy(&total, h + STATUS_TOTAL, sizeof total);
+      memcpy(&ov, h + STATUS_CNT + 12 * sizeof(unsigned long long), sizeof ov);
+      if (ov != 0 || total > cap) {
+        spec_cap_set(ctx, R, S, tau, 0);   // this join runs unspeculated (and sets the capacity again)
+        ++ctx->spec_misses;
+        return join_within_once(ctx, R, S, q, out, st, stats);
+      }
+      n = total;
+    }
   } else {
     PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
@@ -670,14 +733,16 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   if (!strcmp(gmode, "replay")) PJ_CK(cudaEventElapsedTime(&graph_ms, ctx->ev[60], ctx->ev[61]));
   char buf[1500];
   snprintf(buf, sizeof buf,
-           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"graph_ms\":%.4f,"
+           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"spec\":%d,"
+           "\"graph_ms\":%.4f,"
            "\"capacity\":%lld,"
            "\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"tests_needed\":%llu,\"confirmed\":%llu,"
            "\"removed\":%llu,\"redecide\":%llu,"
            "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
-           tau, fp64 ? "fp64" : "fp32", learned ? 1 : 0, gmode, graph_ms, (long long)nn, (long long)n, (long long)m,
+           tau, fp64 ? "fp64" : "fp32", learned ? 1 : 0, gmode, spec ? 1 : 0, graph_ms, (long long)nn, (long long)n,
+           (long long)m,
            cnt[0],
            cnt[1], cnt[5], cnt[6], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
            ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
@@ -698,14 +763,21 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
   js.graph = !strcmp(gmode, "replay") ? 2 : (!strcmp(gmode, "captured") ? 1 : 0);
   js.ms_seq = ms_seq;
   js.graph_ms = graph_ms;
+  js.spec = spec ? 1 : 0;
   if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
   if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
   if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
   if (herr & ERR_NONFINITE) return PJ_ENONFINITE;   // data of a LoD built on demand
+  if (graph_ok && !spec && filter_grid_kept(ctx, R, S, tau)) {
+    // the next join of this shape speculates with a quarter of headroom
+    int64_t c = 256;
+    while (c < n + n / 4) c <<= 1;
+    spec_cap_set(ctx, R, S, tau, c);
+  }
   if (need_capture) {
     // the direct run sized every buffer: capture the same sequence now
     // (recorded, not executed) under a key taken after it
-    const std::string key = graph_key(ctx, R, S, q, cap);
+    const std::string key = key_now();
     const unsigned long long l0 = ctx->launches;
     StepLog glog;
     cudaGraph_t g = nullptr;

@@ -610,7 +610,8 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   std::vector<uint8_t> ex;
   JoinSummary tot;
   int64_t objects = 0;
-  int graph_replays = 0, graph_captures = 0;
+  int graph_replays = 0, graph_captures = 0, spec_joins = 0;
+  const unsigned long long misses0 = ctx->spec_misses;
   ctx->last_tune.clear();
   // the chunk joins run on the context's greatest-priority stream, after
   // whatever the caller queued on st, so that their many small launches are
@@ -693,6 +694,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     tot.refine_ms64 += js.refine_ms64;
     tot.launches += js.launches;
     graph_replays += js.graph == 2;
+    spec_joins += js.spec;
     graph_captures += js.graph == 1;
     for (int64_t i = 0; i < part.n; ++i) {
       rr.push_back((int32_t)(part.r[i] + P.first_id));
@@ -719,19 +721,20 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     memcpy(out->exact, ex.data(), m);
   }
   const double ms_total = tall.ms();
-  char buf[1024];
+  char buf[2048];
   snprintf(buf, sizeof buf,
            "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,"
            "\"bytes_h2d\":%zu,\"bytes_host_read_max\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
            "\"ms_wait_loader\":%.3f,\"ms_issue\":%.3f,\"ms_build\":%.3f,\"ms_join\":%.3f,\"ms_filter\":%.3f,"
            "\"ms_seq\":%.3f,\"graph_ms\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"ms_total\":%.3f,\"launches\":%llu,"
-           "\"graph_replays\":%d,\"graph_captures\":%d",
+           "\"graph_replays\":%d,\"graph_captures\":%d,\"spec_joins\":%d,\"spec_misses\":%llu",
            q->pred == PJ_KNN ? "knn" : "within", N, (long long)objects, (long long)tot.candidates, (long long)m,
            tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, bytes_host_read, ms_h2d,
            ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, ms_issue, ms_build, ms_join, tot.ms_filter, tot.ms_seq, tot.graph_ms,
            tot.refine_ms32,
-           tot.refine_ms64, ms_total, tot.launches, graph_replays, graph_captures);
+           tot.refine_ms64, ms_total, tot.launches, graph_replays, graph_captures, spec_joins,
+           ctx->spec_misses - misses0);
   // the autotuner's choice for the chunks (tuned on the first, reused after)
   stats = std::string(buf) + (ctx->last_tune.empty() ? "" : ",\"autotune\":" + ctx->last_tune) + "}";
   tot.results = m;
