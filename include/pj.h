@@ -158,7 +158,11 @@ typedef struct {
  * "unit_budget_mb" (1 .. 2^20, default 512: the refinement-unit buffer is
  * sized for a step's worst case when that fits this budget; otherwise units
  * are emitted into the buffer as it is, and a join whose units overflowed
- * it grows the buffer to the count needed and runs again) and
+ * it grows the buffer to the count needed and runs again), "chunk_overlap"
+ * (1, the default, or 0: a streamed within-tau / intersection join with
+ * PJ_USE_GRAPH takes its chunks in turn on the context and a second,
+ * internal join context with its own workspace and stream, so that one
+ * chunk's join is issued before the previous one is waited for) and
  * "autotune_cache" (path string).  The options change scheduling only,
  * never a result.  Fails with PJ_ECUDA when the device is not compute
  * capability 10.3 (GB300). */

@@ -500,6 +500,49 @@ static std::string json_str(const char* js, const char* key) {
   return s.substr(p, e - p);
 }
 
+pj_ctx* join_twin(pj_ctx* ctx) {
+  if (!ctx->twin) {
+    pj_ctx* t = new pj_ctx();
+    t->device = ctx->device;
+    t->sm_count = ctx->sm_count;
+    t->cc_major = ctx->cc_major;
+    t->cc_minor = ctx->cc_minor;
+    try {
+      PJ_CK(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
+      int lo = 0, hi = 0;
+      PJ_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      PJ_CK(cudaStreamCreateWithPriority(&t->join_stream, cudaStreamNonBlocking, hi));
+      note_alloc();
+      PJ_CK(cudaMalloc((void**)&t->d_err, sizeof(int)));
+      note_alloc();
+      PJ_CK(cudaMalloc((void**)&t->d_counters, 16 * sizeof(unsigned long long)));
+      PJ_CK(cudaMemset(t->d_err, 0, sizeof(int)));
+      PJ_CK(cudaMemset(t->d_counters, 0, 16 * sizeof(unsigned long long)));
+      for (auto& e : t->ev) PJ_CK(cudaEventCreate(&e));
+      note_alloc();
+      PJ_CK(cudaMalloc((void**)&t->d_snap, 64 * 4 * sizeof(long long)));
+    } catch (...) {
+      pj_destroy(t);
+      throw;
+    }
+    t->borrowed_mlp = true;
+    ctx->twin = t;
+  }
+  pj_ctx* t = ctx->twin;
+  t->ctas_per_sm = ctx->ctas_per_sm;
+  t->refine_variant = ctx->refine_variant;
+  t->variant_fixed = ctx->variant_fixed;
+  t->refine_split = ctx->refine_split;
+  t->refine_tail = ctx->refine_tail;
+  t->split_fixed = ctx->split_fixed;
+  t->sched_start = ctx->sched_start;
+  t->unit_budget = ctx->unit_budget;
+  t->mlp_w = ctx->mlp_w;
+  t->mlp_ready = ctx->mlp_ready;
+  t->tuned = ctx->tuned;
+  return t;
+}
+
 }  // namespace pj
 
 using namespace pj;
@@ -612,6 +655,8 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
     ctx->refine_split = k;
     ctx->split_fixed = true;
   }
+  v = json_str(options_json, "chunk_overlap");
+  if (!v.empty()) ctx->chunk_overlap = atoi(v.c_str()) != 0;
   v = json_str(options_json, "zero_copy");
   if (!v.empty()) ctx->zero_copy = atoi(v.c_str()) != 0;
   v = json_str(options_json, "refine_tail");
@@ -656,13 +701,17 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
 void pj_destroy(pj_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  if (ctx->twin) {
+    pj_destroy(ctx->twin);
+    ctx->twin = nullptr;
+  }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   graphs_clear(ctx);
   destroy_pack_pool(ctx->pack_pool);
   for (auto& b : ctx->ws) cudaFree(b.p);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_counters);
-  cudaFree(ctx->mlp_w);
+  if (!ctx->borrowed_mlp) cudaFree(ctx->mlp_w);
   cudaFree(ctx->d_snap);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   for (void* hp : ctx->stream_pinned)

@@ -228,6 +228,12 @@ struct pj_ctx {
   std::vector<SpecCap> spec_caps;
   unsigned long long spec_misses = 0;   // speculative joins that ran again unspeculated
   pj::PackPool* pack_pool = nullptr;   // created by the first streamed join, kept until pj_destroy
+  // a second join context (own workspace, counters, stage, graphs and join
+  // stream; the proposal weights borrowed) that takes every other chunk of a
+  // streamed within join, so that two chunks' joins overlap on the device
+  pj_ctx* twin = nullptr;
+  bool borrowed_mlp = false;         // mlp_w belongs to another context
+  bool chunk_overlap = true;         // option "chunk_overlap": streamed within joins use the twin
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};
   void* stream_box_pinned[2] = {};  // pinned copies of a chunk's object boxes and error word
@@ -459,5 +465,40 @@ struct Timer {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
 };
+
+// State of a within join between the issue of its device work and its
+// completion (join.cu).
+struct WithinTail {
+  pj_ctx* ctx;
+  const pj_set* R;
+  const pj_set* S;
+  pj_query q;
+  cudaStream_t st;
+  double tau;
+  bool fp64, learned, spec, graph_ok;
+  int64_t n, cap, nn;
+  const char* gmode;
+  StepLog log;
+  unsigned long long launches0;
+  Timer tall, tseq;
+  double ms_filter;
+  bool reran = false;
+};
+
+// A within join whose device work may still be in flight when it returns:
+// with pend set, a join replayed from a graph returns PJ_PENDING after the
+// launch and fills *pend; within_finish then waits for it and completes it.
+// Any other join completes before returning.
+constexpr pj_status PJ_PENDING = (pj_status)1;
+// The context's twin (created on first use); its settings follow ctx's.
+pj_ctx* join_twin(pj_ctx* ctx);
+// The autotuner's choice stored in `from` for the workload set on `to` (it
+// stays set); false when nothing is stored yet.
+bool tuned_apply(pj_ctx* from, pj_ctx* to, const pj_set* R, const pj_set* S, const pj_query* q);
+pj_status join_within_issue(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                            cudaStream_t st, std::string& stats, WithinTail* pend);
+pj_status within_finish(WithinTail& w, pj_result* out, std::string& stats);
+pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                      cudaStream_t st, std::string& stats);
 
 }  // namespace pj

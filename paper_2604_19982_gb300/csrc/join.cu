@@ -521,7 +521,113 @@ static void spec_cap_set(pj_ctx* ctx, const pj_set* R, const pj_set* S, double t
 }
 
 static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q,
-                                  pj_result* out, cudaStream_t st, std::string& stats) {
+                                  pj_result* out, cudaStream_t st, std::string& stats, WithinTail* pend = nullptr);
+
+// The part of a within join after its device work: read the staged status
+// (a speculated capacity that did not hold reruns the join unspeculated),
+// copy the results out and write the stats.  w.reran is set when the join
+// ran again (its results and stats are then the rerun's).
+static pj_status within_tail(WithinTail& w, double ms_seq, pj_result* out, std::string& stats) {
+  pj_ctx* ctx = w.ctx;
+  const pj_set* R = w.R;
+  const pj_set* S = w.S;
+  const pj_query* q = &w.q;
+  cudaStream_t st = w.st;
+  const double tau = w.tau;
+  const bool fp64 = w.fp64, learned = w.learned, spec = w.spec, graph_ok = w.graph_ok;
+  int64_t& n = w.n;
+  const int64_t cap = w.cap, nn = w.nn;
+  const char* gmode = w.gmode;
+  StepLog& log = w.log;
+  const unsigned long long launches0 = w.launches0;
+  const Timer& tall = w.tall;
+  const double ms_filter = w.ms_filter;
+  // after the synchronization the error word, the counters and the step
+  // snapshots are in the pinned stage (with candidates; else read here)
+  int herr = 0;
+  unsigned long long cnt[8];
+  const long long* snap = nullptr;
+  if (nn > 0) {
+    const char* h = staged_status(ctx, nn);
+    memcpy(&herr, h + STATUS_ERR, sizeof(int));
+    memcpy(cnt, h + STATUS_CNT, sizeof cnt);
+    snap = (const long long*)(h + STATUS_SNAP);
+    if (spec) {
+      // the speculated capacity held, and the ranked emit sufficed?
+      int64_t total = 0;
+      unsigned long long ov = 0;
+      memcpy(&total, h + STATUS_TOTAL, sizeof total);
+      memcpy(&ov, h + STATUS_CNT + 12 * sizeof(unsigned long long), sizeof ov);
+      if (ov != 0 || total > cap) {
+        spec_cap_set(ctx, R, S, tau, 0);   // this join runs unspeculated (and sets the capacity again)
+        ++ctx->spec_misses;
+        w.reran = true;
+        return join_within_once(ctx, R, S, q, out, st, stats);
+      }
+      n = total;
+    }
+  } else {
+    PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
+    PJ_CK(cudaStreamSynchronize(st));
+  }
+  // a step whose units overflowed the buffer voids the join (rerun)
+  check_units(ctx, herr);
+  Timer tg;
+  const int64_t m = gather_host(ctx, nn, out);
+  double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
+  int64_t tiles_total = 0;
+  const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total, snap);
+  float graph_ms = 0.f;
+  if (!strcmp(gmode, "replay")) PJ_CK(cudaEventElapsedTime(&graph_ms, ctx->ev[60], ctx->ev[61]));
+  char buf[1500];
+  snprintf(buf, sizeof buf,
+           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"spec\":%d,"
+           "\"graph_ms\":%.4f,"
+           "\"capacity\":%lld,"
+           "\"candidates\":%lld,\"results\":%lld,"
+           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"tests_needed\":%llu,\"confirmed\":%llu,"
+           "\"removed\":%llu,\"redecide\":%llu,"
+           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
+           "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
+           tau, fp64 ? "fp64" : "fp32", learned ? 1 : 0, gmode, spec ? 1 : 0, graph_ms, (long long)nn, (long long)n,
+           (long long)m,
+           cnt[0],
+           cnt[1], cnt[5], cnt[6], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
+           ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
+  stats = std::string(buf) + steps + "}";
+  JoinSummary& js = ctx->last_sum;
+  js.candidates = n;
+  js.results = m;
+  js.units = tiles_total;
+  js.tests32 = cnt[0];
+  js.tests64 = cnt[1];
+  js.confirmed = cnt[2];
+  js.removed = cnt[3];
+  js.ms_filter = ms_filter;
+  js.ms_total = tall.ms();
+  js.refine_ms32 = refine_ms_fp32;
+  js.refine_ms64 = refine_ms_fp64;
+  js.launches = ctx->launches - launches0;
+  js.graph = !strcmp(gmode, "replay") ? 2 : (!strcmp(gmode, "captured") ? 1 : 0);
+  js.ms_seq = ms_seq;
+  js.graph_ms = graph_ms;
+  js.spec = spec ? 1 : 0;
+  if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
+  if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
+  if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
+  if (herr & ERR_NONFINITE) return PJ_ENONFINITE;   // data of a LoD built on demand
+  if (graph_ok && !spec && filter_grid_kept(ctx, R, S, tau)) {
+    // the next join of this shape speculates with a quarter of headroom
+    int64_t c = 256;
+    while (c < n + n / 4) c <<= 1;
+    spec_cap_set(ctx, R, S, tau, c);
+  }
+  return PJ_OK;
+}
+
+static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q,
+                                  pj_result* out, cudaStream_t st, std::string& stats, WithinTail* pend) {
   Timer tall;
   const unsigned long long launches0 = ctx->launches;
   const double tau = q->pred == PJ_INTERSECT ? 0.0 : q->tau;
@@ -684,6 +790,12 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
       ctx->launches += ge->kernels;
       static_cast<StepLogData&>(log) = ge->log;
       gmode = "replay";
+      if (pend) {
+        // the caller completes it (within_finish) after issuing other work
+        *pend = WithinTail{ctx, R, S, *q, st, tau, fp64, learned, spec, graph_ok, n, cap, nn, gmode, log, launches0,
+                           tall, tseq, ms_filter};
+        return PJ_PENDING;
+      }
     } else {
       if (!enqueue(log)) return PJ_ETIMEOUT;
       if (graph) gmode = "captured";
@@ -694,85 +806,11 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
     ms_filter = tf.ms();
   }
   const double ms_seq = tseq.ms();   // the post-filter sequence, issue to completion
-  // after the synchronization the error word, the counters and the step
-  // snapshots are in the pinned stage (with candidates; else read here)
-  int herr = 0;
-  unsigned long long cnt[8];
-  const long long* snap = nullptr;
-  if (nn > 0) {
-    const char* h = staged_status(ctx, nn);
-    memcpy(&herr, h + STATUS_ERR, sizeof(int));
-    memcpy(cnt, h + STATUS_CNT, sizeof cnt);
-    snap = (const long long*)(h + STATUS_SNAP);
-    if (spec) {
-      // the speculated capacity held, and the ranked emit sufficed?
-      int64_t total = 0;
-      unsigned long long ov = 0;
-      memcpy(&total, h + STATUS_TOTAL, sizeof total);
-      memcpy(&ov, h + STATUS_CNT + 12 * sizeof(unsigned long long), sizeof ov);
-      if (ov != 0 || total > cap) {
-        spec_cap_set(ctx, R, S, tau, 0);   // this join runs unspeculated (and sets the capacity again)
-        ++ctx->spec_misses;
-        return join_within_once(ctx, R, S, q, out, st, stats);
-      }
-      n = total;
-    }
-  } else {
-    PJ_CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PJ_CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
-    PJ_CK(cudaStreamSynchronize(st));
-  }
-  // a step whose units overflowed the buffer voids the join (rerun)
-  check_units(ctx, herr);
-  Timer tg;
-  const int64_t m = gather_host(ctx, nn, out);
-  double refine_ms_fp32 = 0, refine_ms_fp64 = 0;
-  int64_t tiles_total = 0;
-  const std::string steps = log.json(ctx, &refine_ms_fp32, &refine_ms_fp64, &tiles_total, snap);
-  float graph_ms = 0.f;
-  if (!strcmp(gmode, "replay")) PJ_CK(cudaEventElapsedTime(&graph_ms, ctx->ev[60], ctx->ev[61]));
-  char buf[1500];
-  snprintf(buf, sizeof buf,
-           "{\"pred\":\"within\",\"tau\":%.17g,\"prec\":\"%s\",\"mlp\":%d,\"graph\":\"%s\",\"spec\":%d,"
-           "\"graph_ms\":%.4f,"
-           "\"capacity\":%lld,"
-           "\"candidates\":%lld,\"results\":%lld,"
-           "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"tests_needed\":%llu,\"confirmed\":%llu,"
-           "\"removed\":%llu,\"redecide\":%llu,"
-           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
-           "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
-           tau, fp64 ? "fp64" : "fp32", learned ? 1 : 0, gmode, spec ? 1 : 0, graph_ms, (long long)nn, (long long)n,
-           (long long)m,
-           cnt[0],
-           cnt[1], cnt[5], cnt[6], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
-           ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
-  stats = std::string(buf) + steps + "}";
-  JoinSummary& js = ctx->last_sum;
-  js.candidates = n;
-  js.results = m;
-  js.units = tiles_total;
-  js.tests32 = cnt[0];
-  js.tests64 = cnt[1];
-  js.confirmed = cnt[2];
-  js.removed = cnt[3];
-  js.ms_filter = ms_filter;
-  js.ms_total = tall.ms();
-  js.refine_ms32 = refine_ms_fp32;
-  js.refine_ms64 = refine_ms_fp64;
-  js.launches = ctx->launches - launches0;
-  js.graph = !strcmp(gmode, "replay") ? 2 : (!strcmp(gmode, "captured") ? 1 : 0);
-  js.ms_seq = ms_seq;
-  js.graph_ms = graph_ms;
-  js.spec = spec ? 1 : 0;
-  if (herr & ERR_MBAR_TIMEOUT) return PJ_ETIMEOUT;
-  if (herr & ERR_CAPACITY) throw ApiError{PJ_ENOMEM, "refinement units above the unit buffer"};
-  if (herr & ERR_BOUNDS) return PJ_EBOUNDS;
-  if (herr & ERR_NONFINITE) return PJ_ENONFINITE;   // data of a LoD built on demand
-  if (graph_ok && !spec && filter_grid_kept(ctx, R, S, tau)) {
-    // the next join of this shape speculates with a quarter of headroom
-    int64_t c = 256;
-    while (c < n + n / 4) c <<= 1;
-    spec_cap_set(ctx, R, S, tau, c);
+  {
+    WithinTail w{ctx, R, S, *q, st, tau, fp64, learned, spec, graph_ok, n, cap, nn, gmode, log, launches0, tall,
+                 tseq, ms_filter};
+    const pj_status rc = within_tail(w, ms_seq, out, stats);
+    if (rc != PJ_OK || w.reran) return rc;
   }
   if (need_capture) {
     // the direct run sized every buffer: capture the same sequence now
@@ -818,6 +856,28 @@ static pj_status join_within_once(pj_ctx* ctx, const pj_set* R, const pj_set* S,
 // A within / intersection join; reruns (at most three times) when a step's
 // refinement units did not fit the unit buffer, which is then grown to the
 // count that step needed.
+pj_status join_within_issue(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
+                            cudaStream_t st, std::string& stats, WithinTail* pend) {
+  try {
+    return join_within_once(ctx, R, S, q, out, st, stats, pend);
+  } catch (const UnitsOverflow& e) {
+    grow_units(ctx, e.units, st);
+    return join_within(ctx, R, S, q, out, st, stats);
+  }
+}
+
+pj_status within_finish(WithinTail& w, pj_result* out, std::string& stats) {
+  PJ_CK(cudaStreamSynchronize(w.st));
+  try {
+    return within_tail(w, w.tseq.ms(), out, stats);
+  } catch (const UnitsOverflow& e) {
+    // the replay's units overflowed the buffer of its capture: grow it and
+    // run the join again (directly, then captured anew)
+    grow_units(w.ctx, e.units, w.st);
+    return join_within(w.ctx, w.R, w.S, &w.q, out, w.st, stats);
+  }
+}
+
 pj_status join_within(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                       cudaStream_t st, std::string& stats) {
   for (int attempt = 0;; ++attempt) {

@@ -339,7 +339,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   bool stop = false;
   pj_status lerr = PJ_OK;
   std::string lmsg;
-  double ms_fill = 0, ms_pack = 0;
+  double ms_fill = 0, ms_pack = 0, ms_plan = 0, ms_loader_idle = 0;
   int L_first = 0;
   struct Events {
     cudaEvent_t e[8] = {};
@@ -377,6 +377,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     for (int c = 0; c < N; ++c) {
       ChunkSlot& sl = slots[c & 1];
       bool copying;
+      auto ti = std::chrono::steady_clock::now();
       {
         std::unique_lock<std::mutex> lk(mu);
         cv.wait(lk, [&] { return stop || sl.state != ChunkSlot::FILLED; });
@@ -384,7 +385,9 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
         copying = sl.state == ChunkSlot::COPYING;
       }
       // the pinned slot is reused once its previous copy has landed
-      if (copying && cudaEventSynchronize(sl.copied) != cudaSuccess) {
+      const bool copy_ok = !copying || cudaEventSynchronize(sl.copied) == cudaSuccess;
+      ms_loader_idle += ms_since(ti);
+      if (!copy_ok) {
         std::lock_guard<std::mutex> lk(mu);
         lerr = PJ_ECUDA;
         lmsg = "loader: waiting for a chunk copy failed";
@@ -405,8 +408,10 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
         msg = "the fill callback returned " + std::to_string((int)rc) + " for chunk " + std::to_string(c);
       } else {
         try {
+          auto tp = std::chrono::steady_clock::now();
           pieces.clear();
           plan_chunk(&d, L_first, P, pieces, offs);
+          ms_plan += ms_since(tp);
           P.pieces = pieces;
           if (c == 0) L_first = P.L;
           P.index = c;
@@ -631,6 +636,83 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       if (e) cudaEventDestroy(e);
     }
   } rejoin(caller, st);
+  // Within joins with graph replay take the chunks in turn on two join
+  // contexts (ctx and its twin, each with its own workspace and join
+  // stream): chunk c's join is issued before chunk c-1's is waited for, so
+  // the two overlap on the device, and the next chunk's copy and set
+  // building are issued once chunk c-1's slot is free.
+  const bool overlap = ctx->chunk_overlap && q->pred != PJ_KNN && (q->flags & PJ_USE_GRAPH) && N > 1;
+  pj_ctx* J[2] = {ctx, overlap ? join_twin(ctx) : ctx};
+  cudaStream_t JS[2] = {st, overlap ? J[1]->join_stream : st};
+  struct KnobSave {   // the tuned choice set on ctx for the chunks is undone on exit
+    pj_ctx* c;
+    int v, s, k, t;
+    ~KnobSave() {
+      c->refine_variant = v;
+      c->sched_start = s;
+      c->refine_split = k;
+      c->refine_tail = t;
+    }
+  } knobs{ctx, ctx->refine_variant, ctx->sched_start, ctx->refine_split, ctx->refine_tail};
+  struct Quiesce {   // no chunk join stays in flight past this call
+    cudaStream_t a, b;
+    ~Quiesce() {
+      cudaStreamSynchronize(a);
+      if (b != a) cudaStreamSynchronize(b);
+    }
+  } quiesce{JS[0], JS[1]};
+  const unsigned long long twin_misses0 = overlap ? J[1]->spec_misses : 0;
+  struct Pending {
+    bool on = false;
+    WithinTail w;
+    pj_result part;
+    int64_t first = 0;
+    int n = 0;
+  } pend;
+  // a completed chunk join: totals and results (chunks complete in order)
+  auto absorb = [&](const JoinSummary& js, pj_result& part, int64_t first, int nobj) {
+    tot.candidates += js.candidates;
+    tot.results += js.results;
+    tot.units += js.units;
+    tot.tests32 += js.tests32;
+    tot.tests64 += js.tests64;
+    tot.confirmed += js.confirmed;
+    tot.removed += js.removed;
+    tot.ms_filter += js.ms_filter;
+    tot.ms_seq += js.ms_seq;
+    tot.graph_ms += js.graph_ms;
+    tot.refine_ms32 += js.refine_ms32;
+    tot.refine_ms64 += js.refine_ms64;
+    tot.launches += js.launches;
+    graph_replays += js.graph == 2;
+    spec_joins += js.spec;
+    graph_captures += js.graph == 1;
+    for (int64_t i = 0; i < part.n; ++i) {
+      rr.push_back((int32_t)(part.r[i] + first));
+      ss.push_back(part.s[i]);
+      dlo.push_back(part.d_lo[i]);
+      dhi.push_back(part.d_hi[i]);
+      dd.push_back(part.d[i]);
+      ex.push_back(part.exact[i]);
+    }
+    free(part.priv);
+    part.priv = nullptr;
+    objects += nobj;
+  };
+  std::string st_chunk;
+  auto finish_pending = [&]() -> pj_status {
+    if (!pend.on) return PJ_OK;
+    pend.on = false;
+    Timer tj;
+    const pj_status rc = within_finish(pend.w, &pend.part, st_chunk);
+    ms_join += tj.ms();
+    if (rc != PJ_OK) {
+      free(pend.part.priv);
+      return rc;
+    }
+    absorb(pend.w.ctx->last_sum, pend.part, pend.first, pend.n);
+    return PJ_OK;
+  };
   for (int c = 0; c < N; ++c) {
     if (q->timeout_s > 0 && tall.ms() > q->timeout_s * 1000.0) return PJ_ETIMEOUT;
     Timer ti;
@@ -640,8 +722,9 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     }
     if (prepared[c & 1] != c) prepare(c);
     const Plan P = plans[c & 1];
-    // the copy and the set building of the next chunk overlap this chunk's join
-    if (c + 1 < N && enqueued == c + 1 && enqueue(c + 1, false)) {
+    // the copy and the set building of the next chunk overlap this chunk's
+    // join (with two joins in flight: issued below, once the slot is free)
+    if (!overlap && c + 1 < N && enqueued == c + 1 && enqueue(c + 1, false)) {
       enqueued = c + 2;
       prepare(c + 1);
     }
@@ -660,7 +743,9 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       const float* hb = (const float*)ctx->stream_box_pinned[c & 1];
       view.mbb_h.assign(hb, hb + (size_t)P.n * 6);
     }
-    PJ_CK(cudaStreamWaitEvent(st, built[c & 1], 0));
+    pj_ctx* Jc = J[c & 1];
+    cudaStream_t sc = JS[c & 1];
+    PJ_CK(cudaStreamWaitEvent(sc, built[c & 1], 0));
     ms_build += tb.ms();
     float h2d = 0;
     if (cudaEventElapsedTime(&h2d, h2d0[c & 1], h2d1[c & 1]) == cudaSuccess) ms_h2d += h2d;
@@ -669,43 +754,49 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     if (q->timeout_s > 0) qc.timeout_s = std::max(1e-3, q->timeout_s - tall.ms() / 1000.0);
     pj_result part;
     memset(&part, 0, sizeof part);
-    std::string st_chunk;
+    WithinTail w;
     Timer tj;
-    pj_status rc = (q->flags & PJ_AUTOTUNE) ? join_autotuned(ctx, &view, S, &qc, &part, st, st_chunk)
-                   : q->pred == PJ_KNN         ? join_knn(ctx, &view, S, &qc, &part, st, st_chunk)
-                                               : join_within(ctx, &view, S, &qc, &part, st, st_chunk);
+    pj_status rc;
+    if (overlap && (!(q->flags & PJ_AUTOTUNE) || tuned_apply(ctx, Jc, &view, S, &qc))) {
+      rc = join_within_issue(Jc, &view, S, &qc, &part, sc, st_chunk, &w);
+    } else {
+      rc = (q->flags & PJ_AUTOTUNE) ? join_autotuned(Jc, &view, S, &qc, &part, sc, st_chunk)
+           : q->pred == PJ_KNN      ? join_knn(Jc, &view, S, &qc, &part, sc, st_chunk)
+                                    : join_within(Jc, &view, S, &qc, &part, sc, st_chunk);
+    }
     ms_join += tj.ms();
-    if (rc != PJ_OK) {
+    if (rc != PJ_OK && rc != PJ_PENDING) {
       free(part.priv);
+      if (Jc != ctx) ctx->last_error = Jc->last_error;
       return rc;
     }
-    const JoinSummary& js = ctx->last_sum;
-    tot.candidates += js.candidates;
-    tot.results += js.results;
-    tot.units += js.units;
-    tot.tests32 += js.tests32;
-    tot.tests64 += js.tests64;
-    tot.confirmed += js.confirmed;
-    tot.removed += js.removed;
-    tot.ms_filter += js.ms_filter;
-    tot.ms_seq += js.ms_seq;
-    tot.graph_ms += js.graph_ms;
-    tot.refine_ms32 += js.refine_ms32;
-    tot.refine_ms64 += js.refine_ms64;
-    tot.launches += js.launches;
-    graph_replays += js.graph == 2;
-    spec_joins += js.spec;
-    graph_captures += js.graph == 1;
-    for (int64_t i = 0; i < part.n; ++i) {
-      rr.push_back((int32_t)(part.r[i] + P.first_id));
-      ss.push_back(part.s[i]);
-      dlo.push_back(part.d_lo[i]);
-      dhi.push_back(part.d_hi[i]);
-      dd.push_back(part.d[i]);
-      ex.push_back(part.exact[i]);
+    // chunk c-1 completes first (in order), then this one or it stays pending
+    const pj_status rp = finish_pending();
+    if (rp != PJ_OK) {
+      free(part.priv);
+      return rp;
     }
-    free(part.priv);
-    objects += P.n;
+    if (rc == PJ_PENDING) {
+      pend.on = true;
+      pend.w = w;
+      pend.part = part;
+      pend.first = P.first_id;
+      pend.n = P.n;
+    } else {
+      absorb(Jc->last_sum, part, P.first_id, P.n);
+    }
+    if (overlap) {
+      Timer ti2;
+      if (c + 1 < N && enqueued == c + 1 && enqueue(c + 1, false)) {
+        enqueued = c + 2;
+        prepare(c + 1);
+      }
+      ms_issue += ti2.ms();
+    }
+  }
+  {
+    const pj_status rp = finish_pending();
+    if (rp != PJ_OK) return rp;
   }
   if (objects != R->n_total)
     throw ApiError{PJ_ESOURCE, "the chunks hold " + std::to_string(objects) + " objects, the streamed set " +
@@ -725,16 +816,17 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   snprintf(buf, sizeof buf,
            "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"confirmed\":%llu,\"removed\":%llu,\"tiles\":%lld,"
-           "\"bytes_h2d\":%zu,\"bytes_host_read_max\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_pack\":%.3f,"
+           "\"bytes_h2d\":%zu,\"bytes_host_read_max\":%zu,\"ms_h2d\":%.3f,\"h2d_gbs\":%.2f,\"ms_fill\":%.3f,\"ms_plan\":%.3f,"
+           "\"ms_pack\":%.3f,\"ms_loader_idle\":%.3f,"
            "\"ms_wait_loader\":%.3f,\"ms_issue\":%.3f,\"ms_build\":%.3f,\"ms_join\":%.3f,\"ms_filter\":%.3f,"
            "\"ms_seq\":%.3f,\"graph_ms\":%.3f,\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"ms_total\":%.3f,\"launches\":%llu,"
            "\"graph_replays\":%d,\"graph_captures\":%d,\"spec_joins\":%d,\"spec_misses\":%llu",
            q->pred == PJ_KNN ? "knn" : "within", N, (long long)objects, (long long)tot.candidates, (long long)m,
            tot.tests32, tot.tests64, tot.confirmed, tot.removed, (long long)tot.units, bytes_h2d, bytes_host_read, ms_h2d,
-           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_pack, ms_wait, ms_issue, ms_build, ms_join, tot.ms_filter, tot.ms_seq, tot.graph_ms,
+           ms_h2d > 0 ? bytes_h2d / (ms_h2d * 1e6) : 0.0, ms_fill, ms_plan, ms_pack, ms_loader_idle, ms_wait, ms_issue, ms_build, ms_join, tot.ms_filter, tot.ms_seq, tot.graph_ms,
            tot.refine_ms32,
            tot.refine_ms64, ms_total, tot.launches, graph_replays, graph_captures, spec_joins,
-           ctx->spec_misses - misses0);
+           ctx->spec_misses - misses0 + (overlap ? J[1]->spec_misses - twin_misses0 : 0));
   // the autotuner's choice for the chunks (tuned on the first, reused after)
   stats = std::string(buf) + (ctx->last_tune.empty() ? "" : ",\"autotune\":" + ctx->last_tune) + "}";
   tot.results = m;

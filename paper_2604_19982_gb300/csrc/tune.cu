@@ -139,6 +139,20 @@ bool tuned_schedule_fixed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const p
   return lookup(ctx, key_of(R, S, q), &c) && c.start >= 0;
 }
 
+// Set the choice stored in `from` for this workload on `to` (it stays
+// set); false when nothing is stored yet.
+bool tuned_apply(pj_ctx* from, pj_ctx* to, const pj_set* R, const pj_set* S, const pj_query* q) {
+  Choice c{0, -1, 0};
+  if (!lookup(from, key_of(R, S, q), &c)) return false;
+  to->refine_variant = c.variant;
+  to->sched_start = c.start;
+  if (c.split > 0) {
+    to->refine_split = c.split;
+    to->refine_tail = ALL_UNITS_TAIL;
+  }
+  return true;
+}
+
 // A join of a resident R (or one streamed chunk) with PJ_AUTOTUNE.
 pj_status join_autotuned(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_query* q, pj_result* out,
                          cudaStream_t st, std::string& stats) {

@@ -81,36 +81,47 @@ def test_graph_streamed_chunks(ctx, sets):
     g.free()
 
 
-def test_graph_streamed_speculative(ctx, sets):
-    """After the first chunk of a streamed R, a chunk's whole join (filter
-    included) runs as one graph with the capacity of the last chunk; a chunk
-    with more pairs than that capacity runs again unspeculated.  Either way
-    the result equals the resident join of the same objects."""
+@pytest.mark.parametrize("overlap", [0, 1])
+def test_graph_streamed_speculative(sets, overlap):
+    """After the first chunk of a streamed R on a join context, a chunk's
+    whole join (filter included) runs as one graph with the capacity of the
+    context's last chunk; a chunk with more pairs than that capacity runs
+    again unspeculated.  With chunk_overlap the chunks alternate between the
+    context and its twin (two joins in flight), each with its own grid and
+    capacity.  Either way the result equals the resident join of the same
+    objects."""
     from paper_2604_19982_gb300 import pj
     from synth.mesh import concat
-    w, gR, gS = sets
+    w, _, _ = sets
+    c = pj.Context(0, {"chunk_overlap": overlap})
+    gS = c.load_set(w.S)
     side = configs.scaled_side(400.0, 20_000, 4000)
     # chunks 0-2: blobs placed like S's, some tens of candidate pairs each;
     # chunk 3: copies of S's first 400 blobs (every one meets its copy), more
-    # pairs than the capacity speculated from chunk 0
+    # pairs than the capacity speculated from the earlier chunks
     parts = [configs.blob_set(400, side, 5, 0), configs.blob_set(400, side, 6, 0),
              configs.blob_set(400, side, 7, 0), configs.blob_set(4000, side, 0, 1, start=0, count=400)]
     whole = concat(parts)
-    gW = ctx.load_set(whole)
-    fl = dict(prec=pj.FP32, flags=pj.TILE_PRUNE | pj.EXACT_DIST)
-    ref = ctx.join(gW, gS, pj.WITHIN, tau=1.0, **fl)
-    g = ctx.load_set_streamed(whole.n, len(parts), lambda c: parts[c])
+    gW = c.load_set(whole)
+    fl = pj.TILE_PRUNE | pj.EXACT_DIST
+    ref = c.join(gW, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl)
+    g = c.load_set_streamed(whole.n, len(parts), lambda i: parts[i])
     for i in range(3):
-        res = ctx.join(g, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl["flags"] | pj.USE_GRAPH)
-        st = ctx.stats()
+        res = c.join(g, gS, pj.WITHIN, tau=1.0, prec=pj.FP32, flags=fl | pj.USE_GRAPH)
+        st = c.stats()
         same(ref, res)
         if i == 0:
-            # chunk 0 unspeculated, 1 and 2 speculated, 3 over the capacity
-            assert st["spec_joins"] == 2 and st["spec_misses"] == 1
+            # the first chunk of each join context runs unspeculated; chunk 3
+            # exceeds the capacity speculated from its context's first chunk
+            assert st["spec_joins"] == (1 if overlap else 2) and st["spec_misses"] == 1
         else:
-            assert st["spec_joins"] >= 2 and st["graph_replays"] >= 2
+            # every chunk speculated; by the third join every graph is captured
+            assert st["spec_joins"] == 4 and st["spec_misses"] == 0
+            assert st["graph_replays"] == 4 or i == 1
     g.free()
     gW.free()
+    gS.free()
+    c.close()
 
 
 def test_graph_flag_ignored_for_knn(ctx, sets):
