@@ -341,6 +341,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   std::string lmsg;
   double ms_fill = 0, ms_pack = 0, ms_plan = 0, ms_loader_idle = 0;
   int L_first = 0;
+  int64_t next_first = 0;
   struct Events {
     cudaEvent_t e[8] = {};
     ~Events() {
@@ -367,14 +368,27 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
   Plan plans[2];   // the calling thread's copy of the plan of each slot in flight
   const int device = ctx->device;
 
-  // ---- loader thread: fill, check, pack
-  std::thread loader([&]() {
+  // ---- loader threads: fill, check, pack.  Two threads, one per slot
+  // (chunk c goes to loader c & 1): the fill callbacks are made in chunk
+  // order, one at a time (next_fill), while a chunk's layout and packing
+  // overlap the next chunk's fill.
+  int next_fill = 0;
+  double ms_fill_l[2] = {0, 0}, ms_plan_l[2] = {0, 0}, ms_pack_l[2] = {0, 0}, ms_idle_l[2] = {0, 0};
+  auto loader_body = [&](int p) {
     cudaSetDevice(device);
-    int64_t first = 0;
     std::vector<Piece> pieces;
     std::vector<PackJob> jobs;
     std::vector<std::vector<int64_t>> offs;
-    for (int c = 0; c < N; ++c) {
+    auto fail_l = [&](pj_status e, const std::string& m) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (lerr == PJ_OK) {
+        lerr = e;
+        lmsg = m;
+      }
+      stop = true;
+      cv.notify_all();
+    };
+    for (int c = p; c < N; c += 2) {
       ChunkSlot& sl = slots[c & 1];
       bool copying;
       auto ti = std::chrono::steady_clock::now();
@@ -386,72 +400,69 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       }
       // the pinned slot is reused once its previous copy has landed
       const bool copy_ok = !copying || cudaEventSynchronize(sl.copied) == cudaSuccess;
-      ms_loader_idle += ms_since(ti);
       if (!copy_ok) {
-        std::lock_guard<std::mutex> lk(mu);
-        lerr = PJ_ECUDA;
-        lmsg = "loader: waiting for a chunk copy failed";
-        stop = true;
-        cv.notify_all();
+        fail_l(PJ_ECUDA, "loader: waiting for a chunk copy failed");
         return;
       }
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || next_fill == c; });
+        if (stop) return;
+      }
+      ms_idle_l[p] += ms_since(ti);
       pj_mesh_set_desc d;
       memset(&d, 0, sizeof d);
       auto t0 = std::chrono::steady_clock::now();
       const pj_status rc = R->fill(R->user, c, &d);
-      ms_fill += ms_since(t0);
-      Plan P;
-      pj_status err = PJ_OK;
-      std::string msg;
-      if (rc != PJ_OK) {
-        err = rc == PJ_ECANCELLED ? PJ_ECANCELLED : PJ_ESOURCE;
-        msg = "the fill callback returned " + std::to_string((int)rc) + " for chunk " + std::to_string(c);
-      } else {
-        try {
-          auto tp = std::chrono::steady_clock::now();
-          pieces.clear();
-          plan_chunk(&d, L_first, P, pieces, offs);
-          ms_plan += ms_since(tp);
-          P.pieces = pieces;
-          if (c == 0) L_first = P.L;
-          P.index = c;
-          P.first_id = first;
-          first += P.n;
-          if (first > R->n_total) throw ApiError{PJ_EINVAL, "the chunks hold more objects than the streamed set"};
-          t0 = std::chrono::steady_clock::now();
-          void*& hp = ctx->stream_pinned[c & 1];
-          size_t& hc = ctx->stream_pinned_cap[c & 1];
-          if (hc < P.bytes) {
-            if (hp) cudaFreeHost(hp);
-            hp = nullptr;
-            hc = 0;
-            note_alloc();
-            if (cudaHostAlloc(&hp, P.bytes, cudaHostAllocDefault) != cudaSuccess)
-              throw ApiError{PJ_ENOMEM, "pinned staging allocation failed"};
-            hc = P.bytes;
-          }
-          pack_parallel(ctx, pieces, static_cast<unsigned char*>(hp), jobs);
-          ms_pack += ms_since(t0);
-        } catch (const ApiError& e) {
-          err = e.st;
-          msg = e.msg;
-        }
+      ms_fill_l[p] += ms_since(t0);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        next_fill = c + 1;
       }
-      std::lock_guard<std::mutex> lk(mu);
-      if (err != PJ_OK) {
-        lerr = err;
-        lmsg = msg;
-        stop = true;
-        cv.notify_all();
+      cv.notify_all();
+      if (rc != PJ_OK) {
+        fail_l(rc == PJ_ECANCELLED ? PJ_ECANCELLED : PJ_ESOURCE,
+               "the fill callback returned " + std::to_string((int)rc) + " for chunk " + std::to_string(c));
         return;
       }
+      Plan P;
+      try {
+        auto tp = std::chrono::steady_clock::now();
+        pieces.clear();
+        plan_chunk(&d, 0, P, pieces, offs);
+        ms_plan_l[p] += ms_since(tp);
+        P.pieces = pieces;
+        P.index = c;
+        t0 = std::chrono::steady_clock::now();
+        void*& hp = ctx->stream_pinned[c & 1];
+        size_t& hc = ctx->stream_pinned_cap[c & 1];
+        if (hc < P.bytes) {
+          if (hp) cudaFreeHost(hp);
+          hp = nullptr;
+          hc = 0;
+          note_alloc();
+          if (cudaHostAlloc(&hp, P.bytes, cudaHostAllocDefault) != cudaSuccess)
+            throw ApiError{PJ_ENOMEM, "pinned staging allocation failed"};
+          hc = P.bytes;
+        }
+        pack_parallel(ctx, pieces, static_cast<unsigned char*>(hp), jobs);
+        ms_pack_l[p] += ms_since(t0);
+      } catch (const ApiError& e) {
+        fail_l(e.st, e.msg);
+        return;
+      }
+      std::lock_guard<std::mutex> lk(mu);
       sl.plan = P;
       sl.state = ChunkSlot::FILLED;
       cv.notify_all();
     }
-  });
+  };
+  std::thread loader0(loader_body, 0);
+  std::thread loader1;
+  if (N > 1) loader1 = std::thread(loader_body, 1);
   struct Joiner {
-    std::thread& t;
+    std::thread& t0;
+    std::thread& t1;
     std::mutex& mu;
     std::condition_variable& cv;
     bool& stop;
@@ -461,9 +472,10 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
         stop = true;
       }
       cv.notify_all();
-      if (t.joinable()) t.join();
+      if (t0.joinable()) t0.join();
+      if (t1.joinable()) t1.join();
     }
-  } joiner{loader, mu, cv, stop};
+  } joiner{loader0, loader1, mu, cv, stop};
 
   // ---- calling thread: copy, build, join
   int enqueued = 0;   // chunks whose copy has been issued
@@ -485,6 +497,13 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
         return false;
       }
     }
+    // object ids continue the previous chunk's; every chunk has the first
+    // chunk's LoD count (chunks are planned in parallel, checked here in order)
+    if (c == 0) L_first = sl.plan.L;
+    else if (sl.plan.L != L_first) throw ApiError{PJ_EINVAL, "chunk: n_lods differs from the first chunk"};
+    sl.plan.first_id = next_first;
+    next_first += sl.plan.n;
+    if (next_first > R->n_total) throw ApiError{PJ_EINVAL, "the chunks hold more objects than the streamed set"};
     const size_t bytes = sl.plan.bytes;
     unsigned char* dev = (unsigned char*)ws_get(ctx, (c & 1) ? WS_STREAM5 : WS_STREAM4, bytes, ctx->copy_stream);
     const unsigned char* pinned = (const unsigned char*)ctx->stream_pinned[c & 1];
@@ -812,6 +831,10 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
     memcpy(out->exact, ex.data(), m);
   }
   const double ms_total = tall.ms();
+  ms_fill = ms_fill_l[0] + ms_fill_l[1];
+  ms_plan = ms_plan_l[0] + ms_plan_l[1];
+  ms_pack = ms_pack_l[0] + ms_pack_l[1];
+  ms_loader_idle = ms_idle_l[0] + ms_idle_l[1];
   char buf[2048];
   snprintf(buf, sizeof buf,
            "{\"pred\":\"%s\",\"streamed\":1,\"chunks\":%d,\"objects\":%lld,\"candidates\":%lld,\"results\":%lld,"
