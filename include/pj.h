@@ -176,7 +176,8 @@ void pj_destroy(pj_ctx* ctx);
 pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out);
 
 /* A set streamed in n_chunks pieces during pj_join (R side only).  For each
- * chunk the library calls fill(user, chunk, &desc) from a loader thread; the
+ * chunk the library calls fill(user, chunk, &desc) from one of its two
+ * loader threads, in chunk order and never two calls at once; the
  * callback fills desc with that chunk's objects.  Object ids of chunk c
  * continue those of chunk c-1.  A fill returning PJ_ECANCELLED stops the
  * join with that status; any other non-zero value gives PJ_ESOURCE.
