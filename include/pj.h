@@ -183,7 +183,8 @@ pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out);
  * join with that status; any other non-zero value gives PJ_ESOURCE.
  * Where the arrays may live, and for how long:
  *   - pageable host memory: packed into the library's pinned staging, so it
- *     must stay valid until the next call of fill or the end of the join;
+ *     must stay valid until fill is called for chunk c + 2 (chunk c + 1 may
+ *     be filled while chunk c is still being packed) or the join ends;
  *   - pinned host memory (cudaHostAlloc / cudaHostRegister): copied to the
  *     device directly, without packing (the link-bound path); the hd, ph,
  *     per-object faces and own vertex arrays of the LoDs between the first
@@ -192,8 +193,8 @@ pj_status pj_load_set(pj_ctx* ctx, const pj_mesh_set_desc* desc, pj_set** out);
  *     unchanged until pj_join returns;
  *   - device memory (verts, faces, hd, ph, anchor only): read in place by
  *     the set-building kernels, likewise until pj_join returns.
- * vert_off and face_off are always host memory (read by the host; PJ_EINVAL
- * otherwise). */
+ * vert_off and face_off are always host memory (read by the host, with the
+ * lifetime of pageable arrays; PJ_EINVAL otherwise). */
 typedef pj_status (*pj_fill_fn)(void* user, int chunk, pj_mesh_set_desc* out);
 pj_status pj_load_set_streamed(pj_ctx* ctx, int64_t n_objects, int n_chunks, pj_fill_fn fill,
                                void* user, pj_set** out);

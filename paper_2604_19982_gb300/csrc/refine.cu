@@ -177,8 +177,11 @@ __global__ void __launch_bounds__(256, 4) k_emit_units(int64_t n, const int32_t*
   const unsigned below = (1u << lane) - 1u;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
-    if (!(status[p] == want && lod0[p] <= step)) continue;
+    // the selection and the ids are loaded together (the ids do not wait
+    // for the selection), then the per-object offsets in one more round
+    const uint8_t stv = status[p], l0v = lod0[p];
     const int r = pr[p], s = ps[p];
+    if (!(stv == want && l0v <= step)) continue;
     const float4 o = origin[p];
     const float t = thr[p];
     // facet, block and chunk indices are below 2^31 (a LoD holds fewer facets)

@@ -303,9 +303,7 @@ void destroy_pack_pool(PackPool* p) { delete p; }
 namespace {
 
 // Copy the packed pieces into the pinned slot: 1 MB slices over the pool's
-// threads (all host cores but two: the calling thread drives the GPU, the
-// loader fills the next chunk; at most 15), inline when there is a single
-// slice.
+// threads, inline when there is a single slice.
 void pack_parallel(pj_ctx* ctx, const std::vector<Piece>& pieces, unsigned char* dst, std::vector<PackJob>& jobs) {
   constexpr size_t SLICE = size_t(1) << 20;
   jobs.clear();
@@ -316,11 +314,7 @@ void pack_parallel(pj_ctx* ctx, const std::vector<Piece>& pieces, unsigned char*
     for (const PackJob& j : jobs) memcpy(dst + j.off, j.src, j.bytes);
     return;
   }
-  if (!ctx->pack_pool) {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    ctx->pack_pool = new PackPool(std::min(15u, hw > 3 ? hw - 3 : 1u));
-  }
-  ctx->pack_pool->run(jobs, dst);
+  ctx->pack_pool->run(jobs, dst);   // created before the loaders start
 }
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
@@ -457,6 +451,12 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       cv.notify_all();
     }
   };
+  if (!ctx->pack_pool) {
+    // all host cores but three: the calling thread drives the GPU, each
+    // loader fills a chunk (and copies too); at most 15
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    ctx->pack_pool = new PackPool(std::min(15u, hw > 3 ? hw - 3 : 1u));
+  }
   std::thread loader0(loader_body, 0);
   std::thread loader1;
   if (N > 1) loader1 = std::thread(loader_body, 1);

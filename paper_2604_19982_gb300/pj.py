@@ -6,6 +6,7 @@ is missing -- there is no CPU fallback.
 """
 from __future__ import annotations
 
+import collections
 import ctypes as C
 import json
 import os
@@ -237,14 +238,17 @@ class Context:
         from the library's loader thread during a join); raising
         :class:`Cancel` stops the join with PJ_ECANCELLED, any other
         exception with PJ_ESOURCE."""
-        keep_box = {}
+        # the arrays of the last two chunks stay referenced: the library may
+        # still lay out chunk c while it fills chunk c + 1 (on its other
+        # loader thread), and is done with it when it asks for chunk c + 2
+        keep_box = collections.deque(maxlen=2)
 
         def fill(user, chunk, out):
             try:
                 ms = chunk_fn(int(chunk))
                 keep = []
                 d = describe(ms, keep)
-                keep_box["cur"] = (keep, d)
+                keep_box.append((keep, d, ms))
                 C.memmove(out, C.byref(d), C.sizeof(MeshSetDesc))
                 return PJ_OK
             except Cancel:
