@@ -464,6 +464,7 @@ def stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32):
     value = sum_over_ranks(pairs, world) / (ms / 1000.0)
     tests = sum(s["tests_fp32"] + s["tests_fp64"] for s in stats)
     launches = int(sum(s["launches"] for s in stats))
+    join(gR, direct)   # tunes the direct key first, so the measured pass runs no trials
     _, kst = timed(ctx, stream, lambda: join(gR, direct), 1)
     roof = roofline(kst, nsm, measured32)
     last = stats[-1]
@@ -569,6 +570,7 @@ def blobs20k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
     sts = []
     ms, _ = timed(ctx, stream, lambda: sts.extend(_two(ctx, gR, gS, pj, stream, tuned)), steps)
     kst = []
+    _two(ctx, gR, gS, pj, stream, direct)   # tunes the direct keys first
     timed(ctx, stream, lambda: kst.extend(_two(ctx, gR, gS, pj, stream, direct)), 2)
     rec = {"workload": WORKLOADS["blobs20k"], "value": cands(sts) / (ms / 1000.0), "ms_per_step": ms / steps,
            "tri_tests_per_s": sum(s["tests_fp32"] + s["tests_fp64"] for s in sts) / (ms / 1000.0),
@@ -645,6 +647,7 @@ def tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
     for _ in range(3):
         run(gR, tuned)
     ms, sts = timed(ctx, stream, lambda: run(gR, tuned), steps)
+    run(gR, direct)   # tunes the direct key first
     _, kst = timed(ctx, stream, lambda: run(gR, direct), 1)
     rec = {"workload": WORKLOADS["tubes2k"], "value": sum(s["candidates"] for s in sts) / (ms / 1000.0),
            "ms_per_step": ms / steps,

@@ -162,8 +162,10 @@ typedef struct {
  * (1, the default, or 0: a streamed within-tau / intersection join with
  * PJ_USE_GRAPH takes its chunks in turn on the context and a second,
  * internal join context with its own workspace and stream, so that one
- * chunk's join is issued before the previous one is waited for) and
- * "autotune_cache" (path string).  The options change scheduling only,
+ * chunk's join is issued before the previous one is waited for),
+ * "host_read" (1, the default, or 0: copy the middle-LoD arrays of streamed
+ * chunks in pinned host memory like the others instead of reading them in
+ * place) and "autotune_cache" (path string).  The options change scheduling only,
  * never a result.  Fails with PJ_ECUDA when the device is not compute
  * capability 10.3 (GB300). */
 pj_status pj_create(pj_ctx** out, int device, const char* options_json);

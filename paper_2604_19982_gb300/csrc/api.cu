@@ -655,15 +655,8 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
     ctx->refine_split = k;
     ctx->split_fixed = true;
   }
-  v = json_str(options_json, "build_priority");
-  if (!v.empty() && atoi(v.c_str()) != 0) {
-    // the set building of streamed chunks at the join streams' priority
-    int lo = 0, hi = 0;
-    PJ_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    PJ_CK(cudaStreamDestroy(ctx->build_stream));
-    ctx->build_stream = nullptr;
-    PJ_CK(cudaStreamCreateWithPriority(&ctx->build_stream, cudaStreamNonBlocking, hi));
-  }
+  v = json_str(options_json, "host_read");
+  if (!v.empty()) ctx->host_read = atoi(v.c_str()) != 0;
   v = json_str(options_json, "chunk_overlap");
   if (!v.empty()) ctx->chunk_overlap = atoi(v.c_str()) != 0;
   v = json_str(options_json, "zero_copy");

@@ -234,6 +234,7 @@ struct pj_ctx {
   pj_ctx* twin = nullptr;
   bool borrowed_mlp = false;         // mlp_w belongs to another context
   bool chunk_overlap = true;         // option "chunk_overlap": streamed within joins use the twin
+  bool host_read = true;             // option "host_read": middle-LoD pinned chunk arrays read in place
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};
   void* stream_box_pinned[2] = {};  // pinned copies of a chunk's object boxes and error word

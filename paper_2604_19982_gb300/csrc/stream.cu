@@ -114,7 +114,7 @@ struct ChunkSlot {
 // vert_off and face_off must be host memory (read here); verts, faces,
 // hd, ph and anchor may lie anywhere.
 void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Piece>& pieces,
-                std::vector<std::vector<int64_t>>& offs) {
+                std::vector<std::vector<int64_t>>& offs, bool host_read) {
   const int n = D->n_objects, L = D->n_lods;
   if (n < 0 || L < 1 || L > PJ_MAX_LODS) throw ApiError{PJ_EINVAL, "chunk: n_objects < 0 or n_lods outside [1, 8]"};
   if (L_expect > 0 && L != L_expect) throw ApiError{PJ_EINVAL, "chunk: n_lods differs from the first chunk"};
@@ -129,7 +129,7 @@ void plan_chunk(const pj_mesh_set_desc* D, int L_expect, Plan& P, std::vector<Pi
   // copied but read in place over the host link by the kernels that lay
   // those objects out.
   const int lazy_from = L >= 2 ? 1 : L;
-  auto host_read_lod = [&](int l) { return l >= lazy_from && l < L - 1; };
+  auto host_read_lod = [&](int l) { return host_read && l >= lazy_from && l < L - 1; };
   // a caller array (kind from its address) or one computed here (packed);
   // a device array takes no room in the slot and is recorded in *dptr, and
   // so does a pinned one when host_read is set (its device address)
@@ -423,7 +423,7 @@ pj_status join_streamed(pj_ctx* ctx, const pj_set* R, const pj_set* S, const pj_
       try {
         auto tp = std::chrono::steady_clock::now();
         pieces.clear();
-        plan_chunk(&d, 0, P, pieces, offs);
+        plan_chunk(&d, 0, P, pieces, offs, ctx->host_read);
         ms_plan_l[p] += ms_since(tp);
         P.pieces = pieces;
         P.index = c;
