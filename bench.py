@@ -488,7 +488,7 @@ def stream_headline(args, data, ctx, pj, stream, world, rank, nsm, measured32):
         # below the link rate
         for _ in range(3):
             join(gRp, tuned)
-        ke = max(1, min(args.steps, 3))
+        ke = max(1, min(args.steps, 5))
         e2e_stats = []
 
         e2e_ms = []

@@ -273,8 +273,10 @@ static UnitCount build_units(pj_ctx* ctx, const pj_set* R, const pj_set* S, int6
   const LodData& LS = S->lod[sp.lodS];
   BoxView vr = box_view(LR), vs = box_view(LS);
   const int th = 256;
-  // a LoD built on demand: lay out the objects this step needs first
-  ensure_lod(ctx, R, sp.lodR, n, pr, status, lod0, sp.want, sp.step, st);
+  // a LoD built on demand: lay out the objects this step needs first (the
+  // FP64 re-decide refines pairs that the full-resolution step before it
+  // refined, so their objects are laid out already)
+  if (sp.want != REDECIDE) ensure_lod(ctx, R, sp.lodR, n, pr, status, lod0, sp.want, sp.step, st);
   PJ_CK(cudaMemsetAsync(ucount, 0, 8, st));
   // one warp per pair; one wave of 4 blocks of 8 warps per SM (the
   // kernel's register bound) walks the pairs
