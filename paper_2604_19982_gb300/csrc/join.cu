@@ -588,13 +588,13 @@ static pj_status within_tail(WithinTail& w, double ms_seq, pj_result* out, std::
            "\"candidates\":%lld,\"results\":%lld,"
            "\"tests_fp32\":%llu,\"tests_fp64\":%llu,\"tests_culled\":%llu,\"tests_needed\":%llu,\"confirmed\":%llu,"
            "\"removed\":%llu,\"redecide\":%llu,"
-           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
+           "\"tiles\":%lld,\"ms_filter\":%.3f,\"ms_seq\":%.3f,\"ms_gather\":%.3f,\"ms_total\":%.3f,"
            "\"refine_ms_fp32\":%.4f,\"refine_ms_fp64\":%.4f,\"launches\":%llu,\"steps\":",
            tau, fp64 ? "fp64" : "fp32", learned ? 1 : 0, gmode, spec ? 1 : 0, graph_ms, (long long)nn, (long long)n,
            (long long)m,
            cnt[0],
            cnt[1], cnt[5], cnt[6], cnt[2], cnt[3], cnt[4], (long long)tiles_total,
-           ms_filter, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
+           ms_filter, ms_seq, tg.ms(), tall.ms(), refine_ms_fp32, refine_ms_fp64, ctx->launches - launches0);
   stats = std::string(buf) + steps + "}";
   JoinSummary& js = ctx->last_sum;
   js.candidates = n;
