@@ -17,6 +17,9 @@ Functions and the passages they follow (arXiv 2604.19982):
 * :func:`pair_bounds`   -- Eq. 1 / Eq. 2 LoD bounds of object pairs
 * :func:`join_within`   -- within-tau / intersection join (section 3)
 * :func:`join_knn`      -- k-NN join, ties broken by object id (section 3)
+
+``oracle.voxel`` holds the voxelization and voxel-pair filtering of
+sections 2.1 and 3.2 (Algorithms 1 and 2) in numpy.
 """
 from __future__ import annotations
 
