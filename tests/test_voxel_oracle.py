@@ -19,11 +19,41 @@ def _object_tris(ms, o):
     return out
 
 
+def _coarse_verts(ms, o):
+    """Vertex array [V, 3] of object o at the coarsest LoD."""
+    vo = ms.vert_off[0]
+    return ms.verts[0][vo[o]:vo[o + 1]].astype(np.float64)
+
+
+def _vox(ms, o):
+    return vx.voxelize(_object_tris(ms, o), _coarse_verts(ms, o))
+
+
 def test_voxel_count_rule():
     assert vx.voxel_count(1280, 80) == 26       # round(25.6)
     assert vx.voxel_count(100, 50) == 2
     assert vx.voxel_count(10, 4) == 1           # at least one
     assert vx.voxel_count(50_000, 12) == 12     # at most the coarsest LoD's facets
+    # round-half-up of F / 50 in integers: (F + 25) // 50 for every F up to 10^6
+    F = np.arange(0, 1_000_001)
+    k = np.floor(vx.VOXEL_FRACTION * F + 0.5).astype(np.int64)
+    assert np.array_equal(k, (F + 25) // 50)
+
+
+def test_initial_centres_evenly_spaced():
+    v = np.arange(30, dtype=np.float64).reshape(10, 3)
+    # floor(0.5 * 10 / 3) = 1, floor(1.5 * 10 / 3) = 5, floor(2.5 * 10 / 3) = 8
+    assert np.array_equal(vx.initial_centres(v, 3), v[[1, 5, 8]])
+    assert np.array_equal(vx.initial_centres(v, 10), v)
+    assert np.array_equal(vx.initial_centres(v, 1), v[[5]])
+
+
+def test_centroid_and_squares_fixed_order():
+    t = np.array([[0.1, 0.2, 0.3, 1e16, 1.0, 2.0, -1e16, 3.0, 5.0]])
+    # (v0 + v1) + v2 loses v0.x to rounding against 1e16
+    assert vx.centroids(t)[0, 0] == ((0.1 + 1e16) + -1e16) / 3.0
+    d = np.array([1e8, 1.0, 1e-8])
+    assert vx.sq3(d) == (1e8 * 1e8 + 1.0 * 1.0) + 1e-8 * 1e-8
 
 
 def test_kmeans_recovers_two_planted_clusters():
@@ -69,7 +99,7 @@ def test_voxelize_partition_properties(kind):
         configs.tube_set(2, 200.0, 2, 1, length_range=(50.0, 70.0))
     for o in range(ms.n):
         tris = _object_tris(ms, o)
-        v = vx.voxelize(tris)
+        v = vx.voxelize(tris, _coarse_verts(ms, o))
         k = v["centres"].shape[0]
         assert k == vx.voxel_count(tris[-1].shape[0], tris[0].shape[0])
         for t, lab in zip(tris, v["labels"]):
@@ -104,7 +134,7 @@ def _pairs():
 def test_voxel_pair_bounds_bracket_facet_distances():
     for Rm, r, Sm, s in _pairs():
         tr, ts = _object_tris(Rm, r), _object_tris(Sm, s)
-        vr, vs = vx.voxelize(tr), vx.voxelize(ts)
+        vr, vs = _vox(Rm, r), _vox(Sm, s)
         lb, ub, op_lb, op_ub = vx.voxel_pair_bounds(vr, vs)
         A = tr[-1].reshape(-1, 3, 3)
         B = ts[-1].reshape(-1, 3, 3)
@@ -121,7 +151,7 @@ def test_voxel_pair_bounds_bracket_facet_distances():
 def test_pruning_keeps_the_voxel_pair_that_realises_the_distance():
     for Rm, r, Sm, s in _pairs():
         tr, ts = _object_tris(Rm, r), _object_tris(Sm, s)
-        vr, vs = vx.voxelize(tr), vx.voxelize(ts)
+        vr, vs = _vox(Rm, r), _vox(Sm, s)
         lb, ub, op_lb, op_ub = vx.voxel_pair_bounds(vr, vs)
         kept = vx.prune_voxel_pairs(lb, op_ub)
         # Algorithm 2 keeps exactly lb <= ub_o, in (i, j) order
@@ -145,7 +175,7 @@ def test_planted_mistake_box_centres_break_the_lower_bound():
     # the bracket pin above would catch it
     Rm, r, Sm, s = _pairs()[0]
     tr, ts = _object_tris(Rm, r), _object_tris(Sm, s)
-    vr, vs = vx.voxelize(tr), vx.voxelize(ts)
+    vr, vs = _vox(Rm, r), _vox(Sm, s)
     A = tr[-1].reshape(-1, 3, 3)
     B = ts[-1].reshape(-1, 3, 3)
     broken = 0
@@ -171,9 +201,9 @@ def test_object_pruning_agrees_with_the_join():
     res = set(zip(r_.tolist(), s_.tolist()))
     seen = [0, 0, 0]
     for r in range(R.n):
-        vr = vx.voxelize(_object_tris(R, r))
+        vr = _vox(R, r)
         for s in range(S.n):
-            vs = vx.voxelize(_object_tris(S, s))
+            vs = _vox(S, s)
             _, _, op_lb, op_ub = vx.voxel_pair_bounds(vr, vs)
             dec = vx.decide_within(op_lb, op_ub, tau)
             seen[dec] += 1
@@ -182,3 +212,30 @@ def test_object_pruning_agrees_with_the_join():
             elif dec == 2:
                 assert (r, s) not in res
     assert seen[2] > 0
+
+
+def test_set_helpers_match_the_per_object_calls():
+    R = configs.blob_set(3, 12.0, 3, 0)
+    S = configs.tube_set(2, 60.0, 3, 1, length_range=(50.0, 55.0))
+    vR, vS = vx.voxelize_set(R), vx.voxelize_set(S)
+    for o in range(R.n):
+        a, b = vR[o], _vox(R, o)
+        assert np.array_equal(a["centres"], b["centres"]) and np.array_equal(a["boxes"], b["boxes"])
+        assert all(np.array_equal(x, y) for x, y in zip(a["labels"], b["labels"]))
+    pr = np.array([0, 1, 2, 2])
+    ps = np.array([0, 1, 0, 1])
+    for tau in (-1.0, 1.0, 1e9):
+        f = vx.voxel_filter(vR, vS, pr, ps, tau)
+        for p in range(len(pr)):
+            lb, ub, olb, oub = vx.voxel_pair_bounds(vR[pr[p]], vS[ps[p]])
+            assert f["op_lb"][p] == olb and f["op_ub"][p] == oub
+            assert np.array_equal(f["vp_lb"][f["vp_off"][p]:f["vp_off"][p + 1]], lb.reshape(-1))
+            kept = f["kept"][f["kept_off"][p]:f["kept_off"][p + 1]]
+            if f["status"][p] == 0:
+                assert np.array_equal(kept, vx.prune_voxel_pairs(lb, oub))
+            else:
+                assert kept.shape[0] == 0
+        if tau < 0:
+            assert (f["status"] == 0).all()
+        if tau == 1e9:
+            assert (f["status"] == 1).all() and f["kept"].shape[0] == 0
