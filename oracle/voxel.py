@@ -58,7 +58,10 @@ VOXEL_FRACTION = 0.02
 
 def voxel_count(f_original: int, f_coarsest: int) -> int:
     """Voxels of an object with ``f_original`` facets at full resolution and
-    ``f_coarsest`` at its coarsest LoD."""
+    ``f_coarsest`` at its coarsest LoD (none without coarsest facets: there
+    is nothing to cluster)."""
+    if f_coarsest <= 0:
+        return 0
     k = int(np.floor(VOXEL_FRACTION * f_original + 0.5))
     return max(1, min(k, int(f_coarsest)))
 
@@ -123,6 +126,10 @@ def voxelize(tris_by_lod, coarse_verts):
     coarse = np.asarray(tris_by_lod[0], np.float64).reshape(-1, 9)
     orig = np.asarray(tris_by_lod[-1], np.float64).reshape(-1, 9)
     k = voxel_count(orig.shape[0], coarse.shape[0])
+    if k == 0:
+        return {"centres": np.zeros((0, 3)),
+                "labels": [np.full(np.asarray(t).reshape(-1, 9).shape[0], -1, np.int64) for t in tris_by_lod],
+                "boxes": np.zeros((0, 6)), "anchors": np.zeros((0, 3))}
     centres = kmeans(centroids(coarse), initial_centres(coarse_verts, k))
     labels = [assign(centroids(t), centres) for t in tris_by_lod]
     lab = labels[-1]
@@ -154,8 +161,9 @@ def box_mindist(a, b) -> float:
 def voxel_pair_bounds(vr, vs):
     """Algorithm 1 for one object pair: for voxel i of r and j of s,
     lb = MINDIST of their boxes, ub = distance of their anchors; voxels
-    without original facets take no part (inf).  Returns (vpLB [nr, ns],
-    vpUB [nr, ns], opLB, opUB)."""
+    without original facets take no part (inf), and a pair with no voxel
+    pair at all has opLB = opUB = inf.  Returns (vpLB [nr, ns], vpUB
+    [nr, ns], opLB, opUB)."""
     nr, ns = vr["boxes"].shape[0], vs["boxes"].shape[0]
     lb = np.full((nr, ns), np.inf)
     ub = np.full((nr, ns), np.inf)
@@ -167,6 +175,8 @@ def voxel_pair_bounds(vr, vs):
                 continue
             lb[i, j] = box_mindist(vr["boxes"][i], vs["boxes"][j])
             ub[i, j] = math.sqrt(float(sq3(vr["anchors"][i] - vs["anchors"][j])))
+    if lb.size == 0:      # an object without voxels: no voxel pair bounds it
+        return lb, ub, math.inf, math.inf
     return lb, ub, float(lb.min()), float(ub.min())
 
 

@@ -10,6 +10,21 @@ from oracle import voxel as vx
 from synth import configs
 
 
+def empty_and_two_triangles():
+    """Two objects over 2 LoDs: object 0 without facets, object 1 two
+    parallel triangles one unit apart."""
+    from synth.mesh import MeshSet
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [0, 1, 1]], np.float32)
+    V = np.ascontiguousarray(tri)
+    F = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    vo = np.array([0, 0, 6], np.int64)
+    fo = np.array([0, 0, 2], np.int64)
+    z = np.zeros(2, np.float32)
+    return MeshSet(n=2, n_lods=2, verts=[V, V], vert_off=[vo, vo], faces=[F, F], face_off=[fo, fo],
+                   hd=[z, None], ph=[z.copy(), None], anchor=np.array([[0, 0, 0], [0, 0, 0]], np.float32),
+                   kind="explicit")
+
+
 def _object_tris(ms, o):
     """Triangles [F_l, 9] of object o at every LoD (coarsest first)."""
     out = []
@@ -239,3 +254,16 @@ def test_set_helpers_match_the_per_object_calls():
             assert (f["status"] == 0).all()
         if tau == 1e9:
             assert (f["status"] == 1).all() and f["kept"].shape[0] == 0
+
+
+def test_object_without_facets_has_no_voxels():
+    ms = empty_and_two_triangles()
+    vs = vx.voxelize_set(ms)
+    assert vx.voxel_count(0, 0) == 0 and vs[0]["centres"].shape == (0, 3)
+    assert all(lab.shape == (0,) for lab in vs[0]["labels"])
+    assert vs[1]["centres"].shape == (1, 3)     # round(2 / 50) = 0, at least one
+    f = vx.voxel_filter(vs, vs, np.array([0, 1]), np.array([1, 1]), 0.5)
+    assert f["op_lb"][0] == np.inf and f["status"][0] == 2 and f["vp_off"][1] == 0
+    assert f["op_lb"][1] == 0.0 and f["status"][1] == 1
+    f = vx.voxel_filter(vs, vs, np.array([0]), np.array([0]), -1.0)
+    assert f["status"][0] == 0 and f["kept"].shape == (0, 2)
