@@ -50,6 +50,8 @@ WORKLOADS = {
     "knn50k": ("knn50k: R, S = 50,000 sub-3 blobs each, 20-cluster Gaussian mixture (sigma 15) in a cube of "
                "side 1,000, k = 3; proposal fitted on the seed-1 run"),
     "tubes2k": "tubes2k: 2,000 tubes (2k-50k facets, 3 LoDs) x 200,000 sub-3 blobs, cube side 2,320, within tau = 2",
+    "voxels_tubes2k": ("voxels_tubes2k: voxel-pair filtering (section 3.2, Algorithms 1 and 2) of the tubes2k box "
+                       "candidates (2,000 tubes x 200,000 blobs, within tau = 2), voxels of 2 % of the facets"),
 }
 WORKLOAD = WORKLOADS["stream2m"]
 STREAM = dict(n=2_000_000, chunks=64, tubes=20_000, side=5000.0, tau=1.0)
@@ -272,6 +274,8 @@ def generate(args, seed: int):
             plan["chunk_seed1"] = [("chunk", 0, seed + 1, STREAM["chunks"])]
         subs = [] if args.no_sub else [x for x in ("blobs20k", "knn50k", "tubes2k") if x != w]
         for name in ([w] if w != "stream2m" else []) + subs:
+            if name == "voxels_tubes2k":
+                name = "tubes2k"
             if name == "blobs20k":
                 n = args.n or 20_000
                 side = 400.0 * (n / 20_000) ** (1 / 3)
@@ -670,7 +674,104 @@ def tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
     return rec
 
 
-SUB_RECORDS = {"blobs20k": blobs20k_record, "knn50k": knn50k_record, "tubes2k": tubes2k_record}
+def _object_boxes(ms):
+    """[n, 6] boxes of every object's original-LoD vertices (host)."""
+    L = ms.n_lods - 1
+    v = ms.verts[L].astype(np.float64)
+    vo = np.asarray(ms.vert_off[L], np.int64)
+    return np.concatenate([np.minimum.reduceat(v, vo[:-1]), np.maximum.reduceat(v, vo[:-1])], axis=1)
+
+
+def box_candidates(R, S, tau):
+    """Object pairs whose boxes lie within tau, grouped by r, s ascending: a
+    sweep along x over S's boxes (bench input for the voxel filter)."""
+    a, b = _object_boxes(R), _object_boxes(S)
+    order = np.argsort(b[:, 0], kind="stable")
+    slo = b[order, 0]
+    ext = float((b[:, 3] - b[:, 0]).max()) if len(b) else 0.0
+    prs, pss = [], []
+    for r in range(len(a)):
+        i0 = np.searchsorted(slo, a[r, 0] - tau - ext, side="left")
+        i1 = np.searchsorted(slo, a[r, 3] + tau, side="right")
+        c = order[i0:i1]
+        bb = b[c]
+        g = np.maximum(0.0, np.maximum(bb[:, :3] - a[r, 3:], a[r, :3] - bb[:, 3:]))
+        c = np.sort(c[(g * g).sum(1) <= tau * tau])
+        prs.append(np.full(len(c), r, np.int32))
+        pss.append(c.astype(np.int32))
+    return np.concatenate(prs), np.concatenate(pss)
+
+
+VOXEL_KEYS = ("voxel_pairs_per_s", "inputs", "voxels", "kept", "kept_frac", "decided", "step_ms")
+VOXEL_BATCH = 1 << 27     # voxel pairs per pj_voxel_filter call (2 GB of bounds, 1 GB of survivors)
+# double-precision operations of one voxel pair's bounds in k_vp_bound:
+# MINDIST 6 differences, 6 maxima, 3 squares, 2 sums, 1 root; anchor
+# distance 3 differences, 3 squares, 2 sums, 1 root
+VOXEL_OPS = 27
+
+
+def voxels_tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
+    import torch
+    R, S = data["t2_R"], data["t2_S"]
+    tau = 2.0
+    vctx = pj.Context(torch.cuda.current_device(), {"voxels": 1})
+    t0 = time.perf_counter()
+    gR, gS = vctx.load_set(R), vctx.load_set(S)
+    load_s = time.perf_counter() - t0
+    kr = np.diff(vctx.voxel_offsets(gR))
+    ks = np.diff(vctx.voxel_offsets(gS))
+    pr, ps = box_candidates(R, S, tau)
+    sz = kr[pr].astype(np.int64) * ks[ps]
+    cum = np.cumsum(sz)
+    n = int(np.searchsorted(cum, VOXEL_BATCH, side="right"))   # pairs of the first batch
+    n = max(1, min(n, len(pr)))
+    cap = int(cum[n - 1])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dpr, dps = dev(pr[:n]), dev(ps[:n])
+    out = {"op_lb": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "op_ub": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "status": torch.empty(n, dtype=torch.uint8, device="cuda"),
+           "vp_off": torch.empty(n + 1, dtype=torch.int64, device="cuda"),
+           "vp_lb": torch.empty(cap, dtype=torch.float64, device="cuda"),
+           "vp_ub": torch.empty(cap, dtype=torch.float64, device="cuda"),
+           "kept_off": torch.empty(n + 1, dtype=torch.int64, device="cuda"),
+           "kept": torch.empty(2 * cap, dtype=torch.int32, device="cuda")}
+    ptr = {k: v.data_ptr() for k, v in out.items()}
+    run = lambda: vctx.voxel_filter(gR, gS, dpr.data_ptr(), dps.data_ptr(), n, tau, ptr, cap,
+                                    stream=stream.cuda_stream)
+    for _ in range(3):
+        kept = run()
+    ms, sts = timed(vctx, stream, run, steps)
+    st = sts[-1]
+    status = out["status"].cpu().numpy()
+    bound_ms = sum(x["ms_bound"] for x in sts) / len(sts)
+    peak64 = vctx.fma_peak(True) / 1000.0
+    ach = cap * VOXEL_OPS / (bound_ms / 1000.0) / 1e12
+    rec = {"workload": WORKLOADS["voxels_tubes2k"], "value": n * steps / (ms / 1000.0), "ms_per_step": ms / steps,
+           "dtype": "f64",
+           "voxel_pairs_per_s": cap * steps / (ms / 1000.0), "tri_tests_per_s": None,
+           "flags": "pj_voxel_filter, tau = 2",
+           "inputs": f"the first {n:,} of {len(pr):,} box candidates (r ascending), {cap:,} voxel pairs "
+                     f"(one call's batch of at most {VOXEL_BATCH:,}); outputs larger than L2",
+           "voxels": {"R": int(kr.sum()), "S": int(ks.sum()), "load_s_with_voxels": load_s},
+           "kept": kept, "kept_frac": kept / cap, "decided": {"results": int((status == 1).sum()),
+                                                             "pruned": int((status == 2).sum()),
+                                                             "undecided": int((status == 0).sum())},
+           "step_ms": {k: st[k] for k in ("ms_sizes", "ms_bound", "ms_count", "ms_scan", "ms_compact")},
+           "roofline": {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
+                        "traffic": None, "kernel": "k_vp_bound (Algorithm 1, double precision)",
+                        "peak_kind": "measured FP64 FMA throughput (pj_fma_peak, FMA = 2 flops)",
+                        "ops_per_voxel_pair": VOXEL_OPS, "kernel_ms": bound_ms,
+                        "hbm_gbs_written": cap * 16 / (bound_ms / 1000.0) / 1e9,
+                        "kernel_timing": "CUDA events around the launch inside pj_voxel_filter"}}
+    gR.free()
+    gS.free()
+    vctx.close()
+    return rec
+
+
+SUB_RECORDS = {"blobs20k": blobs20k_record, "knn50k": knn50k_record, "tubes2k": tubes2k_record,
+               "voxels_tubes2k": voxels_tubes2k_record}
 
 
 # ----------------------------------------------------------------- our arm
@@ -717,6 +818,8 @@ def ours_arm(args):
                 "tri_tests_per_s": rec["tri_tests_per_s"], "plain": rec.get("plain"),
                 "speedup_vs_plain": rec.get("speedup_vs_plain"), "roofline": rec["roofline"], "e2e": None,
                 "gpu_launches": None, "clocks": clk}
+        line["dtype"] = rec.get("dtype", "f32")
+        line.update({k: rec[k] for k in VOXEL_KEYS if k in rec})
     ctx.close()
     if not args.no_sub:
         # each workload in a context of its own (workspace, graphs and tuned

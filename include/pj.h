@@ -165,7 +165,9 @@ typedef struct {
  * chunk's join is issued before the previous one is waited for),
  * "host_read" (1, the default, or 0: copy the middle-LoD arrays of streamed
  * chunks in pinned host memory like the others instead of reading them in
- * place) and "autotune_cache" (path string).  The options change scheduling only,
+ * place), "voxels" (0, the default, or 1: pj_load_set also voxelizes every
+ * object it loads, see pj_voxel_count; joins do not read the voxels) and
+ * "autotune_cache" (path string).  The options change scheduling only,
  * never a result.  Fails with PJ_ECUDA when the device is not compute
  * capability 10.3 (GB300). */
 pj_status pj_create(pj_ctx** out, int device, const char* options_json);
@@ -341,6 +343,84 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
 pj_status pj_pair_bounds_static(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr,
                                 const int32_t* ps, int64_t n, int lod, pj_precision prec, double* lb,
                                 double* ub, void* cuda_stream);
+
+/* ---- Voxels and voxel-pair filtering (section 2.1; section 3.2,
+ * Algorithms 1 and 2) ----
+ * With the context option "voxels": 1, pj_load_set clusters the facets of
+ * every object into voxels:
+ *   - k = round(F / 50) voxels (2 % of the object's original facets F,
+ *     halves rounded up), at least 1 and at most the coarsest LoD's facet
+ *     count; an object without coarsest facets has none;
+ *   - k-means over the centroids ((v0 + v1) + v2) / 3 of the coarsest LoD's
+ *     facets with two centroid updates (a centre without members stays),
+ *     started from the coarsest vertex array's entries at the positions
+ *     floor((2j + 1) V / 2k), V its vertex count;
+ *   - every facet of every LoD belongs to the voxel whose final centre is
+ *     nearest to its centroid (the lowest index on ties), one partition
+ *     for all LoDs;
+ *   - a voxel's box bounds its original-LoD facets, its anchor is the
+ *     vertex of those facets nearest to the box centre (the first in facet
+ *     and corner order among equals).
+ * All in double precision, with every sum and product rounded in the
+ * order written (no fused multiply-add).  Sets streamed with
+ * pj_load_set_streamed are not voxelized.  Objects with more than
+ * PJ_VOXEL_MAX voxels (over about 102,400 original facets) make pj_load_set
+ * fail with PJ_EINVAL. */
+#define PJ_VOXEL_MAX 2048
+
+/* Voxels of all objects of a set (PJ_EINVAL when it has none). */
+pj_status pj_voxel_count(const pj_set* set, int64_t* n_voxels);
+
+/* Copies of a set's voxels to HOST buffers, each may be NULL:
+ *   voxel_off [n_objects + 1]  object o owns voxels voxel_off[o] ..
+ *                              voxel_off[o + 1] - 1 (object-local index
+ *                              v - voxel_off[o]);
+ *   centre    [n_voxels][3]    final k-means centres (double);
+ *   box       [n_voxels][6]    lo.xyz, hi.xyz (+inf / -inf for a voxel with
+ *                              no original facet);
+ *   anchor    [n_voxels][3]    the anchor vertex (NaN for such a voxel).
+ * Synchronous. */
+pj_status pj_voxels_read(pj_ctx* ctx, const pj_set* set, int64_t* voxel_off, double* centre, float* box,
+                         float* anchor);
+
+/* The object-local voxel of every facet of LoD `lod` (HOST int32 [facets of
+ * that LoD], in the set's facet order; -1 for objects without voxels).
+ * Synchronous. */
+pj_status pj_voxel_labels_read(pj_ctx* ctx, const pj_set* set, int lod, int32_t* label);
+
+/* Voxel-pair filtering of n object pairs (pr[p] in R, ps[p] in S), both
+ * sets voxelized.  Every array is a caller-allocated DEVICE buffer:
+ *   pr, ps       int32 [n]        the object pairs (an id outside its set
+ *                                 gives PJ_EBOUNDS, with every output
+ *                                 undefined);
+ *   op_lb, op_ub double [n]       Algorithm 1's object-pair bounds: the
+ *                                 minima over the pair's voxel pairs of
+ *                                 lb = MINDIST of the two voxel boxes and
+ *                                 ub = distance of the two voxel anchors
+ *                                 (+inf when either object has no voxel);
+ *   status       uint8 [n]        with tau >= 0: 1 a result (op_ub <= tau),
+ *                                 2 pruned (op_lb > tau), 0 undecided;
+ *                                 with tau < 0 every pair is undecided
+ *                                 (the k-NN use);
+ *   vp_off       int64 [n + 1]    offsets of each pair's n_r x n_s voxel
+ *                                 pairs in vp_lb / vp_ub (op2vpOffsets);
+ *   vp_lb, vp_ub double [vp_cap]  every voxel pair's bounds, pair p's block
+ *                                 row-major (t = i n_s + j, i the voxel of
+ *                                 pr[p], j of ps[p]);
+ *   kept_off     int64 [n + 1]    offsets of each pair's surviving voxel
+ *                                 pairs (Algorithm 2: those of undecided
+ *                                 pairs with lb <= op_ub);
+ *   kept         int32 [vp_cap][2] the survivors (i, j), row-major order.
+ * n_kept (HOST) receives kept_off[n].  vp_cap below the sum of n_r x n_s
+ * gives PJ_EINVAL (nothing past vp_cap is written).  All distances are in
+ * double precision with the rounding order of the voxel data above.  Works
+ * on cuda_stream (NULL = the context's stream) and returns when the
+ * results are written; pj_get_stats then reports the pair and voxel-pair
+ * counts and each step's device time. */
+pj_status pj_voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
+                          int64_t n, double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off,
+                          double* vp_lb, double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept,
+                          int64_t* n_kept, void* cuda_stream);
 
 /* Measured fused-multiply-add throughput of the device (independent FMA
  * chains on every SM), GFLOP/s with an FMA counted as 2 operations: the

@@ -209,6 +209,7 @@ void free_set_storage(pj_set* s) {
   cudaFree(s->mbb);
   cudaFree(s->anchor);
   s->mbb = s->anchor = nullptr;
+  free_voxels(s);
 }
 
 // Set storage and load temporaries are stream-ordered allocations from the
@@ -470,6 +471,7 @@ pj_status load_set_impl(pj_ctx* ctx, const pj_mesh_set_desc* D, pj_set* s, cudaS
   PJ_CK(cudaMallocAsync((void**)&s->mbb, std::max(1, n) * 6 * sizeof(float), st));
   s->anchor = upload(D->anchor, (size_t)n * 3, st);
   build_set_kernels(ctx, s, raw, st);
+  if (ctx->voxelize) voxelize_set(ctx, s, raw[0].verts, raw[0].voff, st);
   s->mbb_h.resize((size_t)n * 6);
   if (n > 0) PJ_CK(cudaMemcpyAsync(s->mbb_h.data(), s->mbb, (size_t)n * 6 * 4, cudaMemcpyDeviceToHost, st));
   int herr = 0;
@@ -659,6 +661,8 @@ pj_status pj_create(pj_ctx** out, int device, const char* options_json) {
   if (!v.empty()) ctx->host_read = atoi(v.c_str()) != 0;
   v = json_str(options_json, "chunk_overlap");
   if (!v.empty()) ctx->chunk_overlap = atoi(v.c_str()) != 0;
+  v = json_str(options_json, "voxels");
+  if (!v.empty()) ctx->voxelize = atoi(v.c_str()) != 0;
   v = json_str(options_json, "zero_copy");
   if (!v.empty()) ctx->zero_copy = atoi(v.c_str()) != 0;
   v = json_str(options_json, "refine_tail");
@@ -908,6 +912,65 @@ pj_status pj_pair_bounds(pj_ctx* ctx, const pj_set* R, const pj_set* S, const in
       ub[i] = b;
     }
   }
+  return PJ_OK;
+  PJ_API_CATCH(ctx)
+}
+
+pj_status pj_voxel_count(const pj_set* set, int64_t* n_voxels) {
+  if (!set || !n_voxels) return PJ_EINVAL;
+  if (!set->voxels) return PJ_EINVAL;
+  *n_voxels = set->V;
+  return PJ_OK;
+}
+
+pj_status pj_voxels_read(pj_ctx* ctx, const pj_set* set, int64_t* voxel_off, double* centre, float* box,
+                         float* anchor) {
+  if (!ctx || !set) return fail(ctx, PJ_EINVAL, "bad voxels_read arguments");
+  if (!set->voxels) return fail(ctx, PJ_EINVAL, "the set was loaded without voxels (context option \"voxels\")");
+  PJ_API_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  if (voxel_off) memcpy(voxel_off, set->vox_off_h.data(), ((size_t)set->n + 1) * 8);
+  const size_t V = (size_t)set->V;
+  if (centre && V) PJ_CK(cudaMemcpyAsync(centre, set->vox_centre, V * 3 * 8, cudaMemcpyDeviceToHost, st));
+  if (box && V) PJ_CK(cudaMemcpyAsync(box, set->vox_box, V * 6 * 4, cudaMemcpyDeviceToHost, st));
+  if (anchor && V) PJ_CK(cudaMemcpyAsync(anchor, set->vox_anchor, V * 3 * 4, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  return PJ_OK;
+  PJ_API_CATCH(ctx)
+}
+
+pj_status pj_voxel_labels_read(pj_ctx* ctx, const pj_set* set, int lod, int32_t* label) {
+  if (!ctx || !set || !label) return fail(ctx, PJ_EINVAL, "bad voxel_labels_read arguments");
+  if (!set->voxels) return fail(ctx, PJ_EINVAL, "the set was loaded without voxels (context option \"voxels\")");
+  if (lod < 0 || lod >= set->L) return fail(ctx, PJ_EINVAL, "lod out of range");
+  PJ_API_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const size_t F = (size_t)set->lod[lod].F;
+  if (F) PJ_CK(cudaMemcpyAsync(label, set->vox_label[lod], F * 4, cudaMemcpyDeviceToHost, st));
+  PJ_CK(cudaStreamSynchronize(st));
+  return PJ_OK;
+  PJ_API_CATCH(ctx)
+}
+
+pj_status pj_voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
+                          int64_t n, double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off,
+                          double* vp_lb, double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept,
+                          int64_t* n_kept, void* cuda_stream) {
+  if (!ctx || !R || !S || n < 0 || vp_cap < 0 || !n_kept || !vp_off || !kept_off)
+    return fail(ctx, PJ_EINVAL, "bad voxel_filter arguments");
+  if (n > 0 && (!pr || !ps || !op_lb || !op_ub || !status)) return fail(ctx, PJ_EINVAL, "bad voxel_filter arguments");
+  if (vp_cap > 0 && (!vp_lb || !vp_ub || !kept)) return fail(ctx, PJ_EINVAL, "bad voxel_filter arguments");
+  if (!R->voxels || !S->voxels)
+    return fail(ctx, PJ_EINVAL, "a set was loaded without voxels (context option \"voxels\")");
+  if (n >= (1LL << 31)) return fail(ctx, PJ_EINVAL, "more than 2^31 object pairs");
+  PJ_API_TRY
+  PJ_CK(cudaSetDevice(ctx->device));
+  (void)cudaGetLastError();
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  voxel_filter(ctx, R, S, pr, ps, n, tau, op_lb, op_ub, status, vp_off, vp_lb, vp_ub, vp_cap, kept_off, kept,
+               n_kept, st);
   return PJ_OK;
   PJ_API_CATCH(ctx)
 }

@@ -144,6 +144,19 @@ struct pj_set {
   unsigned* lazy_state = nullptr;
   int32_t* lazy_list = nullptr;
   unsigned* lazy_count = nullptr;
+  // voxels (section 2.1), built at load when the context voxelizes:
+  // vox_off [n+1] (host copy vox_off_h), centres [V][3] double, boxes
+  // [V][6] (lo.xyz, hi.xyz of the voxel's original facets), anchors [V][3],
+  // and per LoD the object-local voxel of every facet (-1: none)
+  bool voxels = false;
+  int64_t V = 0;
+  int vox_kmax = 0;
+  int64_t* vox_off = nullptr;
+  std::vector<int64_t> vox_off_h;
+  double* vox_centre = nullptr;
+  float* vox_box = nullptr;
+  float* vox_anchor = nullptr;
+  int32_t* vox_label[PJ_MAX_LODS] = {};
   // streamed R: the chunks are loaded inside pj_join
   bool streamed = false;
   int64_t n_total = 0;
@@ -235,6 +248,7 @@ struct pj_ctx {
   bool borrowed_mlp = false;         // mlp_w belongs to another context
   bool chunk_overlap = true;         // option "chunk_overlap": streamed within joins use the twin
   bool host_read = true;             // option "host_read": middle-LoD pinned chunk arrays read in place
+  bool voxelize = false;             // option "voxels": pj_load_set voxelizes every object it loads
   void* stream_pinned[2] = {};      // pinned staging slots of streamed chunks
   size_t stream_pinned_cap[2] = {};
   void* stream_box_pinned[2] = {};  // pinned copies of a chunk's object boxes and error word
@@ -267,6 +281,19 @@ void* ws_get(pj_ctx* ctx, int slot, size_t bytes, cudaStream_t st);
 
 // ---- set layout (api.cu)
 void free_set_storage(pj_set* s);
+
+// ---- voxels (voxel.cu)
+// Voxels of every object of a set being loaded: verts0 / voff0 are the
+// device copies of its coarsest LoD's vertex array and offsets (the initial
+// k-means centres are taken from them), the facet arrays must be built.
+void voxelize_set(pj_ctx* ctx, pj_set* s, const float* verts0, const int64_t* voff0, cudaStream_t st);
+void free_voxels(pj_set* s);
+// Algorithms 1 and 2 over object pairs pr / ps (device); every output a
+// caller device buffer (see pj_voxel_filter); synchronizes st at the end.
+void voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps, int64_t n,
+                  double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off, double* vp_lb,
+                  double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept, int64_t* n_kept,
+                  cudaStream_t st);
 
 // ---- scan (join.cu): exclusive prefix sum of n int64 values into out[0..n],
 // out[n] = total.  tmp is workspace.

@@ -87,6 +87,11 @@ def lib():
             "pj_pair_bounds": (st, [vp, vp, vp, _i32p, _i32p, C.c_int64, C.c_int, C.c_int, _dp, _dp]),
             "pj_fma_peak": (st, [vp, C.c_int, _dp]),
             "pj_pair_bounds_static": (st, [vp, vp, vp, vp, vp, C.c_int64, C.c_int, C.c_int, vp, vp, vp]),
+            "pj_voxel_count": (st, [vp, _i64p]),
+            "pj_voxels_read": (st, [vp, vp, _i64p, _dp, _fp, _fp]),
+            "pj_voxel_labels_read": (st, [vp, vp, C.c_int, _i32p]),
+            "pj_voxel_filter": (st, [vp, vp, vp, vp, vp, C.c_int64, C.c_double, vp, vp, vp, vp, vp, vp, C.c_int64,
+                                     vp, vp, _i64p, vp]),
             "pj_last_error": (C.c_char_p, [vp]),
             "pj_status_str": (C.c_char_p, [C.c_int]),
         }
@@ -307,6 +312,49 @@ class Context:
         self._check(lib().pj_pair_bounds_static(self.h, R.handle, S.handle, C.c_void_p(pr_dev), C.c_void_p(ps_dev),
                                                 int(n), int(lod), int(prec), C.c_void_p(lb_dev), C.c_void_p(ub_dev),
                                                 C.c_void_p(stream) if stream else None))
+
+    # ---- voxels (context option "voxels": 1)
+    def voxel_count(self, S: Set) -> int:
+        v = C.c_int64()
+        self._check(lib().pj_voxel_count(S.handle, C.byref(v)))
+        return v.value
+
+    def voxels(self, S: Set) -> dict:
+        """A set's voxels: voxel_off [n + 1], centres [V, 3] (double), boxes
+        [V, 6] and anchors [V, 3] (float32)."""
+        V = self.voxel_count(S)
+        off = np.empty(S.n + 1, np.int64)
+        cen = np.empty((V, 3), np.float64)
+        box = np.empty((V, 6), np.float32)
+        anc = np.empty((V, 3), np.float32)
+        self._check(lib().pj_voxels_read(self.h, S.handle, _ptr(off, C.c_int64), _ptr(cen, C.c_double),
+                                         _ptr(box, C.c_float), _ptr(anc, C.c_float)))
+        return {"voxel_off": off, "centres": cen, "boxes": box, "anchors": anc}
+
+    def voxel_offsets(self, S: Set) -> np.ndarray:
+        """voxel_off [n + 1] of a set's voxels."""
+        off = np.empty(S.n + 1, np.int64)
+        self._check(lib().pj_voxels_read(self.h, S.handle, _ptr(off, C.c_int64), None, None, None))
+        return off
+
+    def voxel_labels(self, S: Set, lod: int, n_facets: int) -> np.ndarray:
+        """The object-local voxel of each of the n_facets facets of LoD lod."""
+        lab = np.empty(int(n_facets), np.int32)
+        self._check(lib().pj_voxel_labels_read(self.h, S.handle, int(lod), _ptr(lab, C.c_int32)))
+        return lab
+
+    def voxel_filter(self, R: Set, S: Set, pr_dev: int, ps_dev: int, n: int, tau: float, out: dict,
+                     vp_cap: int, stream: int | None = None) -> int:
+        """pj_voxel_filter: device buffers in and out (``out`` maps op_lb,
+        op_ub, status, vp_off, vp_lb, vp_ub, kept_off, kept to device
+        addresses); returns the number of surviving voxel pairs."""
+        nk = C.c_int64()
+        d = [C.c_void_p(out[k]) for k in ("op_lb", "op_ub", "status", "vp_off", "vp_lb", "vp_ub")]
+        self._check(lib().pj_voxel_filter(self.h, R.handle, S.handle, C.c_void_p(pr_dev), C.c_void_p(ps_dev), int(n),
+                                          float(tau), *d, int(vp_cap), C.c_void_p(out["kept_off"]),
+                                          C.c_void_p(out["kept"]), C.byref(nk),
+                                          C.c_void_p(stream) if stream else None))
+        return nk.value
 
     def fma_peak(self, fp64: bool) -> float:
         """Measured FMA throughput in GFLOP/s (FMA = 2 flops)."""

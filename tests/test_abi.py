@@ -20,7 +20,8 @@ def declared():
 def test_header_declares_entry_points():
     names = declared()
     for n in ("pj_create", "pj_load_set", "pj_join", "pj_join_async", "pj_tri_dist", "pj_pair_bounds",
-              "pj_mlp_train", "pj_load_set_streamed", "pj_get_stats", "pj_last_error"):
+              "pj_mlp_train", "pj_load_set_streamed", "pj_get_stats", "pj_last_error",
+              "pj_voxel_count", "pj_voxels_read", "pj_voxel_labels_read", "pj_voxel_filter"):
         assert n in names
 
 
