@@ -702,12 +702,22 @@ def box_candidates(R, S, tau):
     return np.concatenate(prs), np.concatenate(pss)
 
 
-VOXEL_KEYS = ("voxel_pairs_per_s", "inputs", "voxels", "kept", "kept_frac", "decided", "step_ms")
+VOXEL_KEYS = ("voxel_pairs_per_s", "inputs", "voxels", "kept", "kept_frac", "decided", "step_ms", "f64",
+              "speedup_f32_vs_f64")
 VOXEL_BATCH = 1 << 27     # voxel pairs per pj_voxel_filter call (2 GB of bounds, 1 GB of survivors)
 # double-precision operations of one voxel pair's bounds in k_vp_bound:
 # MINDIST 6 differences, 6 maxima, 3 squares, 2 sums, 1 root; anchor
 # distance 3 differences, 3 squares, 2 sums, 1 root
 VOXEL_OPS = 27
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) of this machine's GPUs, else the
+    fallback figure; and which one it is."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def voxels_tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
@@ -726,6 +736,10 @@ def voxels_tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
     n = int(np.searchsorted(cum, VOXEL_BATCH, side="right"))   # pairs of the first batch
     n = max(1, min(n, len(pr)))
     cap = int(cum[n - 1])
+    # algorithmic bytes of one k_vp_bound launch: the bounds written (2 x 8 B
+    # per voxel pair), each pair's voxel records read once (box 24 B + anchor
+    # 12 B per voxel), ids, offsets, object-pair bounds and status (65 B)
+    bound_bytes = 16 * cap + 36 * int(kr[pr[:n]].sum() + ks[ps[:n]].sum()) + 65 * n
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     dpr, dps = dev(pr[:n]), dev(ps[:n])
     out = {"op_lb": torch.empty(n, dtype=torch.float64, device="cuda"),
@@ -737,32 +751,45 @@ def voxels_tubes2k_record(args, data, ctx, pj, stream, nsm, measured32, steps):
            "kept_off": torch.empty(n + 1, dtype=torch.int64, device="cuda"),
            "kept": torch.empty(2 * cap, dtype=torch.int32, device="cuda")}
     ptr = {k: v.data_ptr() for k, v in out.items()}
-    run = lambda: vctx.voxel_filter(gR, gS, dpr.data_ptr(), dps.data_ptr(), n, tau, ptr, cap,
-                                    stream=stream.cuda_stream)
-    for _ in range(3):
-        kept = run()
-    ms, sts = timed(vctx, stream, run, steps)
-    st = sts[-1]
-    status = out["status"].cpu().numpy()
-    bound_ms = sum(x["ms_bound"] for x in sts) / len(sts)
+
+    def measure(prec):
+        run = lambda: vctx.voxel_filter(gR, gS, dpr.data_ptr(), dps.data_ptr(), n, tau, ptr, cap, prec=prec,
+                                        stream=stream.cuda_stream)
+        for _ in range(3):
+            kept = run()
+        ms, sts = timed(vctx, stream, run, steps)
+        status = out["status"].cpu().numpy()
+        return {"ms": ms, "kept": kept, "bound_ms": sum(x["ms_bound"] for x in sts) / len(sts),
+                "step_ms": {k: sts[-1][k] for k in ("ms_sizes", "ms_bound", "ms_count", "ms_scan", "ms_compact")},
+                "decided": {"results": int((status == 1).sum()), "pruned": int((status == 2).sum()),
+                            "undecided": int((status == 0).sum())}}
+
+    f32 = measure(pj.FP32)
+    f64 = measure(pj.FP64)
+    peak, kind = hbm_peak()
+    gbs = bound_bytes / (f32["bound_ms"] / 1000.0) / 1e9
     peak64 = vctx.fma_peak(True) / 1000.0
-    ach = cap * VOXEL_OPS / (bound_ms / 1000.0) / 1e12
-    rec = {"workload": WORKLOADS["voxels_tubes2k"], "value": n * steps / (ms / 1000.0), "ms_per_step": ms / steps,
-           "dtype": "f64",
-           "voxel_pairs_per_s": cap * steps / (ms / 1000.0), "tri_tests_per_s": None,
-           "flags": "pj_voxel_filter, tau = 2",
+    ach64 = cap * VOXEL_OPS / (f64["bound_ms"] / 1000.0) / 1e12
+    rec = {"workload": WORKLOADS["voxels_tubes2k"], "value": n * steps / (f32["ms"] / 1000.0),
+           "ms_per_step": f32["ms"] / steps, "dtype": "f32",
+           "voxel_pairs_per_s": cap * steps / (f32["ms"] / 1000.0), "tri_tests_per_s": None,
+           "flags": "pj_voxel_filter, PJ_PREC_FP32_REDECIDE (outward-rounded bounds), tau = 2",
            "inputs": f"the first {n:,} of {len(pr):,} box candidates (r ascending), {cap:,} voxel pairs "
                      f"(one call's batch of at most {VOXEL_BATCH:,}); outputs larger than L2",
            "voxels": {"R": int(kr.sum()), "S": int(ks.sum()), "load_s_with_voxels": load_s},
-           "kept": kept, "kept_frac": kept / cap, "decided": {"results": int((status == 1).sum()),
-                                                             "pruned": int((status == 2).sum()),
-                                                             "undecided": int((status == 0).sum())},
-           "step_ms": {k: st[k] for k in ("ms_sizes", "ms_bound", "ms_count", "ms_scan", "ms_compact")},
-           "roofline": {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
-                        "traffic": None, "kernel": "k_vp_bound (Algorithm 1, double precision)",
-                        "peak_kind": "measured FP64 FMA throughput (pj_fma_peak, FMA = 2 flops)",
-                        "ops_per_voxel_pair": VOXEL_OPS, "kernel_ms": bound_ms,
-                        "hbm_gbs_written": cap * 16 / (bound_ms / 1000.0) / 1e9,
+           "kept": f32["kept"], "kept_frac": f32["kept"] / cap, "decided": f32["decided"], "step_ms": f32["step_ms"],
+           "f64": {"value": n * steps / (f64["ms"] / 1000.0), "ms_per_step": f64["ms"] / steps,
+                   "voxel_pairs_per_s": cap * steps / (f64["ms"] / 1000.0), "kept": f64["kept"],
+                   "decided": f64["decided"], "step_ms": f64["step_ms"],
+                   "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                                "frac": ach64 / peak64, "kernel": "k_vp_bound<double>",
+                                "peak_kind": "measured FP64 FMA throughput (pj_fma_peak, FMA = 2 flops)",
+                                "ops_per_voxel_pair": VOXEL_OPS, "kernel_ms": f64["bound_ms"]}},
+           "speedup_f32_vs_f64": f64["ms"] / f32["ms"],
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "traffic": None, "kernel": "k_vp_bound<float> (Algorithm 1, outward-rounded single precision)",
+                        "peak_kind": f"{kind} HBM copy bandwidth", "bytes_per_launch": bound_bytes,
+                        "kernel_ms": f32["bound_ms"],
                         "kernel_timing": "CUDA events around the launch inside pj_voxel_filter"}}
     gR.free()
     gS.free()

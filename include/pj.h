@@ -412,13 +412,19 @@ pj_status pj_voxel_labels_read(pj_ctx* ctx, const pj_set* set, int lod, int32_t*
  *                                 pairs with lb <= op_ub);
  *   kept         int32 [vp_cap][2] the survivors (i, j), row-major order.
  * n_kept (HOST) receives kept_off[n].  vp_cap below the sum of n_r x n_s
- * gives PJ_EINVAL (nothing past vp_cap is written).  All distances are in
- * double precision with the rounding order of the voxel data above.  Works
+ * gives PJ_EINVAL (nothing past vp_cap is written).  prec PJ_PREC_FP64:
+ * the distances in double precision, rounded to nearest in the order of
+ * the voxel data above; PJ_PREC_FP32_REDECIDE: in single precision rounded
+ * outward (lb rounded down, ub up, step by step), so every bound still
+ * holds and the decisions and survivors are those of the exact bounds
+ * except where a bound lies within rounding (about 1e-6 relative) of the
+ * value it is compared with, where the pair stays undecided or the voxel
+ * pair is kept (the outputs stay double arrays).  Works
  * on cuda_stream (NULL = the context's stream) and returns when the
  * results are written; pj_get_stats then reports the pair and voxel-pair
  * counts and each step's device time. */
 pj_status pj_voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
-                          int64_t n, double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off,
+                          int64_t n, double tau, pj_precision prec, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off,
                           double* vp_lb, double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept,
                           int64_t* n_kept, void* cuda_stream);
 

@@ -955,7 +955,7 @@ pj_status pj_voxel_labels_read(pj_ctx* ctx, const pj_set* set, int lod, int32_t*
 }
 
 pj_status pj_voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps,
-                          int64_t n, double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off,
+                          int64_t n, double tau, pj_precision prec, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off,
                           double* vp_lb, double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept,
                           int64_t* n_kept, void* cuda_stream) {
   if (!ctx || !R || !S || n < 0 || vp_cap < 0 || !n_kept || !vp_off || !kept_off)
@@ -965,11 +965,13 @@ pj_status pj_voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const i
   if (!R->voxels || !S->voxels)
     return fail(ctx, PJ_EINVAL, "a set was loaded without voxels (context option \"voxels\")");
   if (n >= (1LL << 31)) return fail(ctx, PJ_EINVAL, "more than 2^31 object pairs");
+  if (prec != PJ_PREC_FP64 && prec != PJ_PREC_FP32_REDECIDE) return fail(ctx, PJ_EINVAL, "unknown precision");
   PJ_API_TRY
   PJ_CK(cudaSetDevice(ctx->device));
   (void)cudaGetLastError();
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
-  voxel_filter(ctx, R, S, pr, ps, n, tau, op_lb, op_ub, status, vp_off, vp_lb, vp_ub, vp_cap, kept_off, kept,
+  voxel_filter(ctx, R, S, pr, ps, n, tau, prec == PJ_PREC_FP64, op_lb, op_ub, status, vp_off, vp_lb, vp_ub, vp_cap,
+               kept_off, kept,
                n_kept, st);
   return PJ_OK;
   PJ_API_CATCH(ctx)

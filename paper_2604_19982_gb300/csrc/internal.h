@@ -291,7 +291,7 @@ void free_voxels(pj_set* s);
 // Algorithms 1 and 2 over object pairs pr / ps (device); every output a
 // caller device buffer (see pj_voxel_filter); synchronizes st at the end.
 void voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps, int64_t n,
-                  double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off, double* vp_lb,
+                  double tau, bool fp64, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off, double* vp_lb,
                   double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept, int64_t* n_kept,
                   cudaStream_t st);
 

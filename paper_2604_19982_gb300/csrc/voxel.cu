@@ -20,9 +20,10 @@
 //
 // Voxel-pair filtering (one CTA per object pair, grid-stride):
 //   k_vp_bound   Algorithm 1: lb = MINDIST of the voxel boxes, ub = distance
-//                of the voxel anchors, both in double; their minima are the
-//                object pair's [lb, ub]; with tau >= 0 the pair is a result
-//                (ub <= tau), pruned (lb > tau) or undecided;
+//                of the voxel anchors (in double, or in single precision
+//                rounded outward); their minima are the object pair's
+//                [lb, ub]; with tau >= 0 the pair is a result (ub <= tau),
+//                pruned (lb > tau) or undecided;
 //   k_vp_count   Algorithm 2 step 1: surviving voxel pairs per undecided pair;
 //   scan_i64     step 2: their offsets;
 //   k_vp_compact step 3: the survivors (i, j) in row-major order.
@@ -291,10 +292,43 @@ struct VoxView {
   int n;
 };
 
+// One voxel pair's bounds: lb = MINDIST of boxes a, b (lo.xyz, hi.xyz), ub =
+// distance of anchors ua, ub_.  F64: double precision rounded to nearest in
+// a fixed order.  Otherwise single precision with outward rounding: every
+// step of lb rounds down and every step of ub rounds up (|x - y| bounded
+// by the larger magnitude of its two directed differences), so lb never
+// exceeds the exact MINDIST and ub is never below the exact distance.
+template <bool F64>
+__device__ __forceinline__ void vp_bounds(const float* a, const float* b, const float* ua, const float* ub_,
+                                          double& lb, double& ub) {
+  if (F64) {
+    double g[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const double d1 = __dsub_rn((double)b[e], (double)a[3 + e]);
+      const double d2 = __dsub_rn((double)a[e], (double)b[3 + e]);
+      g[e] = fmax(0.0, fmax(d1, d2));
+    }
+    lb = __dsqrt_rn(dsq3(g[0], g[1], g[2]));
+    ub = __dsqrt_rn(dsq3(__dsub_rn((double)ua[0], (double)ub_[0]), __dsub_rn((double)ua[1], (double)ub_[1]),
+                         __dsub_rn((double)ua[2], (double)ub_[2])));
+  } else {
+    float g[3], h[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      g[e] = fmaxf(0.f, fmaxf(__fsub_rd(b[e], a[3 + e]), __fsub_rd(a[e], b[3 + e])));
+      h[e] = fmaxf(fabsf(__fsub_ru(ua[e], ub_[e])), fabsf(__fsub_rd(ua[e], ub_[e])));
+    }
+    lb = (double)__fsqrt_rd(__fadd_rd(__fadd_rd(__fmul_rd(g[0], g[0]), __fmul_rd(g[1], g[1])), __fmul_rd(g[2], g[2])));
+    ub = (double)__fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(h[0], h[0]), __fmul_ru(h[1], h[1])), __fmul_ru(h[2], h[2])));
+  }
+}
+
 // Algorithm 1: one CTA per object pair, its n_r x n_s voxel pairs flattened
 // over the threads (row-major t = i n_s + j); vp_off [n+1] holds each
 // pair's first slot.  Pairs whose ids lie outside the sets are skipped
 // (ERR_BOUNDS), slots at or past cap are not written (ERR_CAPACITY).
+template <bool F64>
 __global__ void __launch_bounds__(VOX_T) k_vp_bound(int64_t n, const int32_t* pr, const int32_t* ps, VoxView R,
                                                     VoxView S, const int64_t* vp_off, int64_t cap, double tau,
                                                     double* vp_lb, double* vp_ub, double* op_lb, double* op_ub,
@@ -322,19 +356,7 @@ __global__ void __launch_bounds__(VOX_T) k_vp_bound(int64_t n, const int32_t* pr
       const float* a = R.box + 6 * (i0 + i);
       const float* b = S.box + 6 * (j0 + j);
       double lb = __longlong_as_double(0x7ff0000000000000LL), ub = lb;
-      if (!box_empty(a) && !box_empty(b)) {
-        double g[3];
-        for (int e = 0; e < 3; ++e) {
-          const double d1 = __dsub_rn((double)b[e], (double)a[3 + e]);
-          const double d2 = __dsub_rn((double)a[e], (double)b[3 + e]);
-          g[e] = fmax(0.0, fmax(d1, d2));
-        }
-        lb = __dsqrt_rn(dsq3(g[0], g[1], g[2]));
-        const float* ua = R.anc + 3 * (i0 + i);
-        const float* ub_ = S.anc + 3 * (j0 + j);
-        ub = __dsqrt_rn(dsq3(__dsub_rn((double)ua[0], (double)ub_[0]), __dsub_rn((double)ua[1], (double)ub_[1]),
-                             __dsub_rn((double)ua[2], (double)ub_[2])));
-      }
+      if (!box_empty(a) && !box_empty(b)) vp_bounds<F64>(a, b, R.anc + 3 * (i0 + i), S.anc + 3 * (j0 + j), lb, ub);
       if (room) {
         vp_lb[base + t] = lb;
         vp_ub[base + t] = ub;
@@ -512,7 +534,7 @@ void voxelize_set(pj_ctx* ctx, pj_set* s, const float* verts0, const int64_t* vo
 }
 
 void voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* pr, const int32_t* ps, int64_t n,
-                  double tau, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off, double* vp_lb,
+                  double tau, bool fp64, double* op_lb, double* op_ub, uint8_t* status, int64_t* vp_off, double* vp_lb,
                   double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept, int64_t* n_kept,
                   cudaStream_t st) {
   struct Temps {
@@ -552,8 +574,9 @@ void voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* 
   scan_i64(ctx, sz, vp_off, n, st);
   PJ_CK(cudaEventRecord(ev[1], st));
   if (n > 0) {
-    k_vp_bound<<<gp, VOX_T, 0, st>>>(n, pr, ps, vr, vs, vp_off, vp_cap, tau, vp_lb, vp_ub, op_lb, op_ub, status,
-                                     ctx->d_err);
+    auto kern = fp64 ? k_vp_bound<true> : k_vp_bound<false>;
+    kern<<<gp, VOX_T, 0, st>>>(n, pr, ps, vr, vs, vp_off, vp_cap, tau, vp_lb, vp_ub, op_lb, op_ub, status,
+                               ctx->d_err);
     PJ_CK(cudaGetLastError());
     PJ_COUNT_LAUNCH;
   }
@@ -586,9 +609,10 @@ void voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const int32_t* 
   for (int i = 0; i < 5; ++i) PJ_CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
   char buf[512];
   snprintf(buf, sizeof buf,
-           "{\"op_pairs\": %lld, \"voxel_pairs\": %lld, \"kept\": %lld, \"ms_sizes\": %.6f, \"ms_bound\": %.6f, "
+           "{\"prec\": \"%s\", \"op_pairs\": %lld, \"voxel_pairs\": %lld, \"kept\": %lld, \"ms_sizes\": %.6f, \"ms_bound\": %.6f, "
            "\"ms_count\": %.6f, \"ms_scan\": %.6f, \"ms_compact\": %.6f}",
-           (long long)n, (long long)tot[0], (long long)tot[1], ms[0], ms[1], ms[2], ms[3], ms[4]);
+           fp64 ? "f64" : "f32", (long long)n, (long long)tot[0], (long long)tot[1], ms[0], ms[1], ms[2], ms[3],
+           ms[4]);
   ctx->stats = buf;
 }
 

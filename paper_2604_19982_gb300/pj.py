@@ -90,8 +90,8 @@ def lib():
             "pj_voxel_count": (st, [vp, _i64p]),
             "pj_voxels_read": (st, [vp, vp, _i64p, _dp, _fp, _fp]),
             "pj_voxel_labels_read": (st, [vp, vp, C.c_int, _i32p]),
-            "pj_voxel_filter": (st, [vp, vp, vp, vp, vp, C.c_int64, C.c_double, vp, vp, vp, vp, vp, vp, C.c_int64,
-                                     vp, vp, _i64p, vp]),
+            "pj_voxel_filter": (st, [vp, vp, vp, vp, vp, C.c_int64, C.c_double, C.c_int, vp, vp, vp, vp, vp, vp,
+                                     C.c_int64, vp, vp, _i64p, vp]),
             "pj_last_error": (C.c_char_p, [vp]),
             "pj_status_str": (C.c_char_p, [C.c_int]),
         }
@@ -344,14 +344,14 @@ class Context:
         return lab
 
     def voxel_filter(self, R: Set, S: Set, pr_dev: int, ps_dev: int, n: int, tau: float, out: dict,
-                     vp_cap: int, stream: int | None = None) -> int:
+                     vp_cap: int, prec: int = FP64, stream: int | None = None) -> int:
         """pj_voxel_filter: device buffers in and out (``out`` maps op_lb,
         op_ub, status, vp_off, vp_lb, vp_ub, kept_off, kept to device
         addresses); returns the number of surviving voxel pairs."""
         nk = C.c_int64()
         d = [C.c_void_p(out[k]) for k in ("op_lb", "op_ub", "status", "vp_off", "vp_lb", "vp_ub")]
         self._check(lib().pj_voxel_filter(self.h, R.handle, S.handle, C.c_void_p(pr_dev), C.c_void_p(ps_dev), int(n),
-                                          float(tau), *d, int(vp_cap), C.c_void_p(out["kept_off"]),
+                                          float(tau), int(prec), *d, int(vp_cap), C.c_void_p(out["kept_off"]),
                                           C.c_void_p(out["kept"]), C.byref(nk),
                                           C.c_void_p(stream) if stream else None))
         return nk.value

@@ -3,7 +3,9 @@ and 2) on the GPU against the voxel oracle, element by element: facet
 labels at every LoD, k-means centres, voxel boxes and anchors, every voxel
 pair's bounds, the object-pair bounds and decisions, and the surviving
 voxel pairs in their order.  Both sides evaluate the same double-precision
-expressions in the same order, so every comparison is exact."""
+expressions in the same order, so every comparison is exact.  The
+single-precision filter (outward rounding) is checked against the same
+oracle through the properties its rounding guarantees."""
 import numpy as np
 import pytest
 
@@ -76,7 +78,7 @@ def _pairs(mr, ms_, near, n_far, seed):
     return np.concatenate([r, fr]).astype(np.int32), np.concatenate([s, fs]).astype(np.int32)
 
 
-def _run(ctx, gR, gS, pr, ps, tau, cap):
+def _run(ctx, gR, gS, pr, ps, tau, cap, prec=0):
     import torch
     n = len(pr)
     out = {
@@ -87,7 +89,7 @@ def _run(ctx, gR, gS, pr, ps, tau, cap):
     }
     dpr, dps = to_dev(pr), to_dev(ps)
     nk = ctx.voxel_filter(gR, gS, dpr.data_ptr(), dps.data_ptr(), n, tau, {k: v.data_ptr() for k, v in out.items()},
-                          cap)
+                          cap, prec=prec)
     torch.cuda.synchronize()
     h = {k: v.cpu().numpy() for k, v in out.items()}
     h["kept"] = h["kept"][:2 * nk].reshape(-1, 2)
@@ -122,6 +124,64 @@ def test_filter_equals_oracle(env, case, tau):
         assert 0 < nk < cap     # the pruning keeps some voxel pairs and drops others
 
 
+REL32 = 4e-6     # single-precision bounds: a few roundings of 2^-24 each, outward
+
+
+def _near(x, y):
+    """x within REL32 (relative) of y."""
+    return abs(x - y) <= REL32 * max(abs(x), abs(y))
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{a}-{b}" for a, b, _, _ in CASES])
+@pytest.mark.parametrize("tau", [-1.0, 0.5, 2.0])
+def test_filter_fp32_bounds_are_outward(env, case, tau):
+    """Single precision rounded outward: every lower bound at most the exact
+    (oracle) one and every upper bound at least it, each within REL32; the
+    decisions equal the oracle's except within rounding of tau; the
+    survivors contain the oracle's, and any extra voxel pair lies within
+    rounding of the pair's upper bound."""
+    from paper_2604_19982_gb300 import pj
+    ctx, ms, g, ov = env
+    kr, ks, near, n_far = case
+    if kr == "empty":
+        pr = np.array([0, 1, 0, 1], np.int32)
+        ps = np.array([1, 1, 0, 0], np.int32)
+    else:
+        pr, ps = _pairs(ms[kr], ms[ks], near, n_far, 7)
+    want = vx.voxel_filter(ov[kr], ov[ks], pr, ps, tau)
+    cap = int(want["vp_off"][-1])
+    nk, got = _run(ctx, g[kr], g[ks], pr, ps, tau, cap, prec=pj.FP32)
+    assert np.array_equal(got["vp_off"], want["vp_off"])
+    tiny = 1e-15
+    for lo_key, hi_key in (("vp_lb", "vp_ub"), ("op_lb", "op_ub")):
+        for key, lower in ((lo_key, True), (hi_key, False)):
+            a, b = got[key], want[key]
+            fin = np.isfinite(b)
+            assert np.array_equal(np.isfinite(a), fin), key
+            a, b = a[fin], b[fin]
+            if lower:
+                assert (a <= b * (1 + tiny)).all() and (a >= b * (1 - REL32)).all(), key
+            else:
+                assert (a >= b * (1 - tiny)).all() and (a <= b * (1 + REL32)).all(), key
+    for p in range(len(pr)):
+        gs, ws = int(got["status"][p]), int(want["status"][p])
+        if gs != ws:
+            # only where the deciding bound lies within rounding of tau
+            assert _near(want["op_ub"][p], tau) or _near(want["op_lb"][p], tau), (p, gs, ws)
+        gk = [tuple(x) for x in got["kept"][got["kept_off"][p]:got["kept_off"][p + 1]].tolist()]
+        wk = [tuple(x) for x in want["kept"][want["kept_off"][p]:want["kept_off"][p + 1]].tolist()]
+        assert gk == sorted(gk) and len(set(gk)) == len(gk)
+        if gs == 0 and ws == 0:
+            assert set(wk) <= set(gk)
+        if gs != 0:
+            assert gk == []
+        ns = int(want["vp_off"][p + 1] - want["vp_off"][p]) // max(1, ov[kr][pr[p]]["centres"].shape[0])
+        oub = want["op_ub"][p]
+        for i, j in set(gk) - set(wk):
+            lb = want["vp_lb"][want["vp_off"][p] + i * ns + j]
+            assert lb <= oub * (1 + 3 * REL32), (p, i, j)
+
+
 def test_filter_sizes_and_errors(env):
     from paper_2604_19982_gb300 import pj
     ctx, ms, g, ov = env
@@ -136,6 +196,9 @@ def test_filter_sizes_and_errors(env):
     with pytest.raises(pj.PJError) as e:
         _run(ctx, g["blobs_r"], g["blobs_s"], bad, ps, -1.0, 10 * cap)
     assert e.value.status == pj.PJ_EBOUNDS
+    with pytest.raises(pj.PJError) as e:
+        _run(ctx, g["blobs_r"], g["blobs_s"], pr, ps, -1.0, cap, prec=7)
+    assert e.value.status == pj.PJ_EINVAL
     nk, got = _run(ctx, g["blobs_r"], g["blobs_s"], pr[:0], ps[:0], -1.0, 0)
     assert nk == 0 and got["vp_off"][0] == 0 and got["kept_off"][0] == 0
     # a larger capacity than needed changes nothing
