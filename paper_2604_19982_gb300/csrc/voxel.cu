@@ -351,18 +351,30 @@ __global__ void __launch_bounds__(VOX_T) k_vp_bound(int64_t n, const int32_t* pr
     const bool room = base + m <= cap;
     if (!room && threadIdx.x == 0) set_err(err, ERR_CAPACITY);
     double tl = __longlong_as_double(0x7ff0000000000000LL), tu = tl;
-    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
-      const int64_t i = t / ns, j = t - i * ns;
-      const float* a = R.box + 6 * (i0 + i);
-      const float* b = S.box + 6 * (j0 + j);
-      double lb = __longlong_as_double(0x7ff0000000000000LL), ub = lb;
-      if (!box_empty(a) && !box_empty(b)) vp_bounds<F64>(a, b, R.anc + 3 * (i0 + i), S.anc + 3 * (j0 + j), lb, ub);
-      if (room) {
-        vp_lb[base + t] = lb;
-        vp_ub[base + t] = ub;
+    if (m > 0) {
+      // 32-bit row / column of t, advanced without a division per step
+      // (m <= PJ_VOXEL_MAX^2 < 2^31)
+      const int nsi = (int)ns, mi = (int)m, step = (int)blockDim.x;
+      const int q = step / nsi, rr = step - q * nsi;
+      int t = (int)threadIdx.x, i = t / nsi, j = t - i * nsi;
+      for (; t < mi; t += step) {
+        const float* a = R.box + 6 * (i0 + i);
+        const float* b = S.box + 6 * (j0 + j);
+        double lb = __longlong_as_double(0x7ff0000000000000LL), ub = lb;
+        if (!box_empty(a) && !box_empty(b)) vp_bounds<F64>(a, b, R.anc + 3 * (i0 + i), S.anc + 3 * (j0 + j), lb, ub);
+        if (room) {
+          vp_lb[base + t] = lb;
+          vp_ub[base + t] = ub;
+        }
+        tl = fmin(tl, lb);
+        tu = fmin(tu, ub);
+        i += q;
+        j += rr;
+        if (j >= nsi) {
+          j -= nsi;
+          ++i;
+        }
       }
-      tl = fmin(tl, lb);
-      tu = fmin(tu, ub);
     }
     const double olb = block_min(tl, red);
     const double oub = block_min(tu, red);
@@ -423,9 +435,9 @@ __global__ void __launch_bounds__(VOX_T) k_vp_compact(int64_t n, const int32_t* 
       }
       if (keep) {
         const int64_t q = out + before + __popc(bal & ((1u << lane) - 1u));
-        const int64_t i = t / ns;
-        kept[2 * q] = (int32_t)i;
-        kept[2 * q + 1] = (int32_t)(t - i * ns);
+        const int i = (int)t / (int)ns;
+        kept[2 * q] = i;
+        kept[2 * q + 1] = (int)t - i * (int)ns;
       }
       out += total;
       __syncthreads();
