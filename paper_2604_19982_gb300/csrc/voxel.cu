@@ -299,30 +299,56 @@ struct VoxView {
 // by the larger magnitude of its two directed differences), so lb never
 // exceeds the exact MINDIST and ub is never below the exact distance.
 template <bool F64>
-__device__ __forceinline__ void vp_bounds(const float* a, const float* b, const float* ua, const float* ub_,
-                                          double& lb, double& ub) {
-  if (F64) {
-    double g[3];
+struct VpPrec {
+  using T = double;
+};
+template <>
+struct VpPrec<false> {
+  using T = float;
+};
+
+__device__ __forceinline__ void vp_bounds(const float* a, const float* b, const float* ua, const float* ub_, double& lb,
+                                          double& ub) {
+  double g[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const double d1 = __dsub_rn((double)b[e], (double)a[3 + e]);
-      const double d2 = __dsub_rn((double)a[e], (double)b[3 + e]);
-      g[e] = fmax(0.0, fmax(d1, d2));
-    }
-    lb = __dsqrt_rn(dsq3(g[0], g[1], g[2]));
-    ub = __dsqrt_rn(dsq3(__dsub_rn((double)ua[0], (double)ub_[0]), __dsub_rn((double)ua[1], (double)ub_[1]),
-                         __dsub_rn((double)ua[2], (double)ub_[2])));
-  } else {
-    float g[3], h[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      g[e] = fmaxf(0.f, fmaxf(__fsub_rd(b[e], a[3 + e]), __fsub_rd(a[e], b[3 + e])));
-      h[e] = fmaxf(fabsf(__fsub_ru(ua[e], ub_[e])), fabsf(__fsub_rd(ua[e], ub_[e])));
-    }
-    lb = (double)__fsqrt_rd(__fadd_rd(__fadd_rd(__fmul_rd(g[0], g[0]), __fmul_rd(g[1], g[1])), __fmul_rd(g[2], g[2])));
-    ub = (double)__fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(h[0], h[0]), __fmul_ru(h[1], h[1])), __fmul_ru(h[2], h[2])));
+  for (int e = 0; e < 3; ++e) {
+    const double d1 = __dsub_rn((double)b[e], (double)a[3 + e]);
+    const double d2 = __dsub_rn((double)a[e], (double)b[3 + e]);
+    g[e] = fmax(0.0, fmax(d1, d2));
   }
+  lb = __dsqrt_rn(dsq3(g[0], g[1], g[2]));
+  ub = __dsqrt_rn(dsq3(__dsub_rn((double)ua[0], (double)ub_[0]), __dsub_rn((double)ua[1], (double)ub_[1]),
+                       __dsub_rn((double)ua[2], (double)ub_[2])));
 }
+
+__device__ __forceinline__ void vp_bounds(const float* a, const float* b, const float* ua, const float* ub_, float& lb,
+                                          float& ub) {
+  float g[3], h[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    g[e] = fmaxf(0.f, fmaxf(__fsub_rd(b[e], a[3 + e]), __fsub_rd(a[e], b[3 + e])));
+    h[e] = fmaxf(fabsf(__fsub_ru(ua[e], ub_[e])), fabsf(__fsub_rd(ua[e], ub_[e])));
+  }
+  lb = __fsqrt_rd(__fadd_rd(__fadd_rd(__fmul_rd(g[0], g[0]), __fmul_rd(g[1], g[1])), __fmul_rd(g[2], g[2])));
+  ub = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(h[0], h[0]), __fmul_ru(h[1], h[1])), __fmul_ru(h[2], h[2])));
+}
+
+// The double of a float x >= 0 (or +inf), exactly, by integer operations
+// (exponent rebiased from 127 to 1023, significand shifted up by 29 bits),
+// so that the single-precision path issues no double-precision operation
+// per voxel pair; subnormal x take the conversion instruction.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = u >> 23;
+  const unsigned long long f = (unsigned long long)(u & 0x7fffffu) << 29;
+  if (u == 0) return 0.0;
+  if (e == 0) return (double)x;
+  if (e == 0xffu) return __longlong_as_double((long long)(0x7ff0000000000000ull | f));
+  return __longlong_as_double((long long)(((unsigned long long)(e + 896u) << 52) | f));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
 
 // Algorithm 1: one CTA per object pair, its n_r x n_s voxel pairs flattened
 // over the threads (row-major t = i n_s + j); vp_off [n+1] holds each
@@ -350,7 +376,9 @@ __global__ void __launch_bounds__(VOX_T) k_vp_bound(int64_t n, const int32_t* pr
     const int64_t base = vp_off[p];
     const bool room = base + m <= cap;
     if (!room && threadIdx.x == 0) set_err(err, ERR_CAPACITY);
-    double tl = __longlong_as_double(0x7ff0000000000000LL), tu = tl;
+    using V = typename VpPrec<F64>::T;
+    const V inf = (V)INFINITY;
+    V tl = inf, tu = inf;
     if (m > 0) {
       // 32-bit row / column of t, advanced without a division per step
       // (m <= PJ_VOXEL_MAX^2 < 2^31)
@@ -360,14 +388,14 @@ __global__ void __launch_bounds__(VOX_T) k_vp_bound(int64_t n, const int32_t* pr
       for (; t < mi; t += step) {
         const float* a = R.box + 6 * (i0 + i);
         const float* b = S.box + 6 * (j0 + j);
-        double lb = __longlong_as_double(0x7ff0000000000000LL), ub = lb;
-        if (!box_empty(a) && !box_empty(b)) vp_bounds<F64>(a, b, R.anc + 3 * (i0 + i), S.anc + 3 * (j0 + j), lb, ub);
+        V lb = inf, ub = inf;   // a voxel without facets bounds nothing
+        if (!box_empty(a) && !box_empty(b)) vp_bounds(a, b, R.anc + 3 * (i0 + i), S.anc + 3 * (j0 + j), lb, ub);
         if (room) {
-          vp_lb[base + t] = lb;
-          vp_ub[base + t] = ub;
+          vp_lb[base + t] = widen(lb);
+          vp_ub[base + t] = widen(ub);
         }
-        tl = fmin(tl, lb);
-        tu = fmin(tu, ub);
+        tl = vmin(tl, lb);
+        tu = vmin(tu, ub);
         i += q;
         j += rr;
         if (j >= nsi) {
@@ -376,8 +404,8 @@ __global__ void __launch_bounds__(VOX_T) k_vp_bound(int64_t n, const int32_t* pr
         }
       }
     }
-    const double olb = block_min(tl, red);
-    const double oub = block_min(tu, red);
+    const double olb = block_min(widen(tl), red);
+    const double oub = block_min(widen(tu), red);
     if (threadIdx.x == 0) {
       op_lb[p] = olb;
       op_ub[p] = oub;
