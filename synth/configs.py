@@ -13,7 +13,12 @@ blobs20k    20,000 blobs, sub 1,2,3     20,000 blobs, side 400      tau 0 and 1
 knn50k      50,000 blobs, GMM(20, 15)   50,000 blobs, side 1000     3-NN
 tubes2k     2,000 tubes (3 LoDs)        200,000 blobs, side 2320    within 2
 stream2m    2,000,000 blobs (64 chunks) 20,000 tubes, side 5000     within 1
+cadTI       400 CAD-like models x 100   100 models x 100, side 1500 tau 0, 1
 ==========  ==========================  ==========================  =========
+
+cadTI stands in for the paper's ModelNet T x I join (section 4.1): the
+models are our own furniture-like assemblies (``synth.cad``), replicated
+and shifted as the paper replicates its CAD models.
 """
 from __future__ import annotations
 
@@ -21,6 +26,7 @@ import dataclasses
 
 import numpy as np
 
+from . import cad
 from .mesh import MeshSet, _blob_params, concat, make_blobs, make_tubes
 
 BLOCK = 1024  # objects per random-stream block
@@ -98,6 +104,25 @@ def tube_list(n: int, side: float, seed: int, set_id: int, ids, length_range=(50
     stream), in that order."""
     parts = [tube_set(n, side, seed, set_id, start=int(i), count=1, length_range=length_range) for i in ids]
     return concat(parts) if parts else tube_set(n, side, seed, set_id, start=0, count=0)
+
+
+def cad_set(n_models: int, replicas: int, side: float, seed: int, set_id: int, start: int = 0,
+            count: int | None = None) -> MeshSet:
+    """CAD-like objects (``synth.cad``): n_models furniture-like models
+    (categories in turn), each replicated ``replicas`` times at translations
+    on the 1/64 grid uniform in [0, side)^3; object o is replica
+    o % replicas of model o // replicas (objects start .. start + count)."""
+    n = n_models * replicas
+    count = n - start if count is None else count
+    models, shifts = [], []
+    cache = {}
+    for o in range(start, start + count):
+        j, i = divmod(o, replicas)
+        if j not in cache:
+            cache[j] = cad.model_parts(_rng(seed, set_id, j, 37), cad.CATEGORIES[j % len(cad.CATEGORIES)])
+        models.append(cache[j])
+        shifts.append(cad._q(_rng(seed, set_id, j, i, 41).uniform(0.0, side, size=3)))
+    return cad.make_cad(models, shifts)
 
 
 @dataclasses.dataclass
@@ -183,3 +208,12 @@ def stream_chunks_parallel(chunks, procs: int = 16, seed: int = 0):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(procs) as pool:
         return pool.map(_stream_chunk, [(c, seed) for c in chunks])
+
+
+def cadTI(seed: int = 0, t_models: int = 400, i_models: int = 100, replicas: int = 100,
+          side: float = 1500.0) -> Workload:
+    """CAD-like T x I join: t_models and i_models models, each replicated
+    ``replicas`` times in a cube of side ``side``; intersection and within 1."""
+    T = cad_set(t_models, replicas, side, seed, 0)
+    I_ = cad_set(i_models, replicas, side, seed, 1)
+    return Workload(f"cadTI{t_models}x{i_models}", T, I_, "within", taus=(0.0, 1.0))
