@@ -428,6 +428,62 @@ pj_status pj_voxel_filter(pj_ctx* ctx, const pj_set* R, const pj_set* S, const i
                           double* vp_lb, double* vp_ub, int64_t vp_cap, int64_t* kept_off, int32_t* kept,
                           int64_t* n_kept, void* cuda_stream);
 
+/* ---- Out-of-core chunks: a streamed set read from chunk files ----
+ * The paper streams R from host memory (section 3.2, Algorithm 3) and leaves
+ * facets kept on disk to future work.  A chunk file holds one chunk exactly
+ * as a pj_mesh_set_desc describes it: a 1,024-byte little-endian header
+ * (magic "PJCHUNK1", version 1, counts and the byte offset of every array)
+ * followed by the arrays at 64-byte aligned offsets.  A chunk source reads
+ * such files on a thread of its own, ahead of the join, and is the fill
+ * callback of pj_load_set_streamed:
+ *
+ *   pj_chunk_source* src;  pj_chunk_source_open(paths, n, 2, &src);
+ *   pj_chunk_source_info(src, &n_objects, NULL, NULL);
+ *   pj_load_set_streamed(ctx, n_objects, n, pj_chunk_source_fill, src, &R);
+ *   ... pj_join(ctx, R, S, ...) ...   (any number of joins)
+ *   pj_free_set(R);  pj_chunk_source_close(src);
+ *
+ * None of these calls touches the GPU. */
+typedef struct pj_chunk_source pj_chunk_source; /* opaque */
+
+/* Write the chunk described by desc (HOST arrays, as for pj_load_set) to
+ * path, through a temporary file "<path>.part" renamed into place when
+ * complete.  PJ_EINVAL for an inconsistent desc, PJ_ESOURCE for an I/O
+ * error (the file is then left absent). */
+pj_status pj_chunk_file_write(const char* path, const pj_mesh_set_desc* desc);
+
+/* Open n_chunks chunk files (paths[c] is chunk c; every file with the same
+ * LoD count) and start the reader thread.  The headers are read and checked
+ * here (PJ_ESOURCE: a file cannot be opened; PJ_EINVAL: not a chunk file,
+ * an offset outside the file, or LoD counts that differ).  The source keeps
+ * readahead + 2 chunk buffers in host memory (readahead 0..16): while the
+ * join lays out chunk c the reader loads chunks up to c + readahead.  The
+ * buffers are pageable memory, so the library packs them into its pinned
+ * staging as for any pageable chunk. */
+pj_status pj_chunk_source_open(const char* const* paths, int n_chunks, int readahead, pj_chunk_source** out);
+
+/* Total objects, chunk count and LoD count of an open source (each output
+ * may be NULL). */
+pj_status pj_chunk_source_info(const pj_chunk_source* src, int64_t* n_objects, int* n_chunks, int* n_lods);
+
+/* The pj_fill_fn of a source (user = the source): waits for chunk `chunk`
+ * and points out's arrays into its buffer, valid until the chunk two after
+ * it is asked for (the pageable-array contract of pj_load_set_streamed).
+ * Chunks are asked for in order; a request that does not follow the
+ * previous one (the next join's chunk 0) restarts the reader there.
+ * PJ_ESOURCE when the file can no longer be read or its header changed
+ * since pj_chunk_source_open. */
+pj_status pj_chunk_source_fill(void* src, int chunk, pj_mesh_set_desc* out);
+
+/* JSON statistics of a source: chunks_read, bytes_read, ms_read (time the
+ * reader spent in reads), read_gbs, ms_fill_wait (time fills waited for the
+ * reader: I/O the join did not hide), restarts, buffers. */
+pj_status pj_chunk_source_stats(pj_chunk_source* src, char* json_buf, size_t cap);
+
+/* Stop the reader and free the buffers; no set streamed from the source may
+ * be joined afterwards. */
+void pj_chunk_source_close(pj_chunk_source* src);
+
 /* Measured fused-multiply-add throughput of the device (independent FMA
  * chains on every SM), GFLOP/s with an FMA counted as 2 operations: the
  * arithmetic peak the refinement kernels are compared against (their work

@@ -92,6 +92,12 @@ def lib():
             "pj_voxel_labels_read": (st, [vp, vp, C.c_int, _i32p]),
             "pj_voxel_filter": (st, [vp, vp, vp, vp, vp, C.c_int64, C.c_double, C.c_int, vp, vp, vp, vp, vp, vp,
                                      C.c_int64, vp, vp, _i64p, vp]),
+            "pj_chunk_file_write": (st, [C.c_char_p, C.POINTER(MeshSetDesc)]),
+            "pj_chunk_source_open": (st, [C.POINTER(C.c_char_p), C.c_int, C.c_int, C.POINTER(vp)]),
+            "pj_chunk_source_info": (st, [vp, _i64p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "pj_chunk_source_fill": (st, [vp, C.c_int, C.POINTER(MeshSetDesc)]),
+            "pj_chunk_source_stats": (st, [vp, C.c_char_p, C.c_size_t]),
+            "pj_chunk_source_close": (None, [vp]),
             "pj_last_error": (C.c_char_p, [vp]),
             "pj_status_str": (C.c_char_p, [C.c_int]),
         }
@@ -181,6 +187,85 @@ class Result:
         return list(zip(self.r.tolist(), self.s.tolist()))
 
 
+def write_chunk_file(path: str, ms) -> None:
+    """pj_chunk_file_write: one chunk (a mesh-set object of host arrays) to
+    a chunk file."""
+    keep = []
+    d = describe(ms, keep)
+    st = lib().pj_chunk_file_write(os.fsencode(path), C.byref(d))
+    if st != PJ_OK:
+        raise PJError(st, f"cannot write chunk file {path}")
+
+
+class ChunkView:
+    """Host copies of one chunk as a chunk source hands it out (the fields
+    of a mesh-set object)."""
+
+    def __init__(self, d: MeshSetDesc):
+        n, L = int(d.n_objects), int(d.n_lods)
+        self.n, self.n_lods = n, L
+        arr = (lambda p, count, dt: np.ctypeslib.as_array(p, shape=(count,)).astype(dt, copy=True)
+               if count > 0 else np.zeros(0, dt))
+        self.verts, self.vert_off, self.faces, self.face_off, self.hd, self.ph = [], [], [], [], [], []
+        for l in range(L):
+            vo = arr(d.vert_off[l], n + 1, np.int64)
+            self.vert_off.append(vo)
+            self.verts.append(arr(d.verts[l], 3 * int(vo[-1]), np.float32).reshape(-1, 3))
+            if d.face_off[l]:
+                fo = arr(d.face_off[l], n + 1, np.int64)
+                rows, nf = int(fo[-1]), int(fo[-1])
+                self.face_off.append(fo)
+            else:
+                rows = int(d.n_faces_shared[l]) if n > 0 else 0
+                nf = n * rows
+                self.face_off.append(None)
+            self.faces.append(arr(d.faces[l], 3 * rows, np.int32).reshape(-1, 3))
+            self.hd.append(arr(d.hd[l], nf, np.float32) if d.hd[l] else None)
+            self.ph.append(arr(d.ph[l], nf, np.float32) if d.ph[l] else None)
+        self.anchor = arr(d.anchor, 3 * n, np.float32).reshape(-1, 3)
+
+
+class ChunkSource:
+    """pj_chunk_source_*: chunk files read ahead by a native thread; pass it
+    to :meth:`Context.load_set_files`."""
+
+    def __init__(self, paths, readahead: int = 2):
+        self.paths = [os.fsencode(p) for p in paths]
+        arr = (C.c_char_p * len(self.paths))(*self.paths)
+        h = C.c_void_p()
+        st = lib().pj_chunk_source_open(arr, len(self.paths), int(readahead), C.byref(h))
+        if st != PJ_OK:
+            raise PJError(st, "cannot open the chunk files")
+        self.h = h.value
+        n, c, L = C.c_int64(), C.c_int(), C.c_int()
+        lib().pj_chunk_source_info(self.h, C.byref(n), C.byref(c), C.byref(L))
+        self.n_objects, self.n_chunks, self.n_lods = n.value, c.value, L.value
+
+    def chunk(self, c: int) -> ChunkView:
+        """Ask for chunk c as a join would, and copy it out."""
+        d = MeshSetDesc()
+        st = lib().pj_chunk_source_fill(self.h, int(c), C.byref(d))
+        if st != PJ_OK:
+            raise PJError(st, f"chunk {c}")
+        return ChunkView(d)
+
+    def stats(self) -> dict:
+        buf = C.create_string_buffer(1024)
+        lib().pj_chunk_source_stats(self.h, buf, len(buf))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if self.h:
+            lib().pj_chunk_source_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Set:
     def __init__(self, ctx: "Context", handle: int, n: int, n_lods: int):
         self.ctx = ctx
@@ -267,6 +352,19 @@ class Context:
         s = Set(self, h.value, int(n_objects), 0)
         s._cb = cb
         s._keep = keep_box
+        return s
+
+    def load_set_files(self, src: ChunkSource) -> Set:
+        """A set streamed from chunk files: pj_load_set_streamed with the
+        source's native fill callback (the source must stay open while the
+        set is joined)."""
+        fill = C.cast(lib().pj_chunk_source_fill, FILL_FN)
+        h = C.c_void_p()
+        self._check(lib().pj_load_set_streamed(self.h, int(src.n_objects), int(src.n_chunks), fill,
+                                               C.c_void_p(src.h), C.byref(h)))
+        s = Set(self, h.value, int(src.n_objects), src.n_lods)
+        s._cb = fill
+        s._src = src
         return s
 
     # ---- joins
